@@ -1,0 +1,185 @@
+/*
+ * sc.h -- C ABI of the GB300 spectral-clustering library (libsc_gb300.so).
+ *
+ * The library computes the hot path of spectral clustering as described in
+ * Zhuzhunashvili & Knyazev, "Preconditioned Spectral Clustering for Stochastic Block
+ * Partition Streaming Graph Challenge" (HPEC 2017):
+ *   graph edge list -> symmetrized Laplacian L = D - W            (Sec. II.A, Sec. III)
+ *   -> LOBPCG for the K smallest eigenpairs of L, cold or warm     (Sec. II.B, Sec. III)
+ *   -> unit-normalized rows of the eigenvector block -> k-means    (Sec. II.A)
+ *   -> streaming stages that warm-start from the previous block    (Sec. III, Sec. IV)
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an sc_status; nothing aborts, throws or traps.  The message of the
+ *    last failure on a context is returned by sc_last_error().
+ *  - Host arrays passed in are borrowed for the duration of the call and copied.  Output
+ *    arrays are caller-allocated with the sizes stated per call.  Opaque objects
+ *    (sc_ctx, sc_graph, sc_server) are allocated by the library and freed by the caller.
+ *  - "on_device" arguments say whether the array pointers are device pointers (1) on the
+ *    context's device or host pointers (0).  Device arrays must stay valid until the call
+ *    returns.  All device work is issued on the context stream; calls return after that
+ *    stream has finished the call's work.
+ *  - Dense blocks are row-major: element (i, j) of an n x K block is at [i * K + j].
+ *  - Limits: 1 <= n < 2^31, stored nonzeros < 2^31, 1 <= K <= SC_MAX_K, 3K <= n for LOBPCG.
+ *  - A context is not thread-safe; use one per host thread.  A server is thread-safe.
+ */
+#ifndef SC_GB300_H
+#define SC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_MAX_K 512
+
+typedef struct sc_ctx sc_ctx;
+typedef struct sc_graph sc_graph;
+typedef struct sc_server sc_server;
+
+typedef enum {
+  SC_OK = 0,
+  SC_EINVAL = -1,      /* bad argument (sizes, ranges, null pointers)                  */
+  SC_ENOMEM = -2,      /* device allocation failed or the context HBM budget is spent  */
+  SC_EBREAKDOWN = -3,  /* LOBPCG trial basis lost rank even after dropping P          */
+  SC_ENOTCONV = -4,    /* tolerance requested but not reached within the iterations    */
+  SC_ETIMEOUT = -5,    /* a bounded device wait gave up                                */
+  SC_ECUDA = -6,       /* CUDA runtime error (message in sc_last_error)                */
+  SC_EAGAIN = -7       /* server: queue full / result not ready yet                    */
+} sc_status;
+
+/* Arithmetic of the LOBPCG path.
+ *  SC_PREC_MIXED: FP32 blocks and SpMM; Gram products on tcgen05 tensor cores as
+ *                 3-term split-TF32 products, FP32 accumulation in tensor memory and FP64
+ *                 sums across CTAs; FP64 Cholesky of the K x K Grams; FP32 Rayleigh-Ritz.
+ *  SC_PREC_FP32:  as MIXED, but Gram products on FP32 CUDA cores (FP64 cross-CTA sums).
+ *  SC_PREC_FP64:  every step in FP64 (the plain form and the 1e-10 check mode). */
+typedef enum { SC_PREC_MIXED = 0, SC_PREC_FP32 = 1, SC_PREC_FP64 = 2 } sc_precision;
+
+/* Symmetrization W <- W + W' (Sec. II.A): logical sum (unweighted, duplicates merged,
+ * every stored weight 1) or algebraic sum (weights added, duplicates accumulate). */
+typedef enum { SC_SYM_LOGICAL = 0, SC_SYM_ALGEBRAIC = 1 } sc_sym;
+
+/* ---- context -------------------------------------------------------------------------
+ * sc_ctx_create: bind to CUDA device `device`.  `cuda_stream` is a cudaStream_t to issue
+ * work on (borrowed, must outlive the context) or NULL for a stream the context owns.
+ * `hbm_budget` caps the bytes the context and its graphs may hold on the device (0 = no
+ * cap); allocations beyond it fail with SC_ENOMEM. */
+int sc_ctx_create(sc_ctx** out, int device, void* cuda_stream, size_t hbm_budget);
+void sc_ctx_destroy(sc_ctx* ctx);
+const char* sc_last_error(const sc_ctx* ctx);
+/* Bytes currently held on the device by this context and its graphs. */
+size_t sc_ctx_bytes_in_use(const sc_ctx* ctx);
+/* Number of kernels this context has launched so far (for launch accounting). */
+uint64_t sc_ctx_kernel_launches(const sc_ctx* ctx);
+
+/* ---- Laplacian (Sec. II.A; Sec. III "binary sparse matrix", matrix-free LXfun) ---------
+ * sc_build_laplacian: directed edge list (src[e] -> dst[e], e < m, 0 <= src, dst < n) to
+ * the symmetrized CSR of W and the degrees D of L = D - W.  Self-loops are dropped (they
+ * add the same amount to D and W).  `w` = per-edge weights (NULL = all 1); with
+ * SC_SYM_LOGICAL weights are ignored.  Columns within a row come out sorted ascending.
+ * Out-of-range endpoints give SC_EINVAL.  The graph owns its device CSR until
+ * sc_graph_destroy. */
+int sc_build_laplacian(sc_ctx* ctx, int32_t n, int64_t m, const int32_t* src,
+                       const int32_t* dst, const float* w, int sym, int on_device,
+                       sc_graph** out);
+int sc_graph_info(const sc_graph* g, int32_t* n, int64_t* nnz, double* deg_max);
+/* Copy the CSR to host arrays: row_ptr[n+1], col_idx[nnz], val[nnz] (may be NULL),
+ * deg[n] (may be NULL). */
+int sc_graph_copy_csr(const sc_graph* g, int32_t* row_ptr, int32_t* col_idx, float* val,
+                      double* deg);
+void sc_graph_destroy(sc_graph* g);
+
+/* sc_lap_apply: Y = L V = D V - W V for an n x k block V (one SpMM, Sec. III "a single
+ * multiplication ... per iteration").  prec selects FP32 (V, Y float*) or FP64 (double*);
+ * V and Y are n x k row-major, host or device per on_device. */
+int sc_lap_apply(sc_ctx* ctx, sc_graph* g, int k, int prec, const void* V, void* Y,
+                 int on_device);
+
+/* ---- LOBPCG (Sec. II.B; Sec. III random / warm start; Sec. IV soft locking) -----------
+ * iters:    loop passes after the initial Rayleigh-Ritz on the start block.
+ * tol_abs:  stop before a pass when max_j ||r_j|| <= tol_abs (0 = run all passes).
+ * tol_lock: soft locking; columns with ||r_j|| <= tol_lock leave the active set (0 = off).
+ * prec:     sc_precision.
+ * seed:     seed of the Gaussian start block when one is generated.
+ * cold:     1 = ignore a resident block and start cold.
+ * max_iters_for_tol: when tol_abs > 0, cap on passes (SC_ENOTCONV if not reached). */
+typedef struct {
+  int iters;
+  double tol_abs;
+  double tol_lock;
+  int prec;
+  uint64_t seed;
+  int cold;
+} sc_lobpcg_opts;
+
+typedef struct {
+  int K;
+  int iters_done;      /* passes run                                              */
+  int fallbacks;       /* passes that had to drop the direction block P           */
+  int converged;       /* 1 when tol_abs > 0 was reached                          */
+  double lambda[SC_MAX_K]; /* Ritz values, ascending                              */
+  double resid[SC_MAX_K];  /* ||L x_j - lambda_j x_j||_2 of the returned pairs     */
+  float ms;            /* device time of the call (CUDA events on the ctx stream) */
+  uint64_t kernels;    /* kernels launched by the call                           */
+} sc_eig_info;
+
+/* sc_lobpcg: the K smallest eigenpairs of the graph's Laplacian.
+ * Start block: X0 (host n x K float, row-major) if non-NULL; its first x0_rows rows are
+ * used and the rows below are zero-filled (snowball warm start, Sec. III); otherwise the
+ * graph's resident block from the previous call (warm start) unless opts->cold, otherwise
+ * a seeded Gaussian block (SplitMix64 + Box-Muller, seed opts->seed).  After the call the
+ * graph keeps the new block resident for the next warm start.  X_out (host n x K float)
+ * may be NULL.  info may be NULL. */
+int sc_lobpcg(sc_ctx* ctx, sc_graph* g, int K, const sc_lobpcg_opts* opts, const float* X0,
+              int32_t x0_rows, float* X_out, sc_eig_info* info);
+
+/* sc_embed_rows: E_i = X_i / ||X_i||_2 (rows of norm < 1e-30 stay zero), n x K float. */
+int sc_embed_rows(sc_ctx* ctx, const float* X, int32_t n, int K, float* E, int on_device);
+
+/* ---- k-means on the embedded rows (Sec. II.A) -------------------------------------------
+ * E: n x d float (row-major).  Seeds: init_idx[k] if non-NULL, else k-means++ driven by
+ * the SplitMix64 uniforms of `seed` (decisions taken in FP64).  Lloyd: at most `iters`
+ * assignment/update rounds, nearest centroid by squared distance (ties -> lowest index),
+ * empty clusters keep their centroid, early exit when an assignment repeats.
+ * Outputs (host, may be NULL except labels_out): labels_out[n], centroids_out[k*d]
+ * (float), seeds_out[k], inertia (sum of squared distances), iters_run. */
+int sc_kmeans(sc_ctx* ctx, const float* E, int32_t n, int d, int k, int iters,
+              uint64_t seed, const int32_t* init_idx, int on_device, int32_t* labels_out,
+              float* centroids_out, int32_t* seeds_out, double* inertia, int* iters_run);
+
+/* ---- end to end ------------------------------------------------------------------------
+ * sc_partition: LOBPCG (K vectors) -> unit rows -> k-means (k clusters, kmeans_iters
+ * Lloyd rounds, k-means++ seeded by opts->seed) -> labels_out[n] (host). */
+int sc_partition(sc_ctx* ctx, sc_graph* g, int K, int k, const sc_lobpcg_opts* opts,
+                 int kmeans_iters, int32_t* labels_out, sc_eig_info* info);
+
+/* ---- streaming (Sec. III: emerging edges, snowball) -------------------------------------
+ * sc_stream_update: add m_delta directed edges to the graph and grow it to n_new >= n
+ * vertices (new vertices numbered after the old ones, Sec. III).  The CSR is merged in
+ * place of the old one (same symmetrization mode); the resident eigenvector block, if
+ * any, gains zero rows for the new vertices so the next sc_lobpcg warm-starts. */
+int sc_stream_update(sc_ctx* ctx, sc_graph* g, int32_t n_new, int64_t m_delta,
+                     const int32_t* src, const int32_t* dst, const float* w, int on_device);
+
+/* ---- component entry points (the steps of one LOBPCG pass, exposed for testing) -------
+ * sc_gram: C = A' B in FP64 (a x b, row-major) for n x a block A and n x b block B
+ * (row-major with leading dimensions lda, ldb in elements).  prec selects float or double
+ * blocks and the arithmetic (MIXED = tensor cores, FP32 = CUDA cores, FP64).
+ * A, B device or host per on_device; C host. */
+int sc_gram(sc_ctx* ctx, int prec, int64_t n, int a, int b, const void* A, int64_t lda,
+            const void* B, int64_t ldb, double* C, int on_device);
+
+/* sc_rr_solve: Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of
+ * the symmetric m x m matrix G (host, FP64, row-major; symmetrized on entry).  theta[K]
+ * ascending (host FP64), Y[m*K] (host FP64, row-major, orthonormal columns).
+ * prec: SC_PREC_FP64 solves in FP64, otherwise in FP32. */
+int sc_rr_solve(sc_ctx* ctx, int prec, int m, int K, const double* G, double* theta,
+                double* Y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_GB300_H */

@@ -1,0 +1,27 @@
+"""FP64 CPU oracle for the spectral-clustering hot path (test infrastructure only).
+
+This package is the plain, slow, obviously-correct reference that the CUDA library is
+checked against.  It is imported only by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg; the library never calls it and it never calls the library.
+Every function cites the passage of Zhuzhunashvili & Knyazev, "Preconditioned Spectral
+Clustering for Stochastic Block Partition Streaming Graph Challenge" (HPEC 2017) it
+follows; LOBPCG itself is Knyazev's (SIAM J. Sci. Comput. 2001), which the paper calls
+through SciPy (Sec. II.B).
+"""
+from .spectral import (  # noqa: F401
+    BreakdownError,
+    LobpcgResult,
+    cholqr,
+    embed_rows,
+    kmeans,
+    kmeanspp_seed,
+    lap_apply,
+    laplacian_csr,
+    laplacian_dense,
+    lloyd,
+    lobpcg,
+    partition,
+    partition_metrics,
+    rayleigh_ritz,
+    sin_theta,
+)

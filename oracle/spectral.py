@@ -1,0 +1,421 @@
+"""FP64 oracle: Laplacian, LOBPCG, row embedding, k-means++ / Lloyd, partition metrics.
+
+TEST INFRASTRUCTURE ONLY.  Plain NumPy/SciPy in float64: every step is written out in the
+order the method states it, with library primitives (dense/sparse matmul, Cholesky,
+triangular solve, dense symmetric eigendecomposition, cumulative sum, Hungarian
+assignment) as the only building blocks.  No blocking, fusion or reordering.
+
+Parity status of each function is stated in its docstring ("pinned by ...").
+
+Paper: Zhuzhunashvili & Knyazev, HPEC 2017 (arXiv 1708.07481).
+  Sec. II.A  -- W <- W + W' (logical or algebraic sum), D = row sums, L = D - W; the rows of
+                the eigenvector block are clustered (k-means++ or pivoted QR).
+  Sec. II.B  -- LOBPCG for the smallest eigenpairs, optionally preconditioned.
+  Sec. III   -- random Gaussian start, warm starts (zero fill for new vertices), the
+                matrix-free product diagL.*X - A*X - (X'*A)'.
+  Sec. IV    -- soft locking; Gram matrices cost n*l^2; PM / PR / PP metrics.
+LOBPCG: Knyazev, SIAM J. Sci. Comput. 23(2), 2001 (Rayleigh-Ritz on span{X, W, P}); the
+basis handling (residual projected against X, Cholesky-QR of the residual and direction
+blocks) is the form of SciPy's lobpcg, which is the implementation the paper ran.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.optimize as sopt
+import scipy.sparse as sp
+
+# --------------------------------------------------------------------------------------
+# Laplacian (Sec. II.A, Sec. III)
+# --------------------------------------------------------------------------------------
+
+
+@dataclass
+class Csr:
+    n: int
+    row_ptr: np.ndarray  # int64 [n+1]
+    col_idx: np.ndarray  # int64 [nnz]
+    val: np.ndarray  # float64 [nnz] entries of the symmetrized W (1 for a logical sum)
+    deg: np.ndarray  # float64 [n]   D = row sums of W
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.shape[0])
+
+    def W(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.val, self.col_idx, self.row_ptr), shape=(self.n, self.n))
+
+
+def laplacian_csr(n, src, dst, w=None, sym: str = "logical") -> Csr:
+    """Symmetrized adjacency W and degrees D of L = D - W (Sec. II.A).
+
+    ``sym='logical'``: W[u, v] = 1 iff u != v and (u->v or v->u) is an edge (the logical sum
+    for unweighted graphs, duplicates merged).  ``sym='algebraic'``: W = A + A' with A[u, v]
+    the summed weights of the edges u->v (1 per edge when ``w`` is None).  Self-loops are
+    dropped: a loop adds the same amount to D[u, u] and W[u, u], so L is unchanged.
+
+    Pinned by: dense brute-force construction, L*1 = 0, symmetry, sum(deg) = nnz, PSD,
+    and (algebraic) the paper's matrix-free product diagL.*X - A*X - (X'*A)'.
+    """
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    if src.size and (src.min() < 0 or dst.min() < 0 or src.max() >= n or dst.max() >= n):
+        raise ValueError("edge endpoint out of range")
+    ww = np.ones(src.shape[0]) if w is None else np.asarray(w, dtype=np.float64)
+    keep = src != dst
+    src, dst, ww = src[keep], dst[keep], ww[keep]
+    rows = np.concatenate([src, dst])
+    cols = np.concatenate([dst, src])
+    vals = np.concatenate([ww, ww])
+    keys = rows * n + cols
+    uk, inv = np.unique(keys, return_inverse=True)
+    if sym == "logical":
+        v = np.ones(uk.shape[0])
+    elif sym == "algebraic":
+        v = np.zeros(uk.shape[0])
+        np.add.at(v, inv, vals)
+    else:
+        raise ValueError(sym)
+    r = uk // n
+    c = uk % n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(r, minlength=n))
+    deg = np.zeros(n)
+    np.add.at(deg, r, v)
+    return Csr(n=n, row_ptr=row_ptr, col_idx=c, val=v, deg=deg)
+
+
+def lap_apply(L: Csr, V: np.ndarray) -> np.ndarray:
+    """L V = D V - W V (Sec. II.A), V an n x k block."""
+    V = np.asarray(V, dtype=np.float64)
+    return L.deg[:, None] * V - L.W() @ V
+
+
+def laplacian_dense(L: Csr) -> np.ndarray:
+    """Dense L = D - W of a small graph."""
+    return np.diag(L.deg) - L.W().toarray()
+
+
+# --------------------------------------------------------------------------------------
+# LOBPCG (Sec. II.B, Sec. III, Sec. IV; Knyazev 2001)
+# --------------------------------------------------------------------------------------
+
+
+class BreakdownError(RuntimeError):
+    """The Gram matrix of the trial basis is not numerically positive definite."""
+
+
+# A Cholesky pivot below this (relative to the unit diagonal after scaling) counts as a
+# breakdown of the trial basis.
+PIVOT_TOL = 1e-14
+
+
+def _chol_lower(G: np.ndarray) -> np.ndarray:
+    """Lower Cholesky factor of a symmetric matrix with unit-ish diagonal, or breakdown."""
+    try:
+        C = np.linalg.cholesky(G)
+    except np.linalg.LinAlgError as e:
+        raise BreakdownError(str(e)) from None
+    if np.min(np.diag(C)) ** 2 <= PIVOT_TOL * np.max(np.diag(G)):
+        raise BreakdownError("tiny pivot")
+    return C
+
+
+def cholqr(V: np.ndarray):
+    """Cholesky-QR with column scaling: V = Q C' with Q'Q = I, C lower triangular.
+
+    G = V'V; s = diag(G)^-1/2; s G s = Cs Cs'; Q = V diag(s) Cs^-T; C = diag(1/s) Cs.
+    The scaling keeps columns of very different norms (converged residuals) from
+    tripping the relative pivot test.
+    """
+    G = V.T @ V
+    G = 0.5 * (G + G.T)
+    d = np.diag(G)
+    if np.any(d <= 0):
+        raise BreakdownError("zero column")
+    s = 1.0 / np.sqrt(d)
+    Cs = _chol_lower(G * s[:, None] * s[None, :])
+    Q = sla.solve_triangular(Cs, (V * s[None, :]).T, lower=True).T
+    return Q, Cs / s[:, None]
+
+
+def rayleigh_ritz(GA: np.ndarray, GB: np.ndarray, K: int):
+    """K smallest eigenpairs of the pencil (GA, GB): GA y = theta GB y, Y' GB Y = I.
+
+    Steps: symmetrize; scale by s = diag(GB)^-1/2; Cholesky  s GB s = C C'; reduce
+    M = C^-1 (s GA s) C^-T; eigendecompose M (ascending); Y = diag(s) C^-T V[:, :K].
+    Raises BreakdownError if the scaled GB has a pivot <= PIVOT_TOL.
+
+    Pinned by: LOBPCG convergence to dense eigenpairs; exactness when the basis spans R^n.
+    """
+    GA = 0.5 * (GA + GA.T)
+    GB = 0.5 * (GB + GB.T)
+    d = np.diag(GB)
+    if np.any(d <= 0):
+        raise BreakdownError("zero column in the trial basis")
+    s = 1.0 / np.sqrt(d)
+    Bs = GB * s[:, None] * s[None, :]
+    As = GA * s[:, None] * s[None, :]
+    C = _chol_lower(Bs)
+    T = sla.solve_triangular(C, As, lower=True)  # C^-1 As
+    M = sla.solve_triangular(C, T.T, lower=True)  # C^-1 (C^-1 As)' = C^-1 As C^-T
+    M = 0.5 * (M + M.T)
+    theta, V = np.linalg.eigh(M)
+    Y = sla.solve_triangular(C.T, V[:, :K], lower=False)  # C^-T V_K
+    Y = Y * s[:, None]
+    return theta[:K], Y
+
+
+@dataclass
+class LobpcgResult:
+    lam: np.ndarray  # [K] Ritz values, ascending
+    X: np.ndarray  # [n, K] Ritz vectors
+    resid: np.ndarray  # [K] ||L x_j - lam_j x_j||_2 of the returned pairs
+    iters: int  # loop passes performed after the initial Rayleigh-Ritz
+    fallbacks: int  # iterations where the direction block P had to be dropped
+    history: list = field(default_factory=list)  # per pass: (lam, resid-before-update)
+
+
+def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: float = 0.0,
+           keep_history: bool = False, explicit: bool = False) -> LobpcgResult:
+    """Unpreconditioned block LOBPCG for the K smallest eigenpairs of L (Sec. II.B, III).
+
+    Start: X = CholQR(CholQR(X0)); LX = L X; Rayleigh-Ritz on span(X).
+    Each pass i = 1..iters:
+      R = LX - X diag(lam), rho_j = ||r_j||; active = {j : rho_j > tol_lock} (soft locking,
+      Sec. IV); stop when nothing is active or max rho <= tol_abs.
+      R_a <- R_a - X (X' R_a); R_a <- CholQR(R_a); LR_a = L R_a.
+      For i > 1: P_a <- P_a - [X R_a] F with F = [X R_a]' P_a, then CholQR(P_a); LP_a is
+      transformed alike (the orthonormal trial basis of Hetmaniuk & Lehoucq 2006).
+      S = [X R_a P_a], LS = [LX LR_a LP_a]; Rayleigh-Ritz on (S' LS, S' S), K smallest.
+      With Y = [Y_X; Y_R; Y_P]: P = R_a Y_R + P_a Y_P, X = X Y_X + P (LX, LP alike).
+      A breakdown of the Cholesky of P's Gram (P inside span{X, R}) or of the trial basis
+      drops P for that pass; a breakdown without P is raised.
+    One multiplication by L per pass (Sec. III): LP and LX are carried along implicitly.
+    ``explicit=True`` recomputes LX, LR_a and LP_a as products with L instead -- the same
+    iteration in exact arithmetic, stable when a direction column sinks to rounding level
+    in runs driven to tight tolerances.
+    When every column is active this spans the same trial subspaces as Knyazev's basis
+    [X R P] (span{X_new, P_new} = span{X_new, X_old}), so the iterates agree in exact
+    arithmetic with SciPy's lobpcg, which the paper used.
+    Returns the final Ritz values, vectors, and residual norms of the returned pairs.
+
+    Pinned by: dense eigendecomposition (converged runs), closed-form Laplacian spectra,
+    exactness when [X R] spans R^n, monotone Ritz values, orthonormality.
+    """
+    X0 = np.asarray(X0, dtype=np.float64)
+    n, K = X0.shape
+    X, _ = cholqr(X0)
+    X, _ = cholqr(X)
+    LX = lap_apply(L, X)
+    G = X.T @ LX
+    G = 0.5 * (G + G.T)
+    lam, Q = np.linalg.eigh(G)
+    X = X @ Q
+    LX = LX @ Q
+    P = LP = None
+    hist = []
+    fallbacks = 0
+    done = 0
+    for _ in range(iters):
+        R = LX - X * lam[None, :]
+        rho = np.linalg.norm(R, axis=0)
+        act = rho > tol_lock
+        if keep_history:
+            hist.append((lam.copy(), rho.copy()))
+        if not act.any() or rho.max() <= tol_abs:
+            break
+        Ra = R[:, act]
+        Ra = Ra - X @ (X.T @ Ra)
+        Ra, _ = cholqr(Ra)
+        LRa = lap_apply(L, Ra)
+        blocks = [(X, LX), (Ra, LRa)]
+        if P is not None:
+            Pa, LPa = P[:, act], LP[:, act]
+            XR = np.concatenate([X, Ra], axis=1)
+            LXR = np.concatenate([LX, LRa], axis=1)
+            F = XR.T @ Pa
+            Pa = Pa - XR @ F
+            LPa = LPa - LXR @ F
+            try:
+                Pa, Cp = cholqr(Pa)
+                if explicit:
+                    LPa = lap_apply(L, Pa)
+                else:
+                    LPa = sla.solve_triangular(Cp, LPa.T, lower=True).T
+                blocks.append((Pa, LPa))
+            except BreakdownError:
+                fallbacks += 1
+        try:
+            theta, Y = _rr_blocks(blocks, K)
+        except BreakdownError:
+            if len(blocks) < 3:
+                raise
+            fallbacks += 1
+            blocks = blocks[:2]
+            theta, Y = _rr_blocks(blocks, K)
+        ka = Ra.shape[1]
+        Yx, Yr = Y[:K], Y[K:K + ka]
+        Pn = Ra @ Yr
+        LPn = LRa @ Yr
+        if len(blocks) == 3:
+            Yp = Y[K + ka:]
+            Pn = Pn + blocks[2][0] @ Yp
+            LPn = LPn + blocks[2][1] @ Yp
+        X = X @ Yx + Pn
+        LX = lap_apply(L, X) if explicit else LX @ Yx + LPn
+        P, LP = Pn, LPn
+        lam = theta
+        done += 1
+    R = LX - X * lam[None, :]
+    return LobpcgResult(lam=lam, X=X, resid=np.linalg.norm(R, axis=0), iters=done,
+                        fallbacks=fallbacks, history=hist)
+
+
+def _rr_blocks(blocks, K):
+    S = np.concatenate([b[0] for b in blocks], axis=1)
+    LS = np.concatenate([b[1] for b in blocks], axis=1)
+    return rayleigh_ritz(S.T @ LS, S.T @ S, K)
+
+
+# --------------------------------------------------------------------------------------
+# Embedding and k-means (Sec. II.A)
+# --------------------------------------------------------------------------------------
+
+
+def embed_rows(X: np.ndarray) -> np.ndarray:
+    """Rows of the eigenvector block scaled to unit 2-norm; rows of norm < 1e-30 stay 0."""
+    X = np.asarray(X, dtype=np.float64)
+    nr = np.sqrt(np.sum(X * X, axis=1))
+    E = np.zeros_like(X)
+    ok = nr >= 1e-30
+    E[ok] = X[ok] / nr[ok, None]
+    return E
+
+
+def _sqdist_to(E: np.ndarray, c: np.ndarray) -> np.ndarray:
+    diff = E - c[None, :]
+    return np.sum(diff * diff, axis=1)
+
+
+def kmeanspp_seed(E: np.ndarray, k: int, u: np.ndarray) -> np.ndarray:
+    """k-means++ seeding (Arthur & Vassilvitskii 2007), driven by the uniforms u[0..k-1].
+
+    First seed: floor(u_0 n).  Seed t: with D2_i the squared distance of row i to its
+    nearest chosen seed, take the first i whose cumulative sum of D2 exceeds u_t sum(D2)
+    (clamped to the last row with D2 > 0); when sum(D2) = 0, the lowest unchosen row.
+
+    Pinned by: hand-worked small cases in the tests.
+    """
+    E = np.asarray(E, dtype=np.float64)
+    n = E.shape[0]
+    idx = [min(int(np.floor(u[0] * n)), n - 1)]
+    D2 = _sqdist_to(E, E[idx[0]])
+    for t in range(1, k):
+        total = float(np.sum(D2))
+        if total > 0.0:
+            c = np.cumsum(D2)
+            i = int(np.searchsorted(c, u[t] * total, side="right"))
+            if i >= n:
+                i = int(np.flatnonzero(D2 > 0)[-1])
+        else:
+            chosen = set(idx)
+            i = next(j for j in range(n) if j not in chosen)
+        idx.append(i)
+        D2 = np.minimum(D2, _sqdist_to(E, E[i]))
+    return np.asarray(idx, dtype=np.int64)
+
+
+def _assign(E: np.ndarray, C: np.ndarray) -> np.ndarray:
+    d = np.stack([_sqdist_to(E, C[j]) for j in range(C.shape[0])], axis=1)
+    return np.argmin(d, axis=1)  # first minimum = lowest cluster index on ties
+
+
+def lloyd(E: np.ndarray, C0: np.ndarray, iters: int):
+    """Lloyd iterations: assign every row to its nearest centroid (squared Euclidean,
+    ties to the lowest index), then move each centroid to the mean of its rows (an empty
+    cluster keeps its centroid); stop early when an assignment repeats the previous one.
+
+    Returns (labels, centroids, iterations_run).  Pinned by: monotone inertia, brute-force
+    optimum on tiny sets, zero inertia on k distinct points.
+    """
+    E = np.asarray(E, dtype=np.float64)
+    C = np.array(C0, dtype=np.float64, copy=True)
+    prev = None
+    done = 0
+    labels = _assign(E, C)
+    for _ in range(iters):
+        labels = _assign(E, C)
+        if prev is not None and np.array_equal(labels, prev):
+            break
+        done += 1
+        for j in range(C.shape[0]):
+            mask = labels == j
+            if mask.any():
+                C[j] = E[mask].mean(axis=0)
+        prev = labels
+    return labels.astype(np.int64), C, done
+
+
+def kmeans(E: np.ndarray, k: int, u: np.ndarray, iters: int = 50, init_idx=None):
+    """k-means++ seeding followed by Lloyd; returns (labels, centroids, seed_idx, inertia)."""
+    E = np.asarray(E, dtype=np.float64)
+    idx = kmeanspp_seed(E, k, u) if init_idx is None else np.asarray(init_idx, dtype=np.int64)
+    labels, C, _ = lloyd(E, E[idx], iters)
+    inertia = float(sum(np.sum((E[labels == j] - C[j]) ** 2) for j in range(k)))
+    return labels, C, idx, inertia
+
+
+def partition(L: Csr, X0: np.ndarray, k: int, u: np.ndarray, iters: int = 20,
+              kmeans_iters: int = 50, tol_abs: float = 0.0, tol_lock: float = 0.0):
+    """Spectral partition: LOBPCG block -> unit rows -> k-means (Sec. II.A)."""
+    res = lobpcg(L, X0, iters, tol_abs=tol_abs, tol_lock=tol_lock)
+    E = embed_rows(res.X)
+    labels, C, idx, inertia = kmeans(E, k, u, kmeans_iters)
+    return labels, res, E, idx
+
+
+# --------------------------------------------------------------------------------------
+# Metrics (Sec. IV) and subspace comparison
+# --------------------------------------------------------------------------------------
+
+
+def partition_metrics(truth, found):
+    """(PM, PR, PP): optimal partition matching, pairwise recall, pairwise precision.
+
+    PM = best one-to-one matching of truth and found blocks (Hungarian) / n;
+    PR = sum_ij C(c_ij, 2) / sum_t C(n_t, 2); PP = sum_ij C(c_ij, 2) / sum_f C(n_f, 2),
+    c_ij the contingency counts.  Pinned by hand-worked contingency tables.
+    """
+    truth = np.asarray(truth, dtype=np.int64)
+    found = np.asarray(found, dtype=np.int64)
+    n = truth.shape[0]
+    _, ti = np.unique(truth, return_inverse=True)
+    _, fi = np.unique(found, return_inverse=True)
+    Cm = np.zeros((ti.max() + 1, fi.max() + 1), dtype=np.int64)
+    np.add.at(Cm, (ti, fi), 1)
+    r, c = sopt.linear_sum_assignment(-Cm)
+    pm = Cm[r, c].sum() / n
+
+    def pairs(x):
+        return (x * (x - 1) // 2).sum()
+
+    both = pairs(Cm)
+    pt = pairs(Cm.sum(axis=1))
+    pf = pairs(Cm.sum(axis=0))
+    pr = both / pt if pt else 1.0
+    pp = both / pf if pf else 1.0
+    return float(pm), float(pr), float(pp)
+
+
+def sin_theta(A: np.ndarray, B: np.ndarray) -> float:
+    """Largest principal angle sine between span(A) and span(B) (same column count).
+
+    Q_A, Q_B orthonormal bases; E = Q_B - Q_A (Q_A' Q_B) formed explicitly; sin = ||E||_2.
+    """
+    Qa, _ = np.linalg.qr(np.asarray(A, dtype=np.float64))
+    Qb, _ = np.linalg.qr(np.asarray(B, dtype=np.float64))
+    Em = Qb - Qa @ (Qa.T @ Qb)
+    return float(np.linalg.norm(Em, 2))
