@@ -72,10 +72,17 @@ void sc_ctx_destroy(sc_ctx* ctx);
 const char* sc_last_error(const sc_ctx* ctx);
 /* Bytes currently held on the device by this context and its graphs. */
 size_t sc_ctx_bytes_in_use(const sc_ctx* ctx);
-/* Number of kernels this context has launched so far (for launch accounting). */
+/* Number of kernels the library has launched so far in this process (launch accounting). */
 uint64_t sc_ctx_kernel_launches(const sc_ctx* ctx);
+/* Kernel timing: between sc_profile_begin and sc_profile_end, every launch of a kernel
+ * named in `kernels` (comma-separated names such as "spmm,gram,rr_eig", or "*" for all) is
+ * bracketed by CUDA events on the stream it is launched on.  sc_profile_end synchronizes the
+ * context stream and writes one line "name launches total_ms" per kernel into `report`
+ * (NUL-terminated, truncated to len).  Process-wide: one profiling window at a time. */
+int sc_profile_begin(sc_ctx* ctx, const char* kernels);
+int sc_profile_end(sc_ctx* ctx, char* report, size_t len);
 
-/* ---- Laplacian (Sec. II.A; Sec. III "binary sparse matrix", matrix-free LXfun) ---------
+/* ---- Laplacian (Sec. II.A; Sec. III stores the directed adjacency sparse) --------------
  * sc_build_laplacian: directed edge list (src[e] -> dst[e], e < m, 0 <= src, dst < n) to
  * the symmetrized CSR of W and the degrees D of L = D - W.  Self-loops are dropped (they
  * add the same amount to D and W).  `w` = per-edge weights (NULL = all 1); with
@@ -92,8 +99,8 @@ int sc_graph_copy_csr(const sc_graph* g, int32_t* row_ptr, int32_t* col_idx, flo
                       double* deg);
 void sc_graph_destroy(sc_graph* g);
 
-/* sc_lap_apply: Y = L V = D V - W V for an n x k block V (one SpMM, Sec. III "a single
- * multiplication ... per iteration").  prec selects FP32 (V, Y float*) or FP64 (double*);
+/* sc_lap_apply: Y = L V = D V - W V for an n x k block V (one SpMM; Sec. III: LOBPCG needs
+ * one product of the graph matrix with a multi-vector per iteration).  prec selects FP32 (V, Y float*) or FP64 (double*);
  * V and Y are n x k row-major, host or device per on_device. */
 int sc_lap_apply(sc_ctx* ctx, sc_graph* g, int k, int prec, const void* V, void* Y,
                  int on_device);

@@ -1,0 +1,161 @@
+// Shared declarations of the GB300 spectral-clustering library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+namespace sc {
+
+// ---- device status word bits (written by kernels, read back by the host) ----------------
+enum : int {
+  ST_EDGE_RANGE = 1,   // an edge endpoint outside [0, n)
+  ST_NNZ_OVERFLOW = 2, // stored nonzeros would exceed 2^31 - 1
+  ST_CHOL_FAIL = 4,    // Cholesky pivot below tolerance
+  ST_ROW_TOO_LONG = 8, // internal: a row exceeded the sort capacity
+  ST_NONFINITE = 16,   // NaN/Inf met in a small dense solve
+};
+
+// Up to three column blocks viewed as one n x (c0 + c1 + c2) matrix (row-major blocks).
+template <typename T>
+struct Cat3 {
+  const T* p[3];
+  long long ld[3];
+  int c[3];
+  int nblk;
+  __host__ __device__ int cols() const {
+    int s = 0;
+    for (int i = 0; i < nblk; ++i) s += c[i];
+    return s;
+  }
+};
+
+template <typename T>
+inline Cat3<T> cat(const T* p0, long long ld0, int c0) {
+  Cat3<T> r{};
+  r.p[0] = p0; r.ld[0] = ld0; r.c[0] = c0; r.nblk = 1;
+  return r;
+}
+template <typename T>
+inline Cat3<T> cat(const T* p0, long long ld0, int c0, const T* p1, long long ld1, int c1) {
+  Cat3<T> r = cat(p0, ld0, c0);
+  r.p[1] = p1; r.ld[1] = ld1; r.c[1] = c1; r.nblk = 2;
+  return r;
+}
+template <typename T>
+inline Cat3<T> cat(const T* p0, long long ld0, int c0, const T* p1, long long ld1, int c1,
+                   const T* p2, long long ld2, int c2) {
+  Cat3<T> r = cat(p0, ld0, c0, p1, ld1, c1);
+  r.p[2] = p2; r.ld[2] = ld2; r.c[2] = c2; r.nblk = 3;
+  return r;
+}
+
+// Launch accounting: every kernel launch of the library goes through note_launch().
+void note_launch();
+uint64_t launches_total();
+
+// Per-kernel timing with CUDA events on the launching stream.  A ProfScope placed around a
+// launch records an event pair when profiling is on for that kernel name.
+void prof_begin(cudaStream_t st, const char* name);
+void prof_end(cudaStream_t st, const char* name);
+struct ProfScope {
+  cudaStream_t st;
+  const char* name;
+  ProfScope(cudaStream_t s, const char* n) : st(s), name(n) { prof_begin(st, name); }
+  ~ProfScope() { prof_end(st, name); }
+};
+
+// Seeded N(0,1) start block (SplitMix64 counter stream `key`, Box-Muller on consecutive
+// uniform pairs, rounded to float): element e of the n x K row-major block -> X[e/K][e%K].
+template <typename T>
+cudaError_t gauss_block(cudaStream_t st, long long n, int K, unsigned long long key, T* X,
+                        long long ldx);
+
+// ---- kernel entry points (host wrappers, all asynchronous on `st`) -----------------------
+
+// CSR build (Sec. II.A): edge list -> symmetrized CSR.  Returns cudaError_t of the launches;
+// sizes that depend on device results are returned through the host pointers after an
+// internal stream synchronisation.
+struct CsrDev {
+  int n = 0;
+  long long nnz = 0;
+  int* row_ptr = nullptr;  // n+1
+  int* col_idx = nullptr;  // nnz
+  float* val = nullptr;    // nnz (algebraic) or null (logical: all ones)
+  float* degf = nullptr;   // n
+  double* degd = nullptr;  // n
+  double deg_max = 0;
+};
+
+// Allocation callbacks used by multi-phase host routines.
+struct Alloc {
+  void* (*alloc)(void* self, size_t bytes);
+  void (*free)(void* self, void* p);
+  void* self;
+  template <typename T>
+  T* get(size_t count) { return (T*)alloc(self, count * sizeof(T)); }
+  void put(void* p) { if (p) free(self, p); }
+};
+
+cudaError_t build_csr(cudaStream_t st, Alloc& al, int n, long long m, const int* d_src,
+                      const int* d_dst, const float* d_w, int algebraic, int* d_status,
+                      CsrDev* out, int* host_status);
+cudaError_t merge_csr(cudaStream_t st, Alloc& al, const CsrDev& a, const CsrDev& b,
+                      int algebraic, int* d_status, CsrDev* out, int* host_status);
+
+// SpMM: Y = D V - W V (n x k block, row stride ldv/ldy, ld multiple of 16 bytes).
+template <typename T>
+cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv, T* Y,
+                     long long ldy, int k);
+
+// Gram: C (a x b, FP64 row-major, ldc) = A' B over n rows.  `sym` = A and B are the same
+// matrix: only the upper tile triangle is computed and mirrored.  Workspace from `al`.
+template <typename T>
+cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, const Cat3<T>& B,
+                 double* C, int ldc, bool sym, int use_tc);
+
+// Tall GEMM: out (n x b, ldo) = beta * Cin + A (n x a) W (a x b, row-major ldw, type T).
+template <typename T>
+cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W, int ldw,
+                      int b, T* out, long long ldo, const T* Cin, long long ldc, T beta);
+
+// Residual: R = LX - X diag(theta); rho2[j] = sum_i R_ij^2 (FP64).  Workspace from `al`.
+template <typename T>
+cudaError_t residual(cudaStream_t st, Alloc& al, long long n, int K, const T* X, const T* LX,
+                     long long ld, const double* theta, T* R, double* rho2);
+
+// Gather / scatter of a column subset (cols[j] -> j).
+template <typename T>
+cudaError_t gather_cols(cudaStream_t st, long long n, const T* src, long long lds, T* dst,
+                        long long ldd, const int* cols, int kc);
+
+// dst (rows x cols, T) = scale * src (FP64).
+template <typename T>
+cudaError_t cast_mat(cudaStream_t st, int rows, int cols, const double* src, int lds, T* dst,
+                     int ldd, double scale);
+
+// Row normalization E_i = X_i / ||X_i||.
+template <typename T>
+cudaError_t rownorm(cudaStream_t st, long long n, int K, const T* X, long long ldx, float* E,
+                    long long lde);
+
+// Small dense: Tm = D C^-T for the scaled Cholesky D G D = C C' of G (ka x ka FP64).
+// Tm is ka x ka upper triangular (row-major, T).  Status bit ST_CHOL_FAIL on breakdown.
+template <typename T>
+cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
+                     int* d_status, double pivot_tol);
+
+// Rayleigh-Ritz in an orthonormal basis: K smallest eigenpairs of symmetric m x m G (FP64).
+// theta[K] FP64 (device), Y (m x K, T, row-major).  Arithmetic in T.
+template <typename T>
+cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
+                   double* theta, T* Y, int* d_status);
+
+// k-means.
+cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
+                     long long lde, const double* u_host, int* seeds_dev);
+cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
+                  long long lde, const int* seeds_dev, int iters, int* labels_dev,
+                  double* cent_dev, int* iters_run, double* inertia);
+
+}  // namespace sc

@@ -1,0 +1,176 @@
+// Tall-skinny Gram matrices C = A' B (Sec. IV: the Gram products of the n x l multi-vectors
+// cost O(n l^2) and take over from the O(n l) vector work as the block widens).
+//
+// CUDA-core form (SC_PREC_FP32 / SC_PREC_FP64).  Split-K over row chunks: CTA (tile,
+// chunk) forms a 64 x 64 tile of A'B over its rows with a 4 x 4 register micro-tile per
+// thread (FP32 accumulation for float blocks, FP64 for double), writes the tile as FP64
+// partials, and the last CTA to finish a tile (atomic ticket, no waiting) sums the chunks
+// in fixed chunk order.  The result is deterministic and independent of scheduling.
+// The tensor-core form lives in k_gram_tc.cu.
+#include "common.cuh"
+
+namespace sc {
+namespace {
+
+constexpr int TB = 64;   // output tile
+constexpr int RB = 16;   // rows per smem stage
+constexpr int NT = 256;  // threads
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+struct ColMap {
+  int blk;
+  int lc;
+};
+
+template <typename T>
+__device__ inline void map_cols(const Cat3<T>& M, int c0, ColMap* cm) {
+  for (int t = threadIdx.x; t < TB; t += blockDim.x) {
+    int c = c0 + t;
+    int b = -1, lc = 0;
+    int acc = 0;
+    for (int q = 0; q < M.nblk; ++q) {
+      if (c >= acc && c < acc + M.c[q]) {
+        b = q;
+        lc = c - acc;
+      }
+      acc += M.c[q];
+    }
+    cm[t].blk = b;
+    cm[t].lc = lc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT)
+    k_gram(long long n, Cat3<T> A, Cat3<T> B, int a, int b, const int2* __restrict__ tiles,
+           int nch, long long rows_per_chunk, double* __restrict__ part, int* cnt, double* C,
+           int ldc, int sym) {
+  using AT = typename Acc<T>::type;
+  __shared__ __align__(16) T As[RB][TB];
+  __shared__ __align__(16) T Bs[RB][TB];
+  __shared__ ColMap cma[TB], cmb[TB];
+  __shared__ int last;
+  const int tile = blockIdx.x / nch;
+  const int chunk = blockIdx.x % nch;
+  const int2 tl = tiles[tile];
+  const int ti = tl.x, tj = tl.y;
+  map_cols(A, ti * TB, cma);
+  map_cols(B, tj * TB, cmb);
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  AT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  long long r0 = (long long)chunk * rows_per_chunk;
+  long long r1 = r0 + rows_per_chunk;
+  if (r1 > n) r1 = n;
+  const int lr = threadIdx.x / 16;        // row within the stage
+  const int lc = (threadIdx.x % 16) * 4;  // first of 4 columns
+  for (long long r = r0; r < r1; r += RB) {
+    long long row = r + lr;
+    bool ok = row < r1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ColMap ma = cma[lc + q], mb = cmb[lc + q];
+      T va = 0, vb = 0;
+      if (ok && ma.blk >= 0) va = A.p[ma.blk][row * A.ld[ma.blk] + ma.lc];
+      if (ok && mb.blk >= 0) vb = B.p[mb.blk][row * B.ld[mb.blk] + mb.lc];
+      As[lr][lc + q] = va;
+      Bs[lr][lc + q] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+      AT av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        av[i] = (AT)As[k][ty * 4 + i];
+        bv[i] = (AT)Bs[k][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* mine = part + ((long long)tile * nch + chunk) * TB * TB;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mine[(ty * 4 + i) * TB + tx * 4 + j] = (double)acc[i][j];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&cnt[tile], 1) == nch - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const double* tp = part + (long long)tile * nch * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += NT) {
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += __ldcg(tp + (long long)c * TB * TB + e);
+    int gi = ti * TB + e / TB, gj = tj * TB + e % TB;
+    if (gi < a && gj < b) {
+      C[(long long)gi * ldc + gj] = s;
+      if (sym && ti != tj) C[(long long)gj * ldc + gi] = s;
+    }
+  }
+  if (threadIdx.x == 0) cnt[tile] = 0;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, const Cat3<T>& B,
+                 double* C, int ldc, bool sym, int use_tc) {
+  (void)use_tc;
+  int a = A.cols(), b = B.cols();
+  if (a == 0 || b == 0) return cudaSuccess;
+  if (n == 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * b, a, st);
+  int na = (a + TB - 1) / TB, nb = (b + TB - 1) / TB;
+  int2 tl_host[64 * 64];
+  int nt = 0;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j)
+      if (!sym || i <= j) tl_host[nt++] = make_int2(i, j);
+  if (nt > 64 * 64) return cudaErrorInvalidValue;
+  long long target = 152LL * 4;
+  long long nch = (target + nt - 1) / nt;
+  long long maxch = (n + RB - 1) / RB;
+  if (nch > maxch) nch = maxch;
+  if (nch < 1) nch = 1;
+  long long rpc = (n + nch - 1) / nch;
+  rpc = (rpc + RB - 1) / RB * RB;
+  nch = (n + rpc - 1) / rpc;
+  if (nch < 1) nch = 1;
+  int2* tiles = al.get<int2>(nt);
+  int* cnt = al.get<int>(nt);
+  double* part = al.get<double>((size_t)nt * nch * TB * TB);
+  cudaError_t e = cudaSuccess;
+  if (!tiles || !cnt || !part) {
+    e = cudaErrorMemoryAllocation;
+  } else {
+    cudaMemcpyAsync(tiles, tl_host, sizeof(int2) * nt, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(cnt, 0, sizeof(int) * nt, st);
+    ProfScope ps(st, "gram");
+    k_gram<T><<<(unsigned)(nt * nch), NT, 0, st>>>(n, A, B, a, b, tiles, (int)nch, rpc, part,
+                                                   cnt, C, ldc, sym ? 1 : 0);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  al.put(tiles);
+  al.put(cnt);
+  al.put(part);
+  return e;
+}
+
+template cudaError_t gram<float>(cudaStream_t, Alloc&, long long, const Cat3<float>&,
+                                 const Cat3<float>&, double*, int, bool, int);
+template cudaError_t gram<double>(cudaStream_t, Alloc&, long long, const Cat3<double>&,
+                                  const Cat3<double>&, double*, int, bool, int);
+
+}  // namespace sc

@@ -1,0 +1,447 @@
+// k-means on the unit-normalized rows of the eigenvector block (Sec. II.A: the rows are
+// clustered, traditionally by k-means++).
+//
+// Seeding (Arthur & Vassilvitskii 2007), k sequential rounds, decisions in FP64:
+//   update: D2_i <- min(D2_i, ||E_i - c_t||^2) in FP64 (FP32 data promoted exactly), with
+//           FP64 block sums in a fixed tree order;
+//   pick:   one CTA scans the block sums and then the chosen block's D2 to find the first i
+//           whose running sum exceeds u_t * sum(D2) (clamped to the last row with D2 > 0;
+//           sum(D2) = 0 -> lowest unchosen row).
+// Lloyd rounds:
+//   assign: FP32 distance ||c||^2 - 2 e.c to every centroid with a running best/second best;
+//           rows whose margin is below a threshold are re-decided with direct FP64 distances
+//           ||e - c||^2 (ties -> lowest index), so the labels are those of FP64 arithmetic;
+//   update: per-CTA FP64 sums accumulated in row order (one thread per column), the last
+//           CTA adds the CTA partials in fixed order and divides; empty clusters keep their
+//           centroid.  Deterministic for a given n.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace sc {
+namespace {
+
+constexpr int PB = 1024;  // rows per seeding block
+
+__device__ double block_sum_d(double v, double* sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double s = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[32] = s;
+  }
+  __syncthreads();
+  double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// inclusive scan of doubles across the block (fixed order: warp scan + warp-total scan)
+__device__ double block_incl_scan_d(double v, double* sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    double s = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  double r = x + (wid > 0 ? sh[wid - 1] : 0.0);
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_pp_first(int n, const double* u, int* seeds, int* chosen) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long i = (long long)floor(u[0] * (double)n);
+    if (i > n - 1) i = n - 1;
+    if (i < 0) i = 0;
+    seeds[0] = (int)i;
+    chosen[i] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(PB)
+    k_pp_update(int n, int d, const float* __restrict__ E, long long lde, const int* seeds, int t,
+                double* D2, double* bsum) {
+  extern __shared__ double cs[];  // d + 33
+  double* sh = cs + d;
+  const int s = seeds[t];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) cs[c] = (double)E[(long long)s * lde + c];
+  __syncthreads();
+  long long i = (long long)blockIdx.x * PB + threadIdx.x;
+  double v = 0.0;
+  if (i < n) {
+    const float* e = E + i * lde;
+    double acc = 0.0;
+    for (int c = 0; c < d; ++c) {
+      double df = (double)e[c] - cs[c];
+      acc = fma(df, df, acc);
+    }
+    v = (t == 0) ? acc : fmin(D2[i], acc);
+    D2[i] = v;
+  }
+  double b = block_sum_d(v, sh);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = b;
+}
+
+__global__ void __launch_bounds__(PB)
+    k_pp_pick(int n, int nb, const double* __restrict__ D2, const double* __restrict__ bsum,
+              const double* u, int t, int* seeds, int* chosen) {
+  __shared__ double sh[40];
+  __shared__ int sel;
+  __shared__ double base_sh;
+  // total over block sums in fixed order (thread-strided partial sums, then the tree)
+  double p = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) p += bsum[b];
+  double total = block_sum_d(p, sh);
+  if (threadIdx.x == 0) sel = -1;
+  __syncthreads();
+  if (total > 0.0) {
+    double target = u[t] * total;
+    // running sum over blocks, PB blocks at a time
+    double carry = 0.0;
+    int bstar = -1;
+    for (int b0 = 0; b0 < nb && bstar < 0; b0 += PB) {
+      int b = b0 + threadIdx.x;
+      double v = b < nb ? bsum[b] : 0.0;
+      double inc = block_incl_scan_d(v, sh) + carry;
+      double exc = inc - v;
+      if (b < nb && exc <= target && target < inc) {
+        sel = b;
+        base_sh = exc;
+      }
+      __syncthreads();
+      bstar = sel;
+      double tot = block_sum_d(v, sh);
+      carry += tot;
+      __syncthreads();
+    }
+    if (bstar >= 0) {
+      if (threadIdx.x == 0) sel = -1;
+      __syncthreads();
+      double base = base_sh;
+      long long i = (long long)bstar * PB + threadIdx.x;
+      double v = i < n ? D2[i] : 0.0;
+      double inc = block_incl_scan_d(v, sh) + base;
+      if (i < n && inc > target && inc - v <= target) sel = (int)i;
+      __syncthreads();
+      bstar = sel;
+    }
+    if (threadIdx.x == 0) {
+      int pick = bstar;
+      if (pick < 0) {  // rounding put the target past the end: last row with D2 > 0
+        for (long long i = n - 1; i >= 0; --i)
+          if (D2[i] > 0.0) {
+            pick = (int)i;
+            break;
+          }
+      }
+      seeds[t] = pick;
+      chosen[pick] = 1;
+    }
+  } else {
+    // all remaining rows coincide with chosen seeds: lowest unchosen row
+    if (threadIdx.x == 0) sel = n;
+    __syncthreads();
+    for (long long i = threadIdx.x; i < n; i += blockDim.x)
+      if (!chosen[i]) {
+        atomicMin(&sel, (int)i);
+        break;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int pick = sel < n ? sel : 0;
+      seeds[t] = pick;
+      chosen[pick] = 1;
+    }
+  }
+}
+
+// ---- Lloyd ---------------------------------------------------------------------------------
+
+__global__ void k_init_cent(int d, int k, const float* __restrict__ E, long long lde,
+                            const int* seeds, double* C64, float* C32, float* cn) {
+  int j = blockIdx.x;
+  if (j >= k) return;
+  const float* e = E + (long long)seeds[j] * lde;
+  float s = 0.f;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    C64[(long long)j * d + c] = (double)e[c];
+    C32[(long long)j * d + c] = e[c];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < d; ++c) s = fmaf(C32[(long long)j * d + c], C32[(long long)j * d + c], s);
+    cn[j] = s;
+  }
+}
+
+constexpr int ACH = 64;  // centroids per shared-memory chunk in the assignment
+
+__global__ void __launch_bounds__(256)
+    k_assign(int n, int d, int k, const float* __restrict__ E, long long lde,
+             const float* __restrict__ C32, const float* __restrict__ cn,
+             const double* __restrict__ C64, int* labels, int* changes, int first, double tie) {
+  extern __shared__ float csm[];  // ACH * d
+  __shared__ int nchg;
+  if (threadIdx.x == 0) nchg = 0;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float* e = E + (i < n ? i : 0) * lde;
+  float best = 3.4e38f, second = 3.4e38f;
+  int bj = 0;
+  for (int j0 = 0; j0 < k; j0 += ACH) {
+    int nj = min(ACH, k - j0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nj * d; q += blockDim.x) csm[q] = C32[(long long)j0 * d + q];
+    __syncthreads();
+    if (i < n) {
+      for (int jj = 0; jj < nj; ++jj) {
+        const float* c = csm + jj * d;
+        float dot = 0.f;
+        for (int q = 0; q < d; ++q) dot = fmaf(e[q], c[q], dot);
+        float dist = fmaf(-2.f, dot, cn[j0 + jj]);
+        if (dist < best) {
+          second = best;
+          best = dist;
+          bj = j0 + jj;
+        } else if (dist < second) {
+          second = dist;
+        }
+      }
+    }
+  }
+  if (i < n) {
+    if (k > 1 && second - best < (float)tie) {
+      // near tie: decide with direct FP64 distances to the FP64 centroids
+      double bd = 1e300;
+      int bb = 0;
+      for (int j = 0; j < k; ++j) {
+        const double* c = C64 + (long long)j * d;
+        double acc = 0.0;
+        for (int q = 0; q < d; ++q) {
+          double df = (double)e[q] - c[q];
+          acc = fma(df, df, acc);
+        }
+        if (acc < bd) {
+          bd = acc;
+          bb = j;
+        }
+      }
+      bj = bb;
+    }
+    int old = labels[i];
+    if (first || old != bj) atomicAdd(&nchg, 1);
+    labels[i] = bj;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && nchg) atomicAdd(changes, nchg);
+}
+
+// Per-CTA FP64 cluster sums in row order; thread c owns column c (and thread 0 the counts).
+__global__ void k_cent_partial(int n, int d, int k, const float* __restrict__ E, long long lde,
+                               const int* __restrict__ labels, long long rows_per_cta,
+                               double* part, int* pcnt, int use_smem) {
+  extern __shared__ double acc_sm[];  // k*d (when use_smem)
+  double* acc = use_smem ? acc_sm : part + (long long)blockIdx.x * k * d;
+  int* cnt = pcnt + (long long)blockIdx.x * k;
+  for (long long q = threadIdx.x; q < (long long)k * d; q += blockDim.x) acc[q] = 0.0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cnt[j] = 0;
+  __syncthreads();
+  long long r0 = blockIdx.x * rows_per_cta, r1 = min((long long)n, r0 + rows_per_cta);
+  for (long long r = r0; r < r1; ++r) {
+    int l = labels[r];
+    for (int c = threadIdx.x; c < d; c += blockDim.x)
+      acc[(long long)l * d + c] += (double)E[r * lde + c];
+    if (threadIdx.x == 0) cnt[l] += 1;
+  }
+  __syncthreads();
+  if (use_smem)
+    for (long long q = threadIdx.x; q < (long long)k * d; q += blockDim.x)
+      part[(long long)blockIdx.x * k * d + q] = acc[q];
+}
+
+__global__ void k_cent_reduce(int d, int k, int nct, const double* __restrict__ part,
+                              const int* __restrict__ pcnt, double* C64, float* C32, float* cn) {
+  int j = blockIdx.x;
+  __shared__ long long tot;
+  __shared__ float red[32];
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int c = 0; c < nct; ++c) t += pcnt[(long long)c * k + j];
+    tot = t;
+  }
+  __syncthreads();
+  float s = 0.f;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    if (tot > 0) {
+      double v = 0.0;
+      for (int q = 0; q < nct; ++q) v += part[((long long)q * k + j) * d + c];
+      double m = v / (double)tot;
+      C64[(long long)j * d + c] = m;
+      C32[(long long)j * d + c] = (float)m;
+    }
+    float f = C32[(long long)j * d + c];
+    s = fmaf(f, f, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    cn[j] = t;
+  }
+}
+
+__global__ void k_inertia(int n, int d, const float* __restrict__ E, long long lde,
+                          const int* __restrict__ labels, const double* __restrict__ C64,
+                          double* part) {
+  __shared__ double sh[40];
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double* c = C64 + (long long)labels[i] * d;
+    for (int q = 0; q < d; ++q) {
+      double df = (double)E[i * lde + q] - c[q];
+      v = fma(df, df, v);
+    }
+  }
+  double b = block_sum_d(v, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+}  // namespace
+
+cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
+                     long long lde, const double* u_host, int* seeds) {
+  int nb = (n + PB - 1) / PB;
+  double* u = al.get<double>(k);
+  double* D2 = al.get<double>(n);
+  double* bsum = al.get<double>(nb);
+  int* chosen = al.get<int>(n);
+  cudaError_t e = cudaSuccess;
+  if (!u || !D2 || !bsum || !chosen) {
+    e = cudaErrorMemoryAllocation;
+  } else {
+    cudaMemcpyAsync(u, u_host, sizeof(double) * k, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(chosen, 0, sizeof(int) * n, st);
+    k_pp_first<<<1, 32, 0, st>>>(n, u, seeds, chosen);
+    note_launch();
+    size_t sm = sizeof(double) * (d + 40);
+    for (int t = 0; t < k; ++t) {
+      if (t > 0) {
+        k_pp_pick<<<1, PB, 0, st>>>(n, nb, D2, bsum, u, t, seeds, chosen);
+        note_launch();
+      }
+      if (t + 1 < k) {
+        ProfScope ps(st, "kmeanspp_update");
+        k_pp_update<<<nb, PB, sm, st>>>(n, d, E, lde, seeds, t, D2, bsum);
+        note_launch();
+      }
+    }
+    e = cudaGetLastError();
+    // u_host may be a stack array of the caller: make sure the copy finished
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  al.put(u);
+  al.put(D2);
+  al.put(bsum);
+  al.put(chosen);
+  return e;
+}
+
+cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
+                  long long lde, const int* seeds, int iters, int* labels, double* C64,
+                  int* iters_run, double* inertia) {
+  float* C32 = al.get<float>((size_t)k * d);
+  float* cn = al.get<float>(k);
+  int* changes = al.get<int>(1);
+  long long nct = 152 * 2;
+  if (nct > n) nct = n > 0 ? n : 1;
+  long long rpc = (n + nct - 1) / nct;
+  nct = (n + rpc - 1) / rpc;
+  if (nct < 1) nct = 1;
+  double* part = al.get<double>((size_t)nct * k * d);
+  int* pcnt = al.get<int>((size_t)nct * k);
+  double* ipart = al.get<double>(152);
+  cudaError_t e = cudaSuccess;
+  int done = 0;
+  if (!C32 || !cn || !changes || !part || !pcnt || !ipart) {
+    e = cudaErrorMemoryAllocation;
+    goto out;
+  }
+  {
+    k_init_cent<<<k, 128, 0, st>>>(d, k, E, lde, seeds, C64, C32, cn);
+    note_launch();
+    size_t asm_bytes = sizeof(float) * (size_t)ACH * d;
+    if (asm_bytes > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_assign, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)asm_bytes);
+      if (e != cudaSuccess) goto out;
+    }
+    size_t psm = sizeof(double) * (size_t)k * d;
+    int use_smem = psm <= 160 * 1024;
+    if (use_smem && psm > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_cent_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psm);
+      if (e != cudaSuccess) goto out;
+    }
+    unsigned ab = (unsigned)((n + 255) / 256);
+    for (int it = 0; it < iters; ++it) {
+      cudaMemsetAsync(changes, 0, sizeof(int), st);
+      ProfScope ps(st, "kmeans_assign");
+      k_assign<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes,
+                                            it == 0, 1e-4);
+      note_launch();
+      if (it > 0) {
+        int h = 0;
+        cudaMemcpyAsync(&h, changes, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) goto out;
+        if (h == 0) break;
+      }
+      k_cent_partial<<<(unsigned)nct, 64, use_smem ? psm : 0, st>>>(n, d, k, E, lde, labels, rpc,
+                                                                    part, pcnt, use_smem);
+      note_launch();
+      k_cent_reduce<<<k, 128, 0, st>>>(d, k, (int)nct, part, pcnt, C64, C32, cn);
+      note_launch();
+      ++done;
+    }
+    k_inertia<<<152, 256, 0, st>>>(n, d, E, lde, labels, C64, ipart);
+    note_launch();
+    double hp[152];
+    cudaMemcpyAsync(hp, ipart, sizeof(hp), cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) goto out;
+    double s = 0.0;
+    for (int q = 0; q < 152; ++q) s += hp[q];
+    if (inertia) *inertia = s;
+    if (iters_run) *iters_run = done;
+  }
+out:
+  if (e == cudaSuccess) e = cudaGetLastError();
+  al.put(C32);
+  al.put(cn);
+  al.put(changes);
+  al.put(part);
+  al.put(pcnt);
+  al.put(ipart);
+  return e;
+}
+
+}  // namespace sc

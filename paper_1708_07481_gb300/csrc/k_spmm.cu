@@ -1,0 +1,133 @@
+// SpMM with the graph Laplacian: Y = D V - W V for a row-major n x k block V (Sec. III:
+// LOBPCG needs one multiplication of the graph matrix by a multi-vector per iteration).
+//
+// A team of TL lanes owns one row; each lane owns 16-byte column chunks (float4 / double2)
+// c = lane, lane + TL, ...  The team loads TL neighbour indices at once (one per lane) and
+// broadcasts them with shuffles, so every gathered neighbour row is read as consecutive
+// 16-byte vectors.  TL is picked from the block width so idle lanes stay few.
+// HBM/L2-bound: per row, 4 bytes of index per neighbour plus k * sizeof(T) bytes of the
+// neighbour's row (served from L2 when the block fits there), and the row's own V/Y rows.
+#include "common.cuh"
+
+namespace sc {
+namespace {
+
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  using type = float4;
+  static constexpr int W = 4;
+  __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static void fma(float4& a, float w, const float4& x) {
+    a.x = fmaf(w, x.x, a.x); a.y = fmaf(w, x.y, a.y); a.z = fmaf(w, x.z, a.z); a.w = fmaf(w, x.w, a.w);
+  }
+  __device__ static void add(float4& a, const float4& x) {
+    a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+  }
+  __device__ static float4 lap(float d, const float4& v, const float4& s) {
+    return make_float4(fmaf(d, v.x, -s.x), fmaf(d, v.y, -s.y), fmaf(d, v.z, -s.z), fmaf(d, v.w, -s.w));
+  }
+};
+template <> struct Vec<double> {
+  using type = double2;
+  static constexpr int W = 2;
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static void fma(double2& a, double w, const double2& x) {
+    a.x = fma_(w, x.x, a.x); a.y = fma_(w, x.y, a.y);
+  }
+  __device__ static double fma_(double a, double b, double c) { return ::fma(a, b, c); }
+  __device__ static void add(double2& a, const double2& x) { a.x += x.x; a.y += x.y; }
+  __device__ static double2 lap(double d, const double2& v, const double2& s) {
+    return make_double2(::fma(d, v.x, -s.x), ::fma(d, v.y, -s.y));
+  }
+};
+
+constexpr int MAXC = 4;  // chunks per lane: TL=32 x 4 chunks x 4 floats = 512 columns
+
+template <typename T, int TL>
+__global__ void __launch_bounds__(256)
+    k_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+           const float* __restrict__ val, const T* __restrict__ deg, const T* __restrict__ V,
+           long long ldv, T* __restrict__ Y, long long ldy, int nvec) {
+  using V4 = typename Vec<T>::type;
+  const int lane = threadIdx.x % TL;
+  const unsigned gmask = (TL == 32) ? 0xffffffffu
+                                    : (((1u << TL) - 1u) << ((threadIdx.x & 31) / TL * TL));
+  long long team = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / TL;
+  long long nteams = ((long long)gridDim.x * blockDim.x) / TL;
+  const int nc = (nvec + TL - 1) / TL;
+  for (long long row = team; row < n; row += nteams) {
+    V4 acc[MAXC];
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) acc[c] = Vec<T>::zero();
+    int s = rp[row], e = rp[row + 1];
+    for (int base = s; base < e; base += TL) {
+      int my = base + lane < e ? ci[base + lane] : -1;
+      float mw = (val && base + lane < e) ? val[base + lane] : 1.0f;
+      int cnt = min(TL, e - base);
+      for (int t = 0; t < cnt; ++t) {
+        int j = __shfl_sync(gmask, my, t, TL);
+        T w = (T)__shfl_sync(gmask, mw, t, TL);
+        const V4* vr = reinterpret_cast<const V4*>(V + (long long)j * ldv);
+#pragma unroll
+        for (int c = 0; c < MAXC; ++c) {
+          int q = lane + c * TL;
+          if (c < nc && q < nvec) {
+            V4 x = __ldg(vr + q);
+            if (val) Vec<T>::fma(acc[c], w, x);
+            else Vec<T>::add(acc[c], x);
+          }
+        }
+      }
+    }
+    T d = deg[row];
+    const V4* vi = reinterpret_cast<const V4*>(V + row * ldv);
+    V4* yo = reinterpret_cast<V4*>(Y + row * ldy);
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      int q = lane + c * TL;
+      if (c < nc && q < nvec) yo[q] = Vec<T>::lap(d, vi[q], acc[c]);
+    }
+  }
+}
+
+template <typename T, int TL>
+cudaError_t launch(cudaStream_t st, const CsrDev& g, const T* deg, const T* V, long long ldv,
+                   T* Y, long long ldy, int nvec) {
+  long long teams = g.n;
+  long long threads = teams * TL;
+  long long blocks = (threads + 255) / 256;
+  long long cap = 152LL * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  ProfScope ps(st, "spmm");
+  k_spmm<T, TL><<<(unsigned)blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, deg, V, ldv,
+                                                 Y, ldy, nvec);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv, T* Y,
+                     long long ldy, int k) {
+  constexpr int W = Vec<T>::W;
+  if (ldv % W || ldy % W) return cudaErrorInvalidValue;
+  int nvec = (k + W - 1) / W;
+  if (nvec > 32 * MAXC) return cudaErrorInvalidValue;
+  const T* deg;
+  if constexpr (sizeof(T) == 4) deg = (const T*)g.degf;
+  else deg = (const T*)g.degd;
+  if (g.n == 0) return cudaSuccess;
+  if (nvec <= 4) return launch<T, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 8) return launch<T, 8>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 16) return launch<T, 16>(st, g, deg, V, ldv, Y, ldy, nvec);
+  return launch<T, 32>(st, g, deg, V, ldv, Y, ldy, nvec);
+}
+
+template cudaError_t spmm_lap<float>(cudaStream_t, const CsrDev&, const float*, long long,
+                                     float*, long long, int);
+template cudaError_t spmm_lap<double>(cudaStream_t, const CsrDev&, const double*, long long,
+                                      double*, long long, int);
+
+}  // namespace sc

@@ -1,0 +1,322 @@
+// Tall-skinny block updates of LOBPCG (Sec. IV: the O(n l) multi-vector work): projections
+// R - X F, Cholesky-QR transforms V Tm, the Rayleigh-Ritz update [X R P] Y, the residual
+// R = LX - X diag(theta) with its column norms, column gathers and the row normalization
+// of the embedding (Sec. II.A).
+#include "common.cuh"
+
+namespace sc {
+namespace {
+
+constexpr int TR = 64;  // rows per CTA
+constexpr int TC = 64;  // output columns per CTA
+constexpr int KB = 16;  // inner-dimension stage
+
+// out (n x b) = beta * Cin + A (n x a) * W (a x b).  256 threads, 4 x 4 micro-tile each.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_tall_gemm(long long n, Cat3<T> A, int a, const T* __restrict__ W, int ldw, int b,
+                T* __restrict__ out, long long ldo, const T* Cin, long long ldc, T beta) {
+  __shared__ __align__(16) T As[KB][TR + 4];
+  __shared__ __align__(16) T Ws[KB][TC];
+  __shared__ int mblk[KB], mlc[KB];
+  const long long r0 = (long long)blockIdx.x * TR;
+  const int c0 = blockIdx.y * TC;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int k0 = 0; k0 < a; k0 += KB) {
+    if (threadIdx.x < KB) {
+      int c = k0 + threadIdx.x, blk = -1, lc = 0, s = 0;
+      for (int q = 0; q < A.nblk; ++q) {
+        if (c >= s && c < s + A.c[q]) {
+          blk = q;
+          lc = c - s;
+        }
+        s += A.c[q];
+      }
+      mblk[threadIdx.x] = blk;
+      mlc[threadIdx.x] = lc;
+    }
+    __syncthreads();
+    // A tile: 64 rows x 16 cols; thread -> (row = t / 4, cols (t % 4) * 4 .. + 4)
+    {
+      int lr = threadIdx.x / 4, lk = (threadIdx.x % 4) * 4;
+      long long row = r0 + lr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int kk = lk + q;
+        int blk = mblk[kk];
+        T v = 0;
+        if (row < n && blk >= 0) v = A.p[blk][row * A.ld[blk] + mlc[kk]];
+        As[kk][lr] = v;
+      }
+    }
+    // W tile: 16 x 64; thread -> (k = t / 16, cols (t % 16) * 4 .. + 4)
+    {
+      int lk = threadIdx.x / 16, lc = (threadIdx.x % 16) * 4;
+      int kk = k0 + lk;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int cc = c0 + lc + q;
+        Ws[lk][lc + q] = (kk < a && cc < b) ? W[(long long)kk * ldw + cc] : (T)0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      T av[4], wv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        av[i] = As[k][ty * 4 + i];
+        wv[i] = Ws[k][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], wv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    long long row = r0 + ty * 4 + i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int cc = c0 + tx * 4 + j;
+      if (cc >= b) continue;
+      T v = acc[i][j];
+      if (Cin) v = fma(beta, Cin[row * ldc + cc], v);
+      out[row * ldo + cc] = v;
+    }
+  }
+}
+
+// R = LX - X diag(theta) over columns [0, K); per-CTA FP64 column sums of R^2, reduced in
+// fixed CTA order by the last CTA (ticket counter).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_residual(long long n, int K, const T* __restrict__ X, const T* __restrict__ LX,
+               long long ld, const double* __restrict__ theta, T* __restrict__ R,
+               long long rows_per_cta, double* part, int* ticket, double* rho2) {
+  extern __shared__ double sred[];  // [rp][K]
+  __shared__ int last;
+  const int kc = K < 256 ? K : 256;
+  const int rp = 256 / kc;                 // rows in parallel
+  const int col0 = threadIdx.x % kc;
+  const int rl = threadIdx.x / kc;
+  long long r0 = blockIdx.x * rows_per_cta, r1 = r0 + rows_per_cta;
+  if (r1 > n) r1 = n;
+  for (int cb = 0; cb < K; cb += kc) {
+    int j = cb + col0;
+    double s = 0.0;
+    if (rl < rp && j < K) {
+      T th = (T)theta[j];
+      for (long long r = r0 + rl; r < r1; r += rp) {
+        T v = LX[r * ld + j] - X[r * ld + j] * th;
+        R[r * ld + j] = v;
+        s += (double)v * (double)v;
+      }
+    }
+    if (rl < rp) sred[rl * kc + col0] = s;
+    __syncthreads();
+    if (threadIdx.x < kc && cb + threadIdx.x < K) {
+      double t = 0.0;
+      for (int q = 0; q < rp; ++q) t += sred[q * kc + threadIdx.x];
+      part[(long long)blockIdx.x * K + cb + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    double t = 0.0;
+    for (unsigned c = 0; c < gridDim.x; ++c) t += __ldcg(part + (long long)c * K + j);
+    rho2[j] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0;
+}
+
+template <typename T>
+__global__ void k_gather_cols(long long n, const T* __restrict__ src, long long lds,
+                              T* __restrict__ dst, long long ldd, const int* __restrict__ cols,
+                              int kc) {
+  long long tot = n * kc;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx / kc;
+    int j = (int)(idx % kc);
+    dst[r * ldd + j] = src[r * lds + cols[j]];
+  }
+}
+
+// Warp per row: E_i = X_i / ||X_i||_2 (FP64 norm); rows with norm < 1e-30 become zero.
+template <typename T>
+__global__ void k_rownorm(long long n, int K, const T* __restrict__ X, long long ldx,
+                          float* __restrict__ E, long long lde) {
+  int lane = threadIdx.x & 31;
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = w; r < n; r += nw) {
+    double s = 0.0;
+    for (int j = lane; j < K; j += 32) {
+      double v = (double)X[r * ldx + j];
+      s += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    double nr = sqrt(s);
+    double inv = nr >= 1e-30 ? 1.0 / nr : 0.0;
+    for (int j = lane; j < K; j += 32) E[r * lde + j] = (float)((double)X[r * ldx + j] * inv);
+  }
+}
+
+template <typename T>
+__global__ void k_cast(int rows, int cols, const double* __restrict__ src, int lds,
+                       T* __restrict__ dst, int ldd, double scale) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols;
+       idx += gridDim.x * blockDim.x) {
+    int i = idx / cols, j = idx % cols;
+    dst[(long long)i * ldd + j] = (T)(scale * src[(long long)i * lds + j]);
+  }
+}
+
+__device__ inline unsigned long long d_sm64(unsigned long long key, unsigned long long i) {
+  unsigned long long z = key + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_gauss(long long count, int K, unsigned long long key, T* X, long long ldx) {
+  const double two_pi = 6.283185307179586;
+  long long npair = (count + 1) / 2;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npair;
+       p += (long long)gridDim.x * blockDim.x) {
+    double u1 = (double)(d_sm64(key, 2 * p) >> 11) * (1.0 / 9007199254740992.0);
+    double u2 = (double)(d_sm64(key, 2 * p + 1) >> 11) * (1.0 / 9007199254740992.0);
+    double r = sqrt(-2.0 * log1p(-u1));
+    double sn, cs;
+    sincos(two_pi * u2, &sn, &cs);
+    long long e0 = 2 * p, e1 = 2 * p + 1;
+    X[(e0 / K) * ldx + e0 % K] = (T)(float)(r * cs);
+    if (e1 < count) X[(e1 / K) * ldx + e1 % K] = (T)(float)(r * sn);
+  }
+}
+
+inline unsigned cap_grid(long long g, long long cap) {
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W, int ldw,
+                      int b, T* out, long long ldo, const T* Cin, long long ldc, T beta) {
+  int a = A.cols();
+  if (n == 0 || b == 0) return cudaSuccess;
+  dim3 grid((unsigned)((n + TR - 1) / TR), (unsigned)((b + TC - 1) / TC));
+  ProfScope ps(st, "tall_gemm");
+  k_tall_gemm<T><<<grid, 256, 0, st>>>(n, A, a, W, ldw, b, out, ldo, Cin, ldc, beta);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t residual(cudaStream_t st, Alloc& al, long long n, int K, const T* X, const T* LX,
+                     long long ld, const double* theta, T* R, double* rho2) {
+  long long nct = cap_grid((n + 63) / 64, 152 * 4);
+  long long rpc = (n + nct - 1) / nct;
+  if (rpc < 1) rpc = 1;
+  nct = (n + rpc - 1) / rpc;
+  if (nct < 1) nct = 1;
+  double* part = al.get<double>((size_t)nct * K);
+  int* ticket = al.get<int>(1);
+  if (!part || !ticket) {
+    al.put(part);
+    al.put(ticket);
+    return cudaErrorMemoryAllocation;
+  }
+  cudaMemsetAsync(ticket, 0, sizeof(int), st);
+  int kc = K < 256 ? K : 256;
+  int rp = 256 / kc;
+  size_t sm = sizeof(double) * (size_t)rp * kc;
+  ProfScope ps(st, "residual");
+  k_residual<T><<<(unsigned)nct, 256, sm, st>>>(n, K, X, LX, ld, theta, R, rpc, part, ticket,
+                                                 rho2);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  al.put(part);
+  al.put(ticket);
+  return e;
+}
+
+template <typename T>
+cudaError_t gather_cols(cudaStream_t st, long long n, const T* src, long long lds, T* dst,
+                        long long ldd, const int* cols, int kc) {
+  long long tot = n * kc;
+  if (tot == 0) return cudaSuccess;
+  k_gather_cols<T><<<cap_grid((tot + 255) / 256, 152 * 16), 256, 0, st>>>(n, src, lds, dst, ldd,
+                                                                          cols, kc);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t rownorm(cudaStream_t st, long long n, int K, const T* X, long long ldx, float* E,
+                    long long lde) {
+  if (n == 0) return cudaSuccess;
+  k_rownorm<T><<<cap_grid((n * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(n, K, X, ldx, E, lde);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gauss_block(cudaStream_t st, long long n, int K, unsigned long long key, T* X,
+                        long long ldx) {
+  long long count = n * K;
+  if (count == 0) return cudaSuccess;
+  ProfScope ps(st, "gauss");
+  k_gauss<T><<<cap_grid((count / 2 + 255) / 256, 152 * 8), 256, 0, st>>>(count, K, key, X, ldx);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cast_mat(cudaStream_t st, int rows, int cols, const double* src, int lds, T* dst,
+                     int ldd, double scale) {
+  if (rows * cols == 0) return cudaSuccess;
+  k_cast<T><<<cap_grid((rows * cols + 255) / 256, 152), 256, 0, st>>>(rows, cols, src, lds, dst,
+                                                                     ldd, scale);
+  note_launch();
+  return cudaGetLastError();
+}
+
+#define SC_INST(T)                                                                          \
+  template cudaError_t gauss_block<T>(cudaStream_t, long long, int, unsigned long long, T*,  \
+                                      long long);                                            \
+  template cudaError_t cast_mat<T>(cudaStream_t, int, int, const double*, int, T*, int,      \
+                                   double);                                                  \
+  template cudaError_t tall_gemm<T>(cudaStream_t, long long, const Cat3<T>&, const T*, int,  \
+                                    int, T*, long long, const T*, long long, T);             \
+  template cudaError_t residual<T>(cudaStream_t, Alloc&, long long, int, const T*, const T*, \
+                                   long long, const double*, T*, double*);                   \
+  template cudaError_t gather_cols<T>(cudaStream_t, long long, const T*, long long, T*,      \
+                                      long long, const int*, int);                           \
+  template cudaError_t rownorm<T>(cudaStream_t, long long, int, const T*, long long, float*, \
+                                  long long);
+SC_INST(float)
+SC_INST(double)
+#undef SC_INST
+
+}  // namespace sc

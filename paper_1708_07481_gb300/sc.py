@@ -1,0 +1,310 @@
+"""ctypes binding of libsc_gb300.so (include/sc.h), one Python function per C entry point.
+
+Argument marshalling only: arrays are checked for dtype/contiguity and passed as pointers;
+every step of the computation runs in the library's CUDA kernels.  Device arrays may be
+passed as torch CUDA tensors (``on_device`` is inferred).  Loading fails loudly when the
+library has not been built (run ``python -m paper_1708_07481_gb300.build``); there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsc_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sc.h")
+
+SC_OK, SC_EINVAL, SC_ENOMEM, SC_EBREAKDOWN, SC_ENOTCONV, SC_ETIMEOUT, SC_ECUDA, SC_EAGAIN = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+SC_PREC_MIXED, SC_PREC_FP32, SC_PREC_FP64 = 0, 1, 2
+SC_SYM_LOGICAL, SC_SYM_ALGEBRAIC = 0, 1
+SC_MAX_K = 512
+_NAMES = {0: "SC_OK", -1: "SC_EINVAL", -2: "SC_ENOMEM", -3: "SC_EBREAKDOWN", -4: "SC_ENOTCONV",
+          -5: "SC_ETIMEOUT", -6: "SC_ECUDA", -7: "SC_EAGAIN"}
+
+
+class ScError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class LobpcgOpts(C.Structure):
+    _fields_ = [("iters", C.c_int), ("tol_abs", C.c_double), ("tol_lock", C.c_double),
+                ("prec", C.c_int), ("seed", C.c_uint64), ("cold", C.c_int)]
+
+
+class EigInfo(C.Structure):
+    _fields_ = [("K", C.c_int), ("iters_done", C.c_int), ("fallbacks", C.c_int),
+                ("converged", C.c_int), ("lambda_", C.c_double * SC_MAX_K),
+                ("resid", C.c_double * SC_MAX_K), ("ms", C.c_float), ("kernels", C.c_uint64)]
+
+    def as_dict(self):
+        K = self.K
+        return dict(K=K, iters_done=self.iters_done, fallbacks=self.fallbacks,
+                    converged=self.converged, lam=np.array(self.lambda_[:K]),
+                    resid=np.array(self.resid[:K]), ms=float(self.ms), kernels=int(self.kernels))
+
+
+_lib = None
+
+
+def lib():
+    """Load the library once; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_1708_07481_gb300.build")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    sig = {
+        "sc_ctx_create": ([C.POINTER(vp), C.c_int, vp, C.c_size_t], C.c_int),
+        "sc_ctx_destroy": ([vp], None),
+        "sc_last_error": ([vp], C.c_char_p),
+        "sc_ctx_bytes_in_use": ([vp], C.c_size_t),
+        "sc_ctx_kernel_launches": ([vp], u64),
+        "sc_profile_begin": ([vp, C.c_char_p], C.c_int),
+        "sc_profile_end": ([vp, C.c_char_p, C.c_size_t], C.c_int),
+        "sc_build_laplacian": ([vp, i32, i64, vp, vp, vp, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
+        "sc_graph_info": ([vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(dbl)], C.c_int),
+        "sc_graph_copy_csr": ([vp, vp, vp, vp, vp], C.c_int),
+        "sc_graph_destroy": ([vp], None),
+        "sc_lap_apply": ([vp, vp, C.c_int, C.c_int, vp, vp, C.c_int], C.c_int),
+        "sc_lobpcg": ([vp, vp, C.c_int, C.POINTER(LobpcgOpts), vp, i32, vp, C.POINTER(EigInfo)], C.c_int),
+        "sc_embed_rows": ([vp, vp, i32, C.c_int, vp, C.c_int], C.c_int),
+        "sc_kmeans": ([vp, vp, i32, C.c_int, C.c_int, C.c_int, u64, vp, C.c_int, vp, vp, vp,
+                       C.POINTER(dbl), C.POINTER(C.c_int)], C.c_int),
+        "sc_partition": ([vp, vp, C.c_int, C.c_int, C.POINTER(LobpcgOpts), C.c_int, vp,
+                          C.POINTER(EigInfo)], C.c_int),
+        "sc_stream_update": ([vp, vp, i32, i64, vp, vp, vp, C.c_int], C.c_int),
+        "sc_gram": ([vp, C.c_int, i64, C.c_int, C.c_int, vp, i64, vp, i64, vp, C.c_int], C.c_int),
+        "sc_rr_solve": ([vp, C.c_int, C.c_int, C.c_int, vp, vp, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def declared_symbols(header: str = HEADER) -> list[str]:
+    """Entry points declared in include/sc.h."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sc_[a-z0-9_]+)\s*\(", txt)))
+
+
+# ---------------------------------------------------------------------------------------
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr()), int(bool(a.is_cuda))
+    return a.ctypes.data_as(C.c_void_p), 0
+
+
+def _np(a, dtype):
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Ctx:
+    def __init__(self, device=0, stream=None, budget=0):
+        self.h = C.c_void_p()
+        s = C.c_void_p(stream) if stream else None
+        rc = lib().sc_ctx_create(C.byref(self.h), device, s, budget)
+        if rc != SC_OK:
+            raise ScError(rc, "sc_ctx_create failed")
+
+    def check(self, rc):
+        if rc != SC_OK:
+            raise ScError(rc, lib().sc_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if self.h:
+            lib().sc_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def bytes_in_use(self):
+        return lib().sc_ctx_bytes_in_use(self.h)
+
+    @property
+    def launches(self):
+        return lib().sc_ctx_kernel_launches(self.h)
+
+
+class Graph:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def close(self):
+        if self.h:
+            lib().sc_graph_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sc_ctx_create(device=0, stream=None, budget=0) -> Ctx:
+    return Ctx(device, stream, budget)
+
+
+def sc_profile_begin(ctx: Ctx, kernels: str = "*"):
+    ctx.check(lib().sc_profile_begin(ctx.h, kernels.encode()))
+
+
+def sc_profile_end(ctx: Ctx) -> dict:
+    """-> {kernel: (launches, total device ms)} since sc_profile_begin."""
+    buf = C.create_string_buffer(1 << 16)
+    ctx.check(lib().sc_profile_end(ctx.h, buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def sc_build_laplacian(ctx: Ctx, n, src, dst, w=None, sym=SC_SYM_LOGICAL) -> Graph:
+    src, dst = _np(src, np.int32), _np(dst, np.int32)
+    w = None if w is None else _np(w, np.float32)
+    ps, dev = _ptr(src)
+    pd, _ = _ptr(dst)
+    pw, _ = _ptr(w)
+    m = int(src.shape[0])
+    h = C.c_void_p()
+    ctx.check(lib().sc_build_laplacian(ctx.h, n, m, ps, pd, pw, sym, dev, C.byref(h)))
+    return Graph(ctx, h)
+
+
+def sc_graph_info(g: Graph):
+    n, nnz, dm = C.c_int32(), C.c_int64(), C.c_double()
+    g.ctx.check(lib().sc_graph_info(g.h, C.byref(n), C.byref(nnz), C.byref(dm)))
+    return n.value, nnz.value, dm.value
+
+
+def sc_graph_copy_csr(g: Graph):
+    n, nnz, _ = sc_graph_info(g)
+    rp = np.empty(n + 1, np.int32)
+    ci = np.empty(max(nnz, 1), np.int32)
+    val = np.empty(max(nnz, 1), np.float32)
+    deg = np.empty(n, np.float64)
+    g.ctx.check(lib().sc_graph_copy_csr(g.h, _ptr(rp)[0], _ptr(ci)[0], _ptr(val)[0], _ptr(deg)[0]))
+    return rp, ci[:nnz], val[:nnz], deg
+
+
+def sc_lap_apply(ctx: Ctx, g: Graph, V, prec=SC_PREC_FP32):
+    dt = np.float64 if prec == SC_PREC_FP64 else np.float32
+    V = _np(V, dt)
+    if hasattr(V, "data_ptr"):
+        import torch
+        Y = torch.empty_like(V)
+    else:
+        Y = np.empty_like(V)
+    pv, dev = _ptr(V)
+    ctx.check(lib().sc_lap_apply(ctx.h, g.h, int(V.shape[1]), prec, pv, _ptr(Y)[0], dev))
+    return Y
+
+
+def sc_lobpcg(ctx: Ctx, g: Graph, K, iters=20, tol_abs=0.0, tol_lock=0.0, prec=SC_PREC_MIXED,
+              seed=0, cold=0, X0=None, x0_rows=0, want_X=True):
+    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold)
+    info = EigInfo()
+    n = sc_graph_info(g)[0]
+    X = np.empty((n, K), np.float32) if want_X else None
+    x0 = None if X0 is None else np.ascontiguousarray(X0, dtype=np.float32)
+    rc = lib().sc_lobpcg(ctx.h, g.h, K, C.byref(o), _ptr(x0)[0], int(x0_rows), _ptr(X)[0],
+                         C.byref(info))
+    d = info.as_dict()
+    if rc != SC_OK:
+        err = ScError(rc, lib().sc_last_error(ctx.h).decode())
+        err.info = d
+        raise err
+    return d["lam"], d["resid"], X, d
+
+
+def sc_embed_rows(ctx: Ctx, X):
+    X = _np(X, np.float32)
+    if hasattr(X, "data_ptr"):
+        import torch
+        E = torch.empty_like(X)
+    else:
+        E = np.empty_like(X)
+    px, dev = _ptr(X)
+    ctx.check(lib().sc_embed_rows(ctx.h, px, int(X.shape[0]), int(X.shape[1]), _ptr(E)[0], dev))
+    return E
+
+
+def sc_kmeans(ctx: Ctx, E, k, iters=50, seed=0, init_idx=None):
+    E = _np(E, np.float32)
+    n, d = int(E.shape[0]), int(E.shape[1])
+    labels = np.empty(n, np.int32)
+    cent = np.empty((k, d), np.float32)
+    seeds = np.empty(k, np.int32)
+    inertia = C.c_double()
+    ran = C.c_int()
+    init = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int32)
+    pe, dev = _ptr(E)
+    ctx.check(lib().sc_kmeans(ctx.h, pe, n, d, k, iters, seed, _ptr(init)[0], dev, _ptr(labels)[0],
+                              _ptr(cent)[0], _ptr(seeds)[0], C.byref(inertia), C.byref(ran)))
+    return labels, cent, seeds, inertia.value, ran.value
+
+
+def sc_partition(ctx: Ctx, g: Graph, K, k, iters=20, kmeans_iters=50, prec=SC_PREC_MIXED,
+                 seed=0, tol_abs=0.0, tol_lock=0.0, cold=1):
+    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold)
+    info = EigInfo()
+    n = sc_graph_info(g)[0]
+    labels = np.empty(n, np.int32)
+    ctx.check(lib().sc_partition(ctx.h, g.h, K, k, C.byref(o), kmeans_iters, _ptr(labels)[0],
+                                 C.byref(info)))
+    return labels, info.as_dict()
+
+
+def sc_stream_update(ctx: Ctx, g: Graph, n_new, src, dst, w=None):
+    src, dst = _np(src, np.int32), _np(dst, np.int32)
+    w = None if w is None else _np(w, np.float32)
+    ps, dev = _ptr(src)
+    ctx.check(lib().sc_stream_update(ctx.h, g.h, n_new, int(src.shape[0]), ps, _ptr(dst)[0],
+                                     _ptr(w)[0], dev))
+
+
+def sc_gram(ctx: Ctx, A, B, prec=SC_PREC_FP32):
+    dt = np.float64 if prec == SC_PREC_FP64 else np.float32
+    A, B = _np(A, dt), _np(B, dt)
+    n, a = int(A.shape[0]), int(A.shape[1])
+    b = int(B.shape[1])
+    Cm = np.empty((a, b), np.float64)
+    pa, dev = _ptr(A)
+    ctx.check(lib().sc_gram(ctx.h, prec, n, a, b, pa, a, _ptr(B)[0], b, _ptr(Cm)[0], dev))
+    return Cm
+
+
+def sc_rr_solve(ctx: Ctx, G, K, prec=SC_PREC_FP32):
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    m = G.shape[0]
+    th = np.empty(K, np.float64)
+    Y = np.empty((m, K), np.float64)
+    ctx.check(lib().sc_rr_solve(ctx.h, prec, m, K, _ptr(G)[0], _ptr(th)[0], _ptr(Y)[0]))
+    return th, Y

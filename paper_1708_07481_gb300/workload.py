@@ -205,11 +205,11 @@ def dcsbm(
     def u_at(slot: int, rnd: int, idx: np.ndarray) -> np.ndarray:
         return uniforms(ke, np.uint64(rnd * 4 + slot) * MSTR + idx)
 
-    within = u_at(0, 0, eidx) < ratio / (ratio + 1.0)
+    within = (u_at(0, 0, eidx) < ratio / (ratio + 1.0)) | (K == 1)
     # between: block != b(src) chosen proportional to size
-    t = np.floor(u_at(1, 0, eidx) * (n - sizes[bsrc])).astype(np.int64)
+    t = np.floor(u_at(1, 0, eidx) * np.maximum(n - sizes[bsrc], 1)).astype(np.int64)
     t = np.where(t >= starts[bsrc], t + sizes[bsrc], t)
-    bb = np.searchsorted(starts[1:], t, side="right")
+    bb = np.minimum(np.searchsorted(starts[1:], t, side="right"), K - 1)
     tblock = np.where(within, bsrc, bb)
 
     def draw_target(blk: np.ndarray, uu: np.ndarray) -> np.ndarray:

@@ -1,0 +1,342 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle on the same seeded inputs.
+
+All calls go through the C ABI (ctypes binding).  Tolerances:
+  integer / index work (CSR, labels, seeds): bit-exact;
+  FP64 form: 1e-10 relative to lambda_max (the check mode);
+  FP32 form: |d lambda| / lambda_max <= 1e-5, block sin-theta <= 1e-3 (20 passes), per-element
+  SpMM / Gram errors bounded by a few FP32 ulps of the products' magnitudes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1708_07481_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc():
+    from paper_1708_07481_gb300 import build, sc as S
+
+    build.build()
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(sc):
+    c = sc.sc_ctx_create(0)
+    yield c
+    c.close()
+
+
+def _csr_equal(sc, G, L, algebraic=False):
+    rp, ci, val, deg = sc.sc_graph_copy_csr(G)
+    assert np.array_equal(rp, L.row_ptr)
+    assert np.array_equal(ci, L.col_idx)
+    if algebraic:
+        np.testing.assert_allclose(val, L.val, rtol=1e-6)
+        np.testing.assert_allclose(deg, L.deg, rtol=1e-6)
+    else:
+        assert np.all(val == 1.0)
+        assert np.array_equal(deg, L.deg)
+
+
+# ------------------------------------------------------------------ a1: Laplacian build
+
+
+@pytest.mark.parametrize("n,K,seed", [(1000, 11, 0), (5003, 19, 1), (50000, 44, 0)])
+def test_laplacian_dcsbm(sc, ctx, n, K, seed):
+    g = W.dcsbm(n, K, seed=seed)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    _csr_equal(sc, G, O.laplacian_csr(g.n, g.src, g.dst))
+
+
+def test_laplacian_multigraph_loops_and_algebraic(sc, ctx):
+    rng = np.random.default_rng(3)
+    n, m = 257, 5000
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    w = rng.uniform(0.25, 2.0, m).astype(np.float32)
+    G = sc.sc_build_laplacian(ctx, n, src, dst)
+    _csr_equal(sc, G, O.laplacian_csr(n, src, dst))
+    Ga = sc.sc_build_laplacian(ctx, n, src, dst, w, sym=sc.SC_SYM_ALGEBRAIC)
+    _csr_equal(sc, Ga, O.laplacian_csr(n, src, dst, w.astype(np.float64), sym="algebraic"), True)
+
+
+def test_laplacian_long_rows_and_edge_cases(sc, ctx):
+    # a star: the hub row (9999 entries) exceeds one CTA's shared-memory sort
+    n = 10000
+    src = np.zeros(n - 1, np.int32)
+    dst = np.arange(1, n, dtype=np.int32)
+    extra = np.random.default_rng(4).integers(1, n, 3000).astype(np.int32)
+    src = np.concatenate([src, extra])
+    dst = np.concatenate([dst, np.zeros_like(extra)])  # duplicates of hub edges, reversed
+    G = sc.sc_build_laplacian(ctx, n, src, dst)
+    _csr_equal(sc, G, O.laplacian_csr(n, src, dst))
+    # no edges at all, and only self-loops
+    G0 = sc.sc_build_laplacian(ctx, 5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    rp, ci, _, deg = sc.sc_graph_copy_csr(G0)
+    assert np.all(rp == 0) and ci.size == 0 and np.all(deg == 0)
+    G1 = sc.sc_build_laplacian(ctx, 3, np.array([0, 1, 2], np.int32), np.array([0, 1, 2], np.int32))
+    assert sc.sc_graph_info(G1)[1] == 0
+    with pytest.raises(sc.ScError) as e:
+        sc.sc_build_laplacian(ctx, 4, np.array([0, 4], np.int32), np.array([1, 2], np.int32))
+    assert e.value.code == sc.SC_EINVAL
+
+
+# ------------------------------------------------------------------ a4: SpMM
+
+
+@pytest.mark.parametrize("k", [1, 3, 11, 44, 160])
+def test_spmm_fp32_and_fp64(sc, ctx, k):
+    g = W.dcsbm(3001, 7, seed=5)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    V = np.random.default_rng(k).standard_normal((g.n, k))
+    ref = O.lap_apply(L, V.astype(np.float32).astype(np.float64))
+    Y32 = sc.sc_lap_apply(ctx, G, V.astype(np.float32), sc.SC_PREC_FP32)
+    scale = (L.deg[:, None] + 1) * np.abs(V).max()
+    assert np.all(np.abs(Y32 - ref) <= 4e-7 * scale * np.sqrt(L.deg.max() + 1))
+    Y64 = sc.sc_lap_apply(ctx, G, V, sc.SC_PREC_FP64)
+    np.testing.assert_allclose(Y64, O.lap_apply(L, V), rtol=0, atol=1e-12 * scale.max())
+
+
+def test_spmm_weighted(sc, ctx):
+    rng = np.random.default_rng(6)
+    n, m = 800, 9000
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    w = rng.uniform(0.1, 3.0, m).astype(np.float32)
+    G = sc.sc_build_laplacian(ctx, n, src, dst, w, sym=sc.SC_SYM_ALGEBRAIC)
+    L = O.laplacian_csr(n, src, dst, w.astype(np.float64), sym="algebraic")
+    V = rng.standard_normal((n, 12))
+    Y = sc.sc_lap_apply(ctx, G, V, sc.SC_PREC_FP64)
+    # W is stored in FP32 on the device: compare with the oracle on the same rounded weights
+    Lr = O.laplacian_csr(n, src, dst, w.astype(np.float64), sym="algebraic")
+    Lr.val = Lr.val.astype(np.float32).astype(np.float64)
+    Lr.deg = np.asarray(Lr.W().sum(axis=1)).ravel()
+    np.testing.assert_allclose(Y, O.lap_apply(Lr, V), rtol=0, atol=1e-5 * np.abs(V).max() * L.deg.max())
+
+
+# ------------------------------------------------------------------ a5: Gram
+
+
+@pytest.mark.parametrize("n,a,b", [(1, 3, 5), (37, 11, 11), (1000, 44, 132), (50001, 132, 132), (20000, 160, 480)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_gram(sc, ctx, n, a, b, prec):
+    rng = np.random.default_rng(n + a)
+    A = rng.standard_normal((n, a))
+    B = rng.standard_normal((n, b))
+    if prec == "fp32":
+        A32, B32 = A.astype(np.float32), B.astype(np.float32)
+        Cm = sc.sc_gram(ctx, A32, B32, sc.SC_PREC_FP32)
+        ref = A32.astype(np.float64).T @ B32.astype(np.float64)
+        bound = 1e-6 * np.sqrt(n) * np.outer(np.linalg.norm(A32, axis=0), np.linalg.norm(B32, axis=0)) + 1e-30
+        assert np.all(np.abs(Cm - ref) <= bound)
+    else:
+        Cm = sc.sc_gram(ctx, A, B, sc.SC_PREC_FP64)
+        np.testing.assert_allclose(Cm, A.T @ B, rtol=0, atol=1e-13 * n * 10)
+
+
+def test_gram_empty_rows(sc, ctx):
+    Cm = sc.sc_gram(ctx, np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), sc.SC_PREC_FP32)
+    assert Cm.shape == (4, 6) and np.all(Cm == 0)
+
+
+# ------------------------------------------------------------------ a6: Rayleigh-Ritz solve
+
+
+def _sym_with_spectrum(m, ev, seed):
+    Q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((m, m)))
+    return (Q * ev) @ Q.T
+
+
+@pytest.mark.parametrize("m,K", [(1, 1), (2, 1), (33, 11), (132, 44), (480, 160)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_rr_solve(sc, ctx, m, K, prec):
+    rng = np.random.default_rng(m)
+    ev = np.sort(rng.uniform(0, 100, m))
+    if m > 4:
+        ev[1:4] = ev[1]  # a triple eigenvalue inside the wanted block
+        ev = np.sort(ev)
+    G = _sym_with_spectrum(m, ev, m + 1)
+    p = sc.SC_PREC_FP64 if prec == "fp64" else sc.SC_PREC_FP32
+    th, Y = sc.sc_rr_solve(ctx, G, K, p)
+    w, V = np.linalg.eigh(G)
+    tol = (1e-12 if prec == "fp64" else 2e-5) * max(1.0, np.abs(ev).max())
+    assert np.max(np.abs(th - w[:K])) <= tol
+    np.testing.assert_allclose(Y.T @ Y, np.eye(K), atol=1e-10 if prec == "fp64" else 1e-4)
+    res = np.linalg.norm(G @ Y - Y * th, axis=0)
+    assert res.max() <= (1e-9 if prec == "fp64" else 1e-3) * np.abs(ev).max()
+    if K < m and w[K] - w[K - 1] > 1e-3:
+        assert O.sin_theta(V[:, :K], Y) <= (1e-9 if prec == "fp64" else 1e-3)
+
+
+# ------------------------------------------------------------------ a2, a3, a7: LOBPCG
+
+
+def _lobpcg_pair(sc, ctx, n, K, iters, seed=0, prec=None, **kw):
+    g = W.dcsbm(n, K, seed=seed)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    X0 = W.start_block(seed, g.n, K)
+    p = sc.SC_PREC_MIXED if prec is None else prec
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=iters, prec=p, X0=X0, **kw)
+    x0 = X0.astype(np.float32).astype(np.float64)  # the library takes a float start block
+    ref = O.lobpcg(L, x0, iters, **kw)
+    return g, L, lam, resid, X, info, ref
+
+
+def test_lobpcg_fp64_check_mode_small(sc, ctx):
+    g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 1000, 11, 20, prec=2)
+    lmax = 2 * L.deg.max()
+    assert info["iters_done"] == ref.iters == 20
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-10
+    assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-6  # X returned as float32
+    np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lobpcg_fp32_small(sc, ctx, prec):
+    g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 1000, 11, 20, prec=prec)
+    lmax = 2 * L.deg.max()
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
+    assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-3
+    assert info["fallbacks"] == ref.fallbacks == 0
+
+
+def test_lobpcg_fp32_bench_size(sc, ctx):
+    g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 50000, 44, 20)
+    lmax = 2 * L.deg.max()
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
+    assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-3
+
+
+def test_lobpcg_ragged_sizes(sc, ctx):
+    # K = 1, K not a multiple of 4, n = 3K exactly
+    for n, K in [(300, 1), (61, 7), (36, 12)]:
+        g = W.dcsbm(n, min(K, 4), seed=7, dmin=3, dmax=12)
+        L = O.laplacian_csr(g.n, g.src, g.dst)
+        G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+        X0 = W.start_block(2, n, K)
+        lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=5, prec=2, X0=X0)
+        ref = O.lobpcg(L, X0.astype(np.float32).astype(np.float64), 5)
+        lmax = 2 * L.deg.max()
+        assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-9, (n, K)
+
+
+def test_lobpcg_soft_locking_converges(sc, ctx):
+    g = W.dcsbm(2000, 6, seed=8)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    tol = 1e-3 * ev[-1]
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 6, iters=300, tol_abs=tol, tol_lock=tol,
+                                       prec=sc.SC_PREC_FP32, seed=3)
+    assert info["converged"] == 1
+    assert np.max(np.abs(lam - ev[:6])) <= 1e-4 * ev[-1]
+    assert resid.max() <= tol
+
+
+def test_lobpcg_rejects_bad_sizes(sc, ctx):
+    G = sc.sc_build_laplacian(ctx, 10, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    with pytest.raises(sc.ScError) as e:
+        sc.sc_lobpcg(ctx, G, 4, iters=1)
+    assert e.value.code == sc.SC_EINVAL
+
+
+# ------------------------------------------------------------------ a8: embedding
+
+
+def test_embed_rows(sc, ctx):
+    X = np.random.default_rng(9).standard_normal((5000, 44)).astype(np.float32)
+    X[7] = 0
+    E = sc.sc_embed_rows(ctx, X)
+    np.testing.assert_allclose(E, O.embed_rows(X.astype(np.float64)), rtol=0, atol=2e-7)
+    assert np.all(E[7] == 0)
+
+
+# ------------------------------------------------------------------ a9, a10: k-means
+
+
+def _clustered(n, d, k, seed, spread=0.05):
+    rng = np.random.default_rng(seed)
+    C = rng.standard_normal((k, d))
+    lab = rng.integers(0, k, n)
+    E = C[lab] + spread * rng.standard_normal((n, d))
+    return O.embed_rows(E).astype(np.float32), lab
+
+
+@pytest.mark.parametrize("n,d,k", [(1000, 11, 11), (50000, 44, 44), (3001, 5, 1)])
+def test_kmeans_seeds_and_labels_bit_exact(sc, ctx, n, d, k):
+    E, _ = _clustered(n, d, max(k, 2), n)
+    u = W.kmeans_uniforms(5, k)
+    labels, cent, seeds, inertia, ran = sc.sc_kmeans(ctx, E, k, iters=50, seed=5)
+    Ed = E.astype(np.float64)
+    rl, rC, ridx, rin = O.kmeans(Ed, k, u, 50)
+    assert np.array_equal(seeds, ridx)
+    assert np.array_equal(labels, rl)
+    np.testing.assert_allclose(cent, rC, rtol=0, atol=1e-6)
+    assert abs(inertia - rin) <= 1e-9 * max(rin, 1.0)
+
+
+def test_kmeans_given_seeds_and_duplicates(sc, ctx):
+    E = np.repeat(np.eye(4, dtype=np.float32), 5, axis=0)  # only 4 distinct rows
+    labels, cent, seeds, inertia, ran = sc.sc_kmeans(ctx, E, 6, iters=10, seed=1)
+    rl, rC, ridx, rin = O.kmeans(E.astype(np.float64), 6, W.kmeans_uniforms(1, 6), 10)
+    assert np.array_equal(seeds, ridx) and np.array_equal(labels, rl) and inertia == 0.0
+    init = np.array([0, 5, 10], np.int32)
+    labels, cent, seeds, inertia, ran = sc.sc_kmeans(ctx, E, 3, iters=10, init_idx=init)
+    rl, _, _ = O.lloyd(E.astype(np.float64), E[init].astype(np.float64), 10)
+    assert np.array_equal(labels, rl)
+
+
+# ------------------------------------------------------------------ end to end
+
+
+def test_partition_matches_oracle_labels(sc, ctx):
+    g = W.dcsbm(1000, 11, seed=0)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    labels, info = sc.sc_partition(ctx, G, 11, 11, iters=20, seed=0)
+    X0 = W.start_block(0, g.n, 11).astype(np.float32).astype(np.float64)
+    rl, res, E, idx = O.partition(L, X0, 11, W.kmeans_uniforms(0, 11), 20, 50)
+    assert O.partition_metrics(rl, labels)[0] == 1.0  # identical up to a permutation
+    assert O.partition_metrics(g.truth, labels)[0] == 1.0
+
+
+# ------------------------------------------------------------------ a12: streaming
+
+
+def test_stream_emerging_matches_rebuild(sc, ctx):
+    g = W.dcsbm(5000, 9, seed=10)
+    deltas = W.emerging_deltas(g)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src[deltas[0]], g.dst[deltas[0]])
+    for s in range(1, 10):
+        sc.sc_stream_update(ctx, G, g.n, g.src[deltas[s]], g.dst[deltas[s]])
+        upto = np.concatenate(deltas[: s + 1])
+        _csr_equal(sc, G, O.laplacian_csr(g.n, g.src[upto], g.dst[upto]))
+
+
+def test_stream_snowball_grows_and_warm_starts(sc, ctx):
+    g = W.dcsbm(6000, 8, seed=11)
+    st = W.snowball_stages(g)
+    G = sc.sc_build_laplacian(ctx, st[0].n, st[0].src, st[0].dst)
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 8, iters=20, prec=2, seed=1)
+    for s in range(1, 4):
+        prev = st[s - 1]
+        cur = st[s]
+        # delta = edges of stage s not in stage s-1 (old vertices keep their ids)
+        old = set(zip(prev.src.tolist(), prev.dst.tolist()))
+        pairs = [(a, b) for a, b in zip(cur.src.tolist(), cur.dst.tolist())]
+        new = np.array([p for p in pairs if p not in old] or [(0, 0)], np.int32)
+        sc.sc_stream_update(ctx, G, cur.n, new[:, 0], new[:, 1])
+        _csr_equal(sc, G, O.laplacian_csr(cur.n, cur.src, cur.dst))
+        # warm start = previous block with zero rows for the new vertices
+        Xw = np.zeros((cur.n, 8))
+        Xw[: prev.n] = X
+        lam, resid, X, info = sc.sc_lobpcg(ctx, G, 8, iters=10, prec=2)
+        ref = O.lobpcg(O.laplacian_csr(cur.n, cur.src, cur.dst), Xw, 10)
+        lmax = 2 * ref.lam.max() + 1
+        assert np.max(np.abs(lam - ref.lam)) <= 1e-8 * max(lmax, 1)
