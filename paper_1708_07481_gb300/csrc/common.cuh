@@ -114,6 +114,13 @@ template <typename T>
 cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, const Cat3<T>& B,
                  double* C, int ldc, bool sym, int use_tc);
 
+// Tensor-core Gram (3-term split TF32 on tcgen05): C = A' B for FP32 blocks A = columns
+// [0, a) of a row-major block with stride lda (16-byte aligned, lda % 4 == 0), B alike.
+// segA/segB: (start, count) pairs listing the columns that appear in the compact output C.
+cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, long long lda,
+                    int a, const int* segA, int nsegA, const float* B, long long ldb, int b,
+                    const int* segB, int nsegB, double* C, int ldc, bool sym, int* d_status);
+
 // Tall GEMM: out (n x b, ldo) = beta * Cin + A (n x a) W (a x b, row-major ldw, type T).
 template <typename T>
 cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W, int ldw,
@@ -143,7 +150,7 @@ cudaError_t rownorm(cudaStream_t st, long long n, int K, const T* X, long long l
 // Tm is ka x ka upper triangular (row-major, T).  Status bit ST_CHOL_FAIL on breakdown.
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
-                     int* d_status, double pivot_tol);
+                     int* d_status, double pivot_tol, int* fail_col = nullptr);
 
 // Rayleigh-Ritz in an orthonormal basis: K smallest eigenpairs of symmetric m x m G (FP64).
 // theta[K] FP64 (device), Y (m x K, T, row-major).  Arithmetic in T.

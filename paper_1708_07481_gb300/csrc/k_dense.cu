@@ -73,87 +73,130 @@ __device__ T block_max(T v, T* red) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Cholesky-QR transform (FP64).  W is ka x ka FP64 workspace (shared or global).
+// ---- block-wide small dense kernels (all threads of the CTA take part) -------------------
+
+// In-place lower Cholesky of the ka x ka matrix W (stride ldw) in the arithmetic of T.
+// rdiag[k] = 1 / L_kk.  Returns the first column whose pivot is <= tol (or -1).
 template <typename T>
-__global__ void __launch_bounds__(NT)
-    k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm,
-               double* Wg, int in_smem, int* status, double pivot_tol) {
-  extern __shared__ __align__(16) double dsm[];
-  double* s = dsm;                 // ka scale factors
-  double* red = s + ka;            // 34
-  double* W = in_smem ? red + 34 : Wg;
-  __shared__ int fail;
-  if (threadIdx.x == 0) fail = 0;
+__device__ int blk_chol(int ka, T* W, int ldw, T* rdiag, T tol, int* sflag) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  if (tid == 0) *sflag = -1;
   __syncthreads();
-  for (int i = threadIdx.x; i < ka; i += blockDim.x) {
-    double d = G[(long long)i * ldg + i];
-    s[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
-    if (!(d > 0.0)) fail = 1;
+  for (int k = 0; k < ka; ++k) {
+    if (tid == 0) {
+      T piv = W[k * ldw + k];
+      if (!(piv > tol)) {
+        *sflag = k;
+      } else {
+        T r = rsqrt(piv);
+        rdiag[k] = r;
+        W[k * ldw + k] = piv * r;
+      }
+    }
+    __syncthreads();
+    if (*sflag >= 0) return *sflag;
+    const T r = rdiag[k];
+    for (int i = k + 1 + tid; i < ka; i += nt) W[i * ldw + k] *= r;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < ka; i += nw) {
+      const T lik = W[i * ldw + k];
+      T* wi = W + i * ldw;
+#pragma unroll 4
+      for (int j = k + 1 + lane; j <= i; j += 32) wi[j] = fma(-lik, W[j * ldw + k], wi[j]);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < ka * ka; idx += blockDim.x) {
+  return -1;
+}
+
+// Linv = L^-1 (lower, ka x ka, stride ldi) from the factor in W and rdiag, row by row:
+// Linv[i][j] = -rdiag[i] * sum_{q=j}^{i-1} L[i][q] Linv[q][j]; one warp per (i, j), lanes
+// split q.
+template <typename T>
+__device__ void blk_tri_inv(int ka, const T* W, int ldw, const T* rdiag, T* Li, int ldi) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int idx = tid; idx < ka * ka; idx += nt) {
     int i = idx / ka, j = idx % ka;
-    double g = 0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]);
-    W[idx] = g * s[i] * s[j];
+    Li[i * ldi + j] = (i == j) ? rdiag[i] : (T)0;
   }
   __syncthreads();
-  // right-looking Cholesky, lower triangle in place
-  for (int k = 0; k < ka && !fail; ++k) {
-    double piv = W[k * ka + k];
-    if (!(piv > pivot_tol)) {
-      __syncthreads();
-      if (threadIdx.x == 0) fail = 1;
-      __syncthreads();
-      break;
-    }
-    double ck = sqrt(piv);
-    for (int i = k + 1 + threadIdx.x; i < ka; i += blockDim.x) W[i * ka + k] /= ck;
-    __syncthreads();
-    if (threadIdx.x == 0) W[k * ka + k] = ck;
-    int nr = ka - k - 1;
-    for (int idx = threadIdx.x; idx < nr * nr; idx += blockDim.x) {
-      int i = k + 1 + idx / nr, j = k + 1 + idx % nr;
-      if (j <= i) W[i * ka + j] -= W[i * ka + k] * W[j * ka + k];
+  for (int i = 1; i < ka; ++i) {
+    const T* li = W + i * ldw;
+    for (int j = warp; j < i; j += nw) {
+      T a0 = 0, a1 = 0;
+      int q = j + lane;
+      for (; q + 32 < i; q += 64) {
+        a0 = fma(li[q], Li[q * ldi + j], a0);
+        a1 = fma(li[q + 32], Li[(q + 32) * ldi + j], a1);
+      }
+      if (q < i) a0 = fma(li[q], Li[q * ldi + j], a0);
+      T acc = a0 + a1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) Li[i * ldi + j] = -acc * rdiag[i];
     }
     __syncthreads();
   }
-  if (fail) {
-    if (threadIdx.x == 0) atomicOr(status, ST_CHOL_FAIL);
+}
+
+// Cholesky-QR transform in the arithmetic of T: from the FP64 Gram G (accumulated in FP64
+// across CTAs), scale s = diag(G)^-1/2 in FP64, factor s G s = L L' in T, and write
+// Tm = diag(s) L^-T (ka x ka upper triangular) so that V Tm has orthonormal columns.
+// On a pivot <= pivot_tol: ST_CHOL_FAIL in *status and the failing column in *fail_col.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
+               int in_smem, int* status, int* fail_col, double pivot_tol) {
+  extern __shared__ __align__(16) unsigned char craw[];
+  T* s = (T*)craw;        // ka scale factors
+  T* rdiag = s + ka;      // ka
+  T* W = in_smem ? rdiag + ka : Wg;               // ka x ka factor
+  T* Li = in_smem ? W + (size_t)ka * ka : Wg + (size_t)ka * ka;  // ka x ka inverse
+  __shared__ int sflag;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < ka; i += nt) {
+    double dgi = G[(long long)i * ldg + i];
+    s[i] = dgi > 0.0 ? (T)rsqrt(dgi) : (T)0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ka * ka; idx += nt) {
+    int i = idx / ka, j = idx % ka;
+    if (j > i) continue;
+    double g = 0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]);
+    W[i * ka + j] = (T)g * s[i] * s[j];
+  }
+  __syncthreads();
+  int fc = blk_chol<T>(ka, W, ka, rdiag, (T)pivot_tol, &sflag);
+  for (int i = 0; i < ka && fc < 0; ++i)
+    if (s[i] == (T)0) fc = i;  // a zero column
+  if (fc >= 0) {
+    if (tid == 0) {
+      atomicOr(status, ST_CHOL_FAIL);
+      if (fail_col) *fail_col = fc;
+    }
     return;
   }
-  // inverse of the lower factor, column j by thread j (forward substitution), stored in
-  // the strict upper triangle transposed: U[j][i] = Linv[i][j] for i >= j.
-  for (int j = threadIdx.x; j < ka; j += blockDim.x) {
-    // Linv[j][j]
-    double xj = 1.0 / W[j * ka + j];
-    Tm[(long long)j * ka + j] = (T)(s[j] * xj);
-    // x_i for i > j go to the (free) strict upper triangle: W[j][i] = Linv[i][j]
-    for (int i = j + 1; i < ka; ++i) {
-      double acc = W[i * ka + j] * xj;
-      for (int q = j + 1; q < i; ++q) acc += W[i * ka + q] * W[j * ka + q];
-      double xi = -acc / W[i * ka + i];
-      W[j * ka + i] = xi;  // strictly upper part is free (lower holds C)
-    }
-  }
-  __syncthreads();
-  // Tm[i][j] = s_i * (C^-1)[j][i] for j >= i  (C^-1 stored as W[col][row] above diagonal)
-  for (int idx = threadIdx.x; idx < ka * ka; idx += blockDim.x) {
+  blk_tri_inv<T>(ka, W, ka, rdiag, Li, ka);
+  for (int idx = tid; idx < ka * ka; idx += nt) {
     int i = idx / ka, j = idx % ka;
-    T v = 0;
-    if (j > i) v = (T)(s[i] * W[i * ka + j]);
-    if (j != i) Tm[(long long)i * ka + j] = v;
+    Tm[(long long)i * ka + j] = (j >= i) ? s[i] * Li[j * ka + i] : (T)0;
   }
 }
 
 // ---------------------------------------------------------------------------------------
+__device__ inline float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ inline double sdiv(double a, double b) { return a / b; }
+
 template <typename T>
-__device__ int sturm_count(int m, const T* d, const T* e2, T x, T pivmin) {
+__device__ int sturm_count(int m, const T* __restrict__ d, const T* __restrict__ e2, T x,
+                           T pivmin) {
   int c = 0;
   T q = d[0] - x;
   if (fabs(q) <= pivmin) q = -pivmin;
   if (q <= 0) ++c;
+#pragma unroll 4
   for (int i = 1; i < m; ++i) {
-    q = d[i] - x - e2[i - 1] / q;
+    q = d[i] - x - sdiv(e2[i - 1], q);
     if (fabs(q) <= pivmin) q = -pivmin;
     if (q <= 0) ++c;
   }
@@ -161,18 +204,60 @@ __device__ int sturm_count(int m, const T* d, const T* e2, T x, T pivmin) {
 }
 
 // Pseudo-random start entries in (-1, 1) for inverse iteration (SplitMix64 output mix).
-__device__ inline double start_entry(int i, int j) {
+__device__ inline float start_entry(int i, int j) {
   unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(i * 7919 + j * 104729 + 1);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   z ^= z >> 31;
-  return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+  return (float)(z >> 40) * (2.0f / 16777216.0f) - 1.0f;
 }
 
+#ifdef SC_RR_PHASES
+__device__ long long g_rr_phase[8];
+__device__ long long g_rr_sub[4];
+#define RR_SUB(i, t0)                                                  \
+  do {                                                                 \
+    if (threadIdx.x == 0) {                                            \
+      long long t1 = clock64();                                        \
+      g_rr_sub[i] += t1 - t0;                                          \
+      t0 = t1;                                                         \
+    }                                                                  \
+  } while (0)
+#else
+#define RR_SUB(i, t0) \
+  do {                \
+  } while (0)
+#endif
+#ifdef SC_RR_PHASES
+#define RR_MARK(i)                                   \
+  do {                                               \
+    __syncthreads();                                 \
+    if (threadIdx.x == 0) g_rr_phase[i] = clock64(); \
+  } while (0)
+#else
+#define RR_MARK(i) \
+  do {             \
+  } while (0)
+#endif
+
+constexpr int RR_NT = 1024;
+
+// Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of the symmetric
+// m x m matrix G (FP64 in, arithmetic in T), one CTA of 1024 threads.
+//  1. Householder tridiagonalization (Golub & Van Loan Alg. 8.3.1), three barriers per step:
+//     warp 0 forms the reflector; p = beta A' v with 8 lanes per row and four accumulators,
+//     per-warp partial sums of p'v (summed in fixed order); the rank-2 update.
+//  2. The K smallest eigenvalues of T by 17-point multisection on Sturm counts (16 lanes
+//     per eigenvalue, up to 64 eigenvalues at once).
+//  3. Eigenvectors of T by inverse iteration (tridiagonal LU with partial pivoting, shifts
+//     kept 10 eps ||T|| apart), two sweeps, each followed by a block Cholesky-QR (a second
+//     pass when the block was far from orthonormal; in-order Gram-Schmidt if it breaks).
+//  4. Back-transformation with the stored reflectors.
 template <typename T>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(RR_NT)
     k_rr_eig(int m, int K, const double* __restrict__ G, int ldg, double* __restrict__ theta,
-             T* __restrict__ Y, T* Ag, T* Zg, T* lu, int a_smem, int z_smem, int* status) {
+             T* __restrict__ Y, T* Ag, T* Zg, T* lu, T* Gsg, int a_smem, int z_smem,
+             int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* d = (T*)smraw;
   T* e = d + m;
@@ -181,191 +266,242 @@ __global__ void __launch_bounds__(NT)
   T* pv = vv + m;
   T* wv = pv + m;
   T* lam = wv + m;   // K
-  T* red = lam + K;  // 64
-  T* nxt = red + 64;
+  T* red = lam + K;  // 128
+  T* nxt = red + 128;
   T* A = a_smem ? nxt : Ag;
   if (a_smem) nxt += (long long)m * m;
   T* Z = z_smem ? nxt : Zg;
+  __shared__ int sflag;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = nt / 32;
 
-  for (int idx = tid; idx < m * m; idx += nt) {
-    int i = idx / m, j = idx % m;
-    A[idx] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
-  }
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < m; j += 32)
+      A[(long long)i * m + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
   __syncthreads();
-
-  // 1. Householder tridiagonalization; reflector k stored in row k, cols k+1..m-1 (v0 = 1)
+  RR_MARK(0);
+  // ---- 1. tridiagonalization
+  long long tsub = clock64();
   for (int k = 0; k + 2 < m; ++k) {
     const int n1 = m - k - 1;
     T* x = A + (long long)k * m + k + 1;
-    T part = 0;
-    for (int i = tid + 1; i < n1; i += nt) part += x[i] * x[i];
-    T sigma = block_sum(part, red);
-    if (tid == 0) {
-      T x0 = x[0], bet, ek, v0 = 1;
-      if (sigma == (T)0) {
-        bet = 0;
-        ek = x0;
-      } else {
-        T mu = sqrt(x0 * x0 + sigma);
-        v0 = (x0 <= (T)0) ? x0 - mu : -sigma / (x0 + mu);
-        bet = (T)2 * v0 * v0 / (sigma + v0 * v0);
-        ek = mu;
+    if (warp == 0) {
+      T p0 = 0, p1 = 0;
+      int i = lane + 1;
+      for (; i + 32 < n1; i += 64) {
+        p0 = fma(x[i], x[i], p0);
+        p1 = fma(x[i + 32], x[i + 32], p1);
       }
-      beta[k] = bet;
-      e[k] = ek;
-      red[40] = v0;
+      if (i < n1) p0 = fma(x[i], x[i], p0);
+      T sigma = p0 + p1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sigma += __shfl_xor_sync(0xffffffffu, sigma, o);
+      T bet = 0, iv0 = 1;
+      if (lane == 0) {
+        T x0 = x[0], ek;
+        if (sigma == (T)0) {
+          bet = 0;
+          ek = x0;
+        } else {
+          T mu = sqrt(x0 * x0 + sigma);
+          T v0 = (x0 <= (T)0) ? x0 - mu : -sigma / (x0 + mu);
+          bet = (T)2 * v0 * v0 / (sigma + v0 * v0);
+          iv0 = (T)1 / v0;
+          ek = mu;
+        }
+        beta[k] = bet;
+        e[k] = ek;
+      }
+      bet = __shfl_sync(0xffffffffu, bet, 0);
+      iv0 = __shfl_sync(0xffffffffu, iv0, 0);
+      if (bet != (T)0) {
+        for (int q = lane; q < n1; q += 32) {
+          T vq = (q == 0) ? (T)1 : x[q] * iv0;
+          vv[q] = vq;
+          x[q] = vq;
+        }
+      }
     }
     __syncthreads();
+    RR_SUB(0, tsub);
     const T bet = beta[k];
-    const T v0 = red[40];
     if (bet == (T)0) continue;  // uniform
-    for (int i = tid; i < n1; i += nt) vv[i] = (i == 0) ? (T)1 : x[i] / v0;
-    __syncthreads();
-    for (int i = tid; i < n1; i += nt) x[i] = vv[i];
-    // p = bet * A' v (A' symmetric trailing block; thread groups of g lanes per row)
-    int g = 32;
-    while (g > 1 && n1 * g > nt) g >>= 1;
-    const int rows_pp = nt / g;
-    for (int i0 = 0; i0 < n1; i0 += rows_pp) {
-      int i = i0 + tid / g, sl = tid % g;
-      T acc = 0;
-      if (i < n1) {
-        const T* col = A + (long long)(k + 1) * m + (k + 1 + i);
-        for (int j = sl; j < n1; j += g) acc += col[(long long)j * m] * vv[j];
+    {
+      const int g = 8;
+      const int rows_pp = nt / g;
+      T wpart = 0;
+      for (int i0 = 0; i0 < n1; i0 += rows_pp) {
+        const int i = i0 + tid / g, sl = tid % g;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        if (i < n1) {
+          const T* row = A + (long long)(k + 1 + i) * m + (k + 1);
+          int j = sl;
+          for (; j + 3 * g < n1; j += 4 * g) {
+            a0 = fma(row[j], vv[j], a0);
+            a1 = fma(row[j + g], vv[j + g], a1);
+            a2 = fma(row[j + 2 * g], vv[j + 2 * g], a2);
+            a3 = fma(row[j + 3 * g], vv[j + 3 * g], a3);
+          }
+          for (; j < n1; j += g) a0 = fma(row[j], vv[j], a0);
+        }
+        T acc = (a0 + a1) + (a2 + a3);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (i < n1 && sl == 0) {
+          pv[i] = bet * acc;
+          wpart = fma(bet * acc, vv[i], wpart);
+        }
       }
-      for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, g);
-      if (i < n1 && sl == 0) pv[i] = bet * acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wpart += __shfl_xor_sync(0xffffffffu, wpart, o);
+      if (lane == 0) red[warp] = wpart;
     }
     __syncthreads();
-    part = 0;
-    for (int i = tid; i < n1; i += nt) part += pv[i] * vv[i];
-    T pdv = block_sum(part, red);
-    T kc = bet * (T)0.5 * pdv;
-    for (int i = tid; i < n1; i += nt) wv[i] = pv[i] - kc * vv[i];
-    __syncthreads();
-    const long long tot = (long long)n1 * n1;
-    for (long long idx = tid; idx < tot; idx += nt) {
-      int i = (int)(idx / n1), j = (int)(idx % n1);
-      T* a = A + (long long)(k + 1 + i) * m + (k + 1 + j);
-      *a -= vv[i] * wv[j] + wv[i] * vv[j];
+    RR_SUB(1, tsub);
+    T pdv = 0;
+    for (int w = 0; w < nw; ++w) pdv += red[w];  // fixed order
+    const T kc = bet * (T)0.5 * pdv;
+    for (int i = warp; i < n1; i += nw) {
+      const T vi = vv[i], wi = pv[i] - kc * vi;
+      T* arow = A + (long long)(k + 1 + i) * m + (k + 1);
+#pragma unroll 4
+      for (int j = lane; j < n1; j += 32) arow[j] -= vi * (pv[j] - kc * vv[j]) + wi * vv[j];
     }
     __syncthreads();
+    RR_SUB(2, tsub);
   }
+  (void)tsub;
   for (int i = tid; i < m; i += nt) d[i] = A[(long long)i * m + i];
-  if (tid == 0 && m >= 2) {
-    e[m - 2] = A[(long long)(m - 1) * m + (m - 2)];
-    if (m - 2 >= 0) beta[m - 2] = 0;
+  if (tid == 0) {
+    if (m >= 2) e[m - 2] = A[(long long)(m - 1) * m + (m - 2)];
+    e[m - 1] = 0;
   }
-  if (tid == 0) e[m - 1] = 0;
   __syncthreads();
+  RR_MARK(1);
 
-  // 2. Gershgorin bounds and multisection for eigenvalues 0..K-1
+  // ---- 2. Gershgorin bounds; 17-point multisection, 16 lanes per eigenvalue
   T* e2 = wv;
-  T lo_p = (T)3e38, hi_p = (T)-3e38, emax = 0;
-  for (int i = tid; i < m; i += nt) {
-    T r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0);
-    lo_p = min(lo_p, d[i] - r);
-    hi_p = max(hi_p, d[i] + r);
-    emax = max(emax, e[i] * e[i]);
-    if (!isfinite(d[i]) || !isfinite(e[i])) atomicOr(status, ST_NONFINITE);
-  }
-  __syncthreads();
-  for (int i = tid; i < m; i += nt) e2[i] = e[i] * e[i];
-  T lo = -block_max(-lo_p, red);
-  T hi = block_max(hi_p, red);
-  emax = block_max(emax, red);
-  const T tnorm = max(fabs(lo), fabs(hi));
-  const T pivmin = Lim<T>::tiny() * max((T)1, emax);
-  lo -= (T)2 * Lim<T>::eps() * tnorm + pivmin;
-  hi += (T)2 * Lim<T>::eps() * tnorm + pivmin;
-  for (int j = warp; j < K; j += nt / 32) {
-    T a = lo, b = hi;
-    for (int it = 0; it < 40; ++it) {
-      T tol = (T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)) + (T)4 * pivmin;
-      if (b - a <= tol) break;
-      T h = (b - a) / (T)33;
-      T xq = a + h * (T)(lane + 1);
-      int c = sturm_count(m, d, e2, xq, pivmin);
-      unsigned bal = __ballot_sync(0xffffffffu, c > j);
-      int first = bal ? (__ffs(bal) - 1) : 32;
-      T na = first == 0 ? a : a + h * (T)first;
-      T nb = first == 32 ? b : a + h * (T)(first + 1);
-      if (!(nb > na)) break;
-      a = na;
-      b = nb;
+  {
+    T lo_p = (T)3e38, hi_p = (T)-3e38, emax = 0;
+    for (int i = tid; i < m; i += nt) {
+      T r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0);
+      lo_p = min(lo_p, d[i] - r);
+      hi_p = max(hi_p, d[i] + r);
+      emax = max(emax, e[i] * e[i]);
+      e2[i] = e[i] * e[i];
+      if (!isfinite(d[i]) || !isfinite(e[i])) atomicOr(status, ST_NONFINITE);
     }
-    if (lane == 0) lam[j] = (T)0.5 * (a + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo_p = min(lo_p, __shfl_xor_sync(0xffffffffu, lo_p, o));
+      hi_p = max(hi_p, __shfl_xor_sync(0xffffffffu, hi_p, o));
+      emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    }
+    if (lane == 0) {
+      red[warp] = lo_p;
+      red[32 + warp] = hi_p;
+      red[64 + warp] = emax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T lo = red[0], hi = red[32], em = red[64];
+      for (int w = 1; w < nw; ++w) {
+        lo = min(lo, red[w]);
+        hi = max(hi, red[32 + w]);
+        em = max(em, red[64 + w]);
+      }
+      red[120] = lo;
+      red[121] = hi;
+      red[122] = em;
+    }
+    __syncthreads();
+  }
+  const T tnorm = max(fabs(red[120]), fabs(red[121]));
+  const T pivmin = Lim<T>::tiny() * max((T)1, red[122]);
+  const T glo = red[120] - (T)2 * Lim<T>::eps() * tnorm - pivmin;
+  const T ghi = red[121] + (T)2 * Lim<T>::eps() * tnorm + pivmin;
+  {
+    const int grp = tid >> 4, sl = tid & 15;
+    const unsigned gmask = 0xFFFFu << (lane & 16);
+    for (int j = grp; j < K; j += nt >> 4) {
+      T a = glo, b = ghi;
+      for (int it = 0; it < 48; ++it) {
+        T tol = (T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)) + (T)4 * pivmin;
+        if (b - a <= tol) break;
+        T h = (b - a) / (T)17;
+        int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
+        unsigned bal = __ballot_sync(gmask, c > j) >> (lane & 16);
+        int first = bal ? (__ffs(bal) - 1) : 16;
+        T na = first == 0 ? a : a + h * (T)first;
+        T nb = first == 16 ? b : a + h * (T)(first + 1);
+        if (!(nb > na)) break;
+        a = na;
+        b = nb;
+      }
+      if (sl == 0) lam[j] = (T)0.5 * (a + b);
+    }
   }
   __syncthreads();
+  RR_MARK(2);
 
-  // 3. inverse iteration: shifts separated by sep, LU of (T - s I) per eigenvalue
+  // ---- 3. inverse iteration
   const T sep = (T)10 * Lim<T>::eps() * tnorm + pivmin;
-  T* shift = pv;  // K <= m
+  T* shift = pv;
   if (tid == 0) {
     T prev = (T)0;
     for (int j = 0; j < K; ++j) {
-      T s = lam[j];
-      if (j > 0 && s < prev + sep) s = prev + sep;
-      shift[j] = s;
-      prev = s;
+      T sj = lam[j];
+      if (j > 0 && sj < prev + sep) sj = prev + sep;
+      shift[j] = sj;
+      prev = sj;
     }
   }
   __syncthreads();
   const T small_piv = Lim<T>::eps() * tnorm + pivmin;
+#define LU(i, a) lu[((long long)(i) * 5 + (a)) * K + j]
   for (int j = tid; j < K; j += nt) {
-    T* u0 = lu + (long long)j * 5 * m;
-    T* u1 = u0 + m;
-    T* u2 = u1 + m;
-    T* ml = u2 + m;
-    T* sw = ml + m;  // 1 = rows i, i+1 swapped
-    T s = shift[j];
-    T al = d[0] - s, bt = m > 1 ? e[0] : (T)0;
+    const T sj = shift[j];
+    T al = d[0] - sj, bt = m > 1 ? e[0] : (T)0;
     for (int i = 0; i + 1 < m; ++i) {
-      T dl = e[i];                                   // (i+1, i)
-      T an = d[i + 1] - s, bn = (i + 2 < m) ? e[i + 1] : (T)0;  // row i+1: diag, super
+      const T dl = e[i];
+      const T an = d[i + 1] - sj, bn = (i + 2 < m) ? e[i + 1] : (T)0;
       if (fabs(al) >= fabs(dl)) {
         if (al == (T)0) al = small_piv;
-        T mlt = dl / al;
-        u0[i] = al; u1[i] = bt; u2[i] = 0; ml[i] = mlt; sw[i] = 0;
+        const T mlt = dl / al;
+        LU(i, 0) = al; LU(i, 1) = bt; LU(i, 2) = 0; LU(i, 3) = mlt; LU(i, 4) = 0;
         al = an - mlt * bt;
         bt = bn;
       } else {
-        T mlt = al / dl;
-        u0[i] = dl; u1[i] = an; u2[i] = bn; ml[i] = mlt; sw[i] = 1;
+        const T mlt = al / dl;
+        LU(i, 0) = dl; LU(i, 1) = an; LU(i, 2) = bn; LU(i, 3) = mlt; LU(i, 4) = 1;
         al = bt - mlt * an;
         bt = -mlt * bn;
       }
     }
     if (fabs(al) < small_piv) al = al < (T)0 ? -small_piv : small_piv;
-    u0[m - 1] = al;
-    u1[m - 1] = 0;
-    u2[m - 1] = 0;
-    ml[m - 1] = 0;
-    sw[m - 1] = 0;
-    for (int i = 0; i < m; ++i) Z[(long long)i * K + j] = (T)start_entry(i, j);
+    LU(m - 1, 0) = al; LU(m - 1, 1) = 0; LU(m - 1, 2) = 0; LU(m - 1, 3) = 0; LU(m - 1, 4) = 0;
   }
+  for (long long idx = tid; idx < (long long)m * K; idx += nt)
+    Z[idx] = (T)start_entry((int)(idx / K), (int)(idx % K));
   __syncthreads();
+  RR_MARK(3);
+  T* Gs = Gsg;          // K x K Gram / factor (global scratch)
+  T* Li = Gsg + (size_t)K * K;
+  T* rd = pv;           // K reciprocal pivots (pv is free now)
   for (int sweep = 0; sweep < 2; ++sweep) {
     for (int j = tid; j < K; j += nt) {
-      const T* u0 = lu + (long long)j * 5 * m;
-      const T* u1 = u0 + m;
-      const T* u2 = u1 + m;
-      const T* ml = u2 + m;
-      const T* sw = ml + m;
-      // forward: apply row swaps and multipliers
       for (int i = 0; i + 1 < m; ++i) {
         T bi = Z[(long long)i * K + j], bn = Z[(long long)(i + 1) * K + j];
-        if (sw[i] != (T)0) {
+        if (LU(i, 4) != (T)0) {
           T t = bi; bi = bn; bn = t;
         }
         Z[(long long)i * K + j] = bi;
-        Z[(long long)(i + 1) * K + j] = bn - ml[i] * bi;
+        Z[(long long)(i + 1) * K + j] = bn - LU(i, 3) * bi;
       }
-      // back substitution with U (diag u0, super u1, second super u2)
       T z1 = 0, z2 = 0, mx = 0;
       for (int i = m - 1; i >= 0; --i) {
-        T zi = (Z[(long long)i * K + j] - u1[i] * z1 - u2[i] * z2) / u0[i];
+        T zi = (Z[(long long)i * K + j] - LU(i, 1) * z1 - LU(i, 2) * z2) / LU(i, 0);
         Z[(long long)i * K + j] = zi;
         z2 = z1;
         z1 = zi;
@@ -375,84 +511,160 @@ __global__ void __launch_bounds__(NT)
       for (int i = 0; i < m; ++i) Z[(long long)i * K + j] *= inv;
     }
     __syncthreads();
-    // classical Gram-Schmidt twice per column, in eigenvalue order, then normalize
-    T* coef = vv;  // K <= m
-    for (int j = 0; j < K; ++j) {
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int q = warp; q < j; q += nt / 32) {
-          T acc = 0;
-          for (int i = lane; i < m; i += 32) acc += Z[(long long)i * K + q] * Z[(long long)i * K + j];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == 0) coef[q] = acc;
+    bool ok = true;
+    for (int pass = 0; pass < 2 && ok; ++pass) {
+      // Gram Z'Z (lower triangle), one thread per entry, four accumulators
+      for (int p = tid; p < K * K; p += nt) {
+        int a = p / K, b = p % K;
+        if (b > a) continue;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int r = 0;
+        for (; r + 3 < m; r += 4) {
+          a0 = fma(Z[(long long)r * K + a], Z[(long long)r * K + b], a0);
+          a1 = fma(Z[(long long)(r + 1) * K + a], Z[(long long)(r + 1) * K + b], a1);
+          a2 = fma(Z[(long long)(r + 2) * K + a], Z[(long long)(r + 2) * K + b], a2);
+          a3 = fma(Z[(long long)(r + 3) * K + a], Z[(long long)(r + 3) * K + b], a3);
         }
-        __syncthreads();
-        if (j > 0) {
+        for (; r < m; ++r) a0 = fma(Z[(long long)r * K + a], Z[(long long)r * K + b], a0);
+        Gs[a * K + b] = (a0 + a1) + (a2 + a3);
+      }
+      __syncthreads();
+      // scale to unit diagonal, factor, invert
+      for (int a = tid; a < K; a += nt) wv[a] = rsqrt(max(Gs[a * K + a], Lim<T>::tiny()));
+      __syncthreads();
+      T mindiag = (T)1;
+      for (int p = tid; p < K * K; p += nt) {
+        int a = p / K, b = p % K;
+        if (b <= a) Gs[a * K + b] *= wv[a] * wv[b];
+      }
+      __syncthreads();
+      int fc = blk_chol<T>(K, Gs, K, rd, (T)(sizeof(T) == 4 ? 1e-6 : 1e-14), &sflag);
+      if (fc >= 0) {
+        ok = false;
+        break;
+      }
+      // minimum pivot decides whether a second pass is needed
+      if (tid == 0) {
+        for (int a = 0; a < K; ++a) mindiag = min(mindiag, Gs[a * K + a] * Gs[a * K + a]);
+        red[44] = mindiag;
+      }
+      blk_tri_inv<T>(K, Gs, K, rd, Li, K);
+      // Z <- Z diag(wv) Li' : out_b = sum_{a <= b} z_a wv_a Li[b][a]; a warp per row, lanes
+      // own output columns (buffered in registers until the whole row has been read)
+      for (int r = warp; r < m; r += nw) {
+        T* zr = Z + (long long)r * K;
+        T out[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int b = lane + 32 * q;
+          T acc = 0;
+          if (b < K) {
+            const T* lb = Li + b * K;
+            for (int a = 0; a <= b; ++a) acc = fma(zr[a] * wv[a], lb[a], acc);
+          }
+          out[q] = acc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int b = lane + 32 * q;
+          if (b < K) zr[b] = out[q];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      if (red[44] > (T)0.5) break;  // nearly orthonormal input: one pass was enough
+    }
+    if (!ok) {
+      // in-order modified Gram-Schmidt (tight clusters)
+      T* coef = vv;
+      for (int j = 0; j < K; ++j) {
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int q = warp; q < j; q += nw) {
+            T acc = 0;
+            for (int i = lane; i < m; i += 32) acc += Z[(long long)i * K + q] * Z[(long long)i * K + j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) coef[q] = acc;
+          }
+          __syncthreads();
           for (int i = tid; i < m; i += nt) {
             T acc = 0;
             for (int q = 0; q < j; ++q) acc += coef[q] * Z[(long long)i * K + q];
             Z[(long long)i * K + j] -= acc;
           }
+          __syncthreads();
+        }
+        if (warp == 0) {
+          T part = 0;
+          for (int i = lane; i < m; i += 32) part += Z[(long long)i * K + j] * Z[(long long)i * K + j];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          if (lane == 0) red[41] = part > (T)0 ? (T)1 / sqrt(part) : (T)0;
         }
         __syncthreads();
+        for (int i = tid; i < m; i += nt) Z[(long long)i * K + j] *= red[41];
+        __syncthreads();
       }
-      T part = 0;
-      for (int i = tid; i < m; i += nt) {
-        T z = Z[(long long)i * K + j];
-        part += z * z;
-      }
-      T nrm2 = block_sum(part, red);
-      T inv = nrm2 > (T)0 ? (T)1 / sqrt(nrm2) : (T)0;
-      for (int i = tid; i < m; i += nt) Z[(long long)i * K + j] *= inv;
-      __syncthreads();
     }
   }
+#undef LU
+  RR_MARK(4);
 
-  // 4. back-transformation Z <- H_0 ... H_{m-3} Z
+  // ---- 4. back-transformation Z <- H_0 ... H_{m-3} Z (warp-per-column dots, then update)
   T* coef = vv;
   for (int k = m - 3; k >= 0; --k) {
     const T bet = beta[k];
     if (bet == (T)0) continue;
     const int n1 = m - k - 1;
     const T* v = A + (long long)k * m + k + 1;
-    for (int j = warp; j < K; j += nt / 32) {
-      T acc = 0;
-      for (int i = lane; i < n1; i += 32) acc += v[i] * Z[(long long)(k + 1 + i) * K + j];
+    for (int j = warp; j < K; j += nw) {
+      T a0 = 0, a1 = 0;
+      int i = lane;
+      for (; i + 32 < n1; i += 64) {
+        a0 = fma(v[i], Z[(long long)(k + 1 + i) * K + j], a0);
+        a1 = fma(v[i + 32], Z[(long long)(k + 33 + i) * K + j], a1);
+      }
+      if (i < n1) a0 = fma(v[i], Z[(long long)(k + 1 + i) * K + j], a0);
+      T acc = a0 + a1;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) coef[j] = bet * acc;
     }
     __syncthreads();
-    const long long tot = (long long)n1 * K;
-    for (long long idx = tid; idx < tot; idx += nt) {
-      int i = (int)(idx / K), j = (int)(idx % K);
-      Z[(long long)(k + 1 + i) * K + j] -= coef[j] * v[i];
+    for (int i = warp; i < n1; i += nw) {
+      const T vi = v[i];
+      T* zr = Z + (long long)(k + 1 + i) * K;
+#pragma unroll 2
+      for (int j = lane; j < K; j += 32) zr[j] -= coef[j] * vi;
     }
     __syncthreads();
   }
+  RR_MARK(5);
   for (int j = tid; j < K; j += nt) theta[j] = (double)lam[j];
   for (long long idx = tid; idx < (long long)m * K; idx += nt) Y[idx] = Z[idx];
+  RR_MARK(6);
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
-                     int* d_status, double pivot_tol) {
-  size_t base = sizeof(double) * ((size_t)ka + 34);
-  size_t wbytes = sizeof(double) * (size_t)ka * ka;
+                     int* d_status, double pivot_tol, int* fail_col) {
+  size_t base = sizeof(T) * (2 * (size_t)ka);
+  size_t wbytes = sizeof(T) * (size_t)ka * ka * 2;
   int in_smem = base + wbytes <= 200 * 1024;
   size_t sm = base + (in_smem ? wbytes : 0);
-  double* Wg = nullptr;
+  T* Wg = nullptr;
   if (!in_smem) {
-    Wg = al.get<double>((size_t)ka * ka);
+    Wg = al.get<T>((size_t)ka * ka * 2);
     if (!Wg) return cudaErrorMemoryAllocation;
   }
   cudaError_t e = cudaFuncSetAttribute(k_chol_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
   ProfScope ps(st, "chol_inv");
-  k_chol_inv<T><<<1, NT, sm, st>>>(ka, G, ldg, Tm, Wg, in_smem, d_status, pivot_tol);
+  k_chol_inv<T><<<1, 256, sm, st>>>(ka, G, ldg, Tm, Wg, in_smem, d_status, fail_col, pivot_tol);
   note_launch();
   e = cudaGetLastError();
   al.put(Wg);
@@ -463,7 +675,7 @@ template <typename T>
 cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
                    double* theta, T* Y, int* d_status) {
   if (m < 1 || K < 1 || K > m) return cudaErrorInvalidValue;
-  size_t base = sizeof(T) * ((size_t)6 * m + K + 64);
+  size_t base = sizeof(T) * ((size_t)6 * m + K + 128);
   size_t abytes = sizeof(T) * (size_t)m * m;
   size_t zbytes = sizeof(T) * (size_t)m * K;
   const size_t cap = 220 * 1024;
@@ -473,15 +685,16 @@ cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, in
   T* Ag = a_smem ? nullptr : al.get<T>((size_t)m * m);
   T* Zg = z_smem ? nullptr : al.get<T>((size_t)m * K);
   T* lu = al.get<T>((size_t)K * 5 * m);
+  T* Gs = al.get<T>((size_t)K * K * 2);
   cudaError_t e = cudaSuccess;
-  if ((!a_smem && !Ag) || (!z_smem && !Zg) || !lu) {
+  if ((!a_smem && !Ag) || (!z_smem && !Zg) || !lu || !Gs) {
     e = cudaErrorMemoryAllocation;
   } else {
     e = cudaFuncSetAttribute(k_rr_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) {
       ProfScope ps(st, "rr_eig");
-      k_rr_eig<T><<<1, NT, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, lu, a_smem, z_smem,
-                                     d_status);
+      k_rr_eig<T><<<1, RR_NT, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, lu, Gs, a_smem, z_smem,
+                                        d_status);
       note_launch();
       e = cudaGetLastError();
     }
@@ -489,13 +702,14 @@ cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, in
   al.put(Ag);
   al.put(Zg);
   al.put(lu);
+  al.put(Gs);
   return e;
 }
 
 template cudaError_t chol_inv<float>(cudaStream_t, Alloc&, int, const double*, int, float*,
-                                     int*, double);
+                                     int*, double, int*);
 template cudaError_t chol_inv<double>(cudaStream_t, Alloc&, int, const double*, int, double*,
-                                      int*, double);
+                                      int*, double, int*);
 template cudaError_t rr_eig<float>(cudaStream_t, Alloc&, int, int, const double*, int, double*,
                                    float*, int*);
 template cudaError_t rr_eig<double>(cudaStream_t, Alloc&, int, int, const double*, int,

@@ -4,9 +4,11 @@
 // CUDA-core form (SC_PREC_FP32 / SC_PREC_FP64).  Split-K over row chunks: CTA (tile,
 // chunk) forms a 64 x 64 tile of A'B over its rows with a 4 x 4 register micro-tile per
 // thread (FP32 accumulation for float blocks, FP64 for double), writes the tile as FP64
-// partials, and the last CTA to finish a tile (atomic ticket, no waiting) sums the chunks
-// in fixed chunk order.  The result is deterministic and independent of scheduling.
+// partials; a second kernel sums the chunks in fixed chunk order, one thread per output
+// element.  The result is deterministic and independent of scheduling.
 // The tensor-core form lives in k_gram_tc.cu.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sc {
@@ -44,14 +46,12 @@ __device__ inline void map_cols(const Cat3<T>& M, int c0, ColMap* cm) {
 
 template <typename T>
 __global__ void __launch_bounds__(NT)
-    k_gram(long long n, Cat3<T> A, Cat3<T> B, int a, int b, const int2* __restrict__ tiles,
-           int nch, long long rows_per_chunk, double* __restrict__ part, int* cnt, double* C,
-           int ldc, int sym) {
+    k_gram(long long n, Cat3<T> A, Cat3<T> B, const int2* __restrict__ tiles, int nch,
+           int ntiles, long long rows_per_chunk, double* __restrict__ part) {
   using AT = typename Acc<T>::type;
   __shared__ __align__(16) T As[RB][TB];
   __shared__ __align__(16) T Bs[RB][TB];
   __shared__ ColMap cma[TB], cmb[TB];
-  __shared__ int last;
   const int tile = blockIdx.x / nch;
   const int chunk = blockIdx.x % nch;
   const int2 tl = tiles[tile];
@@ -98,28 +98,31 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
   }
-  double* mine = part + ((long long)tile * nch + chunk) * TB * TB;
+  double* mine = part + ((long long)chunk * ntiles + tile) * TB * TB;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) mine[(ty * 4 + i) * TB + tx * 4 + j] = (double)acc[i][j];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(&cnt[tile], 1) == nch - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  const double* tp = part + (long long)tile * nch * TB * TB;
-  for (int e = threadIdx.x; e < TB * TB; e += NT) {
+}
+
+// C[tile element] = sum over chunks in chunk order; one thread per tile element, so the
+// chunk loop reads consecutive addresses across a warp.
+__global__ void k_gram_reduce(const double* __restrict__ part, int nch, int ntiles,
+                              const int2* __restrict__ tiles, int a, int b, double* C, int ldc,
+                              int sym) {
+  long long tot = (long long)ntiles * TB * TB;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot;
+       g += (long long)gridDim.x * blockDim.x) {
+    int tile = (int)(g / (TB * TB));
+    int e = (int)(g % (TB * TB));
+    int2 tl = tiles[tile];
+    int gi = tl.x * TB + e / TB, gj = tl.y * TB + e % TB;
+    if (gi >= a || gj >= b) continue;
     double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += __ldcg(tp + (long long)c * TB * TB + e);
-    int gi = ti * TB + e / TB, gj = tj * TB + e % TB;
-    if (gi < a && gj < b) {
-      C[(long long)gi * ldc + gj] = s;
-      if (sym && ti != tj) C[(long long)gj * ldc + gi] = s;
-    }
+    for (int c = 0; c < nch; ++c) s += part[((long long)c * ntiles + tile) * TB * TB + e];
+    C[(long long)gi * ldc + gj] = s;
+    if (sym && tl.x != tl.y) C[(long long)gj * ldc + gi] = s;
   }
-  if (threadIdx.x == 0) cnt[tile] = 0;
 }
 
 }  // namespace
@@ -138,9 +141,11 @@ cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, cons
     for (int j = 0; j < nb; ++j)
       if (!sym || i <= j) tl_host[nt++] = make_int2(i, j);
   if (nt > 64 * 64) return cudaErrorInvalidValue;
-  long long target = 152LL * 4;
+  // Row chunks: enough CTAs to fill the GPU twice, but at least 512 rows per chunk so the
+  // FP64 partial tiles stay small next to the rows they summarise.
+  long long target = 152LL * 2;
   long long nch = (target + nt - 1) / nt;
-  long long maxch = (n + RB - 1) / RB;
+  long long maxch = (n + 511) / 512;
   if (nch > maxch) nch = maxch;
   if (nch < 1) nch = 1;
   long long rpc = (n + nch - 1) / nch;
@@ -148,22 +153,24 @@ cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, cons
   nch = (n + rpc - 1) / rpc;
   if (nch < 1) nch = 1;
   int2* tiles = al.get<int2>(nt);
-  int* cnt = al.get<int>(nt);
   double* part = al.get<double>((size_t)nt * nch * TB * TB);
   cudaError_t e = cudaSuccess;
-  if (!tiles || !cnt || !part) {
+  if (!tiles || !part) {
     e = cudaErrorMemoryAllocation;
   } else {
     cudaMemcpyAsync(tiles, tl_host, sizeof(int2) * nt, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(cnt, 0, sizeof(int) * nt, st);
-    ProfScope ps(st, "gram");
-    k_gram<T><<<(unsigned)(nt * nch), NT, 0, st>>>(n, A, B, a, b, tiles, (int)nch, rpc, part,
-                                                   cnt, C, ldc, sym ? 1 : 0);
-    note_launch();
+    {
+      ProfScope ps(st, "gram");
+      k_gram<T><<<(unsigned)(nt * nch), NT, 0, st>>>(n, A, B, tiles, (int)nch, nt, rpc, part);
+      note_launch();
+      long long tot = (long long)nt * TB * TB;
+      unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
+      k_gram_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, tiles, a, b, C, ldc, sym ? 1 : 0);
+      note_launch();
+    }
     e = cudaGetLastError();
   }
   al.put(tiles);
-  al.put(cnt);
   al.put(part);
   return e;
 }

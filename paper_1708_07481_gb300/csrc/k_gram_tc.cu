@@ -1,0 +1,428 @@
+// Tensor-core Gram matrices on sm_103a: C = A' B for tall FP32 blocks A (n x a), B (n x b)
+// (Sec. IV: Gram products of the n x l multi-vectors, O(n l^2)).
+//
+// 3-term split TF32 (Markidis et al. 2018 style error-free splitting): x = x_big + x_small
+// with x_big = tf32(x) and x_small = tf32(x - x_big); A'B ~ Ab'Bb + Ab'Bs + As'Bb, products on
+// tcgen05 (kind::tf32, FP32 accumulation in tensor memory), ~2^-21 relative per product.
+//
+// CTA = one 128 x 128 output tile over one chunk of rows.  Per stage of 32 rows:
+//   TMA (cp.async.bulk.tensor.2d) brings the FP32 row blocks of A and B into shared memory
+//   (double-buffered, mbarrier complete_tx); all 256 threads split them into big/small TF32
+//   operands written in the K-major 128-byte-swizzled layout the MMA reads (the transpose
+//   from row-major to K-major happens here, for free); one thread issues 4 K-steps x 3
+//   products of tcgen05.mma 128x128x8 into a TMEM accumulator and commits to an mbarrier
+//   that frees the operand buffer.  The epilogue reads TMEM with tcgen05.ld and writes the
+//   tile's FP64 partial; a second kernel sums the partials over chunks in fixed order.
+// Every wait is bounded: on a timeout the CTA records ST_TIMEOUT, waits (bounded) for its
+// own outstanding copies and MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace sc {
+namespace {
+
+constexpr int TM = 128, TN = 128, BK = 32, NTH = 256;
+constexpr int STAGE_BYTES = BK * TM * 4;     // 16 KB: FP32 rows of one operand
+constexpr int OP_BYTES = TM * BK * 4;        // 16 KB: one TF32 operand tile
+constexpr int SMEM_BYTES = 2 * 2 * STAGE_BYTES + 2 * 4 * OP_BYTES + 1024 + 256;
+constexpr long long SPIN_LIMIT = 1LL << 26;  // bounded waits (~ seconds)
+constexpr int ST_TIMEOUT = 32;
+
+struct SegMap {
+  int start[3];
+  int count[3];
+  int nseg;
+};
+
+__device__ inline int seg_index(const SegMap& s, int c) {
+  int off = 0;
+  for (int q = 0; q < s.nseg; ++q) {
+    if (c >= s.start[q] && c < s.start[q] + s.count[q]) return off + c - s.start[q];
+    off += s.count[q];
+  }
+  return -1;
+}
+
+__device__ inline uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ inline void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; returns false on timeout.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < SPIN_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                   uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ inline uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                          // layout: SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32() {
+  return (1u << 4)                 // c_format F32
+         | (2u << 7)               // a_format TF32
+         | (2u << 10)              // b_format TF32
+         | ((uint32_t)(TN >> 3) << 17)
+         | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ inline void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ inline void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// Byte offset of TF32 element (row r, k) in a K-major SW128 tile of TM rows x BK=32 values.
+__device__ inline uint32_t sw128_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7))) << 4) + (k & 3) * 4);
+}
+
+// Split one FP32 stage (BK rows x TM columns, row-major) into big/small K-major operands.
+__device__ inline void convert_stage(const float* stage, uint8_t* big, uint8_t* small) {
+  const int r = threadIdx.x & (TM - 1);  // operand row = column of the block
+  for (int kc = threadIdx.x >> 7; kc < BK / 4; kc += NTH / TM) {
+    uint32_t bg[4], sm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float x = stage[(kc * 4 + q) * TM + r];
+      uint32_t b = to_tf32(x);
+      bg[q] = b;
+      sm[q] = to_tf32(x - __uint_as_float(b));
+    }
+    uint32_t off = sw128_off(r, kc * 4);
+    *reinterpret_cast<uint4*>(big + off) = make_uint4(bg[0], bg[1], bg[2], bg[3]);
+    *reinterpret_cast<uint4*>(small + off) = make_uint4(sm[0], sm[1], sm[2], sm[3]);
+  }
+}
+
+__global__ void __launch_bounds__(NTH, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              long long n, const int2* __restrict__ tiles, int nch, int ntiles,
+              long long rows_per_chunk, int a, int b, double* __restrict__ part, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte aligned base for the swizzled operands
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* opA = base;                           // [buf][big/small] 16 KB each
+  uint8_t* opB = opA + 4 * OP_BYTES;
+  float* stA = (float*)(opB + 4 * OP_BYTES);     // [slot] 16 KB
+  float* stB = stA + 2 * (STAGE_BYTES / 4);
+  uint64_t* bars = (uint64_t*)(stB + 2 * (STAGE_BYTES / 4));
+  uint64_t* full = bars;         // [2] TMA landed
+  uint64_t* mdone = bars + 2;    // [2] MMAs of a buffer finished
+  uint32_t* tmem_slot = (uint32_t*)(bars + 4);
+  __shared__ int abort_flag;
+
+  const int tile = blockIdx.x / nch, chunk = blockIdx.x % nch;
+  const int2 tl = tiles[tile];
+  const int ca = tl.x * TM, cb = tl.y * TN;
+  const long long r0 = (long long)chunk * rows_per_chunk;
+  long long r1 = r0 + rows_per_chunk;
+  if (r1 > n) r1 = n;
+  const int nst = (int)((r1 - r0 + BK - 1) / BK);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int q = 0; q < 4; ++q) mbar_init(&bars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t IDESC = idesc_tf32();
+
+  // prologue: stages 0 and 1 in flight
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 && s < nst; ++s) {
+      mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
+      int y = (int)(r0 + (long long)s * BK);
+      tma_load_2d(stA + s * (STAGE_BYTES / 4), &mapA, ca, y, &full[s]);
+      tma_load_2d(stB + s * (STAGE_BYTES / 4), &mapB, cb, y, &full[s]);
+    }
+  }
+  int issued_commits[2] = {0, 0};
+  int loads_issued[2] = {nst > 0 ? 1 : 0, nst > 1 ? 1 : 0};  // thread 0's bookkeeping
+  int loads_done[2] = {0, 0};
+  for (int s = 0; s < nst; ++s) {
+    const int slot = s & 1;
+    bool ok = mbar_wait(&full[slot], (uint32_t)((s >> 1) & 1));
+    if (ok) loads_done[slot] += 1;
+    if (ok && s >= 2) ok = mbar_wait(&mdone[slot], (uint32_t)(((s - 2) >> 1) & 1));
+    if (!ok) atomicExch(&abort_flag, 1);
+    __syncthreads();
+    if (abort_flag) break;
+    uint8_t* aB = opA + (slot * 2) * OP_BYTES;
+    uint8_t* aS = aB + OP_BYTES;
+    uint8_t* bB = opB + (slot * 2) * OP_BYTES;
+    uint8_t* bS = bB + OP_BYTES;
+    convert_stage(stA + slot * (STAGE_BYTES / 4), aB, aS);
+    convert_stage(stB + slot * (STAGE_BYTES / 4), bB, bS);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ab = smem_u32(aB), as_ = smem_u32(aS), bb = smem_u32(bB), bs = smem_u32(bS);
+#pragma unroll
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        const uint32_t ko = ks * 32;  // 8 TF32 values along K
+        uint32_t acc0 = (s > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, sw128_desc(as_ + ko), sw128_desc(bb + ko), IDESC, acc0);
+        mma_tf32(tmem, sw128_desc(ab + ko), sw128_desc(bs + ko), IDESC, 1u);
+        mma_tf32(tmem, sw128_desc(ab + ko), sw128_desc(bb + ko), IDESC, 1u);
+      }
+      mma_commit(&mdone[slot]);
+      issued_commits[slot] += 1;
+      // the staging slot was consumed by the conversion above: refill it with stage s + 2
+      if (s + 2 < nst) {
+        loads_issued[slot] += 1;
+        mbar_expect_tx(&full[slot], 2 * STAGE_BYTES);
+        int y = (int)(r0 + (long long)(s + 2) * BK);
+        tma_load_2d(stA + slot * (STAGE_BYTES / 4), &mapA, ca, y, &full[slot]);
+        tma_load_2d(stB + slot * (STAGE_BYTES / 4), &mapB, cb, y, &full[slot]);
+      }
+    }
+  }
+  // wait for the last MMAs (both buffers' latest commits); thread 0 knows the counts
+  __shared__ int last_ok;
+  if (threadIdx.x == 0) {
+    bool ok = !abort_flag;
+    for (int q = 0; q < 2; ++q)
+      if (issued_commits[q] > 0)
+        ok = mbar_wait(&mdone[q], (uint32_t)((issued_commits[q] - 1) & 1)) && ok;
+    // after an abort, copies may still be in flight: wait (bounded) for the latest one
+    for (int q = 0; q < 2; ++q)
+      if (loads_issued[q] > loads_done[q])
+        ok = mbar_wait(&full[q], (uint32_t)((loads_issued[q] - 1) & 1)) && ok;
+    last_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (last_ok && nst > 0) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32, columns 64 (w / 4) .. +64
+    const int lrow = 32 * (warp & 3) + lane;
+    const int cbase = 64 * (warp >> 2);
+    double* dst = part + ((long long)chunk * ntiles + tile) * TM * TN;
+    const int gi = ca + lrow;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cbase + 32 * h);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (gi < a) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          int j = cbase + 32 * h + q;
+          if (cb + j < b) dst[(long long)lrow * TN + j] = (double)__uint_as_float(v[q]);
+        }
+      }
+    }
+  } else if (!last_ok && threadIdx.x == 0) {
+    atomicOr(status, ST_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN)
+                 : "memory");
+  }
+}
+
+__global__ void k_gram_tc_reduce(const double* __restrict__ part, int nch, int ntiles,
+                                 const int2* __restrict__ tiles, int a, int b, SegMap ma,
+                                 SegMap mb, double* C, int ldc, int sym) {
+  long long tot = (long long)ntiles * TM * TN;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot;
+       g += (long long)gridDim.x * blockDim.x) {
+    int tile = (int)(g / (TM * TN));
+    int e = (int)(g % (TM * TN));
+    int2 tl = tiles[tile];
+    int gi = tl.x * TM + e / TN, gj = tl.y * TN + e % TN;
+    if (gi >= a || gj >= b) continue;
+    int oi = seg_index(ma, gi), oj = seg_index(mb, gj);
+    if (oi < 0 || oj < 0) continue;
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += part[((long long)c * ntiles + tile) * TM * TN + e];
+    C[(long long)oi * ldc + oj] = s;
+    if (sym && tl.x != tl.y) C[(long long)oj * ldc + oi] = s;
+  }
+}
+
+// ---- host: tensor maps through the driver entry point (no -lcuda link dependency) ---------
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const float* ptr, long long rows, int cols, long long ld,
+              int box_cols) {
+  EncodeFn enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)BK};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int gram_tc_smem_bytes() { return SMEM_BYTES; }
+
+// C (compact, FP64) = A' B with A = columns [0, a) of a row-major FP32 block (stride lda) and
+// B = columns [0, b) of another; the segment maps drop padding columns from the output.
+cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, long long lda,
+                    int a, const int* segA, int nsegA, const float* B, long long ldb, int b,
+                    const int* segB, int nsegB, double* C, int ldc, bool sym, int* d_status) {
+  if (a == 0 || b == 0) return cudaSuccess;
+  SegMap ma{}, mb{};
+  ma.nseg = nsegA;
+  mb.nseg = nsegB;
+  for (int q = 0; q < nsegA; ++q) { ma.start[q] = segA[2 * q]; ma.count[q] = segA[2 * q + 1]; }
+  for (int q = 0; q < nsegB; ++q) { mb.start[q] = segB[2 * q]; mb.count[q] = segB[2 * q + 1]; }
+  int oa = 0, ob = 0;
+  for (int q = 0; q < nsegA; ++q) oa += ma.count[q];
+  for (int q = 0; q < nsegB; ++q) ob += mb.count[q];
+  if (n == 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * ob, oa, st);
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || (lda & 3) || (ldb & 3))
+    return cudaErrorInvalidValue;
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, A, n, a, lda, TM) || !make_map(&mapB, B, n, b, ldb, TN))
+    return cudaErrorNotSupported;
+  const int na = (a + TM - 1) / TM, nb = (b + TN - 1) / TN;
+  int2 tl_host[144];
+  int nt = 0;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j)
+      if (!sym || i <= j) tl_host[nt++] = make_int2(i, j);
+  long long nch = std::max<long long>(1, (152 + nt - 1) / nt);
+  long long maxch = (n + 4 * BK - 1) / (4 * BK);  // at least 4 stages per CTA
+  if (nch > maxch) nch = maxch;
+  long long rpc = (n + nch - 1) / nch;
+  rpc = (rpc + BK - 1) / BK * BK;
+  nch = (n + rpc - 1) / rpc;
+  int2* tiles = al.get<int2>(nt);
+  double* part = al.get<double>((size_t)nt * nch * TM * TN);
+  cudaError_t e = cudaSuccess;
+  if (!tiles || !part) {
+    e = cudaErrorMemoryAllocation;
+  } else {
+    cudaMemcpyAsync(tiles, tl_host, sizeof(int2) * nt, cudaMemcpyHostToDevice, st);
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+      cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    });
+    {
+      ProfScope ps(st, "gram_tc");
+      k_gram_tc<<<(unsigned)(nt * nch), NTH, SMEM_BYTES, st>>>(mapA, mapB, n, tiles, (int)nch, nt,
+                                                               rpc, a, b, part, d_status);
+      note_launch();
+      long long tot = (long long)nt * TM * TN;
+      unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
+      k_gram_tc_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, tiles, a, b, ma, mb, C, ldc,
+                                           sym ? 1 : 0);
+      note_launch();
+    }
+    e = cudaGetLastError();
+  }
+  al.put(tiles);
+  al.put(part);
+  return e;
+}
+
+}  // namespace sc

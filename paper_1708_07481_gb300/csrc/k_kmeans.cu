@@ -195,48 +195,67 @@ __global__ void k_init_cent(int d, int k, const float* __restrict__ E, long long
 
 constexpr int ACH = 64;  // centroids per shared-memory chunk in the assignment
 
+// One row per thread; the row lives in registers (D >= d, D a multiple of 4), the centroids
+// stream through shared memory in chunks of ACH.
+template <int D>
 __global__ void __launch_bounds__(256)
     k_assign(int n, int d, int k, const float* __restrict__ E, long long lde,
              const float* __restrict__ C32, const float* __restrict__ cn,
              const double* __restrict__ C64, int* labels, int* changes, int first, double tie) {
-  extern __shared__ float csm[];  // ACH * d
+  extern __shared__ float csm[];  // ACH * D
   __shared__ int nchg;
   if (threadIdx.x == 0) nchg = 0;
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const float* e = E + (i < n ? i : 0) * lde;
+  float ev[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) ev[q] = (i < n && q < d) ? E[i * lde + q] : 0.f;
   float best = 3.4e38f, second = 3.4e38f;
   int bj = 0;
   for (int j0 = 0; j0 < k; j0 += ACH) {
     int nj = min(ACH, k - j0);
     __syncthreads();
-    for (int q = threadIdx.x; q < nj * d; q += blockDim.x) csm[q] = C32[(long long)j0 * d + q];
+    for (int q = threadIdx.x; q < nj * D; q += blockDim.x) {
+      int jj = q / D, c = q % D;
+      csm[q] = c < d ? C32[(long long)(j0 + jj) * d + c] : 0.f;
+    }
     __syncthreads();
-    if (i < n) {
-      for (int jj = 0; jj < nj; ++jj) {
-        const float* c = csm + jj * d;
-        float dot = 0.f;
-        for (int q = 0; q < d; ++q) dot = fmaf(e[q], c[q], dot);
-        float dist = fmaf(-2.f, dot, cn[j0 + jj]);
-        if (dist < best) {
-          second = best;
-          best = dist;
-          bj = j0 + jj;
-        } else if (dist < second) {
-          second = dist;
-        }
+    for (int jj = 0; jj < nj; ++jj) {
+      const float4* c4 = reinterpret_cast<const float4*>(csm + jj * D);
+      float dot = 0.f;
+#pragma unroll
+      for (int q = 0; q < D / 4; ++q) {
+        float4 cv = c4[q];
+        dot = fmaf(ev[4 * q], cv.x, dot);
+        dot = fmaf(ev[4 * q + 1], cv.y, dot);
+        dot = fmaf(ev[4 * q + 2], cv.z, dot);
+        dot = fmaf(ev[4 * q + 3], cv.w, dot);
+      }
+      float dist = fmaf(-2.f, dot, cn[j0 + jj]);
+      if (dist < best) {
+        second = best;
+        best = dist;
+        bj = j0 + jj;
+      } else if (dist < second) {
+        second = dist;
       }
     }
   }
   if (i < n) {
     if (k > 1 && second - best < (float)tie) {
-      // near tie: decide with direct FP64 distances to the FP64 centroids
+      // near tie: re-decide among the centroids within the margin, with direct FP64
+      // distances ||e - c||^2 to the FP64 centroids (ties -> lowest index)
       double bd = 1e300;
       int bb = 0;
       for (int j = 0; j < k; ++j) {
+        float dot = 0.f;
+        const float* cj = C32 + (long long)j * d;
+        for (int q = 0; q < d; ++q) dot = fmaf(E[i * lde + q], cj[q], dot);
+        float dist = fmaf(-2.f, dot, cn[j]);
+        if (dist - best >= (float)tie) continue;
         const double* c = C64 + (long long)j * d;
         double acc = 0.0;
         for (int q = 0; q < d; ++q) {
-          double df = (double)e[q] - c[q];
+          double df = (double)E[i * lde + q] - c[q];
           acc = fma(df, df, acc);
         }
         if (acc < bd) {
@@ -252,6 +271,21 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   if (threadIdx.x == 0 && nchg) atomicAdd(changes, nchg);
+}
+
+using AssignFn = void (*)(int, int, int, const float*, long long, const float*, const float*,
+                          const double*, int*, int*, int, double);
+
+inline AssignFn assign_for(int d, int* D) {
+  if (d <= 16) { *D = 16; return k_assign<16>; }
+  if (d <= 32) { *D = 32; return k_assign<32>; }
+  if (d <= 48) { *D = 48; return k_assign<48>; }
+  if (d <= 64) { *D = 64; return k_assign<64>; }
+  if (d <= 96) { *D = 96; return k_assign<96>; }
+  if (d <= 128) { *D = 128; return k_assign<128>; }
+  if (d <= 192) { *D = 192; return k_assign<192>; }
+  *D = 512;
+  return k_assign<512>;
 }
 
 // Per-CTA FP64 cluster sums in row order; thread c owns column c (and thread 0 the counts).
@@ -390,10 +424,11 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
   {
     k_init_cent<<<k, 128, 0, st>>>(d, k, E, lde, seeds, C64, C32, cn);
     note_launch();
-    size_t asm_bytes = sizeof(float) * (size_t)ACH * d;
+    int Dp = 0;
+    AssignFn afn = assign_for(d, &Dp);
+    size_t asm_bytes = sizeof(float) * (size_t)ACH * Dp;
     if (asm_bytes > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_assign, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)asm_bytes);
+      e = cudaFuncSetAttribute(afn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_bytes);
       if (e != cudaSuccess) goto out;
     }
     size_t psm = sizeof(double) * (size_t)k * d;
@@ -407,8 +442,10 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
     for (int it = 0; it < iters; ++it) {
       cudaMemsetAsync(changes, 0, sizeof(int), st);
       ProfScope ps(st, "kmeans_assign");
-      k_assign<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes,
-                                            it == 0, 1e-4);
+      // FP32 distances of unit rows to centroids of norm <= 1 carry at most ~2.5e-7 d of
+      // rounding each; margins below twice that (plus slack) are re-decided in FP64
+      afn<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes, it == 0,
+                                       2e-5 + 5e-7 * d);
       note_launch();
       if (it > 0) {
         int h = 0;

@@ -43,7 +43,10 @@ template <> struct Vec<double> {
 
 constexpr int MAXC = 4;  // chunks per lane: TL=32 x 4 chunks x 4 floats = 512 columns
 
-template <typename T, int TL>
+// NC = 16-byte chunks per lane (compile time).  Neighbours are processed four at a time with
+// all of their row loads issued before the first accumulation, so each lane keeps 4 * NC
+// gathers in flight instead of one.
+template <typename T, int TL, int NC>
 __global__ void __launch_bounds__(256)
     k_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci,
            const float* __restrict__ val, const T* __restrict__ deg, const T* __restrict__ V,
@@ -54,43 +57,66 @@ __global__ void __launch_bounds__(256)
                                     : (((1u << TL) - 1u) << ((threadIdx.x & 31) / TL * TL));
   long long team = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / TL;
   long long nteams = ((long long)gridDim.x * blockDim.x) / TL;
-  const int nc = (nvec + TL - 1) / TL;
+  bool act[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) act[c] = lane + c * TL < nvec;
   for (long long row = team; row < n; row += nteams) {
-    V4 acc[MAXC];
+    V4 acc[NC];
 #pragma unroll
-    for (int c = 0; c < MAXC; ++c) acc[c] = Vec<T>::zero();
-    int s = rp[row], e = rp[row + 1];
+    for (int c = 0; c < NC; ++c) acc[c] = Vec<T>::zero();
+    const int s = rp[row], e = rp[row + 1];
     for (int base = s; base < e; base += TL) {
-      int my = base + lane < e ? ci[base + lane] : -1;
-      float mw = (val && base + lane < e) ? val[base + lane] : 1.0f;
-      int cnt = min(TL, e - base);
-      for (int t = 0; t < cnt; ++t) {
-        int j = __shfl_sync(gmask, my, t, TL);
-        T w = (T)__shfl_sync(gmask, mw, t, TL);
-        const V4* vr = reinterpret_cast<const V4*>(V + (long long)j * ldv);
+      const int my = base + lane < e ? ci[base + lane] : 0;
+      const float mw = (val && base + lane < e) ? val[base + lane] : 1.0f;
+      const int cnt = min(TL, e - base);
+      int t = 0;
+      for (; t + 4 <= cnt; t += 4) {
+        int j[4];
+        T w[4];
 #pragma unroll
-        for (int c = 0; c < MAXC; ++c) {
-          int q = lane + c * TL;
-          if (c < nc && q < nvec) {
-            V4 x = __ldg(vr + q);
-            if (val) Vec<T>::fma(acc[c], w, x);
+        for (int u = 0; u < 4; ++u) {
+          j[u] = __shfl_sync(gmask, my, t + u, TL);
+          w[u] = (T)__shfl_sync(gmask, mw, t + u, TL);
+        }
+        V4 x[4][NC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const V4* vr = reinterpret_cast<const V4*>(V + (long long)j[u] * ldv);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) x[u][c] = act[c] ? __ldg(vr + lane + c * TL) : Vec<T>::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (val) Vec<T>::fma(acc[c], w[u], x[u][c]);
+            else Vec<T>::add(acc[c], x[u][c]);
+          }
+      }
+      for (; t < cnt; ++t) {
+        const int jj = __shfl_sync(gmask, my, t, TL);
+        const T ww = (T)__shfl_sync(gmask, mw, t, TL);
+        const V4* vr = reinterpret_cast<const V4*>(V + (long long)jj * ldv);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if (act[c]) {
+            V4 x = __ldg(vr + lane + c * TL);
+            if (val) Vec<T>::fma(acc[c], ww, x);
             else Vec<T>::add(acc[c], x);
           }
         }
       }
     }
-    T d = deg[row];
+    const T d = deg[row];
     const V4* vi = reinterpret_cast<const V4*>(V + row * ldv);
     V4* yo = reinterpret_cast<V4*>(Y + row * ldy);
 #pragma unroll
-    for (int c = 0; c < MAXC; ++c) {
-      int q = lane + c * TL;
-      if (c < nc && q < nvec) yo[q] = Vec<T>::lap(d, vi[q], acc[c]);
-    }
+    for (int c = 0; c < NC; ++c)
+      if (act[c]) yo[lane + c * TL] = Vec<T>::lap(d, vi[lane + c * TL], acc[c]);
   }
 }
 
-template <typename T, int TL>
+template <typename T, int TL, int NC>
 cudaError_t launch(cudaStream_t st, const CsrDev& g, const T* deg, const T* V, long long ldv,
                    T* Y, long long ldy, int nvec) {
   long long teams = g.n;
@@ -100,8 +126,8 @@ cudaError_t launch(cudaStream_t st, const CsrDev& g, const T* deg, const T* V, l
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   ProfScope ps(st, "spmm");
-  k_spmm<T, TL><<<(unsigned)blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, deg, V, ldv,
-                                                 Y, ldy, nvec);
+  k_spmm<T, TL, NC><<<(unsigned)blocks, 256, 0, st>>>(g.n, g.row_ptr, g.col_idx, g.val, deg, V,
+                                                     ldv, Y, ldy, nvec);
   note_launch();
   return cudaGetLastError();
 }
@@ -119,10 +145,13 @@ cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv
   if constexpr (sizeof(T) == 4) deg = (const T*)g.degf;
   else deg = (const T*)g.degd;
   if (g.n == 0) return cudaSuccess;
-  if (nvec <= 4) return launch<T, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 8) return launch<T, 8>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 16) return launch<T, 16>(st, g, deg, V, ldv, Y, ldy, nvec);
-  return launch<T, 32>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 4) return launch<T, 4, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 8) return launch<T, 8, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 16) return launch<T, 16, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 32) return launch<T, 32, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 64) return launch<T, 32, 2>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (nvec <= 96) return launch<T, 32, 3>(st, g, deg, V, ldv, Y, ldy, nvec);
+  return launch<T, 32, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
 }
 
 template cudaError_t spmm_lap<float>(cudaStream_t, const CsrDev&, const float*, long long,

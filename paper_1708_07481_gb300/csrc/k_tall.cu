@@ -7,28 +7,39 @@
 namespace sc {
 namespace {
 
-constexpr int TR = 64;  // rows per CTA
-constexpr int TC = 64;  // output columns per CTA
-constexpr int KB = 16;  // inner-dimension stage
 
-// out (n x b) = beta * Cin + A (n x a) * W (a x b).  256 threads, 4 x 4 micro-tile each.
+// out (n x b) = beta * Cin + A (n x a) * W (a x b).
+// A CTA owns RT = 128 rows and a column slice of CB = 64 outputs; W streams through shared
+// memory in chunks of KC rows, the A rows of the chunk are staged once per CTA (transposed,
+// k-major, so a thread's 4 rows are one 16-byte read).  256 threads = 32 row groups x 8
+// column groups; a thread keeps a 4-row x 8-column register tile (rows 4 rg .. 4 rg + 3,
+// columns 8 cg .. 8 cg + 7) and reads 3 vectors of shared memory per k for 32 FMAs.
+constexpr int RT = 128, CB = 64;
+
+template <typename T> struct V4T;
+template <> struct V4T<float> { using type = float4; };
+template <> struct V4T<double> { using type = double4; };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_tall_gemm(long long n, Cat3<T> A, int a, const T* __restrict__ W, int ldw, int b,
                 T* __restrict__ out, long long ldo, const T* Cin, long long ldc, T beta) {
-  __shared__ __align__(16) T As[KB][TR + 4];
-  __shared__ __align__(16) T Ws[KB][TC];
-  __shared__ int mblk[KB], mlc[KB];
-  const long long r0 = (long long)blockIdx.x * TR;
-  const int c0 = blockIdx.y * TC;
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  T acc[4][4];
+  constexpr int KC = sizeof(T) == 4 ? 32 : 16;
+  using V4 = typename V4T<T>::type;
+  __shared__ __align__(16) T As[KC][RT];
+  __shared__ __align__(16) T Ws[KC][CB];
+  __shared__ int mblk[KC], mlc[KC];
+  const long long r0 = (long long)blockIdx.x * RT;
+  const int c0 = blockIdx.y * CB;
+  const int rg = threadIdx.x / 8;  // rows 4 rg .. 4 rg + 3
+  const int cg = threadIdx.x % 8;  // cols 8 cg .. 8 cg + 7
+  T acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-  for (int k0 = 0; k0 < a; k0 += KB) {
-    if (threadIdx.x < KB) {
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+  for (int k0 = 0; k0 < a; k0 += KC) {
+    if (threadIdx.x < KC) {
       int c = k0 + threadIdx.x, blk = -1, lc = 0, s = 0;
       for (int q = 0; q < A.nblk; ++q) {
         if (c >= s && c < s + A.c[q]) {
@@ -41,52 +52,46 @@ __global__ void __launch_bounds__(256)
       mlc[threadIdx.x] = lc;
     }
     __syncthreads();
-    // A tile: 64 rows x 16 cols; thread -> (row = t / 4, cols (t % 4) * 4 .. + 4)
     {
-      int lr = threadIdx.x / 4, lk = (threadIdx.x % 4) * 4;
-      long long row = r0 + lr;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int kk = lk + q;
-        int blk = mblk[kk];
-        T v = 0;
-        if (row < n && blk >= 0) v = A.p[blk][row * A.ld[blk] + mlc[kk]];
-        As[kk][lr] = v;
+      int kk = threadIdx.x % KC;
+      int blk = mblk[kk];
+      const T* p = blk >= 0 ? A.p[blk] : nullptr;
+      long long ld = blk >= 0 ? A.ld[blk] : 0;
+      int lc = mlc[kk];
+#pragma unroll 4
+      for (int rr = threadIdx.x / KC; rr < RT; rr += 256 / KC) {
+        long long row = r0 + rr;
+        As[kk][rr] = (blk >= 0 && row < n) ? p[row * ld + lc] : (T)0;
       }
     }
-    // W tile: 16 x 64; thread -> (k = t / 16, cols (t % 16) * 4 .. + 4)
-    {
-      int lk = threadIdx.x / 16, lc = (threadIdx.x % 16) * 4;
-      int kk = k0 + lk;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int cc = c0 + lc + q;
-        Ws[lk][lc + q] = (kk < a && cc < b) ? W[(long long)kk * ldw + cc] : (T)0;
-      }
+    for (int q = threadIdx.x; q < KC * CB; q += 256) {
+      int kk = q / CB, cc = q % CB;
+      int gk = k0 + kk, gc = c0 + cc;
+      Ws[kk][cc] = (gk < a && gc < b) ? W[(long long)gk * ldw + gc] : (T)0;
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KB; ++k) {
-      T av[4], wv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        av[i] = As[k][ty * 4 + i];
-        wv[i] = Ws[k][tx * 4 + i];
-      }
+    const int kmax = min(KC, a - k0);
+#pragma unroll 4
+    for (int k = 0; k < kmax; ++k) {
+      const V4 av = *reinterpret_cast<const V4*>(&As[k][4 * rg]);
+      const V4 w0 = *reinterpret_cast<const V4*>(&Ws[k][8 * cg]);
+      const V4 w1 = *reinterpret_cast<const V4*>(&Ws[k][8 * cg + 4]);
+      const T ar[4] = {av.x, av.y, av.z, av.w};
+      const T wr[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], wv[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(ar[i], wr[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    long long row = r0 + ty * 4 + i;
+    long long row = r0 + 4 * rg + i;
     if (row >= n) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int cc = c0 + tx * 4 + j;
+    for (int j = 0; j < 8; ++j) {
+      int cc = c0 + 8 * cg + j;
       if (cc >= b) continue;
       T v = acc[i][j];
       if (Cin) v = fma(beta, Cin[row * ldc + cc], v);
@@ -225,7 +230,7 @@ cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W
                       int b, T* out, long long ldo, const T* Cin, long long ldc, T beta) {
   int a = A.cols();
   if (n == 0 || b == 0) return cudaSuccess;
-  dim3 grid((unsigned)((n + TR - 1) / TR), (unsigned)((b + TC - 1) / TC));
+  dim3 grid((unsigned)((n + RT - 1) / RT), (unsigned)((b + CB - 1) / CB));
   ProfScope ps(st, "tall_gemm");
   k_tall_gemm<T><<<grid, 256, 0, st>>>(n, A, a, W, ldw, b, out, ldo, Cin, ldc, beta);
   note_launch();

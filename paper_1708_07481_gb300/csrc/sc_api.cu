@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -285,6 +286,18 @@ static int read_status(sc_ctx* c, int* out) {
   return SC_OK;
 }
 
+// Status word plus the failing column a Cholesky kernel reported (-1 when none).
+static int read_status_col(sc_ctx* c, int* out, const int* dfail, int* col) {
+  int h[2] = {0, -1};
+  CK(cudaMemcpyAsync(&h[0], c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status");
+  CK(cudaMemcpyAsync(&h[1], dfail, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status");
+  CK(cudaStreamSynchronize(c->stream), "status");
+  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "status");
+  *out = h[0];
+  *col = h[1];
+  return SC_OK;
+}
+
 // Copy an edge list to the device (or use it in place) and build a CSR.
 static int edges_to_csr(sc_ctx* c, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                         const float* w, int algebraic, int on_device, CsrDev* out) {
@@ -455,60 +468,120 @@ struct Lob {
   }
 };
 
-// Cholesky-QR of block V (n x kc, stride kp) into out; optionally applies the same
-// transform to LV (into lout).  Returns ST_CHOL_FAIL on breakdown (nothing written).
+struct Seg {
+  int start, count;
+};
+
+// C (compact FP64) = A' B over the listed column segments of two strided blocks.  FP32 with
+// tensor cores selected -> tcgen05 kernel; otherwise the CUDA-core kernel.
 template <typename T>
-int cholqr_step(Lob<T>& L, const T* V, int kc, T* out, double* G, T* Tm, const T* LV, T* lout,
-                int* status_out) {
+cudaError_t gram_seg(Lob<T>& L, const T* A, long long lda, std::initializer_list<Seg> sa,
+                     const T* B, long long ldb, std::initializer_list<Seg> sb, double* C,
+                     int ldc, bool sym) {
+  std::vector<Seg> va(sa), vb(sb);
+  if constexpr (sizeof(T) == 4) {
+    if (L.use_tc) {
+      int pa[6], pb[6], spa = 0, spb = 0;
+      for (size_t q = 0; q < va.size(); ++q) {
+        pa[2 * q] = va[q].start;
+        pa[2 * q + 1] = va[q].count;
+        spa = std::max(spa, va[q].start + va[q].count);
+      }
+      for (size_t q = 0; q < vb.size(); ++q) {
+        pb[2 * q] = vb[q].start;
+        pb[2 * q + 1] = vb[q].count;
+        spb = std::max(spb, vb[q].start + vb[q].count);
+      }
+      return gram_tc(L.c->stream, L.al, L.n, (const float*)A, lda, spa, pa, (int)va.size(),
+                     (const float*)B, ldb, spb, pb, (int)vb.size(), C, ldc, sym, L.c->d_status);
+    }
+  }
+  Cat3<T> ca{}, cb{};
+  ca.nblk = (int)va.size();
+  cb.nblk = (int)vb.size();
+  for (size_t q = 0; q < va.size(); ++q) {
+    ca.p[q] = A + va[q].start;
+    ca.ld[q] = lda;
+    ca.c[q] = va[q].count;
+  }
+  for (size_t q = 0; q < vb.size(); ++q) {
+    cb.p[q] = B + vb[q].start;
+    cb.ld[q] = ldb;
+    cb.c[q] = vb[q].count;
+  }
+  return gram<T>(L.c->stream, L.al, L.n, ca, cb, C, ldc, sym, 0);
+}
+
+// Cholesky-QR of block V (n x kc, stride ldv) into out (stride ldo); optionally applies the
+// same transform to LV (into lout).  Reports ST_CHOL_FAIL in *status_out (nothing written).
+template <typename T>
+int cholqr_step(Lob<T>& L, const T* V, long long ldv, int kc, T* out, long long ldo, double* G,
+                T* Tm, const T* LV, long long ldlv, T* lout, long long ldlo, int* status_out) {
   sc_ctx* c = L.c;
   cudaStream_t st = c->stream;
-  CK(gram<T>(st, L.al, L.n, cat<T>(V, L.kp, kc), cat<T>(V, L.kp, kc), G, kc, true, L.use_tc), "gram");
+  CK(gram_seg<T>(L, V, ldv, {{0, kc}}, V, ldv, {{0, kc}}, G, kc, true), "gram");
   CK(chol_inv<T>(st, L.al, kc, G, kc, Tm, c->d_status, L.pivot_tol), "chol");
   int hs = 0;
   int rc = read_status(c, &hs);
   if (rc != SC_OK) return rc;
   *status_out = hs;
+  if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
   if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return SC_OK;
-  CK(tall_gemm<T>(st, L.n, cat<T>(V, L.kp, kc), Tm, kc, kc, out, L.kp, nullptr, 0, (T)0), "tall");
-  if (LV) CK(tall_gemm<T>(st, L.n, cat<T>(LV, L.kp, kc), Tm, kc, kc, lout, L.kp, nullptr, 0, (T)0), "tall");
+  CK(tall_gemm<T>(st, L.n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0), "tall");
+  if (LV) CK(tall_gemm<T>(st, L.n, cat<T>(LV, ldlv, kc), Tm, kc, kc, lout, ldlo, nullptr, 0, (T)0), "tall");
   return SC_OK;
 }
 
+// Block layout: S = [X | R | P] and LS = [LX | LR | LP], each n x 3kp row-major (column slots
+// of kp = K rounded up to 16 bytes), so every Gram operand is one strided matrix.
 template <typename T>
 int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const float* X0,
                int32_t x0_rows, float* X_out, sc_eig_info* info) {
   const int n = g->csr.n;
   const int W = 16 / sizeof(T);
-  Lob<T> L{c, alloc_of(c), g, n, K, (K + W - 1) / W * W, o->prec == SC_PREC_MIXED ? 1 : 0,
+  const int kp = (K + W - 1) / W * W;
+  const long long ld3 = 3LL * kp;
+  Lob<T> L{c, alloc_of(c), g, n, K, kp, (sizeof(T) == 4 && o->prec == SC_PREC_MIXED) ? 1 : 0,
            sizeof(T) == 4 ? 1e-8 : 1e-14, {}, {}};
   cudaStream_t st = c->stream;
-  const int kp = L.kp;
   const int mmax = 3 * K;
-  T* X = L.get_block();
-  T* LX = L.get_block();
-  T* R = L.get_block();
-  T* P = L.get_block();
-  T* LP = L.get_block();
-  T* Xn = L.get_block();
-  T* LXn = L.get_block();
-  T* Pn = L.get_block();
-  T* LPn = L.get_block();
-  T* A1 = L.get_block();
-  T* A2 = L.get_block();
-  T* LRa = L.get_block();
-  T* B1 = L.get_block();
-  T* B2 = L.get_block();
-  T* C1 = L.get_block();
-  T* C2 = L.get_block();
+  auto big = [&]() {
+    T* p = L.al.template get<T>((size_t)n * ld3);
+    if (p) {
+      L.pool.push_back(p);
+      cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n * ld3, st);
+    }
+    return p;
+  };
+  T* S = big();
+  T* LS = big();
+  T* S2 = big();
+  T* LS2 = big();
+  T* T1 = L.get_block();
+  auto wide = [&]() {
+    T* p = L.al.template get<T>((size_t)n * 2 * kp);
+    if (p) {
+      L.pool.push_back(p);
+      cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n * 2 * kp, st);
+    }
+    return p;
+  };
+  T* W1 = wide();
+  T* W2 = wide();
+  T* Q1 = wide();
+  T* LQ1 = wide();
   double* G = L.template get_small<double>((size_t)mmax * mmax);
   T* Tm = L.template get_small<T>((size_t)mmax * mmax);
   T* Y = L.template get_small<T>((size_t)mmax * K);
   double* theta = L.template get_small<double>(K);
   double* rho2 = L.template get_small<double>(K);
   int* dcols = L.template get_small<int>(K);
-  if (!X || !LX || !R || !P || !LP || !Xn || !LXn || !Pn || !LPn || !A1 || !A2 || !LRa || !B1 ||
-      !B2 || !C1 || !C2 || !G || !Tm || !Y || !theta || !rho2 || !dcols)
+  int* dfail = L.template get_small<int>(1);
+  if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !Y || !theta ||
+      !rho2 || !dcols || !dfail)
     return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
+  auto X = [&]() { return S; };
+  auto LX = [&]() { return LS; };
 
   // ---- start block --------------------------------------------------------------------
   {
@@ -524,49 +597,46 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
       dev_src = true;
     }
     if (!src) {
-      CK(gauss_block<T>(st, n, K, stream_key(o->seed, 1, 0), X, kp), "x0");
-      rows = 0;
-    }
-    float* stage = L.template get_small<float>((size_t)rows * K + 1);
-    if (!stage) return fail(c, SC_ENOMEM, "sc_lobpcg: staging");
-    if (rows > 0) {
-    CK(cudaMemcpyAsync(stage, src, sizeof(float) * (size_t)rows * K,
-                       dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "x0");
-    if (sizeof(T) == 4) {
-      CK(cudaMemcpy2DAsync(X, sizeof(T) * kp, stage, sizeof(float) * K, sizeof(float) * K, rows,
-                           cudaMemcpyDeviceToDevice, st), "x0");
+      CK(gauss_block<T>(st, n, K, stream_key(o->seed, 1, 0), S, ld3), "x0");
+    } else if (sizeof(T) == 4) {
+      CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, src, sizeof(float) * K, sizeof(float) * K, rows,
+                           dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "x0");
     } else {
-      // widen float -> double through the cast kernel (as a rows x K FP64 view is not
-      // available, stage through a double buffer on the host side)
       std::vector<float> hf((size_t)rows * K);
-      CK(cudaMemcpyAsync(hf.data(), stage, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, st), "x0");
-      CK(cudaStreamSynchronize(st), "x0");
+      if (dev_src) {
+        CK(cudaMemcpyAsync(hf.data(), src, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, st), "x0");
+        CK(cudaStreamSynchronize(st), "x0");
+      } else {
+        std::memcpy(hf.data(), src, sizeof(float) * hf.size());
+      }
       std::vector<double> hd(hf.begin(), hf.end());
-      CK(cudaMemcpy2DAsync(X, sizeof(T) * kp, hd.data(), sizeof(double) * K, sizeof(double) * K,
+      CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, hd.data(), sizeof(double) * K, sizeof(double) * K,
                            rows, cudaMemcpyHostToDevice, st), "x0");
-      CK(cudaStreamSynchronize(st), "x0");
-    }
     }
     CK(cudaStreamSynchronize(st), "x0");
   }
   CK(cudaEventRecord(c->ev0, st), "event");
   const uint64_t l0 = launches_total();
   int hs = 0;
-  // X <- CholQR(CholQR(X0))
-  for (int pass = 0; pass < 2; ++pass) {
-    int rc = cholqr_step<T>(L, X, K, Xn, G, Tm, nullptr, nullptr, &hs);
+  // X <- CholQR(CholQR(X0)):  X slot -> T1 -> X slot
+  {
+    int rc = cholqr_step<T>(L, S, ld3, K, T1, kp, G, Tm, nullptr, 0, nullptr, 0, &hs);
     if (rc != SC_OK) return rc;
     if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
-    std::swap(X, Xn);
+    rc = cholqr_step<T>(L, T1, kp, K, S, ld3, G, Tm, nullptr, 0, nullptr, 0, &hs);
+    if (rc != SC_OK) return rc;
+    if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
   }
-  CK(spmm_lap<T>(st, g->csr, X, kp, LX, kp, K), "spmm");
-  CK(gram<T>(st, L.al, n, cat<T>(X, kp, K), cat<T>(LX, kp, K), G, K, false, L.use_tc), "gram");
+  CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
+  CK(gram_seg<T>(L, S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, false), "gram");
   CK(rr_eig<T>(st, L.al, K, K, G, K, theta, Y, c->d_status), "rr");
-  CK(tall_gemm<T>(st, n, cat<T>(X, kp, K), Y, K, K, Xn, kp, nullptr, 0, (T)0), "tall");
-  CK(tall_gemm<T>(st, n, cat<T>(LX, kp, K), Y, K, K, LXn, kp, nullptr, 0, (T)0), "tall");
-  std::swap(X, Xn);
-  std::swap(LX, LXn);
-  CK(residual<T>(st, L.al, n, K, X, LX, kp, theta, R, rho2), "residual");
+  CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0), "tall");
+  CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0), "tall");
+  std::swap(S, S2);
+  std::swap(LS, LS2);
+  CK(residual<T>(st, L.al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
+  (void)X;
+  (void)LX;
 
   std::vector<double> hrho(K), hth(K);
   bool haveP = false;
@@ -591,83 +661,118 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
     }
     const int ka = (int)act.size();
     const bool all = ka == K;
-    // R_a (into A1), projected against X, then CholQR twice
-    T* Ra = A1;
-    if (all) {
-      CK(cudaMemcpyAsync(A1, R, sizeof(T) * (size_t)n * kp, cudaMemcpyDeviceToDevice, st), "copy");
-    } else {
+    T* Rslot = S + kp;
+    T* LRslot = LS + kp;
+    T* Pslot = S + 2 * kp;
+    T* LPslot = LS + 2 * kp;
+    // Working copies of the active R and P columns.  With every column active they are the
+    // S slots themselves ([R P] = columns kp.. and 2kp.. of S); otherwise the active columns
+    // are gathered into W1 = [R_a | P_a] (n x 2kp) and W2 = [. | LP_a].
+    T* WR = Rslot;
+    T* WP = Pslot;
+    T* WLP = LPslot;
+    long long ldw = ld3;
+    int offP = kp;  // column offset of P in the working block (relative to WR)
+    if (!all) {
       CK(cudaMemcpyAsync(dcols, act.data(), sizeof(int) * ka, cudaMemcpyHostToDevice, st), "cols");
-      CK(gather_cols<T>(st, n, R, kp, A1, kp, dcols, ka), "gather");
+      CK(gather_cols<T>(st, n, Rslot, ld3, W1, 2 * kp, dcols, ka), "gather");
+      WR = W1;
+      WP = W1 + kp;
+      ldw = 2 * kp;
+      if (haveP) {
+        CK(gather_cols<T>(st, n, Pslot, ld3, WP, ldw, dcols, ka), "gather");
+        CK(gather_cols<T>(st, n, LPslot, ld3, W2 + kp, ldw, dcols, ka), "gather");
+        WLP = W2 + kp;
+      }
     }
-    CK(gram<T>(st, L.al, n, cat<T>(X, kp, K), cat<T>(Ra, kp, ka), G, ka, false, L.use_tc), "gram");
-    CK(cast_mat<T>(st, K, ka, G, ka, Tm, ka, -1.0), "cast");
-    CK(tall_gemm<T>(st, n, cat<T>(X, kp, K), Tm, ka, ka, Ra, kp, Ra, kp, (T)1), "tall");
-    T* Rq = A2;
-    for (int pass = 0; pass < 2; ++pass) {
-      int rc = cholqr_step<T>(L, Ra, ka, Rq, G, Tm, nullptr, nullptr, &hs);
-      if (rc != SC_OK) return rc;
-      if (hs & (ST_CHOL_FAIL | ST_NONFINITE))
-        return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-      std::swap(Ra, Rq);
-    }
-    CK(spmm_lap<T>(st, g->csr, Ra, kp, LRa, kp, ka), "spmm");
-    // P_a, LP_a: project against [X R_a], CholQR twice (dropped on breakdown)
-    T *Pa = nullptr, *LPa = nullptr;
+    const int w = haveP ? 2 * ka : ka;
+    // (1) project [R_a P_a] against X: F = X' [R_a P_a]; R_a -= X F_R, P_a -= X F_P, LP_a -= LX F_P
+    if (haveP)
+      CK(gram_seg<T>(L, S, ld3, {{0, K}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, false), "gram");
+    else
+      CK(gram_seg<T>(L, S, ld3, {{0, K}}, WR, ldw, {{0, ka}}, G, w, false), "gram");
+    CK(cast_mat<T>(st, K, w, G, w, Tm, w, -1.0), "cast");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, w, ka, WR, ldw, WR, ldw, (T)1), "tall");
     if (haveP) {
-      T* pa = B1;
-      T* lpa = C1;
-      if (all) {
-        CK(cudaMemcpyAsync(pa, P, sizeof(T) * (size_t)n * kp, cudaMemcpyDeviceToDevice, st), "copy");
-        CK(cudaMemcpyAsync(lpa, LP, sizeof(T) * (size_t)n * kp, cudaMemcpyDeviceToDevice, st), "copy");
-      } else {
-        CK(gather_cols<T>(st, n, P, kp, pa, kp, dcols, ka), "gather");
-        CK(gather_cols<T>(st, n, LP, kp, lpa, kp, dcols, ka), "gather");
-      }
-      const int kxr = K + ka;
-      CK(gram<T>(st, L.al, n, cat<T>(X, kp, K, Ra, kp, ka), cat<T>(pa, kp, ka), G, ka, false, L.use_tc), "gram");
-      CK(cast_mat<T>(st, kxr, ka, G, ka, Tm, ka, -1.0), "cast");
-      CK(tall_gemm<T>(st, n, cat<T>(X, kp, K, Ra, kp, ka), Tm, ka, ka, pa, kp, pa, kp, (T)1), "tall");
-      CK(tall_gemm<T>(st, n, cat<T>(LX, kp, K, LRa, kp, ka), Tm, ka, ka, lpa, kp, lpa, kp, (T)1), "tall");
-      T* pq = B2;
-      T* lpq = C2;
-      bool ok = true;
-      for (int pass = 0; pass < 2 && ok; ++pass) {
-        int rc = cholqr_step<T>(L, pa, ka, pq, G, Tm, lpa, lpq, &hs);
+      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm + ka, w, ka, WP, ldw, WP, ldw, (T)1), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm + ka, w, ka, WLP, ldw, WLP, ldw, (T)1), "tall");
+    }
+    // (2) LR_a = L R_a (the one SpMM of the pass), into the LR slot / working block
+    T* WLR = all ? LRslot : W2;
+    CK(spmm_lap<T>(st, g->csr, WR, ldw, WLR, ldw, ka), "spmm");
+    // (3) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R as well),
+    //     with [LR_a LP_a] transformed alike; a breakdown inside the P columns drops P.
+    bool useP = haveP;
+    {
+      int wq = w;
+      // pass 1: working block -> Q1 = [Q_R | Q_P] (n x 2kp, contiguous columns)
+      Cat3<T> Vw = useP ? cat<T>(WR, ldw, ka, WP, ldw, ka) : cat<T>(WR, ldw, ka);
+      Cat3<T> LVw = useP ? cat<T>(WLR, ldw, ka, WLP, ldw, ka) : cat<T>(WLR, ldw, ka);
+      if (useP)
+        CK(gram_seg<T>(L, WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
+      else
+        CK(gram_seg<T>(L, WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
+      CK(cudaMemsetAsync(dfail, 0xff, sizeof(int), st), "fail");
+      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail), "chol");
+      int fc = -1;
+      int rc = read_status_col(c, &hs, dfail, &fc);
+      if (rc != SC_OK) return rc;
+      if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
+      if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) {
+        if (!useP || fc < ka) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
+        useP = false;  // P lies in span{X, R}: drop it for this pass (R part of G is intact)
+        wq = ka;
+        Vw = cat<T>(WR, ldw, ka);
+        LVw = cat<T>(WLR, ldw, ka);
+        CK(chol_inv<T>(st, L.al, ka, G, w, Tm, c->d_status, L.pivot_tol, dfail), "chol");
+        rc = read_status_col(c, &hs, dfail, &fc);
         if (rc != SC_OK) return rc;
-        if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) {
-          ok = false;
-          break;
-        }
-        std::swap(pa, pq);
-        std::swap(lpa, lpq);
+        if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
       }
-      if (ok) {
-        Pa = pa;
-        LPa = lpa;
-      } else {
-        ++fallbacks;
+      CK(tall_gemm<T>(st, n, Vw, Tm, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
+      CK(tall_gemm<T>(st, n, LVw, Tm, wq, wq, LQ1, 2 * kp, nullptr, 0, (T)0), "tall");
+      // pass 2: Q1 -> S / LS slots (R part from the Q_R columns only: Tm is upper triangular)
+      CK(gram_seg<T>(L, Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
+      CK(cudaMemsetAsync(dfail, 0xff, sizeof(int), st), "fail");
+      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail), "chol");
+      rc = read_status_col(c, &hs, dfail, &fc);
+      if (rc != SC_OK) return rc;
+      if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) {
+        if (!useP || fc < ka) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
+        useP = false;
+        wq = ka;
+        CK(chol_inv<T>(st, L.al, ka, G, 2 * ka, Tm, c->d_status, L.pivot_tol, dfail), "chol");
+        rc = read_status_col(c, &hs, dfail, &fc);
+        if (rc != SC_OK) return rc;
+        if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
       }
+      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), Tm, wq, ka, Rslot, ld3, nullptr, 0, (T)0), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, ka), Tm, wq, ka, LRslot, ld3, nullptr, 0, (T)0), "tall");
+      if (useP) {
+        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), Tm + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0), "tall");
+        CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, wq), Tm + ka, wq, ka, LPslot, ld3, nullptr, 0, (T)0), "tall");
+      }
+      if (haveP && !useP) ++fallbacks;
     }
     // Rayleigh-Ritz on S = [X R_a P_a]
-    const int m = K + ka + (Pa ? ka : 0);
-    Cat3<T> S = Pa ? cat<T>(X, kp, K, Ra, kp, ka, Pa, kp, ka) : cat<T>(X, kp, K, Ra, kp, ka);
-    Cat3<T> LS = Pa ? cat<T>(LX, kp, K, LRa, kp, ka, LPa, kp, ka) : cat<T>(LX, kp, K, LRa, kp, ka);
-    CK(gram<T>(st, L.al, n, S, LS, G, m, false, L.use_tc), "gram");
+    const int m = K + ka + (useP ? ka : 0);
+    if (useP)
+      CK(gram_seg<T>(L, S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, false), "gram");
+    else
+      CK(gram_seg<T>(L, S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, false), "gram");
     CK(rr_eig<T>(st, L.al, m, K, G, m, theta, Y, c->d_status), "rr");
-    // update: P = [R_a P_a] Y_RP, X = X Y_X + P (and the L-images alike), R = LX - X theta
+    // update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike), R = LX - X theta
     const T* Yrp = Y + (size_t)K * K;
-    Cat3<T> RP = Pa ? cat<T>(Ra, kp, ka, Pa, kp, ka) : cat<T>(Ra, kp, ka);
-    Cat3<T> LRP = Pa ? cat<T>(LRa, kp, ka, LPa, kp, ka) : cat<T>(LRa, kp, ka);
-    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, Pn, kp, nullptr, 0, (T)0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(X, kp, K), Y, K, K, Xn, kp, Pn, kp, (T)1), "tall");
-    CK(tall_gemm<T>(st, n, LRP, Yrp, K, K, LPn, kp, nullptr, 0, (T)0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(LX, kp, K), Y, K, K, LXn, kp, LPn, kp, (T)1), "tall");
-    std::swap(X, Xn);
-    std::swap(LX, LXn);
-    std::swap(P, Pn);
-    std::swap(LP, LPn);
+    Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
+    Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);
+    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1), "tall");
+    CK(tall_gemm<T>(st, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1), "tall");
+    std::swap(S, S2);
+    std::swap(LS, LS2);
     haveP = true;
-    CK(residual<T>(st, L.al, n, K, X, LX, kp, theta, R, rho2), "residual");
+    CK(residual<T>(st, L.al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
     ++done;
   }
   CK(cudaEventRecord(c->ev1, st), "event");
@@ -675,6 +780,7 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
   int st_final = 0;
   int rc = read_status(c, &st_final);
   if (rc != SC_OK) return rc;
+  if (st_final & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
   if (st_final & ST_NONFINITE) return fail(c, SC_EBREAKDOWN, "non-finite values in Rayleigh-Ritz");
   CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
   CK(cudaMemcpyAsync(hth.data(), theta, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
@@ -686,11 +792,11 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
   }
   if (g->X) {
     if (sizeof(T) == 4) {
-      CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, X, sizeof(T) * kp, sizeof(float) * K, n,
+      CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
                            cudaMemcpyDeviceToDevice, st), "resident");
     } else {
       std::vector<double> hd((size_t)n * K);
-      CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, X, sizeof(T) * kp, sizeof(double) * K, n,
+      CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, S, sizeof(T) * ld3, sizeof(double) * K, n,
                            cudaMemcpyDeviceToHost, st), "resident");
       CK(cudaStreamSynchronize(st), "resident");
       std::vector<float> hf(hd.begin(), hd.end());
@@ -700,7 +806,7 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
     }
   }
   if (X_out && sizeof(T) == 4) {
-    CK(cudaMemcpy2DAsync(X_out, sizeof(float) * K, X, sizeof(T) * kp, sizeof(float) * K, n,
+    CK(cudaMemcpy2DAsync(X_out, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
                          cudaMemcpyDeviceToHost, st), "xout");
   }
   CK(cudaStreamSynchronize(st), "sync");
@@ -903,13 +1009,26 @@ static int gram_t(sc_ctx* c, int prec, int64_t n, int a, int b, const T* A, int6
     CK(cudaMemcpy2DAsync(dA, sizeof(T) * ap, A, sizeof(T) * lda, sizeof(T) * a, n, kin, c->stream), "gram");
     CK(cudaMemcpy2DAsync(dB, sizeof(T) * bp, B, sizeof(T) * ldb, sizeof(T) * b, n, kin, c->stream), "gram");
   }
-  CK(gram<T>(c->stream, al, n, cat<T>(dA, ap, a), cat<T>(dB, bp, b), dC, b, false,
-             prec == SC_PREC_MIXED ? 1 : 0), "gram");
+  if constexpr (sizeof(T) == 4) {
+    if (prec == SC_PREC_MIXED) {
+      int sa[2] = {0, a}, sb[2] = {0, b};
+      CK(gram_tc(c->stream, al, n, (const float*)dA, ap, a, sa, 1, (const float*)dB, bp, b, sb, 1,
+                 dC, b, false, c->d_status), "gram_tc");
+    } else {
+      CK(gram<T>(c->stream, al, n, cat<T>(dA, ap, a), cat<T>(dB, bp, b), dC, b, false, 0), "gram");
+    }
+  } else {
+    CK(gram<T>(c->stream, al, n, cat<T>(dA, ap, a), cat<T>(dB, bp, b), dC, b, false, 0), "gram");
+  }
   CK(cudaMemcpyAsync(C, dC, sizeof(double) * (size_t)a * b, cudaMemcpyDeviceToHost, c->stream), "gram");
   CK(cudaStreamSynchronize(c->stream), "gram");
   al.put(dA);
   al.put(dB);
   al.put(dC);
+  int hs = 0;
+  int rc = read_status(c, &hs);
+  if (rc != SC_OK) return rc;
+  if (hs & 32) return fail(c, SC_ETIMEOUT, "sc_gram: a bounded device wait gave up");
   return SC_OK;
 }
 

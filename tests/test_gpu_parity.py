@@ -123,14 +123,15 @@ def test_spmm_weighted(sc, ctx):
 
 
 @pytest.mark.parametrize("n,a,b", [(1, 3, 5), (37, 11, 11), (1000, 44, 132), (50001, 132, 132), (20000, 160, 480)])
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "fp32", "fp64"])
 def test_gram(sc, ctx, n, a, b, prec):
     rng = np.random.default_rng(n + a)
     A = rng.standard_normal((n, a))
     B = rng.standard_normal((n, b))
-    if prec == "fp32":
+    if prec in ("fp32", "mixed"):
+        # mixed: tcgen05 3-term split TF32 (~2^-21 per product); fp32: CUDA cores
         A32, B32 = A.astype(np.float32), B.astype(np.float32)
-        Cm = sc.sc_gram(ctx, A32, B32, sc.SC_PREC_FP32)
+        Cm = sc.sc_gram(ctx, A32, B32, sc.SC_PREC_MIXED if prec == "mixed" else sc.SC_PREC_FP32)
         ref = A32.astype(np.float64).T @ B32.astype(np.float64)
         bound = 1e-6 * np.sqrt(n) * np.outer(np.linalg.norm(A32, axis=0), np.linalg.norm(B32, axis=0)) + 1e-30
         assert np.all(np.abs(Cm - ref) <= bound)
@@ -139,9 +140,22 @@ def test_gram(sc, ctx, n, a, b, prec):
         np.testing.assert_allclose(Cm, A.T @ B, rtol=0, atol=1e-13 * n * 10)
 
 
-def test_gram_empty_rows(sc, ctx):
-    Cm = sc.sc_gram(ctx, np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), sc.SC_PREC_FP32)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gram_empty_rows(sc, ctx, prec):
+    Cm = sc.sc_gram(ctx, np.zeros((0, 4), np.float32), np.zeros((0, 6), np.float32), prec)
     assert Cm.shape == (4, 6) and np.all(Cm == 0)
+
+
+def test_gram_tc_ragged_and_structured(sc, ctx):
+    # rows not a multiple of the 32-row stage, columns not a multiple of 4, rank-one data
+    rng = np.random.default_rng(11)
+    for n, a, b in [(33, 5, 7), (4099, 130, 3), (777, 257, 129)]:
+        A = rng.standard_normal((n, a)).astype(np.float32)
+        B = (rng.standard_normal((n, 1)) @ rng.standard_normal((1, b))).astype(np.float32)
+        Cm = sc.sc_gram(ctx, A, B, sc.SC_PREC_MIXED)
+        ref = A.astype(np.float64).T @ B.astype(np.float64)
+        bound = 2e-6 * np.sqrt(n) * np.outer(np.linalg.norm(A, axis=0), np.linalg.norm(B, axis=0)) + 1e-30
+        assert np.all(np.abs(Cm - ref) <= bound), (n, a, b)
 
 
 # ------------------------------------------------------------------ a6: Rayleigh-Ritz solve
