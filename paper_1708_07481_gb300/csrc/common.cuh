@@ -148,15 +148,21 @@ cudaError_t rownorm(cudaStream_t st, long long n, int K, const T* X, long long l
 
 // Small dense: Tm = D C^-T for the scaled Cholesky D G D = C C' of G (ka x ka FP64).
 // Tm is ka x ka upper triangular (row-major, T).  Status bit ST_CHOL_FAIL on breakdown.
+// With pflag != null and a breakdown at a column >= keep, the transform of the leading keep
+// columns is returned (zeros elsewhere) and *pflag is cleared instead of reporting failure.
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
-                     int* d_status, double pivot_tol, int* fail_col = nullptr);
+                     int* d_status, double pivot_tol, int* fail_col = nullptr, int keep = 0,
+                     int* pflag = nullptr);
 
 // Rayleigh-Ritz in an orthonormal basis: K smallest eigenpairs of symmetric m x m G (FP64).
 // theta[K] FP64 (device), Y (m x K, T, row-major).  Arithmetic in T.
+// pflag (optional, device): 0 = the trailing mP basis columns were dropped; the solve then
+// uses the leading m - mP block, zeroes the rest of Y, bumps *nfallback and re-arms *pflag.
 template <typename T>
 cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
-                   double* theta, T* Y, int* d_status);
+                   double* theta, T* Y, int* d_status, int* pflag = nullptr, int mP = 0,
+                   int* nfallback = nullptr);
 
 // k-means.
 cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,

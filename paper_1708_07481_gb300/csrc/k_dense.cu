@@ -143,15 +143,17 @@ __device__ void blk_tri_inv(int ka, const T* W, int ldw, const T* rdiag, T* Li, 
 // across CTAs), scale s = diag(G)^-1/2 in FP64, factor s G s = L L' in T, and write
 // Tm = diag(s) L^-T (ka x ka upper triangular) so that V Tm has orthonormal columns.
 // On a pivot <= pivot_tol: ST_CHOL_FAIL in *status and the failing column in *fail_col.
-template <typename T>
+// SM = the factor and inverse live in shared memory (typed shared-memory pointers let the
+// compiler issue shared loads instead of generic ones).
+template <typename T, bool SM>
 __global__ void __launch_bounds__(256)
     k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
-               int in_smem, int* status, int* fail_col, double pivot_tol) {
+               int* status, int* fail_col, double pivot_tol, int keep, int* pflag) {
   extern __shared__ __align__(16) unsigned char craw[];
   T* s = (T*)craw;        // ka scale factors
   T* rdiag = s + ka;      // ka
-  T* W = in_smem ? rdiag + ka : Wg;               // ka x ka factor
-  T* Li = in_smem ? W + (size_t)ka * ka : Wg + (size_t)ka * ka;  // ka x ka inverse
+  T* W = SM ? rdiag + ka : Wg;                                // ka x ka factor
+  T* Li = SM ? rdiag + ka + (size_t)ka * ka : Wg + (size_t)ka * ka;  // ka x ka inverse
   __shared__ int sflag;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < ka; i += nt) {
@@ -166,20 +168,30 @@ __global__ void __launch_bounds__(256)
     W[i * ka + j] = (T)g * s[i] * s[j];
   }
   __syncthreads();
-  int fc = blk_chol<T>(ka, W, ka, rdiag, (T)pivot_tol, &sflag);
-  for (int i = 0; i < ka && fc < 0; ++i)
-    if (s[i] == (T)0) fc = i;  // a zero column
+  int fz = -1;
+  for (int i = 0; i < ka && fz < 0; ++i)
+    if (s[i] == (T)0) fz = i;  // a zero column
+  int fc = blk_chol<T>(fz >= 0 ? fz : ka, W, ka, rdiag, (T)pivot_tol, &sflag);
+  if (fc < 0) fc = fz;
+  int kk = ka;  // size of the factored leading block that is returned
   if (fc >= 0) {
-    if (tid == 0) {
-      atomicOr(status, ST_CHOL_FAIL);
-      if (fail_col) *fail_col = fc;
+    if (pflag && keep > 0 && fc >= keep) {
+      // the trailing (direction) columns lie in the span of the leading ones: keep the
+      // leading block's transform, zero the rest, and tell the later steps to drop them
+      kk = keep;
+      if (tid == 0) *pflag = 0;
+    } else {
+      if (tid == 0) {
+        atomicOr(status, ST_CHOL_FAIL);
+        if (fail_col) *fail_col = fc;
+      }
+      return;
     }
-    return;
   }
-  blk_tri_inv<T>(ka, W, ka, rdiag, Li, ka);
+  blk_tri_inv<T>(kk, W, ka, rdiag, Li, ka);
   for (int idx = tid; idx < ka * ka; idx += nt) {
     int i = idx / ka, j = idx % ka;
-    Tm[(long long)i * ka + j] = (j >= i) ? s[i] * Li[j * ka + i] : (T)0;
+    Tm[(long long)i * ka + j] = (j >= i && j < kk) ? s[i] * Li[j * ka + i] : (T)0;
   }
 }
 
@@ -253,11 +265,13 @@ constexpr int RR_NT = 1024;
 //     kept 10 eps ||T|| apart), two sweeps, each followed by a block Cholesky-QR (a second
 //     pass when the block was far from orthonormal; in-order Gram-Schmidt if it breaks).
 //  4. Back-transformation with the stored reflectors.
-template <typename T>
+template <typename T, bool SM>
 __global__ void __launch_bounds__(RR_NT)
-    k_rr_eig(int m, int K, const double* __restrict__ G, int ldg, double* __restrict__ theta,
-             T* __restrict__ Y, T* Ag, T* Zg, T* lu, T* Gsg, int a_smem, int z_smem,
-             int* status) {
+    k_rr_eig(int m_full, int K, const double* __restrict__ G, int ldg,
+             double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* lu, T* Gsg,
+             int* status, int* pflag, int mP, int* nfallback) {
+  // a dropped direction block P (trailing mP columns of the basis) shrinks the problem
+  const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* d = (T*)smraw;
   T* e = d + m;
@@ -268,9 +282,8 @@ __global__ void __launch_bounds__(RR_NT)
   T* lam = wv + m;   // K
   T* red = lam + K;  // 128
   T* nxt = red + 128;
-  T* A = a_smem ? nxt : Ag;
-  if (a_smem) nxt += (long long)m * m;
-  T* Z = z_smem ? nxt : Zg;
+  T* A = SM ? nxt : Ag;                        // m_full x m_full (row stride m)
+  T* Z = SM ? nxt + (long long)m * m : Zg;     // m x K
   __shared__ int sflag;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = nt / 32;
@@ -359,14 +372,31 @@ __global__ void __launch_bounds__(RR_NT)
     }
     __syncthreads();
     RR_SUB(1, tsub);
-    T pdv = 0;
-    for (int w = 0; w < nw; ++w) pdv += red[w];  // fixed order
+    // p'v: the warp partials reduced by shuffles (same fixed tree in every warp)
+    T pdv = lane < nw ? red[lane] : (T)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pdv += __shfl_xor_sync(0xffffffffu, pdv, o);
     const T kc = bet * (T)0.5 * pdv;
+    // this lane's columns j = lane + 32 u of v and w stay in registers for every row
+    T vj[8], wj[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = lane + 32 * u;
+      vj[u] = j < n1 ? vv[j] : (T)0;
+      wj[u] = j < n1 ? pv[j] - kc * vj[u] : (T)0;
+    }
     for (int i = warp; i < n1; i += nw) {
       const T vi = vv[i], wi = pv[i] - kc * vi;
       T* arow = A + (long long)(k + 1 + i) * m + (k + 1);
-#pragma unroll 4
-      for (int j = lane; j < n1; j += 32) arow[j] -= vi * (pv[j] - kc * vv[j]) + wi * vv[j];
+      if (n1 <= 256) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = lane + 32 * u;
+          if (j < n1) arow[j] -= vi * wj[u] + wi * vj[u];
+        }
+      } else {
+        for (int j = lane; j < n1; j += 32) arow[j] -= vi * (pv[j] - kc * vv[j]) + wi * vv[j];
+      }
     }
     __syncthreads();
     RR_SUB(2, tsub);
@@ -642,7 +672,12 @@ __global__ void __launch_bounds__(RR_NT)
   }
   RR_MARK(5);
   for (int j = tid; j < K; j += nt) theta[j] = (double)lam[j];
-  for (long long idx = tid; idx < (long long)m * K; idx += nt) Y[idx] = Z[idx];
+  for (long long idx = tid; idx < (long long)m_full * K; idx += nt)
+    Y[idx] = idx < (long long)m * K ? Z[idx] : (T)0;
+  if (pflag && tid == 0) {
+    if (*pflag == 0 && nfallback) *nfallback += 1;
+    *pflag = 1;  // re-armed for the next pass
+  }
   RR_MARK(6);
 }
 
@@ -650,7 +685,7 @@ __global__ void __launch_bounds__(RR_NT)
 
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
-                     int* d_status, double pivot_tol, int* fail_col) {
+                     int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag) {
   size_t base = sizeof(T) * (2 * (size_t)ka);
   size_t wbytes = sizeof(T) * (size_t)ka * ka * 2;
   int in_smem = base + wbytes <= 200 * 1024;
@@ -660,11 +695,11 @@ cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ld
     Wg = al.get<T>((size_t)ka * ka * 2);
     if (!Wg) return cudaErrorMemoryAllocation;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_chol_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  auto kern = in_smem ? k_chol_inv<T, true> : k_chol_inv<T, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   ProfScope ps(st, "chol_inv");
-  k_chol_inv<T><<<1, 256, sm, st>>>(ka, G, ldg, Tm, Wg, in_smem, d_status, fail_col, pivot_tol);
+  kern<<<1, 256, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag);
   note_launch();
   e = cudaGetLastError();
   al.put(Wg);
@@ -673,28 +708,28 @@ cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ld
 
 template <typename T>
 cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
-                   double* theta, T* Y, int* d_status) {
+                   double* theta, T* Y, int* d_status, int* pflag, int mP, int* nfallback) {
   if (m < 1 || K < 1 || K > m) return cudaErrorInvalidValue;
   size_t base = sizeof(T) * ((size_t)6 * m + K + 128);
   size_t abytes = sizeof(T) * (size_t)m * m;
   size_t zbytes = sizeof(T) * (size_t)m * K;
   const size_t cap = 220 * 1024;
-  int a_smem = base + abytes <= cap;
-  int z_smem = a_smem && base + abytes + zbytes <= cap;
-  size_t sm = base + (a_smem ? abytes : 0) + (z_smem ? zbytes : 0);
-  T* Ag = a_smem ? nullptr : al.get<T>((size_t)m * m);
-  T* Zg = z_smem ? nullptr : al.get<T>((size_t)m * K);
+  const bool insm = base + abytes + zbytes <= cap;
+  size_t sm = base + (insm ? abytes + zbytes : 0);
+  T* Ag = insm ? nullptr : al.get<T>((size_t)m * m);
+  T* Zg = insm ? nullptr : al.get<T>((size_t)m * K);
   T* lu = al.get<T>((size_t)K * 5 * m);
   T* Gs = al.get<T>((size_t)K * K * 2);
   cudaError_t e = cudaSuccess;
-  if ((!a_smem && !Ag) || (!z_smem && !Zg) || !lu || !Gs) {
+  if ((!insm && (!Ag || !Zg)) || !lu || !Gs) {
     e = cudaErrorMemoryAllocation;
   } else {
-    e = cudaFuncSetAttribute(k_rr_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = insm ? k_rr_eig<T, true> : k_rr_eig<T, false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) {
       ProfScope ps(st, "rr_eig");
-      k_rr_eig<T><<<1, RR_NT, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, lu, Gs, a_smem, z_smem,
-                                        d_status);
+      kern<<<1, RR_NT, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, lu, Gs, d_status, pflag, mP,
+                                 nfallback);
       note_launch();
       e = cudaGetLastError();
     }
@@ -707,12 +742,12 @@ cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, in
 }
 
 template cudaError_t chol_inv<float>(cudaStream_t, Alloc&, int, const double*, int, float*,
-                                     int*, double, int*);
+                                     int*, double, int*, int, int*);
 template cudaError_t chol_inv<double>(cudaStream_t, Alloc&, int, const double*, int, double*,
-                                      int*, double, int*);
+                                      int*, double, int*, int, int*);
 template cudaError_t rr_eig<float>(cudaStream_t, Alloc&, int, int, const double*, int, double*,
-                                   float*, int*);
+                                   float*, int*, int*, int, int*);
 template cudaError_t rr_eig<double>(cudaStream_t, Alloc&, int, int, const double*, int,
-                                    double*, double*, int*);
+                                    double*, double*, int*, int*, int, int*);
 
 }  // namespace sc

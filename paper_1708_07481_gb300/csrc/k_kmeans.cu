@@ -316,17 +316,26 @@ __global__ void k_cent_reduce(int d, int k, int nct, const double* __restrict__ 
   int j = blockIdx.x;
   __shared__ long long tot;
   __shared__ float red[32];
-  if (threadIdx.x == 0) {
-    long long t = 0;
-    for (int c = 0; c < nct; ++c) t += pcnt[(long long)c * k + j];
-    tot = t;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  {
+    long long t = 0;  // integer counts: any summation order gives the same total
+    for (int c = threadIdx.x; c < nct; c += blockDim.x) t += pcnt[(long long)c * k + j];
+    atomicAdd((unsigned long long*)&tot, (unsigned long long)t);
   }
   __syncthreads();
   float s = 0.f;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     if (tot > 0) {
-      double v = 0.0;
-      for (int q = 0; q < nct; ++q) v += part[((long long)q * k + j) * d + c];
+      // fixed-order sum over the CTA partials, 8 independent loads in flight per step
+      double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int q = 0;
+      for (; q + 8 <= nct; q += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] += part[((long long)(q + u) * k + j) * d + c];
+      }
+      for (; q < nct; ++q) t[0] += part[((long long)q * k + j) * d + c];
+      double v = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
       double m = v / (double)tot;
       C64[(long long)j * d + c] = m;
       C32[(long long)j * d + c] = (float)m;

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256)
                 T* __restrict__ out, long long ldo, const T* Cin, long long ldc, T beta) {
   constexpr int KC = sizeof(T) == 4 ? 32 : 16;
   using V4 = typename V4T<T>::type;
-  __shared__ __align__(16) T As[KC][RT];
+  __shared__ __align__(16) T As[KC][RT + 4];  // +4: staging writes 4-way at worst, rows 16 B aligned
   __shared__ __align__(16) T Ws[KC][CB];
   __shared__ int mblk[KC], mlc[KC];
   const long long r0 = (long long)blockIdx.x * RT;
@@ -141,10 +141,16 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // fixed-order sum over the CTA partials: 8 independent loads in flight per step
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    double t = 0.0;
-    for (unsigned c = 0; c < gridDim.x; ++c) t += __ldcg(part + (long long)c * K + j);
-    rho2[j] = t;
+    double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned c = 0;
+    for (; c + 8 <= gridDim.x; c += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] += __ldcg(part + (long long)(c + u) * K + j);
+    }
+    for (; c < gridDim.x; ++c) t[0] += __ldcg(part + (long long)c * K + j);
+    rho2[j] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
   }
   if (threadIdx.x == 0) *ticket = 0;
 }

@@ -286,18 +286,6 @@ static int read_status(sc_ctx* c, int* out) {
   return SC_OK;
 }
 
-// Status word plus the failing column a Cholesky kernel reported (-1 when none).
-static int read_status_col(sc_ctx* c, int* out, const int* dfail, int* col) {
-  int h[2] = {0, -1};
-  CK(cudaMemcpyAsync(&h[0], c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status");
-  CK(cudaMemcpyAsync(&h[1], dfail, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status");
-  CK(cudaStreamSynchronize(c->stream), "status");
-  CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "status");
-  *out = h[0];
-  *col = h[1];
-  return SC_OK;
-}
-
 // Copy an edge list to the device (or use it in place) and build a CSR.
 static int edges_to_csr(sc_ctx* c, int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
                         const float* w, int algebraic, int on_device, CsrDev* out) {
@@ -577,8 +565,10 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
   double* rho2 = L.template get_small<double>(K);
   int* dcols = L.template get_small<int>(K);
   int* dfail = L.template get_small<int>(1);
+  int* dP = L.template get_small<int>(1);   // 1 = direction block in use this pass
+  int* dfb = L.template get_small<int>(1);  // passes that dropped it
   if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !Y || !theta ||
-      !rho2 || !dcols || !dfail)
+      !rho2 || !dcols || !dfail || !dP || !dfb)
     return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
   auto X = [&]() { return S; };
   auto LX = [&]() { return LS; };
@@ -615,6 +605,12 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
     }
     CK(cudaStreamSynchronize(st), "x0");
   }
+  {
+    int one = 1, zero = 0;
+    CK(cudaMemcpyAsync(dP, &one, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
+    CK(cudaMemcpyAsync(dfb, &zero, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
+    CK(cudaStreamSynchronize(st), "flags");
+  }
   CK(cudaEventRecord(c->ev0, st), "event");
   const uint64_t l0 = launches_total();
   int hs = 0;
@@ -641,15 +637,24 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
   std::vector<double> hrho(K), hth(K);
   bool haveP = false;
   int done = 0, fallbacks = 0, converged = 0;
+  // The host reads the residual norms between passes only when it has to decide something
+  // (a stopping tolerance or soft locking); otherwise the passes are issued back to back.
+  const bool watch = o->tol_abs > 0 || o->tol_lock > 0;
+  std::vector<int> all_cols(K);
+  for (int j = 0; j < K; ++j) all_cols[j] = j;
   for (int it = 0; it < o->iters; ++it) {
-    CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "rho");
-    CK(cudaStreamSynchronize(st), "rho");
     std::vector<int> act;
     double mx = 0.0;
-    for (int j = 0; j < K; ++j) {
-      double r = std::sqrt(std::max(hrho[j], 0.0));
-      mx = std::max(mx, r);
-      if (r > o->tol_lock) act.push_back(j);
+    if (watch) {
+      CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "rho");
+      CK(cudaStreamSynchronize(st), "rho");
+      for (int j = 0; j < K; ++j) {
+        double r = std::sqrt(std::max(hrho[j], 0.0));
+        mx = std::max(mx, r);
+        if (r > o->tol_lock) act.push_back(j);
+      }
+    } else {
+      act = all_cols;
     }
     if (o->tol_abs > 0 && mx <= o->tol_abs) {
       converged = 1;
@@ -701,66 +706,39 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
     T* WLR = all ? LRslot : W2;
     CK(spmm_lap<T>(st, g->csr, WR, ldw, WLR, ldw, ka), "spmm");
     // (3) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R as well),
-    //     with [LR_a LP_a] transformed alike; a breakdown inside the P columns drops P.
-    bool useP = haveP;
+    //     with [LR_a LP_a] transformed alike.  A breakdown inside the P columns is handled on
+    //     the device: the kernel keeps the R transform, zeroes P's, and clears *dP, which the
+    //     Rayleigh-Ritz step reads to solve without P (a fallback).  A breakdown inside R is
+    //     reported through the status word.
     {
-      int wq = w;
-      // pass 1: working block -> Q1 = [Q_R | Q_P] (n x 2kp, contiguous columns)
-      Cat3<T> Vw = useP ? cat<T>(WR, ldw, ka, WP, ldw, ka) : cat<T>(WR, ldw, ka);
-      Cat3<T> LVw = useP ? cat<T>(WLR, ldw, ka, WLP, ldw, ka) : cat<T>(WLR, ldw, ka);
-      if (useP)
+      const int wq = w;
+      int* pf = haveP ? dP : nullptr;
+      Cat3<T> Vw = haveP ? cat<T>(WR, ldw, ka, WP, ldw, ka) : cat<T>(WR, ldw, ka);
+      Cat3<T> LVw = haveP ? cat<T>(WLR, ldw, ka, WLP, ldw, ka) : cat<T>(WLR, ldw, ka);
+      if (haveP)
         CK(gram_seg<T>(L, WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
       else
         CK(gram_seg<T>(L, WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
-      CK(cudaMemsetAsync(dfail, 0xff, sizeof(int), st), "fail");
-      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail), "chol");
-      int fc = -1;
-      int rc = read_status_col(c, &hs, dfail, &fc);
-      if (rc != SC_OK) return rc;
-      if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
-      if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) {
-        if (!useP || fc < ka) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-        useP = false;  // P lies in span{X, R}: drop it for this pass (R part of G is intact)
-        wq = ka;
-        Vw = cat<T>(WR, ldw, ka);
-        LVw = cat<T>(WLR, ldw, ka);
-        CK(chol_inv<T>(st, L.al, ka, G, w, Tm, c->d_status, L.pivot_tol, dfail), "chol");
-        rc = read_status_col(c, &hs, dfail, &fc);
-        if (rc != SC_OK) return rc;
-        if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-      }
+      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail, ka, pf), "chol");
       CK(tall_gemm<T>(st, n, Vw, Tm, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
       CK(tall_gemm<T>(st, n, LVw, Tm, wq, wq, LQ1, 2 * kp, nullptr, 0, (T)0), "tall");
-      // pass 2: Q1 -> S / LS slots (R part from the Q_R columns only: Tm is upper triangular)
       CK(gram_seg<T>(L, Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
-      CK(cudaMemsetAsync(dfail, 0xff, sizeof(int), st), "fail");
-      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail), "chol");
-      rc = read_status_col(c, &hs, dfail, &fc);
-      if (rc != SC_OK) return rc;
-      if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) {
-        if (!useP || fc < ka) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-        useP = false;
-        wq = ka;
-        CK(chol_inv<T>(st, L.al, ka, G, 2 * ka, Tm, c->d_status, L.pivot_tol, dfail), "chol");
-        rc = read_status_col(c, &hs, dfail, &fc);
-        if (rc != SC_OK) return rc;
-        if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-      }
+      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail, ka, pf), "chol");
       CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), Tm, wq, ka, Rslot, ld3, nullptr, 0, (T)0), "tall");
       CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, ka), Tm, wq, ka, LRslot, ld3, nullptr, 0, (T)0), "tall");
-      if (useP) {
+      if (haveP) {
         CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), Tm + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0), "tall");
         CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, wq), Tm + ka, wq, ka, LPslot, ld3, nullptr, 0, (T)0), "tall");
       }
-      if (haveP && !useP) ++fallbacks;
     }
+    const bool useP = haveP;
     // Rayleigh-Ritz on S = [X R_a P_a]
     const int m = K + ka + (useP ? ka : 0);
     if (useP)
       CK(gram_seg<T>(L, S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, false), "gram");
     else
       CK(gram_seg<T>(L, S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, false), "gram");
-    CK(rr_eig<T>(st, L.al, m, K, G, m, theta, Y, c->d_status), "rr");
+    CK(rr_eig<T>(st, L.al, m, K, G, m, theta, Y, c->d_status, useP ? dP : nullptr, ka, dfb), "rr");
     // update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike), R = LX - X theta
     const T* Yrp = Y + (size_t)K * K;
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
@@ -782,6 +760,8 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
   if (rc != SC_OK) return rc;
   if (st_final & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
   if (st_final & ST_NONFINITE) return fail(c, SC_EBREAKDOWN, "non-finite values in Rayleigh-Ritz");
+  if (st_final & ST_CHOL_FAIL) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
+  CK(cudaMemcpyAsync(&fallbacks, dfb, sizeof(int), cudaMemcpyDeviceToHost, st), "out");
   CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
   CK(cudaMemcpyAsync(hth.data(), theta, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
   // resident block (float, n x K) for warm starts and the embedding
