@@ -68,6 +68,7 @@ typedef enum { SC_SYM_LOGICAL = 0, SC_SYM_ALGEBRAIC = 1 } sc_sym;
  * `hbm_budget` caps the bytes the context and its graphs may hold on the device (0 = no
  * cap); allocations beyond it fail with SC_ENOMEM. */
 int sc_ctx_create(sc_ctx** out, int device, void* cuda_stream, size_t hbm_budget);
+/* Destroy the graphs and servers created on a context before the context itself. */
 void sc_ctx_destroy(sc_ctx* ctx);
 const char* sc_last_error(const sc_ctx* ctx);
 /* Bytes currently held on the device by this context and its graphs. */
@@ -157,11 +158,25 @@ int sc_kmeans(sc_ctx* ctx, const float* E, int32_t n, int d, int k, int iters,
               uint64_t seed, const int32_t* init_idx, int on_device, int32_t* labels_out,
               float* centroids_out, int32_t* seeds_out, double* inertia, int* iters_run);
 
+/* sc_lobpcg_batch: sc_lobpcg (seeded start block, or the resident block when !cold) for
+ * `count` graphs at once.  Each solve runs on its own stream and the passes of all solves
+ * are issued in turn, so their kernels overlap on the device -- in particular the one-CTA
+ * small dense solves of different graphs run on different SMs.  Results are identical to
+ * solving each graph alone (every reduction has a fixed order).  infos[count] may be NULL. */
+int sc_lobpcg_batch(sc_ctx* ctx, int count, sc_graph* const* graphs, const int* K,
+                    const sc_lobpcg_opts* opts, sc_eig_info* infos);
+
 /* ---- end to end ------------------------------------------------------------------------
  * sc_partition: LOBPCG (K vectors) -> unit rows -> k-means (k clusters, kmeans_iters
  * Lloyd rounds, k-means++ seeded by opts->seed) -> labels_out[n] (host). */
 int sc_partition(sc_ctx* ctx, sc_graph* g, int K, int k, const sc_lobpcg_opts* opts,
                  int kmeans_iters, int32_t* labels_out, sc_eig_info* info);
+
+/* sc_partition_batch: sc_partition over `count` graphs with batched LOBPCG (labels_out[q]
+ * has n_q entries; host). */
+int sc_partition_batch(sc_ctx* ctx, int count, sc_graph* const* graphs, const int* K,
+                       const int* k, const sc_lobpcg_opts* opts, int kmeans_iters,
+                       int32_t* const* labels_out, sc_eig_info* infos);
 
 /* ---- streaming (Sec. III: emerging edges, snowball) -------------------------------------
  * sc_stream_update: add m_delta directed edges to the graph and grow it to n_new >= n
@@ -170,6 +185,49 @@ int sc_partition(sc_ctx* ctx, sc_graph* g, int K, int k, const sc_lobpcg_opts* o
  * any, gains zero rows for the new vertices so the next sc_lobpcg warm-starts. */
 int sc_stream_update(sc_ctx* ctx, sc_graph* g, int32_t n_new, int64_t m_delta,
                      const int32_t* src, const int32_t* dst, const float* w, int on_device);
+
+/* ---- serving loop (continuous batching of partition requests) ----------------------------
+ * A server owns a context (used only by its worker thread; its HBM budget is the admission
+ * limit).  Requests wait in a queue of queue_cap entries; up to max_slots solves run at once,
+ * each advancing one LOBPCG pass per round on its own stream, and a request that arrives
+ * while others run joins at the next pass boundary.  Graphs stay resident by graph_id:
+ *   SC_REQ_COLD  -- build graph graph_id from the edge list (replacing a previous one) and
+ *                   partition it from a seeded Gaussian start block;
+ *   SC_REQ_DELTA -- add the edges to graph graph_id, grow it to n vertices (new vertices
+ *                   numbered last) and partition it warm-started from its resident block
+ *                   (zero rows for new vertices, Sec. III).
+ * Edge arrays are copied by sc_server_submit.  Results are identical to running the same
+ * request alone.  A request whose estimated footprint exceeds the budget fails SC_ENOMEM.
+ * The server functions are thread-safe. */
+enum { SC_REQ_COLD = 0, SC_REQ_DELTA = 1 };
+typedef struct {
+  int kind;
+  int graph_id;
+  int32_t n;
+  int64_t m;
+  const int32_t* src;
+  const int32_t* dst;
+  int K;            /* LOBPCG block size                       */
+  int k;            /* clusters                                */
+  int iters;        /* LOBPCG passes (cap when tol_abs > 0)     */
+  int kmeans_iters;
+  int prec;         /* sc_precision                            */
+  double tol_abs;   /* 0 = run `iters` passes                  */
+  uint64_t seed;
+} sc_request;
+int sc_server_create(sc_ctx* ctx, int max_slots, int queue_cap, sc_server** out);
+/* SC_EAGAIN when the queue is full. */
+int sc_server_submit(sc_server* s, const sc_request* r, uint64_t* ticket);
+/* Result of a finished request (labels_out: n_cap entries, host); SC_EAGAIN while pending.
+ * latency_ms = submit to completion.  The ticket is consumed when the result is returned. */
+int sc_server_poll(sc_server* s, uint64_t ticket, int32_t* labels_out, int32_t n_cap,
+                   sc_eig_info* info, double* latency_ms);
+/* As sc_server_poll, blocking up to timeout_ms (SC_ETIMEOUT when it runs out). */
+int sc_server_wait(sc_server* s, uint64_t ticket, int timeout_ms, int32_t* labels_out,
+                   int32_t n_cap, sc_eig_info* info, double* latency_ms);
+int sc_server_stats(sc_server* s, int* active, int* queued, uint64_t* completed);
+/* Finishes queued and running requests, then frees the server and its resident graphs. */
+void sc_server_destroy(sc_server* s);
 
 /* ---- component entry points (the steps of one LOBPCG pass, exposed for testing) -------
  * sc_gram: C = A' B in FP64 (a x b, row-major) for n x a block A and n x b block B

@@ -378,9 +378,11 @@ __global__ void __launch_bounds__(RR_NT)
     for (int o = 16; o > 0; o >>= 1) pdv += __shfl_xor_sync(0xffffffffu, pdv, o);
     const T kc = bet * (T)0.5 * pdv;
     // this lane's columns j = lane + 32 u of v and w stay in registers for every row
+    const int nu = (n1 + 31) >> 5;  // uniform: register slots actually used this step
     T vj[8], wj[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
+      if (u >= nu) break;
       const int j = lane + 32 * u;
       vj[u] = j < n1 ? vv[j] : (T)0;
       wj[u] = j < n1 ? pv[j] - kc * vj[u] : (T)0;
@@ -391,6 +393,7 @@ __global__ void __launch_bounds__(RR_NT)
       if (n1 <= 256) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
+          if (u >= nu) break;
           const int j = lane + 32 * u;
           if (j < n1) arow[j] -= vi * wj[u] + wi * vj[u];
         }
@@ -584,8 +587,10 @@ __global__ void __launch_bounds__(RR_NT)
       for (int r = warp; r < m; r += nw) {
         T* zr = Z + (long long)r * K;
         T out[16];
+        const int nq = (K + 31) >> 5;  // uniform
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
+          if (q >= nq) break;
           const int b = lane + 32 * q;
           T acc = 0;
           if (b < K) {
@@ -597,6 +602,7 @@ __global__ void __launch_bounds__(RR_NT)
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
+          if (q >= nq) break;
           const int b = lane + 32 * q;
           if (b < K) zr[b] = out[q];
         }

@@ -5,6 +5,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -426,168 +430,220 @@ int sc_lap_apply(sc_ctx* c, sc_graph* g, int k, int prec, const void* V, void* Y
 
 namespace {
 
-template <typename T>
-struct Lob {
+// Stream-bound allocator of one LOBPCG run: stream-ordered allocations on the run's stream,
+// counted against the context budget.
+struct RunAlloc {
   sc_ctx* c;
-  Alloc al;
-  sc_graph* g;
-  int n, K, kp;  // kp: padded row stride of every block
-  int use_tc;
-  double pivot_tol;
-  std::vector<T*> pool;
-  std::vector<void*> misc;
-  T* get_block() {
-    T* p = al.get<T>((size_t)n * kp);
-    if (p) {
-      pool.push_back(p);
-      cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n * kp, c->stream);
-    }
-    return p;
-  }
-  template <typename U>
-  U* get_small(size_t count) {
-    U* p = al.get<U>(count);
-    if (p) misc.push_back(p);
-    return p;
-  }
-  ~Lob() {
-    for (T* p : pool) al.put(p);
-    for (void* p : misc) al.put(p);
-  }
+  cudaStream_t st;
 };
+void* run_alloc(void* self, size_t bytes) {
+  RunAlloc* r = (RunAlloc*)self;
+  sc_ctx* c = r->c;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (c->budget && c->in_use + bytes > c->budget) return nullptr;
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, r->st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->sizes[p] = bytes;
+  c->in_use += bytes;
+  return p;
+}
+void run_free(void* self, void* p) {
+  RunAlloc* r = (RunAlloc*)self;
+  if (!p) return;
+  auto it = r->c->sizes.find(p);
+  if (it != r->c->sizes.end()) {
+    r->c->in_use -= it->second;
+    r->c->sizes.erase(it);
+  }
+  cudaFreeAsync(p, r->st);
+}
 
 struct Seg {
   int start, count;
 };
 
-// C (compact FP64) = A' B over the listed column segments of two strided blocks.  FP32 with
-// tensor cores selected -> tcgen05 kernel; otherwise the CUDA-core kernel.
-template <typename T>
-cudaError_t gram_seg(Lob<T>& L, const T* A, long long lda, std::initializer_list<Seg> sa,
-                     const T* B, long long ldb, std::initializer_list<Seg> sb, double* C,
-                     int ldc, bool sym) {
-  std::vector<Seg> va(sa), vb(sb);
-  if constexpr (sizeof(T) == 4) {
-    if (L.use_tc) {
-      int pa[6], pb[6], spa = 0, spb = 0;
-      for (size_t q = 0; q < va.size(); ++q) {
-        pa[2 * q] = va[q].start;
-        pa[2 * q + 1] = va[q].count;
-        spa = std::max(spa, va[q].start + va[q].count);
-      }
-      for (size_t q = 0; q < vb.size(); ++q) {
-        pb[2 * q] = vb[q].start;
-        pb[2 * q + 1] = vb[q].count;
-        spb = std::max(spb, vb[q].start + vb[q].count);
-      }
-      return gram_tc(L.c->stream, L.al, L.n, (const float*)A, lda, spa, pa, (int)va.size(),
-                     (const float*)B, ldb, spb, pb, (int)vb.size(), C, ldc, sym, L.c->d_status);
-    }
-  }
-  Cat3<T> ca{}, cb{};
-  ca.nblk = (int)va.size();
-  cb.nblk = (int)vb.size();
-  for (size_t q = 0; q < va.size(); ++q) {
-    ca.p[q] = A + va[q].start;
-    ca.ld[q] = lda;
-    ca.c[q] = va[q].count;
-  }
-  for (size_t q = 0; q < vb.size(); ++q) {
-    cb.p[q] = B + vb[q].start;
-    cb.ld[q] = ldb;
-    cb.c[q] = vb[q].count;
-  }
-  return gram<T>(L.c->stream, L.al, L.n, ca, cb, C, ldc, sym, 0);
-}
-
-// Cholesky-QR of block V (n x kc, stride ldv) into out (stride ldo); optionally applies the
-// same transform to LV (into lout).  Reports ST_CHOL_FAIL in *status_out (nothing written).
-template <typename T>
-int cholqr_step(Lob<T>& L, const T* V, long long ldv, int kc, T* out, long long ldo, double* G,
-                T* Tm, const T* LV, long long ldlv, T* lout, long long ldlo, int* status_out) {
-  sc_ctx* c = L.c;
-  cudaStream_t st = c->stream;
-  CK(gram_seg<T>(L, V, ldv, {{0, kc}}, V, ldv, {{0, kc}}, G, kc, true), "gram");
-  CK(chol_inv<T>(st, L.al, kc, G, kc, Tm, c->d_status, L.pivot_tol), "chol");
-  int hs = 0;
-  int rc = read_status(c, &hs);
-  if (rc != SC_OK) return rc;
-  *status_out = hs;
-  if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
-  if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return SC_OK;
-  CK(tall_gemm<T>(st, L.n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0), "tall");
-  if (LV) CK(tall_gemm<T>(st, L.n, cat<T>(LV, ldlv, kc), Tm, kc, kc, lout, ldlo, nullptr, 0, (T)0), "tall");
-  return SC_OK;
-}
-
+// One LOBPCG solve as a state machine: setup() (start block and initial Rayleigh-Ritz),
+// pass() (one LOBPCG iteration, issued asynchronously), finish() (outputs).  Every run owns
+// its stream, allocator and device status word, so several runs can be interleaved pass by
+// pass and their kernels overlap on the device (batched solves, the serving loop).
 // Block layout: S = [X | R | P] and LS = [LX | LR | LP], each n x 3kp row-major (column slots
 // of kp = K rounded up to 16 bytes), so every Gram operand is one strided matrix.
-template <typename T>
-int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const float* X0,
-               int32_t x0_rows, float* X_out, sc_eig_info* info) {
-  const int n = g->csr.n;
-  const int W = 16 / sizeof(T);
-  const int kp = (K + W - 1) / W * W;
-  const long long ld3 = 3LL * kp;
-  Lob<T> L{c, alloc_of(c), g, n, K, kp, (sizeof(T) == 4 && o->prec == SC_PREC_MIXED) ? 1 : 0,
-           sizeof(T) == 4 ? 1e-8 : 1e-14, {}, {}};
-  cudaStream_t st = c->stream;
-  const int mmax = 3 * K;
-  auto big = [&]() {
-    T* p = L.al.template get<T>((size_t)n * ld3);
-    if (p) {
-      L.pool.push_back(p);
-      cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n * ld3, st);
-    }
-    return p;
-  };
-  T* S = big();
-  T* LS = big();
-  T* S2 = big();
-  T* LS2 = big();
-  T* T1 = L.get_block();
-  auto wide = [&]() {
-    T* p = L.al.template get<T>((size_t)n * 2 * kp);
-    if (p) {
-      L.pool.push_back(p);
-      cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n * 2 * kp, st);
-    }
-    return p;
-  };
-  T* W1 = wide();
-  T* W2 = wide();
-  T* Q1 = wide();
-  T* LQ1 = wide();
-  double* G = L.template get_small<double>((size_t)mmax * mmax);
-  T* Tm = L.template get_small<T>((size_t)mmax * mmax);
-  T* Y = L.template get_small<T>((size_t)mmax * K);
-  double* theta = L.template get_small<double>(K);
-  double* rho2 = L.template get_small<double>(K);
-  int* dcols = L.template get_small<int>(K);
-  int* dfail = L.template get_small<int>(1);
-  int* dP = L.template get_small<int>(1);   // 1 = direction block in use this pass
-  int* dfb = L.template get_small<int>(1);  // passes that dropped it
-  if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !Y || !theta ||
-      !rho2 || !dcols || !dfail || !dP || !dfb)
-    return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
-  auto X = [&]() { return S; };
-  auto LX = [&]() { return LS; };
+struct RunBase {
+  virtual ~RunBase() {}
+  virtual int setup(const float* X0, int32_t x0_rows) = 0;
+  virtual int pass() = 0;
+  virtual int finish(float* X_out, sc_eig_info* info) = 0;
+  virtual bool finished() const = 0;
+  virtual cudaStream_t stream() const = 0;
+};
 
-  // ---- start block --------------------------------------------------------------------
-  {
+template <typename T>
+struct LobRun : RunBase {
+  sc_ctx* c;
+  sc_graph* g;
+  int n, K, kp;
+  long long ld3;
+  sc_lobpcg_opts o;
+  cudaStream_t st;
+  RunAlloc ra;
+  Alloc al;
+  int use_tc;
+  double pivot_tol;
+  std::vector<void*> bufs;
+  T *S = nullptr, *LS = nullptr, *S2 = nullptr, *LS2 = nullptr, *T1 = nullptr, *W1 = nullptr,
+    *W2 = nullptr, *Q1 = nullptr, *LQ1 = nullptr, *Tm = nullptr, *Y = nullptr;
+  double *G = nullptr, *theta = nullptr, *rho2 = nullptr;
+  int *dcols = nullptr, *dfail = nullptr, *dP = nullptr, *dfb = nullptr, *dstatus = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint64_t l0 = 0;
+  int it = 0, done_passes = 0, converged = 0;
+  bool haveP = false, over = false;
+  std::vector<double> hrho, hth;
+
+  LobRun(sc_ctx* c_, sc_graph* g_, int K_, const sc_lobpcg_opts* o_, cudaStream_t st_)
+      : c(c_), g(g_), n(g_->csr.n), K(K_), o(*o_), st(st_) {
+    const int W = 16 / sizeof(T);
+    kp = (K + W - 1) / W * W;
+    ld3 = 3LL * kp;
+    ra = RunAlloc{c, st};
+    al = Alloc{run_alloc, run_free, &ra};
+    use_tc = (sizeof(T) == 4 && o.prec == SC_PREC_MIXED) ? 1 : 0;
+    pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-14;
+    hrho.assign(K, 0.0);
+    hth.assign(K, 0.0);
+  }
+  ~LobRun() override {
+    for (void* p : bufs) al.put(p);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaStreamSynchronize(st);
+  }
+  bool finished() const override { return over; }
+  cudaStream_t stream() const override { return st; }
+
+  template <typename U>
+  U* get(size_t count, bool zero = false) {
+    U* p = al.template get<U>(count);
+    if (p) {
+      bufs.push_back(p);
+      if (zero) cudaMemsetAsync(p, 0, sizeof(U) * count, st);
+    }
+    return p;
+  }
+  int read_status(int* out) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    CK(cudaStreamSynchronize(st), "status");
+    CK(cudaMemsetAsync(dstatus, 0, sizeof(int), st), "status");
+    *out = h;
+    return SC_OK;
+  }
+
+  // C (compact FP64) = A' B over column segments of two strided blocks.  FP32 with tensor
+  // cores selected -> tcgen05 kernel; otherwise the CUDA-core kernel.
+  cudaError_t gram_seg(const T* A, long long lda, std::initializer_list<Seg> sa, const T* B,
+                       long long ldb, std::initializer_list<Seg> sb, double* C, int ldc,
+                       bool sym) {
+    std::vector<Seg> va(sa), vb(sb);
+    if constexpr (sizeof(T) == 4) {
+      if (use_tc) {
+        int pa[6], pb[6], spa = 0, spb = 0;
+        for (size_t q = 0; q < va.size(); ++q) {
+          pa[2 * q] = va[q].start;
+          pa[2 * q + 1] = va[q].count;
+          spa = std::max(spa, va[q].start + va[q].count);
+        }
+        for (size_t q = 0; q < vb.size(); ++q) {
+          pb[2 * q] = vb[q].start;
+          pb[2 * q + 1] = vb[q].count;
+          spb = std::max(spb, vb[q].start + vb[q].count);
+        }
+        return gram_tc(st, al, n, (const float*)A, lda, spa, pa, (int)va.size(), (const float*)B,
+                       ldb, spb, pb, (int)vb.size(), C, ldc, sym, dstatus);
+      }
+    }
+    Cat3<T> ca{}, cb{};
+    ca.nblk = (int)va.size();
+    cb.nblk = (int)vb.size();
+    for (size_t q = 0; q < va.size(); ++q) {
+      ca.p[q] = A + va[q].start;
+      ca.ld[q] = lda;
+      ca.c[q] = va[q].count;
+    }
+    for (size_t q = 0; q < vb.size(); ++q) {
+      cb.p[q] = B + vb[q].start;
+      cb.ld[q] = ldb;
+      cb.c[q] = vb[q].count;
+    }
+    return gram<T>(st, al, n, ca, cb, C, ldc, sym, 0);
+  }
+
+  // Cholesky-QR of V (n x kc, stride ldv) into out (stride ldo); failure -> *failed.
+  int cholqr_step(const T* V, long long ldv, int kc, T* out, long long ldo, bool* failed) {
+    CK(gram_seg(V, ldv, {{0, kc}}, V, ldv, {{0, kc}}, G, kc, true), "gram");
+    CK(chol_inv<T>(st, al, kc, G, kc, Tm, dstatus, pivot_tol), "chol");
+    int hs = 0;
+    int rc = read_status(&hs);
+    if (rc != SC_OK) return rc;
+    if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
+    *failed = (hs & (ST_CHOL_FAIL | ST_NONFINITE)) != 0;
+    if (*failed) return SC_OK;
+    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0), "tall");
+    return SC_OK;
+  }
+
+  int setup(const float* X0, int32_t x0_rows) override {
+    if (!ev0) {
+      cudaEventCreate(&ev0);
+      cudaEventCreate(&ev1);
+    }
+    const int mmax = 3 * K;
+    S = get<T>((size_t)n * ld3, true);
+    LS = get<T>((size_t)n * ld3, true);
+    S2 = get<T>((size_t)n * ld3, true);
+    LS2 = get<T>((size_t)n * ld3, true);
+    T1 = get<T>((size_t)n * kp, true);
+    W1 = get<T>((size_t)n * 2 * kp, true);
+    W2 = get<T>((size_t)n * 2 * kp, true);
+    Q1 = get<T>((size_t)n * 2 * kp, true);
+    LQ1 = get<T>((size_t)n * 2 * kp, true);
+    G = get<double>((size_t)mmax * mmax);
+    Tm = get<T>((size_t)mmax * mmax);
+    Y = get<T>((size_t)mmax * K);
+    theta = get<double>(K);
+    rho2 = get<double>(K);
+    dcols = get<int>(K);
+    dfail = get<int>(1);
+    dP = get<int>(1);
+    dfb = get<int>(1);
+    dstatus = get<int>(1, true);
+    if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !Y ||
+        !theta || !rho2 || !dcols || !dfail || !dP || !dfb || !dstatus)
+      return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
+    {
+      int one = 1, zero = 0;
+      CK(cudaMemcpyAsync(dP, &one, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
+      CK(cudaMemcpyAsync(dfb, &zero, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
+    }
+    // ---- start block: given X0 (top x0_rows rows, zero fill below), the resident block of
+    //      the previous call (warm start), or a seeded Gaussian block generated on the device
     const float* src = nullptr;
     int rows = 0;
     bool dev_src = false;
     if (X0) {
       src = X0;
       rows = x0_rows > 0 ? std::min(x0_rows, n) : n;
-    } else if (g->X && g->K == K && !o->cold) {
+    } else if (g->X && g->K == K && !o.cold) {
       src = g->X;
       rows = n;
       dev_src = true;
     }
     if (!src) {
-      CK(gauss_block<T>(st, n, K, stream_key(o->seed, 1, 0), S, ld3), "x0");
+      CK(gauss_block<T>(st, n, K, stream_key(o.seed, 1, 0), S, ld3), "x0");
     } else if (sizeof(T) == 4) {
       CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, src, sizeof(float) * K, sizeof(float) * K, rows,
                            dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "x0");
@@ -604,65 +660,57 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
                            rows, cudaMemcpyHostToDevice, st), "x0");
     }
     CK(cudaStreamSynchronize(st), "x0");
-  }
-  {
-    int one = 1, zero = 0;
-    CK(cudaMemcpyAsync(dP, &one, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
-    CK(cudaMemcpyAsync(dfb, &zero, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
-    CK(cudaStreamSynchronize(st), "flags");
-  }
-  CK(cudaEventRecord(c->ev0, st), "event");
-  const uint64_t l0 = launches_total();
-  int hs = 0;
-  // X <- CholQR(CholQR(X0)):  X slot -> T1 -> X slot
-  {
-    int rc = cholqr_step<T>(L, S, ld3, K, T1, kp, G, Tm, nullptr, 0, nullptr, 0, &hs);
+    CK(cudaEventRecord(ev0, st), "event");
+    l0 = launches_total();
+    // X <- CholQR(CholQR(X0)):  X slot -> T1 -> X slot
+    bool bad = false;
+    int rc = cholqr_step(S, ld3, K, T1, kp, &bad);
     if (rc != SC_OK) return rc;
-    if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
-    rc = cholqr_step<T>(L, T1, kp, K, S, ld3, G, Tm, nullptr, 0, nullptr, 0, &hs);
+    if (!bad) rc = cholqr_step(T1, kp, K, S, ld3, &bad);
     if (rc != SC_OK) return rc;
-    if (hs & (ST_CHOL_FAIL | ST_NONFINITE)) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
+    if (bad) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
+    CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
+    CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, false), "gram");
+    CK(rr_eig<T>(st, al, K, K, G, K, theta, Y, dstatus), "rr");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0), "tall");
+    std::swap(S, S2);
+    std::swap(LS, LS2);
+    CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
+    it = 0;
+    over = o.iters <= 0;
+    return SC_OK;
   }
-  CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
-  CK(gram_seg<T>(L, S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, false), "gram");
-  CK(rr_eig<T>(st, L.al, K, K, G, K, theta, Y, c->d_status), "rr");
-  CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0), "tall");
-  CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0), "tall");
-  std::swap(S, S2);
-  std::swap(LS, LS2);
-  CK(residual<T>(st, L.al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
-  (void)X;
-  (void)LX;
 
-  std::vector<double> hrho(K), hth(K);
-  bool haveP = false;
-  int done = 0, fallbacks = 0, converged = 0;
-  // The host reads the residual norms between passes only when it has to decide something
-  // (a stopping tolerance or soft locking); otherwise the passes are issued back to back.
-  const bool watch = o->tol_abs > 0 || o->tol_lock > 0;
-  std::vector<int> all_cols(K);
-  for (int j = 0; j < K; ++j) all_cols[j] = j;
-  for (int it = 0; it < o->iters; ++it) {
+  // One LOBPCG pass (Sec. II.B), issued on the run's stream.  The host reads the residual
+  // norms between passes only when it has to decide something (a stopping tolerance or soft
+  // locking); otherwise passes are issued back to back without synchronization.
+  int pass() override {
+    if (over) return SC_OK;
+    const bool watch = o.tol_abs > 0 || o.tol_lock > 0;
     std::vector<int> act;
-    double mx = 0.0;
     if (watch) {
       CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "rho");
       CK(cudaStreamSynchronize(st), "rho");
+      double mx = 0.0;
       for (int j = 0; j < K; ++j) {
         double r = std::sqrt(std::max(hrho[j], 0.0));
         mx = std::max(mx, r);
-        if (r > o->tol_lock) act.push_back(j);
+        if (r > o.tol_lock) act.push_back(j);
+      }
+      if (o.tol_abs > 0 && mx <= o.tol_abs) {
+        converged = 1;
+        over = true;
+        return SC_OK;
+      }
+      if (act.empty()) {
+        converged = o.tol_abs > 0 ? 1 : 0;
+        over = true;
+        return SC_OK;
       }
     } else {
-      act = all_cols;
-    }
-    if (o->tol_abs > 0 && mx <= o->tol_abs) {
-      converged = 1;
-      break;
-    }
-    if (act.empty()) {
-      converged = o->tol_abs > 0 ? 1 : 0;
-      break;
+      act.resize(K);
+      for (int j = 0; j < K; ++j) act[j] = j;
     }
     const int ka = (int)act.size();
     const bool all = ka == K;
@@ -670,14 +718,13 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
     T* LRslot = LS + kp;
     T* Pslot = S + 2 * kp;
     T* LPslot = LS + 2 * kp;
-    // Working copies of the active R and P columns.  With every column active they are the
-    // S slots themselves ([R P] = columns kp.. and 2kp.. of S); otherwise the active columns
-    // are gathered into W1 = [R_a | P_a] (n x 2kp) and W2 = [. | LP_a].
+    // Working copies of the active R and P columns: the S slots themselves when every column
+    // is active; otherwise gathered into W1 = [R_a | P_a] and W2 = [LR_a | LP_a] (n x 2kp).
     T* WR = Rslot;
     T* WP = Pslot;
     T* WLP = LPslot;
     long long ldw = ld3;
-    int offP = kp;  // column offset of P in the working block (relative to WR)
+    const int offP = kp;
     if (!all) {
       CK(cudaMemcpyAsync(dcols, act.data(), sizeof(int) * ka, cudaMemcpyHostToDevice, st), "cols");
       CK(gather_cols<T>(st, n, Rslot, ld3, W1, 2 * kp, dcols, ka), "gather");
@@ -689,41 +736,43 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
         CK(gather_cols<T>(st, n, LPslot, ld3, W2 + kp, ldw, dcols, ka), "gather");
         WLP = W2 + kp;
       }
+      // the gathered column list must stay valid until the copy ran
+      CK(cudaStreamSynchronize(st), "cols");
     }
     const int w = haveP ? 2 * ka : ka;
-    // (1) project [R_a P_a] against X: F = X' [R_a P_a]; R_a -= X F_R, P_a -= X F_P, LP_a -= LX F_P
+    // (1) project [R_a P_a] against X: F = X'[R_a P_a]; R_a -= X F_R, P_a -= X F_P, LP_a -= LX F_P
     if (haveP)
-      CK(gram_seg<T>(L, S, ld3, {{0, K}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, false), "gram");
+      CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, false), "gram");
     else
-      CK(gram_seg<T>(L, S, ld3, {{0, K}}, WR, ldw, {{0, ka}}, G, w, false), "gram");
+      CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}}, G, w, false), "gram");
     CK(cast_mat<T>(st, K, w, G, w, Tm, w, -1.0), "cast");
     CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, w, ka, WR, ldw, WR, ldw, (T)1), "tall");
     if (haveP) {
       CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm + ka, w, ka, WP, ldw, WP, ldw, (T)1), "tall");
       CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm + ka, w, ka, WLP, ldw, WLP, ldw, (T)1), "tall");
     }
-    // (2) LR_a = L R_a (the one SpMM of the pass), into the LR slot / working block
+    // (2) LR_a = L R_a: the one multiplication by L of the pass (Sec. III)
     T* WLR = all ? LRslot : W2;
     CK(spmm_lap<T>(st, g->csr, WR, ldw, WLR, ldw, ka), "spmm");
-    // (3) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R as well),
+    // (3) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too),
     //     with [LR_a LP_a] transformed alike.  A breakdown inside the P columns is handled on
     //     the device: the kernel keeps the R transform, zeroes P's, and clears *dP, which the
-    //     Rayleigh-Ritz step reads to solve without P (a fallback).  A breakdown inside R is
-    //     reported through the status word.
+    //     Rayleigh-Ritz step reads to solve without P.  A breakdown inside R goes to the
+    //     status word.
     {
       const int wq = w;
       int* pf = haveP ? dP : nullptr;
       Cat3<T> Vw = haveP ? cat<T>(WR, ldw, ka, WP, ldw, ka) : cat<T>(WR, ldw, ka);
       Cat3<T> LVw = haveP ? cat<T>(WLR, ldw, ka, WLP, ldw, ka) : cat<T>(WLR, ldw, ka);
       if (haveP)
-        CK(gram_seg<T>(L, WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
+        CK(gram_seg(WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
       else
-        CK(gram_seg<T>(L, WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail, ka, pf), "chol");
+        CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
+      CK(chol_inv<T>(st, al, wq, G, wq, Tm, dstatus, pivot_tol, dfail, ka, pf), "chol");
       CK(tall_gemm<T>(st, n, Vw, Tm, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
       CK(tall_gemm<T>(st, n, LVw, Tm, wq, wq, LQ1, 2 * kp, nullptr, 0, (T)0), "tall");
-      CK(gram_seg<T>(L, Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, L.al, wq, G, wq, Tm, c->d_status, L.pivot_tol, dfail, ka, pf), "chol");
+      CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
+      CK(chol_inv<T>(st, al, wq, G, wq, Tm, dstatus, pivot_tol, dfail, ka, pf), "chol");
       CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), Tm, wq, ka, Rslot, ld3, nullptr, 0, (T)0), "tall");
       CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, ka), Tm, wq, ka, LRslot, ld3, nullptr, 0, (T)0), "tall");
       if (haveP) {
@@ -731,15 +780,15 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
         CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, wq), Tm + ka, wq, ka, LPslot, ld3, nullptr, 0, (T)0), "tall");
       }
     }
+    // (4) Rayleigh-Ritz on S = [X R_a P_a]
     const bool useP = haveP;
-    // Rayleigh-Ritz on S = [X R_a P_a]
     const int m = K + ka + (useP ? ka : 0);
     if (useP)
-      CK(gram_seg<T>(L, S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, false), "gram");
+      CK(gram_seg(S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, false), "gram");
     else
-      CK(gram_seg<T>(L, S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, false), "gram");
-    CK(rr_eig<T>(st, L.al, m, K, G, m, theta, Y, c->d_status, useP ? dP : nullptr, ka, dfb), "rr");
-    // update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike), R = LX - X theta
+      CK(gram_seg(S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, false), "gram");
+    CK(rr_eig<T>(st, al, m, K, G, m, theta, Y, dstatus, useP ? dP : nullptr, ka, dfb), "rr");
+    // (5) update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike); R = LX - X theta
     const T* Yrp = Y + (size_t)K * K;
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
     Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);
@@ -750,76 +799,134 @@ int run_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const flo
     std::swap(S, S2);
     std::swap(LS, LS2);
     haveP = true;
-    CK(residual<T>(st, L.al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
-    ++done;
+    CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
+    ++done_passes;
+    if (++it >= o.iters) over = true;
+    return SC_OK;
   }
-  CK(cudaEventRecord(c->ev1, st), "event");
-  CK(cudaStreamSynchronize(st), "sync");
-  int st_final = 0;
-  int rc = read_status(c, &st_final);
-  if (rc != SC_OK) return rc;
-  if (st_final & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
-  if (st_final & ST_NONFINITE) return fail(c, SC_EBREAKDOWN, "non-finite values in Rayleigh-Ritz");
-  if (st_final & ST_CHOL_FAIL) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-  CK(cudaMemcpyAsync(&fallbacks, dfb, sizeof(int), cudaMemcpyDeviceToHost, st), "out");
-  CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
-  CK(cudaMemcpyAsync(hth.data(), theta, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
-  // resident block (float, n x K) for warm starts and the embedding
-  if (!g->X || g->K != K) {
-    ctx_free(c, g->X);
-    g->X = (float*)ctx_alloc(c, sizeof(float) * (size_t)n * K);
-    g->K = g->X ? K : 0;
-  }
-  if (g->X) {
-    if (sizeof(T) == 4) {
-      CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
-                           cudaMemcpyDeviceToDevice, st), "resident");
-    } else {
-      std::vector<double> hd((size_t)n * K);
-      CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, S, sizeof(T) * ld3, sizeof(double) * K, n,
-                           cudaMemcpyDeviceToHost, st), "resident");
-      CK(cudaStreamSynchronize(st), "resident");
-      std::vector<float> hf(hd.begin(), hd.end());
-      CK(cudaMemcpyAsync(g->X, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, st), "resident");
-      if (X_out) std::memcpy(X_out, hf.data(), sizeof(float) * hf.size());
-      CK(cudaStreamSynchronize(st), "resident");
+
+  int finish(float* X_out, sc_eig_info* info) override {
+    CK(cudaEventRecord(ev1, st), "event");
+    CK(cudaStreamSynchronize(st), "sync");
+    int st_final = 0;
+    int rc = read_status(&st_final);
+    if (rc != SC_OK) return rc;
+    if (st_final & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
+    if (st_final & ST_NONFINITE) return fail(c, SC_EBREAKDOWN, "non-finite values in Rayleigh-Ritz");
+    if (st_final & ST_CHOL_FAIL) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
+    int fallbacks = 0;
+    CK(cudaMemcpyAsync(&fallbacks, dfb, sizeof(int), cudaMemcpyDeviceToHost, st), "out");
+    CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
+    CK(cudaMemcpyAsync(hth.data(), theta, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
+    // resident block (float, n x K) for warm starts and the embedding
+    if (!g->X || g->K != K) {
+      if (g->X) ctx_free(c, g->X);
+      g->X = (float*)run_alloc(&ra, sizeof(float) * (size_t)n * K);
+      g->K = g->X ? K : 0;
     }
-  }
-  if (X_out && sizeof(T) == 4) {
-    CK(cudaMemcpy2DAsync(X_out, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
-                         cudaMemcpyDeviceToHost, st), "xout");
-  }
-  CK(cudaStreamSynchronize(st), "sync");
-  if (info) {
-    info->K = K;
-    info->iters_done = done;
-    info->fallbacks = fallbacks;
-    info->converged = converged;
-    for (int j = 0; j < K; ++j) {
-      info->lambda[j] = hth[j];
-      info->resid[j] = std::sqrt(std::max(hrho[j], 0.0));
+    if (g->X) {
+      if (sizeof(T) == 4) {
+        CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
+                             cudaMemcpyDeviceToDevice, st), "resident");
+      } else {
+        std::vector<double> hd((size_t)n * K);
+        CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, S, sizeof(T) * ld3, sizeof(double) * K,
+                             n, cudaMemcpyDeviceToHost, st), "resident");
+        CK(cudaStreamSynchronize(st), "resident");
+        std::vector<float> hf(hd.begin(), hd.end());
+        CK(cudaMemcpyAsync(g->X, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, st), "resident");
+        if (X_out) std::memcpy(X_out, hf.data(), sizeof(float) * hf.size());
+        CK(cudaStreamSynchronize(st), "resident");
+      }
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    info->ms = ms;
-    info->kernels = launches_total() - l0;
+    if (X_out && sizeof(T) == 4) {
+      CK(cudaMemcpy2DAsync(X_out, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
+                           cudaMemcpyDeviceToHost, st), "xout");
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    if (info) {
+      info->K = K;
+      info->iters_done = done_passes;
+      info->fallbacks = fallbacks;
+      info->converged = converged;
+      for (int j = 0; j < K; ++j) {
+        info->lambda[j] = hth[j];
+        info->resid[j] = std::sqrt(std::max(hrho[j], 0.0));
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      info->ms = ms;
+      info->kernels = launches_total() - l0;
+    }
+    if (o.tol_abs > 0 && !converged) return fail(c, SC_ENOTCONV, "tolerance not reached");
+    return SC_OK;
   }
-  if (o->tol_abs > 0 && !converged) return fail(c, SC_ENOTCONV, "tolerance not reached");
+};
+
+RunBase* make_run(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, cudaStream_t st) {
+  if (o->prec == SC_PREC_FP64) return new LobRun<double>(c, g, K, o, st);
+  return new LobRun<float>(c, g, K, o, st);
+}
+
+int check_lobpcg_args(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o) {
+  if (!c || !g || !o || K < 1 || K > SC_MAX_K || o->iters < 0) return SC_EINVAL;
+  if ((int64_t)3 * K > g->csr.n) return fail(c, SC_EINVAL, "sc_lobpcg: need 3K <= n");
+  if (o->prec < SC_PREC_MIXED || o->prec > SC_PREC_FP64) return fail(c, SC_EINVAL, "bad precision");
   return SC_OK;
 }
 
 }  // namespace
 
-// FP64 copies of the double-precision resident block go through the host (the library keeps
-// one float block per graph); the FP64 path writes X_out from that copy.
 int sc_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const float* X0,
               int32_t x0_rows, float* X_out, sc_eig_info* info) {
-  if (!c || !g || !o || K < 1 || K > SC_MAX_K || o->iters < 0) return SC_EINVAL;
-  if ((int64_t)3 * K > g->csr.n) return fail(c, SC_EINVAL, "sc_lobpcg: need 3K <= n");
-  if (o->prec < SC_PREC_MIXED || o->prec > SC_PREC_FP64) return fail(c, SC_EINVAL, "bad precision");
+  int rc = check_lobpcg_args(c, g, K, o);
+  if (rc != SC_OK) return rc;
   cudaSetDevice(c->device);
-  if (o->prec == SC_PREC_FP64) return run_lobpcg<double>(c, g, K, o, X0, x0_rows, X_out, info);
-  return run_lobpcg<float>(c, g, K, o, X0, x0_rows, X_out, info);
+  RunBase* r = make_run(c, g, K, o, c->stream);
+  rc = r->setup(X0, x0_rows);
+  while (rc == SC_OK && !r->finished()) rc = r->pass();
+  if (rc == SC_OK) rc = r->finish(X_out, info);
+  delete r;
+  return rc;
+}
+
+// Batched solves: the runs are issued pass by pass in turn, each on its own stream, so their
+// kernels -- in particular the one-CTA small dense solves -- overlap on the device.
+int sc_lobpcg_batch(sc_ctx* c, int count, sc_graph* const* graphs, const int* K,
+                    const sc_lobpcg_opts* opts, sc_eig_info* infos) {
+  if (!c || count < 0 || (count > 0 && (!graphs || !K || !opts))) return SC_EINVAL;
+  for (int q = 0; q < count; ++q) {
+    int rc = check_lobpcg_args(c, graphs[q], K[q], &opts[q]);
+    if (rc != SC_OK) return rc;
+  }
+  cudaSetDevice(c->device);
+  std::vector<cudaStream_t> streams(count);
+  std::vector<RunBase*> runs(count, nullptr);
+  int rc = SC_OK;
+  for (int q = 0; q < count && rc == SC_OK; ++q) {
+    if (cudaStreamCreateWithFlags(&streams[q], cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(c, SC_ECUDA, "stream creation failed");
+      streams[q] = nullptr;
+      break;
+    }
+    runs[q] = make_run(c, graphs[q], K[q], &opts[q], streams[q]);
+    rc = runs[q]->setup(nullptr, 0);
+  }
+  bool any = true;
+  while (rc == SC_OK && any) {
+    any = false;
+    for (int q = 0; q < count && rc == SC_OK; ++q)
+      if (!runs[q]->finished()) {
+        rc = runs[q]->pass();
+        any = true;
+      }
+  }
+  for (int q = 0; q < count && rc == SC_OK; ++q) rc = runs[q]->finish(nullptr, infos ? &infos[q] : nullptr);
+  for (int q = 0; q < count; ++q) {
+    delete runs[q];
+    if (streams[q]) cudaStreamDestroy(streams[q]);
+  }
+  return rc;
 }
 
 int sc_embed_rows(sc_ctx* c, const float* X, int32_t n, int K, float* E, int on_device) {
@@ -1055,4 +1162,303 @@ int sc_rr_solve(sc_ctx* c, int prec, int m, int K, const double* G, double* thet
   cudaSetDevice(c->device);
   if (prec == SC_PREC_FP64) return rr_t<double>(c, m, K, G, theta, Y);
   return rr_t<float>(c, m, K, G, theta, Y);
+}
+
+int sc_partition_batch(sc_ctx* c, int count, sc_graph* const* graphs, const int* K, const int* k,
+                       const sc_lobpcg_opts* opts, int kmeans_iters, int32_t* const* labels_out,
+                       sc_eig_info* infos) {
+  if (!c || count < 0 || (count > 0 && (!graphs || !K || !k || !opts || !labels_out)))
+    return SC_EINVAL;
+  int rc = sc_lobpcg_batch(c, count, graphs, K, opts, infos);
+  if (rc != SC_OK) return rc;
+  for (int q = 0; q < count && rc == SC_OK; ++q) {
+    sc_graph* g = graphs[q];
+    Alloc al = alloc_of(c);
+    const int n = g->csr.n;
+    float* E = al.get<float>((size_t)n * K[q]);
+    if (!E) return fail(c, SC_ENOMEM, "sc_partition_batch");
+    CK(rownorm<float>(c->stream, n, K[q], g->X, K[q], E, K[q]), "embed");
+    rc = kmeans_dev(c, E, n, K[q], k[q], kmeans_iters, opts[q].seed, nullptr, labels_out[q],
+                    nullptr, nullptr, nullptr, nullptr);
+    cudaStreamSynchronize(c->stream);
+    al.put(E);
+  }
+  return rc;
+}
+
+// ---- serving loop ---------------------------------------------------------------------
+// A worker thread owns the context.  Requests wait in a bounded queue; the worker admits
+// them while slots and the HBM budget allow (continuous batching at LOBPCG-pass granularity:
+// a request that arrives while others run joins at the next pass boundary), advances every
+// active solve by one pass per round on its own stream, and finishes each with the row
+// embedding and k-means.  Graphs stay resident by id, so a streaming delta warm-starts from
+// the block its graph kept.
+
+namespace {
+using Clock = std::chrono::steady_clock;
+
+struct SrvReq {
+  uint64_t ticket;
+  sc_request r;
+  std::vector<int32_t> src, dst;
+  Clock::time_point t0;
+};
+
+struct SrvResult {
+  int status = SC_EAGAIN;
+  std::vector<int32_t> labels;
+  sc_eig_info info{};
+  double latency_ms = 0.0;
+};
+
+struct SrvSlot {
+  SrvReq req;
+  sc_graph* g = nullptr;
+  RunBase* run = nullptr;
+  cudaStream_t st = nullptr;
+  size_t est = 0;
+};
+
+size_t footprint(const sc_request& r) {
+  const size_t kp = (size_t)(r.K + 3) / 4 * 4;
+  const size_t el = r.prec == SC_PREC_FP64 ? 8 : 4;
+  return (size_t)r.n * kp * 21 * el + (size_t)r.m * 48 + (size_t)r.n * 64 + (1u << 20);
+}
+}  // namespace
+
+struct sc_server {
+  sc_ctx* c = nullptr;
+  int max_slots = 1, queue_cap = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<SrvReq> queue;
+  std::unordered_map<uint64_t, SrvResult> results;
+  std::unordered_map<int, sc_graph*> graphs;
+  std::vector<SrvSlot> active;
+  uint64_t next = 1, completed = 0;
+  size_t reserved = 0;
+  bool stop = false;
+  std::thread worker;
+};
+
+static void srv_complete(sc_server* s, SrvSlot& sl, int status) {
+  SrvResult res;
+  res.status = status;
+  if (status == SC_OK && sl.run) {
+    // outputs (and the resident block the embedding reads) first; a tolerance that was not
+    // met is reported but still yields labels
+    status = sl.run->finish(nullptr, &res.info);
+    res.status = status;
+  }
+  if (status == SC_OK || status == SC_ENOTCONV) {
+    sc_ctx* c = s->c;
+    const int n = sl.g->csr.n, K = sl.req.r.K;
+    Alloc al = alloc_of(c);
+    float* E = al.get<float>((size_t)n * K);
+    if (!E) {
+      res.status = SC_ENOMEM;
+    } else {
+      res.labels.resize(n);
+      cudaError_t e = rownorm<float>(c->stream, n, K, sl.g->X, K, E, K);
+      int krc = e == cudaSuccess ? kmeans_dev(c, E, n, K, sl.req.r.k, sl.req.r.kmeans_iters,
+                                              sl.req.r.seed, nullptr, res.labels.data(), nullptr,
+                                              nullptr, nullptr, nullptr)
+                                 : SC_ECUDA;
+      if (krc != SC_OK) res.status = krc;
+      cudaStreamSynchronize(c->stream);
+      al.put(E);
+    }
+  }
+  res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t0).count();
+  delete sl.run;
+  sl.run = nullptr;
+  if (sl.st) cudaStreamDestroy(sl.st);
+  sl.st = nullptr;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->reserved -= sl.est;
+  s->results[sl.req.ticket] = std::move(res);
+  s->completed++;
+  s->cv_done.notify_all();
+}
+
+// Build or update the slot's graph and set up its solve; returns an sc_status.
+static int srv_start(sc_server* s, SrvSlot& sl) {
+  sc_ctx* c = s->c;
+  const sc_request& r = sl.req.r;
+  int rc = SC_OK;
+  if (r.kind == SC_REQ_COLD) {
+    auto it = s->graphs.find(r.graph_id);
+    if (it != s->graphs.end()) {
+      sc_graph_destroy(it->second);
+      s->graphs.erase(it);
+    }
+    sc_graph* g = nullptr;
+    rc = sc_build_laplacian(c, r.n, (int64_t)sl.req.src.size(), sl.req.src.data(), sl.req.dst.data(),
+                            nullptr, SC_SYM_LOGICAL, 0, &g);
+    if (rc != SC_OK) return rc;
+    s->graphs[r.graph_id] = g;
+    sl.g = g;
+  } else {
+    auto it = s->graphs.find(r.graph_id);
+    if (it == s->graphs.end()) return fail(c, SC_EINVAL, "delta for an unknown graph id");
+    sl.g = it->second;
+    rc = sc_stream_update(c, sl.g, r.n, (int64_t)sl.req.src.size(), sl.req.src.data(),
+                          sl.req.dst.data(), nullptr, 0);
+    if (rc != SC_OK) return rc;
+  }
+  sc_lobpcg_opts o{r.iters, r.tol_abs, 0.0, r.prec, r.seed, r.kind == SC_REQ_COLD ? 1 : 0};
+  rc = check_lobpcg_args(c, sl.g, r.K, &o);
+  if (rc != SC_OK) return rc;
+  if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(c, SC_ECUDA, "stream creation failed");
+  sl.run = make_run(c, sl.g, r.K, &o, sl.st);
+  return sl.run->setup(nullptr, 0);
+}
+
+static void srv_loop(sc_server* s) {
+  cudaSetDevice(s->c->device);
+  for (;;) {
+    std::vector<SrvReq> admit;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->active.empty() && s->queue.empty())
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(20),
+                            [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop && s->queue.empty() && s->active.empty()) break;
+      const size_t budget = s->c->budget;
+      while (!s->queue.empty() && (int)(s->active.size() + admit.size()) < s->max_slots) {
+        size_t est = footprint(s->queue.front().r);
+        if (budget && est > budget) {  // can never fit: reject
+          SrvResult res;
+          res.status = SC_ENOMEM;
+          s->results[s->queue.front().ticket] = std::move(res);
+          s->completed++;
+          s->queue.pop_front();
+          s->cv_done.notify_all();
+          continue;
+        }
+        if (budget && s->c->in_use + s->reserved + est > budget && !(s->active.empty() && admit.empty()))
+          break;  // wait for memory to free up
+        s->reserved += est;
+        admit.push_back(std::move(s->queue.front()));
+        admit.back().r.src = nullptr;
+        s->queue.pop_front();
+      }
+    }
+    for (auto& rq : admit) {
+      SrvSlot sl;
+      sl.est = footprint(rq.r);
+      sl.req = std::move(rq);
+      int rc = srv_start(s, sl);
+      if (rc != SC_OK) {
+        srv_complete(s, sl, rc);
+        continue;
+      }
+      s->active.push_back(std::move(sl));
+    }
+    // one pass for every active solve, then retire the finished ones
+    for (auto& sl : s->active) {
+      if (!sl.run->finished()) {
+        int rc = sl.run->pass();
+        if (rc != SC_OK) {
+          delete sl.run;
+          sl.run = nullptr;
+          srv_complete(s, sl, rc);
+        }
+      }
+    }
+    std::vector<SrvSlot> keep;
+    for (auto& sl : s->active) {
+      if (!sl.run) continue;  // failed and completed above
+      if (sl.run->finished()) srv_complete(s, sl, SC_OK);
+      else keep.push_back(std::move(sl));
+    }
+    s->active.swap(keep);
+  }
+}
+
+int sc_server_create(sc_ctx* c, int max_slots, int queue_cap, sc_server** out) {
+  if (!c || !out || max_slots < 1 || queue_cap < 1) return SC_EINVAL;
+  sc_server* s = new sc_server();
+  s->c = c;
+  s->max_slots = max_slots;
+  s->queue_cap = queue_cap;
+  s->worker = std::thread(srv_loop, s);
+  *out = s;
+  return SC_OK;
+}
+
+int sc_server_submit(sc_server* s, const sc_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket || r->n < 1 || r->m < 0 || (r->m > 0 && (!r->src || !r->dst)) ||
+      (r->kind != SC_REQ_COLD && r->kind != SC_REQ_DELTA) || r->K < 1 || r->k < 1)
+    return SC_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if ((int)s->queue.size() >= s->queue_cap) return SC_EAGAIN;
+  SrvReq q;
+  q.ticket = s->next++;
+  q.r = *r;
+  q.src.assign(r->src, r->src + r->m);
+  q.dst.assign(r->dst, r->dst + r->m);
+  q.t0 = Clock::now();
+  s->results[q.ticket] = SrvResult{};
+  *ticket = q.ticket;
+  s->queue.push_back(std::move(q));
+  s->cv_work.notify_one();
+  return SC_OK;
+}
+
+static int srv_take(sc_server* s, uint64_t ticket, int32_t* labels_out, int32_t n_cap,
+                    sc_eig_info* info, double* latency_ms) {
+  auto it = s->results.find(ticket);
+  if (it == s->results.end()) return SC_EINVAL;
+  if (it->second.status == SC_EAGAIN) return SC_EAGAIN;
+  SrvResult res = std::move(it->second);
+  s->results.erase(it);
+  if (res.status == SC_OK && labels_out) {
+    if ((int32_t)res.labels.size() > n_cap) return SC_EINVAL;
+    std::memcpy(labels_out, res.labels.data(), sizeof(int32_t) * res.labels.size());
+  }
+  if (info) *info = res.info;
+  if (latency_ms) *latency_ms = res.latency_ms;
+  return res.status;
+}
+
+int sc_server_poll(sc_server* s, uint64_t ticket, int32_t* labels_out, int32_t n_cap,
+                   sc_eig_info* info, double* latency_ms) {
+  if (!s) return SC_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  return srv_take(s, ticket, labels_out, n_cap, info, latency_ms);
+}
+
+int sc_server_wait(sc_server* s, uint64_t ticket, int timeout_ms, int32_t* labels_out,
+                   int32_t n_cap, sc_eig_info* info, double* latency_ms) {
+  if (!s) return SC_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto ready = [&] {
+    auto it = s->results.find(ticket);
+    return it == s->results.end() || it->second.status != SC_EAGAIN;
+  };
+  if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return SC_ETIMEOUT;
+  return srv_take(s, ticket, labels_out, n_cap, info, latency_ms);
+}
+
+int sc_server_stats(sc_server* s, int* active, int* queued, uint64_t* completed) {
+  if (!s) return SC_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (active) *active = (int)s->active.size();
+  if (queued) *queued = (int)s->queue.size();
+  if (completed) *completed = s->completed;
+  return SC_OK;
+}
+
+void sc_server_destroy(sc_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->graphs) sc_graph_destroy(kv.second);
+  delete s;
 }

@@ -38,6 +38,16 @@ class LobpcgOpts(C.Structure):
                 ("prec", C.c_int), ("seed", C.c_uint64), ("cold", C.c_int)]
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("graph_id", C.c_int), ("n", C.c_int32), ("m", C.c_int64),
+                ("src", C.c_void_p), ("dst", C.c_void_p), ("K", C.c_int), ("k", C.c_int),
+                ("iters", C.c_int), ("kmeans_iters", C.c_int), ("prec", C.c_int),
+                ("tol_abs", C.c_double), ("seed", C.c_uint64)]
+
+
+SC_REQ_COLD, SC_REQ_DELTA = 0, 1
+
+
 class EigInfo(C.Structure):
     _fields_ = [("K", C.c_int), ("iters_done", C.c_int), ("fallbacks", C.c_int),
                 ("converged", C.c_int), ("lambda_", C.c_double * SC_MAX_K),
@@ -84,6 +94,14 @@ def lib():
         "sc_stream_update": ([vp, vp, i32, i64, vp, vp, vp, C.c_int], C.c_int),
         "sc_gram": ([vp, C.c_int, i64, C.c_int, C.c_int, vp, i64, vp, i64, vp, C.c_int], C.c_int),
         "sc_rr_solve": ([vp, C.c_int, C.c_int, C.c_int, vp, vp, vp], C.c_int),
+        "sc_lobpcg_batch": ([vp, C.c_int, vp, vp, vp, vp], C.c_int),
+        "sc_partition_batch": ([vp, C.c_int, vp, vp, vp, vp, C.c_int, vp, vp], C.c_int),
+        "sc_server_create": ([vp, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
+        "sc_server_submit": ([vp, C.POINTER(Request), C.POINTER(u64)], C.c_int),
+        "sc_server_poll": ([vp, u64, vp, i32, C.POINTER(EigInfo), C.POINTER(dbl)], C.c_int),
+        "sc_server_wait": ([vp, u64, C.c_int, vp, i32, C.POINTER(EigInfo), C.POINTER(dbl)], C.c_int),
+        "sc_server_stats": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(u64)], C.c_int),
+        "sc_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -120,7 +138,10 @@ def _np(a, dtype):
 
 class Ctx:
     def __init__(self, device=0, stream=None, budget=0):
+        import weakref
+
         self.h = C.c_void_p()
+        self.children = weakref.WeakSet()  # graphs and servers that must go first
         s = C.c_void_p(stream) if stream else None
         rc = lib().sc_ctx_create(C.byref(self.h), device, s, budget)
         if rc != SC_OK:
@@ -133,6 +154,8 @@ class Ctx:
 
     def close(self):
         if self.h:
+            for ch in list(self.children):
+                ch.close()
             lib().sc_ctx_destroy(self.h)
             self.h = C.c_void_p()
 
@@ -154,11 +177,12 @@ class Ctx:
 class Graph:
     def __init__(self, ctx, h):
         self.ctx, self.h = ctx, h
+        ctx.children.add(self)
 
     def close(self):
-        if self.h:
+        if self.h and self.ctx.h:
             lib().sc_graph_destroy(self.h)
-            self.h = C.c_void_p()
+        self.h = C.c_void_p()
 
     def __del__(self):
         try:
@@ -308,3 +332,83 @@ def sc_rr_solve(ctx: Ctx, G, K, prec=SC_PREC_FP32):
     Y = np.empty((m, K), np.float64)
     ctx.check(lib().sc_rr_solve(ctx.h, prec, m, K, _ptr(G)[0], _ptr(th)[0], _ptr(Y)[0]))
     return th, Y
+
+
+def sc_lobpcg_batch(ctx: Ctx, graphs, K, iters=20, tol_abs=0.0, prec=SC_PREC_MIXED, seeds=None,
+                    cold=1):
+    """Batched LOBPCG over several graphs; returns a list of info dicts."""
+    cnt = len(graphs)
+    Ks = (C.c_int * cnt)(*([K] * cnt if isinstance(K, int) else K))
+    hs = (C.c_void_p * cnt)(*[g.h.value for g in graphs])
+    seeds = seeds or [0] * cnt
+    opts = (LobpcgOpts * cnt)(*[LobpcgOpts(iters, tol_abs, 0.0, prec, s, cold) for s in seeds])
+    infos = (EigInfo * cnt)()
+    ctx.check(lib().sc_lobpcg_batch(ctx.h, cnt, hs, Ks, opts, infos))
+    return [infos[q].as_dict() for q in range(cnt)]
+
+
+def sc_partition_batch(ctx: Ctx, graphs, K, k, iters=20, kmeans_iters=50, prec=SC_PREC_MIXED,
+                       seeds=None):
+    cnt = len(graphs)
+    Kl = [K] * cnt if isinstance(K, int) else list(K)
+    kl = [k] * cnt if isinstance(k, int) else list(k)
+    seeds = seeds or [0] * cnt
+    outs = [np.empty(sc_graph_info(g)[0], np.int32) for g in graphs]
+    lp = (C.c_void_p * cnt)(*[o.ctypes.data for o in outs])
+    hs = (C.c_void_p * cnt)(*[g.h.value for g in graphs])
+    opts = (LobpcgOpts * cnt)(*[LobpcgOpts(iters, 0.0, 0.0, prec, s, 1) for s in seeds])
+    infos = (EigInfo * cnt)()
+    ctx.check(lib().sc_partition_batch(ctx.h, cnt, hs, (C.c_int * cnt)(*Kl), (C.c_int * cnt)(*kl),
+                                       opts, kmeans_iters, lp, infos))
+    return outs, [infos[q].as_dict() for q in range(cnt)]
+
+
+class Server:
+    """Continuous-batching partition server (thread-safe)."""
+
+    def __init__(self, ctx: Ctx, max_slots=8, queue_cap=64):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        ctx.check(lib().sc_server_create(ctx.h, max_slots, queue_cap, C.byref(self.h)))
+        ctx.children.add(self)
+
+    def submit(self, kind, graph_id, n, src, dst, K, k, iters=20, kmeans_iters=50,
+               prec=SC_PREC_MIXED, tol_abs=0.0, seed=0):
+        src = np.ascontiguousarray(src, np.int32)
+        dst = np.ascontiguousarray(dst, np.int32)
+        r = Request(kind, graph_id, n, src.shape[0], src.ctypes.data, dst.ctypes.data, K, k, iters,
+                    kmeans_iters, prec, tol_abs, seed)
+        t = C.c_uint64()
+        rc = lib().sc_server_submit(self.h, C.byref(r), C.byref(t))
+        if rc != SC_OK:
+            raise ScError(rc, "sc_server_submit")
+        return t.value
+
+    def wait(self, ticket, n_cap, timeout_ms=600000):
+        labels = np.empty(max(n_cap, 1), np.int32)
+        info = EigInfo()
+        lat = C.c_double()
+        rc = lib().sc_server_wait(self.h, ticket, timeout_ms, labels.ctypes.data, n_cap,
+                                  C.byref(info), C.byref(lat))
+        return rc, labels[:n_cap], info.as_dict(), lat.value
+
+    def stats(self):
+        a, q, d = C.c_int(), C.c_int(), C.c_uint64()
+        lib().sc_server_stats(self.h, C.byref(a), C.byref(q), C.byref(d))
+        return a.value, q.value, d.value
+
+    def close(self):
+        if self.h and self.ctx.h:
+            lib().sc_server_destroy(self.h)
+        self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sc_server_create(ctx: Ctx, max_slots=8, queue_cap=64) -> Server:
+    return Server(ctx, max_slots, queue_cap)
+

@@ -1,0 +1,128 @@
+"""Batched solves and the serving loop (GPU): each result equals the same request run alone."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1708_07481_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sc():
+    from paper_1708_07481_gb300 import build, sc as S
+
+    build.build()
+    return S
+
+
+@pytest.fixture(scope="module")
+def ctx(sc):
+    c = sc.sc_ctx_create(0)
+    yield c
+    c.close()
+
+
+SPECS = [(3000, 8, 1), (7001, 11, 2), (20000, 20, 3), (1500, 5, 4)]
+
+
+def _graphs(sc, ctx):
+    gs = [W.dcsbm(n, K, seed=s) for n, K, s in SPECS]
+    return gs, [sc.sc_build_laplacian(ctx, g.n, g.src, g.dst) for g in gs]
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batch_equals_single(sc, ctx, prec):
+    gs, Gs = _graphs(sc, ctx)
+    Ks = [K for _, K, _ in SPECS]
+    seeds = [11, 12, 13, 14]
+    infos = sc.sc_lobpcg_batch(ctx, Gs, Ks, iters=12, prec=prec, seeds=seeds)
+    for q, (G, K) in enumerate(zip(Gs, Ks)):
+        lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=12, prec=prec, seed=seeds[q], cold=1)
+        assert np.array_equal(lam, infos[q]["lam"])
+        assert np.array_equal(resid, infos[q]["resid"])
+
+
+def test_partition_batch_equals_single_and_oracle(sc, ctx):
+    gs, Gs = _graphs(sc, ctx)
+    Ks = [K for _, K, _ in SPECS]
+    outs, infos = sc.sc_partition_batch(ctx, Gs, Ks, Ks, iters=20, seeds=[0, 0, 0, 0])
+    for q, (g, G, K) in enumerate(zip(gs, Gs, Ks)):
+        labels, _ = sc.sc_partition(ctx, G, K, K, iters=20, seed=0)
+        assert np.array_equal(labels, outs[q])
+        L = O.laplacian_csr(g.n, g.src, g.dst)
+        X0 = W.start_block(0, g.n, K).astype(np.float32).astype(np.float64)
+        ref, _, _, _ = O.partition(L, X0, K, W.kmeans_uniforms(0, K), 20, 50)
+        # 20 passes leave residual norms near 3 on these graphs, so the FP32 and FP64
+        # blocks agree only to rounding amplified by the unconverged subspace; a row on a
+        # k-means boundary may switch.  Agreement up to a permutation, and the same quality
+        # against the planted blocks as the oracle's own labels.
+        assert O.partition_metrics(ref, labels)[0] >= 0.995, q
+        pm_ref = O.partition_metrics(g.truth, ref)[0]
+        assert abs(O.partition_metrics(g.truth, labels)[0] - pm_ref) <= 5e-3, q
+
+
+def test_server_results_equal_standalone(sc, ctx):
+    # a streaming graph (cold stage then two emerging-edge deltas) interleaved with other
+    # cold requests; every result must equal the same sequence run alone
+    g = W.dcsbm(6000, 9, seed=21)
+    deltas = W.emerging_deltas(g, stages=3)
+    others = [W.dcsbm(n, K, seed=s) for n, K, s in [(4000, 7, 22), (9000, 12, 23), (2500, 6, 24)]]
+    ref_ctx = sc.sc_ctx_create(0)
+    try:
+        G = sc.sc_build_laplacian(ref_ctx, g.n, g.src[deltas[0]], g.dst[deltas[0]])
+        ref_stream = [sc.sc_partition(ref_ctx, G, 9, 9, iters=15, seed=5, cold=1)[0]]
+        for s in (1, 2):
+            sc.sc_stream_update(ref_ctx, G, g.n, g.src[deltas[s]], g.dst[deltas[s]])
+            ref_stream.append(sc.sc_partition(ref_ctx, G, 9, 9, iters=8, seed=5, cold=0)[0])
+        ref_other = []
+        for o in others:
+            Go = sc.sc_build_laplacian(ref_ctx, o.n, o.src, o.dst)
+            ref_other.append(sc.sc_partition(ref_ctx, Go, o.K, o.K, iters=15, seed=6, cold=1)[0])
+    finally:
+        ref_ctx.close()
+
+    srv_ctx = sc.sc_ctx_create(0)
+    srv = sc.sc_server_create(srv_ctx, max_slots=3, queue_cap=16)
+    try:
+        t_other = [srv.submit(sc.SC_REQ_COLD, 100 + q, o.n, o.src, o.dst, o.K, o.K, iters=15, seed=6)
+                   for q, o in enumerate(others)]
+        t0 = srv.submit(sc.SC_REQ_COLD, 7, g.n, g.src[deltas[0]], g.dst[deltas[0]], 9, 9, iters=15, seed=5)
+        rc, lab0, info0, lat0 = srv.wait(t0, g.n)
+        assert rc == sc.SC_OK and np.array_equal(lab0, ref_stream[0])
+        for s in (1, 2):
+            t = srv.submit(sc.SC_REQ_DELTA, 7, g.n, g.src[deltas[s]], g.dst[deltas[s]], 9, 9, iters=8, seed=5)
+            rc, lab, info, lat = srv.wait(t, g.n)
+            assert rc == sc.SC_OK and np.array_equal(lab, ref_stream[s]), s
+            assert lat > 0
+        for q, o in enumerate(others):
+            rc, lab, info, lat = srv.wait(t_other[q], o.n)
+            assert rc == sc.SC_OK and np.array_equal(lab, ref_other[q])
+    finally:
+        srv.close()
+        srv_ctx.close()
+
+
+def test_server_admission_and_queue_limits(sc):
+    small = W.dcsbm(2000, 5, seed=30)
+    ctx = sc.sc_ctx_create(0, budget=64 << 20)
+    srv = sc.sc_server_create(ctx, max_slots=1, queue_cap=2)
+    try:
+        big = W.dcsbm(400000, 40, seed=31, dmin=2, dmax=3)
+        t_big = srv.submit(sc.SC_REQ_COLD, 1, big.n, big.src, big.dst, 40, 40)
+        rc, _, _, _ = srv.wait(t_big, big.n)
+        assert rc == sc.SC_ENOMEM
+        tickets, refused = [], 0
+        for q in range(12):
+            try:
+                tickets.append(srv.submit(sc.SC_REQ_COLD, 2 + q, small.n, small.src, small.dst, 5, 5, iters=5))
+            except sc.ScError as e:
+                assert e.code == sc.SC_EAGAIN
+                refused += 1
+        assert refused > 0
+        for t in tickets:
+            rc, lab, _, _ = srv.wait(t, small.n)
+            assert rc == sc.SC_OK
+    finally:
+        srv.close()
+        ctx.close()
