@@ -244,6 +244,28 @@ int sc_gram(sc_ctx* ctx, int prec, int64_t n, int a, int b, const void* A, int64
 int sc_rr_solve(sc_ctx* ctx, int prec, int m, int K, const double* G, double* theta,
                 double* Y);
 
+/* ---- Gram without allocation -------------------------------------------------------------
+ * sc_gram_static: C = A' B (FP64, a x b row-major) for FP32 device blocks A (n x a, stride
+ * lda) and B (n x b, stride ldb), computed like sc_gram with SC_PREC_FP32 (CUDA cores, FP64
+ * sums across row chunks) but allocating nothing: no cudaMalloc or cudaFree, no allocation by
+ * any library, no context.  It is meant for callers that cannot allocate device memory, for
+ * instance code inside a host framework that owns and partitions all device memory, or a
+ * latency-critical loop that must not enter the allocator.  A, B and C are device pointers on
+ * the current device; work is issued on cuda_stream (NULL = the legacy default stream) and
+ * the call returns without waiting for it.
+ * Scratch: the split-K partials and the tile list live in one fixed 8 MiB device array that
+ * the library defines (every GPU that loads the library holds it until the process exits).
+ * The first call on a device looks up that array's device address; make that first call
+ * before any stream capture.  All calls share the array and it keeps the previous call's
+ * contents, so calls whose work overlaps on the GPU (other streams, other threads) race and
+ * must be serialized by the caller.
+ * Limits: 1 <= a, b <= SC_GRAM_STATIC_MAX_COLS (SC_EINVAL beyond); n >= 0.
+ * Errors: SC_EINVAL (sizes, null pointers), SC_ECUDA (launch or symbol lookup failed).
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate. */
+#define SC_GRAM_STATIC_MAX_COLS 1024
+int sc_gram_static(int64_t n, int a, int b, const float* A, int64_t lda, const float* B,
+                   int64_t ldb, double* C, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -181,3 +181,87 @@ template cudaError_t gram<double>(cudaStream_t, Alloc&, long long, const Cat3<do
                                   const Cat3<double>&, double*, int, bool, int);
 
 }  // namespace sc
+
+// ---- Gram without allocation --------------------------------------------------------------
+// The split-K partials and the tile list of sc_gram_static live in this fixed device array
+// instead of memory allocated per call.  8 MiB: 64 x 64-tile partials for up to 256 tile-
+// chunk pairs plus the tile list.  Every GPU that loads the library keeps it until exit.
+#include <mutex>
+
+#include "../../include/sc.h"
+
+namespace sc {
+namespace {
+constexpr size_t GRAM_STATIC_DOUBLES = (size_t)1 << 20;  // 8 MiB
+constexpr int GRAM_STATIC_TILES = 256;                    // tile list at the end
+static __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
+
+// Device address of g_gram_static for the current device, looked up once per device (the
+// host-side name of the array is only a stand-in, never a device address).
+double* gram_static_addr(int dev) {
+  static std::mutex mu;
+  static double* addr[64] = {nullptr};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_gram_static) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    addr[dev] = (double*)p;
+  }
+  return addr[dev];
+}
+
+// The (row tile, column tile) list of an na x nb tile grid, written on the device so the
+// call needs no host-to-device copy.
+__global__ void k_tile_list(int2* tiles, int na, int nb) {
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) tiles[t] = make_int2(t / nb, t % nb);
+}
+}  // namespace
+}  // namespace sc
+
+extern "C" int sc_gram_static(int64_t n, int a, int b, const float* A, int64_t lda,
+                              const float* B, int64_t ldb, double* C, void* cuda_stream) {
+  using namespace sc;
+  if (n < 0 || a < 1 || b < 1 || a > SC_GRAM_STATIC_MAX_COLS || b > SC_GRAM_STATIC_MAX_COLS ||
+      lda < a || ldb < b || !A || !B || !C)
+    return SC_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SC_ECUDA;
+  double* scratch = gram_static_addr(dev);
+  if (!scratch) return SC_ECUDA;
+  if (n == 0) {
+    return cudaMemset2DAsync(C, sizeof(double) * b, 0, sizeof(double) * b, a, st) == cudaSuccess
+               ? SC_OK
+               : SC_ECUDA;
+  }
+  const int na = (a + TB - 1) / TB, nb = (b + TB - 1) / TB;
+  const int nt = na * nb;  // <= 16 x 16 = 256 tiles
+  // chunks: fill the GPU, at least 512 rows each, and fit the partials in the array
+  const long long cap_pairs = (long long)(GRAM_STATIC_DOUBLES - GRAM_STATIC_TILES) / (TB * TB);
+  long long nch = (152LL * 2 + nt - 1) / nt;
+  long long maxch = (n + 511) / 512;
+  if (nch > maxch) nch = maxch;
+  if (nch * nt > cap_pairs) nch = cap_pairs / nt;
+  if (nch < 1) nch = 1;
+  long long rpc = (n + nch - 1) / nch;
+  rpc = (rpc + RB - 1) / RB * RB;
+  nch = (n + rpc - 1) / rpc;
+  int2* tiles = (int2*)(scratch + (GRAM_STATIC_DOUBLES - GRAM_STATIC_TILES));
+  double* part = scratch;
+  // the tile list is rewritten on every call (the array keeps the previous call's contents);
+  // the partials need no clearing: every entry the reduction reads is written by this call
+  k_tile_list<<<1, 256, 0, st>>>(tiles, na, nb);
+  note_launch();
+  Cat3<float> ca = cat<float>(A, lda, a), cb = cat<float>(B, ldb, b);
+  k_gram<float><<<(unsigned)(nt * nch), NT, 0, st>>>(n, ca, cb, tiles, (int)nch, nt, rpc, part);
+  note_launch();
+  long long tot = (long long)nt * TB * TB;
+  unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
+  k_gram_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, tiles, a, b, C, b, 0);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? SC_OK : SC_ECUDA;
+}

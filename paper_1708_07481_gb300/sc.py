@@ -102,6 +102,7 @@ def lib():
         "sc_server_wait": ([vp, u64, C.c_int, vp, i32, C.POINTER(EigInfo), C.POINTER(dbl)], C.c_int),
         "sc_server_stats": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(u64)], C.c_int),
         "sc_server_destroy": ([vp], None),
+        "sc_gram_static": ([i64, C.c_int, C.c_int, vp, i64, vp, i64, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -412,3 +413,26 @@ class Server:
 def sc_server_create(ctx: Ctx, max_slots=8, queue_cap=64) -> Server:
     return Server(ctx, max_slots, queue_cap)
 
+
+def sc_gram_static(A, B, C_out, stream=None):
+    """C_out = A' B without any device allocation (see include/sc.h): A (n x a), B (n x b) are
+    float32 CUDA tensors, C_out an (a x b) float64 CUDA tensor; issued on `stream` (a
+    cudaStream_t handle, default stream when None) without waiting for it."""
+    import torch
+
+    if A.dtype != torch.float32 or B.dtype != torch.float32 or C_out.dtype != torch.float64:
+        raise TypeError("sc_gram_static: A, B float32 and C_out float64 expected")
+    if not (A.is_cuda and B.is_cuda and C_out.is_cuda):
+        raise ValueError("sc_gram_static: device tensors expected")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[0] != B.shape[0]:
+        raise ValueError("sc_gram_static: A (n x a) and B (n x b) expected")
+    n, a = int(A.shape[0]), int(A.shape[1])
+    b = int(B.shape[1])
+    if (A.stride(1) != 1 and a > 1) or (B.stride(1) != 1 and b > 1) or \
+            tuple(C_out.shape) != (a, b) or not C_out.is_contiguous():
+        raise ValueError("sc_gram_static: row-major A, B and a contiguous (a x b) C_out expected")
+    rc = lib().sc_gram_static(n, a, b, C.c_void_p(A.data_ptr()), int(A.stride(0)),
+                              C.c_void_p(B.data_ptr()), int(B.stride(0)),
+                              C.c_void_p(C_out.data_ptr()), C.c_void_p(stream) if stream else None)
+    if rc != SC_OK:
+        raise ScError(rc, "sc_gram_static")
