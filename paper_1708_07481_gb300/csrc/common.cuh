@@ -7,6 +7,19 @@
 
 namespace sc {
 
+// Tile (i, j) of tile number t of a Gram over an na x nb tile grid, numbered row by row over
+// all tiles, or (sym, na == nb) over the tiles with i <= j only.
+__device__ __forceinline__ int2 tile_coord(int t, int nb, int sym) {
+  if (!sym) return make_int2(t / nb, t % nb);
+  int i = 0;
+  while (t >= nb - i) {
+    t -= nb - i;
+    ++i;
+  }
+  return make_int2(i, i + t);
+}
+
+
 // ---- device status word bits (written by kernels, read back by the host) ----------------
 enum : int {
   ST_EDGE_RANGE = 1,   // an edge endpoint outside [0, n)

@@ -139,22 +139,60 @@ __device__ void blk_tri_inv(int ka, const T* W, int ldw, const T* rdiag, T* Li, 
   }
 }
 
+// In-place LDL' factorization of the symmetric n x n matrix held in the lower triangle of M
+// (row stride ldm), with the unit lower factor L replaced by L^-1 column by column as the
+// elimination proceeds (Gauss-Jordan style: at step k every row i > k is reduced by
+// l_ik = W_ik / d_k, which updates its trailing part W_ij (j > k) with the pivot column and
+// its leading part (L^-1)_ic (c < k) with row k of L^-1).  On return M[i][c] (c < i) holds
+// (L^-1)_ic and dd[k] the pivot d_k.  One barrier per column: the pivot column is passed on
+// through the double buffer cb (2 n entries) by the rows that finish it.  Returns the first
+// k with d_k <= tol (rows and pivots before it are final), else -1.
+template <typename T>
+__device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int i = tid; i < n; i += nt) cb[i] = M[(long long)i * ldm];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const T* cur = cb + (k & 1) * n;
+    T* nxt = cb + ((k + 1) & 1) * n;
+    const T dk = cur[k];
+    if (!(dk > tol)) return k;  // every thread read the same value
+    if (tid == 0) dd[k] = dk;
+    const T invd = (T)1 / dk;
+    const T* rowk = M + (long long)k * ldm;
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      T* mi = M + (long long)i * ldm;
+      const T l = cur[i] * invd;
+      for (int c = lane; c <= i; c += 32) {
+        // c < k: row k of L^-1; c == k: the new entry -l; c > k: the pivot column
+        const T y = (c < k ? rowk : cur)[c];
+        const T v = (c == k) ? -l : fma(-l, y, mi[c]);
+        mi[c] = v;
+        if (c == k + 1) nxt[i] = v;
+      }
+    }
+    __syncthreads();
+  }
+  return -1;
+}
+
 // Cholesky-QR transform in the arithmetic of T: from the FP64 Gram G (accumulated in FP64
-// across CTAs), scale s = diag(G)^-1/2 in FP64, factor s G s = L L' in T, and write
-// Tm = diag(s) L^-T (ka x ka upper triangular) so that V Tm has orthonormal columns.
-// On a pivot <= pivot_tol: ST_CHOL_FAIL in *status and the failing column in *fail_col.
-// SM = the factor and inverse live in shared memory (typed shared-memory pointers let the
-// compiler issue shared loads instead of generic ones).
+// across CTAs), scale s = diag(G)^-1/2 in FP64, factor s G s = L D L' in T (with L^-1 formed
+// alongside), and write Tm = diag(s) L^-T D^-1/2 (ka x ka upper triangular) so that V Tm has
+// orthonormal columns.  A zero column has a zero pivot.  On a pivot <= pivot_tol:
+// ST_CHOL_FAIL in *status and the failing column in *fail_col, unless the failure lies in
+// the trailing columns >= keep (the direction block), in which case the leading keep columns
+// are returned, the rest zeroed, and *pflag cleared.
+// SM = the matrix lives in shared memory.
 template <typename T, bool SM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
                int* status, int* fail_col, double pivot_tol, int keep, int* pflag) {
   extern __shared__ __align__(16) unsigned char craw[];
-  T* s = (T*)craw;        // ka scale factors
-  T* rdiag = s + ka;      // ka
-  T* W = SM ? rdiag + ka : Wg;                                // ka x ka factor
-  T* Li = SM ? rdiag + ka + (size_t)ka * ka : Wg + (size_t)ka * ka;  // ka x ka inverse
-  __shared__ int sflag;
+  T* s = (T*)craw;    // ka scale factors
+  T* dd = s + ka;     // ka pivots
+  T* cb = dd + ka;    // 2 ka pivot-column buffer
+  T* W = SM ? cb + 2 * ka : Wg;  // ka x ka
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < ka; i += nt) {
     double dgi = G[(long long)i * ldg + i];
@@ -168,16 +206,11 @@ __global__ void __launch_bounds__(256)
     W[i * ka + j] = (T)g * s[i] * s[j];
   }
   __syncthreads();
-  int fz = -1;
-  for (int i = 0; i < ka && fz < 0; ++i)
-    if (s[i] == (T)0) fz = i;  // a zero column
-  int fc = blk_chol<T>(fz >= 0 ? fz : ka, W, ka, rdiag, (T)pivot_tol, &sflag);
-  if (fc < 0) fc = fz;
-  int kk = ka;  // size of the factored leading block that is returned
+  const int fc = blk_ldl_inv<T>(ka, W, ka, dd, cb, (T)pivot_tol);
+  __syncthreads();
+  int kk = ka;  // size of the leading block whose transform is returned
   if (fc >= 0) {
     if (pflag && keep > 0 && fc >= keep) {
-      // the trailing (direction) columns lie in the span of the leading ones: keep the
-      // leading block's transform, zero the rest, and tell the later steps to drop them
       kk = keep;
       if (tid == 0) *pflag = 0;
     } else {
@@ -188,10 +221,14 @@ __global__ void __launch_bounds__(256)
       return;
     }
   }
-  blk_tri_inv<T>(kk, W, ka, rdiag, Li, ka);
+  for (int i = tid; i < kk; i += nt) cb[i] = rsqrt(dd[i]);
+  __syncthreads();
+  // Tm[r][c] = s_r (L^-1)_cr d_c^-1/2 for r <= c < kk
   for (int idx = tid; idx < ka * ka; idx += nt) {
-    int i = idx / ka, j = idx % ka;
-    Tm[(long long)i * ka + j] = (j >= i && j < kk) ? s[i] * Li[j * ka + i] : (T)0;
+    int r = idx / ka, c = idx % ka;
+    T v = 0;
+    if (r <= c && c < kk) v = s[r] * (r == c ? (T)1 : W[c * ka + r]) * cb[c];
+    Tm[(long long)r * ka + c] = v;
   }
 }
 
@@ -227,6 +264,16 @@ __device__ inline float start_entry(int i, int j) {
 #ifdef SC_RR_PHASES
 __device__ long long g_rr_phase[8];
 __device__ long long g_rr_sub[4];
+__device__ long long g_rr_inv[4];
+#define RR_INV(i, t0)                                                  \
+  do {                                                                 \
+    __syncthreads();                                                   \
+    if (threadIdx.x == 0) {                                            \
+      long long t1 = clock64();                                        \
+      g_rr_inv[i] += t1 - t0;                                          \
+      t0 = t1;                                                         \
+    }                                                                  \
+  } while (0)
 #define RR_SUB(i, t0)                                                  \
   do {                                                                 \
     if (threadIdx.x == 0) {                                            \
@@ -236,6 +283,9 @@ __device__ long long g_rr_sub[4];
     }                                                                  \
   } while (0)
 #else
+#define RR_INV(i, t0) \
+  do {                \
+  } while (0)
 #define RR_SUB(i, t0) \
   do {                \
   } while (0)
@@ -687,28 +737,599 @@ __global__ void __launch_bounds__(RR_NT)
   RR_MARK(6);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Rayleigh-Ritz, register-slot form for m <= 32 NS: the same four steps as k_rr_eig with
+// less synchronization.
+//  1. Tridiagonalization, one barrier per Householder step.  Warp w owns rows i = w + NW t,
+//     so row i's entry of a vector held as lane (i & 31), slot (i >> 5) is reachable with a
+//     compile-time slot index.  Every warp keeps the reflector v, the vector w and the next
+//     row x in registers (columns j = lane + 32 u), forms the next reflector itself from x
+//     (no barrier), computes p = beta A v on its own rows, and after the one barrier (which
+//     publishes p and the per-warp parts of p'v) forms w, the next row x (row k+1 with the
+//     two-sided update applied, computed by every warp from the not-yet-updated row) and the
+//     rank-2 update of its own rows.  The reflector of step k is stored in row k.
+//  2. Multisection on Sturm counts as in k_rr_eig, converged to eps ||T|| (the accuracy the
+//     reduction itself has).
+//  3. Inverse iteration: LU with partial pivoting of T - sigma I fused with the forward
+//     elimination of the right-hand side (only U is stored), back substitution; two sweeps,
+//     each followed by a block Cholesky-QR through blk_ldl_inv.
+//  4. Back-transformation with one warp per column pair, no barriers.
+template <typename T, int NS>
+__device__ __forceinline__ T slot_sel(const T (&a)[NS], int u) {
+  T r = a[0];
+#pragma unroll
+  for (int q = 1; q < NS; ++q)
+    if (q == u) r = a[q];
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int NS, int NW, bool SM>
+__global__ void __launch_bounds__(NW * 32)
+    k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
+                 double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
+                 int* status, int* pflag, int mP, int* nfallback) {
+  constexpr int NT = NW * 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* d = (T*)smraw;     // m
+  T* e = d + m;         // m
+  T* beta = e + m;      // m
+  T* e2 = beta + m;     // m
+  T* Pb = e2 + m;       // 2 m: p of the current step
+  T* Vsh = Pb + 2 * m;  // 2 m: the reflector of the current step (double-buffered)
+  T* lam = Vsh + 2 * m; // K
+  T* shift = lam + K;   // K
+  T* dd = shift + K;    // K pivots of the block Cholesky
+  T* cbuf = dd + K;     // 2 K
+  T* wv = cbuf + 2 * K; // K
+  T* coef = wv + K;     // K
+  T* red = coef + K;    // 3 NW per-warp parts, then scalar slots RS ..
+  T* nxt = red + 3 * NW + 8;
+  T* A = SM ? nxt : Ag;                             // m x m (row stride m)
+  T* Z = SM ? A + (size_t)m * m : Zg;               // m x K
+  T* U = SM ? Z + (size_t)m * K : Ug;               // 3 m K
+  T* Gs = SM ? U + (size_t)3 * m * K : Gsg;         // K x K
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int RS = 3 * NW;  // red[RS + 0..4]: lo, hi, max e^2, min pivot, MGS scale
+
+  for (int i = warp; i < m; i += NW)
+    for (int j = lane; j < m; j += 32)
+      A[i * m + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+  __syncthreads();
+  RR_MARK(0);
+
+  // ---- 1. tridiagonalization
+  // Warp 0 forms the reflectors: from x = row k (with the updates of the steps before k) it
+  // writes v_k to a double-buffered shared vector; after the first barrier the worker warps
+  // form p = beta A v on the rows they own (row class i mod NWR), two rows at a time; after
+  // the second barrier the workers form w = p - (beta/2)(p'v) v and apply the rank-2 update
+  // to their rows while warp 0 computes the next row x and the next reflector.  Warps that
+  // share warp 0's scheduler (warp % 4 == 0) own no rows, so the reflector's dependent chain
+  // is not starved of issue slots by the update.
+  constexpr int NWR = NW - NW / 4;  // row-owning warps: warp % 4 != 0
+  const int wk = (warp & 3) ? warp - (warp >> 2) - 1 : -1;  // worker index
+  T x[NS];
+  if (warp == 0) {
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int j = lane + 32 * u;
+      x[u] = j < m ? A[j] : (T)0;  // row 0
+    }
+  }
+  // warp 0: reflector of step kk from x into vbuf, plus d, e, beta
+  auto reflector = [&](int kk, T* vbuf) {
+    const int k1 = kk + 1;
+    const T x0 = __shfl_sync(FULL, slot_sel(x, k1 >> 5), k1 & 31);
+    const T xk = __shfl_sync(FULL, slot_sel(x, kk >> 5), kk & 31);
+    T sg = 0;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int j = lane + 32 * u;
+      if (j > k1 && j < m) sg = fma(x[u], x[u], sg);
+    }
+    sg = warp_sum(sg);
+    T bet = 0, iv0 = 0, ek = x0;
+    if (sg != (T)0) {
+      const T mu = sqrt(x0 * x0 + sg);
+      const T v0 = (x0 <= (T)0) ? x0 - mu : -sg / (x0 + mu);
+      bet = (T)2 * v0 * v0 / (sg + v0 * v0);
+      iv0 = (T)1 / v0;
+      ek = mu;
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int j = lane + 32 * u;
+      if (j < m) vbuf[j] = (j == k1) ? (T)1 : ((j > k1) ? x[u] * iv0 : (T)0);
+    }
+    if (lane == 0) {
+      d[kk] = xk;
+      e[kk] = ek;
+      beta[kk] = bet;
+    }
+  };
+  if (warp == 0 && m > 2) reflector(0, Vsh);
+  int k = 0;
+  long long tsub = clock64();
+  for (; k + 2 < m; ++k) {
+    const int k1 = k + 1;
+    const T* __restrict__ vk = Vsh + (k & 1) * m;
+    __syncthreads();
+    RR_SUB(0, tsub);
+    const T bet = beta[k];
+    const int umin = k1 >> 5;
+    T vr[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int j = lane + 32 * u;
+      vr[u] = j < m ? vk[j] : (T)0;
+    }
+    // p_i = beta (A v)_i on this warp's rows i >= k1, two rows at a time
+    if (wk >= 0) {
+      int off = (wk - k1) % NWR;
+      if (off < 0) off += NWR;
+      for (int i = k1 + off; i < m; i += 2 * NWR) {
+        const int i2 = i + NWR;
+        const bool has2 = i2 < m;  // uniform in the warp
+        const T* __restrict__ ra = A + i * m;
+        const T* __restrict__ rb = A + (has2 ? i2 : i) * m;
+        T sa = 0, sb = 0;
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const int j = lane + 32 * u;
+          if (u >= umin && j < m) {
+            sa = fma(ra[j], vr[u], sa);
+            sb = fma(rb[j], vr[u], sb);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          sa += __shfl_xor_sync(FULL, sa, o);
+          sb += __shfl_xor_sync(FULL, sb, o);
+        }
+        if (lane == 0) {
+          Pb[i] = bet * sa;
+          if (has2) Pb[i2] = bet * sb;
+        }
+      }
+    }
+    RR_SUB(1, tsub);
+    __syncthreads();
+    RR_SUB(2, tsub);
+    if (warp != 0 && wk < 0) continue;  // idle warps: straight to the next step's barrier
+    // w = p - (beta/2)(p'v) v (every warp forms p'v itself, same order everywhere)
+    T wr[NS];
+    T pv = 0;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int j = lane + 32 * u;
+      wr[u] = (j >= k1 && j < m) ? Pb[j] : (T)0;
+      pv = fma(wr[u], vr[u], pv);
+    }
+    pv = warp_sum(pv);
+    const T kc = bet * (T)0.5 * pv;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) wr[u] = fma(-kc, vr[u], wr[u]);
+    if (warp == 0) {
+      // the next row (row k1 with this step's update; no warp updates row k1) and the
+      // reflector of step k, kept in row k for the back-transformation
+      const T wk1 = Pb[k1] - kc;
+      const T* r1 = A + k1 * m;
+      T* rk = A + k * m;
+#pragma unroll
+      for (int u = 0; u < NS; ++u) {
+        const int j = lane + 32 * u;
+        x[u] = (j >= k1 && j < m) ? r1[j] - wr[u] - wk1 * vr[u] : (T)0;
+        if (j > k1 && j < m) rk[j] = vr[u];
+      }
+      if (k1 + 2 < m) reflector(k1, Vsh + (k1 & 1) * m);
+    } else {
+      // rank-2 update of this warp's rows i > k1, two rows at a time
+      const int r0 = k1 + 1;
+      int off = (wk - r0) % NWR;
+      if (off < 0) off += NWR;
+      for (int i = r0 + off; i < m; i += 2 * NWR) {
+        const int i2 = i + NWR;
+        const bool has2 = i2 < m;
+        const T via = vk[i], wia = Pb[i] - kc * via;
+        const T vib = has2 ? vk[i2] : (T)0, wib = has2 ? Pb[i2] - kc * vib : (T)0;
+        T* __restrict__ ra = A + i * m;
+        T* __restrict__ rb = A + (has2 ? i2 : i) * m;
+        T na[NS], nb[NS];
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const int j = lane + 32 * u;
+          if (u >= umin && j < m) {
+            na[u] = ra[j] - (via * wr[u] + wia * vr[u]);
+            nb[u] = rb[j] - (vib * wr[u] + wib * vr[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+          const int j = lane + 32 * u;
+          if (u >= umin && j < m) {
+            ra[j] = na[u];
+            if (has2) rb[j] = nb[u];
+          }
+        }
+      }
+    }
+    RR_SUB(3, tsub);
+  }
+  (void)tsub;
+  __syncthreads();  // the last row's diagonal was updated by its owner
+  if (warp == 0) {
+    // x = row k (k = m - 2, or 0 when m == 1)
+    const T xa = __shfl_sync(FULL, slot_sel(x, k >> 5), k & 31);
+    const int k1 = k + 1 < m ? k + 1 : k;
+    const T xb = __shfl_sync(FULL, slot_sel(x, k1 >> 5), k1 & 31);
+    if (lane == 0) {
+      d[k] = xa;
+      if (m >= 2) {
+        e[k] = xb;
+        d[m - 1] = A[(m - 1) * m + (m - 1)];
+      }
+      e[m - 1] = 0;
+    }
+  }
+  __syncthreads();
+  RR_MARK(1);
+
+  // ---- 2. Gershgorin bounds; 17-point multisection, 16 lanes per eigenvalue
+  {
+    T lo_p = (T)3e38, hi_p = (T)-3e38, emax = 0;
+    for (int i = tid; i < m; i += NT) {
+      T r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0);
+      lo_p = min(lo_p, d[i] - r);
+      hi_p = max(hi_p, d[i] + r);
+      emax = max(emax, e[i] * e[i]);
+      e2[i] = e[i] * e[i];
+      if (!isfinite(d[i]) || !isfinite(e[i])) atomicOr(status, ST_NONFINITE);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo_p = min(lo_p, __shfl_xor_sync(FULL, lo_p, o));
+      hi_p = max(hi_p, __shfl_xor_sync(FULL, hi_p, o));
+      emax = max(emax, __shfl_xor_sync(FULL, emax, o));
+    }
+    if (lane == 0) {
+      red[warp] = lo_p;
+      red[NW + warp] = hi_p;
+      red[2 * NW + warp] = emax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      T lo = red[0], hi = red[NW], em = red[2 * NW];
+      for (int q = 1; q < NW; ++q) {
+        lo = min(lo, red[q]);
+        hi = max(hi, red[NW + q]);
+        em = max(em, red[2 * NW + q]);
+      }
+      red[RS] = lo;
+      red[RS + 1] = hi;
+      red[RS + 2] = em;
+    }
+    __syncthreads();
+  }
+  const T tnorm = max(fabs(red[RS]), fabs(red[RS + 1]));
+  const T pivmin = Lim<T>::tiny() * max((T)1, red[RS + 2]);
+  const T glo = red[RS] - (T)2 * Lim<T>::eps() * tnorm - pivmin;
+  const T ghi = red[RS + 1] + (T)2 * Lim<T>::eps() * tnorm + pivmin;
+  const T abstol = Lim<T>::eps() * tnorm;
+  {
+    const int grp = tid >> 4, sl = tid & 15;
+    const unsigned gmask = 0xFFFFu << (lane & 16);
+    for (int j = grp; j < K; j += NT >> 4) {
+      T a = glo, b = ghi;
+      for (int it = 0; it < 48; ++it) {
+        T tol = max((T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)), abstol) + (T)4 * pivmin;
+        if (b - a <= tol) break;
+        T h = (b - a) / (T)17;
+        int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
+        unsigned bal = __ballot_sync(gmask, c > j) >> (lane & 16);
+        int first = bal ? (__ffs(bal) - 1) : 16;
+        T na = first == 0 ? a : a + h * (T)first;
+        T nb = first == 16 ? b : a + h * (T)(first + 1);
+        if (!(nb > na)) break;
+        a = na;
+        b = nb;
+      }
+      if (sl == 0) lam[j] = (T)0.5 * (a + b);
+    }
+  }
+  __syncthreads();
+  RR_MARK(2);
+
+  // ---- 3. inverse iteration
+  const T sep = (T)10 * Lim<T>::eps() * tnorm + pivmin;
+  if (tid == 0) {
+    T prev = (T)0;
+    for (int j = 0; j < K; ++j) {
+      T sj = lam[j];
+      if (j > 0 && sj < prev + sep) sj = prev + sep;
+      shift[j] = sj;
+      prev = sj;
+    }
+  }
+  for (int idx = tid; idx < m * K; idx += NT) Z[idx] = (T)start_entry(idx / K, idx % K);
+  __syncthreads();
+  RR_MARK(3);
+  const T small_piv = Lim<T>::eps() * tnorm + pivmin;
+#define UF(i, a) U[((i) * 3 + (a)) * K + j]
+  long long tinv = clock64();
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    for (int j = tid; j < K; j += NT) {
+      // LU with partial pivoting of T - s I, the right-hand side eliminated alongside
+      const T sj = shift[j];
+      T al = d[0] - sj, bt = m > 1 ? e[0] : (T)0;
+      T bc = Z[j];
+      for (int i = 0; i + 1 < m; ++i) {
+        const T dl = e[i];
+        const T an = d[i + 1] - sj, bn = (i + 2 < m) ? e[i + 1] : (T)0;
+        const T bx = Z[(i + 1) * K + j];
+        // partial pivoting between rows i and i + 1, written without branches (the choice
+        // differs between the lanes of a warp)
+        const bool keep = fabs(al) >= fabs(dl);
+        if (keep && al == (T)0) al = small_piv;
+        const T piv = keep ? al : dl;
+        const T mlt = sdiv(keep ? dl : al, piv);
+        UF(i, 0) = piv;
+        UF(i, 1) = keep ? bt : an;
+        UF(i, 2) = keep ? (T)0 : bn;
+        Z[i * K + j] = keep ? bc : bx;
+        const T bnew = keep ? bx - mlt * bc : bc - mlt * bx;
+        const T anew = keep ? an - mlt * bt : bt - mlt * an;
+        const T btn = keep ? bn : -mlt * bn;
+        bc = bnew;
+        al = anew;
+        bt = btn;
+      }
+      if (fabs(al) < small_piv) al = al < (T)0 ? -small_piv : small_piv;
+      UF(m - 1, 0) = al;
+      UF(m - 1, 1) = 0;
+      UF(m - 1, 2) = 0;
+      Z[(m - 1) * K + j] = bc;
+      T z1 = 0, z2 = 0, mx = 0;
+      for (int i = m - 1; i >= 0; --i) {
+        const T zi = sdiv(Z[i * K + j] - UF(i, 1) * z1 - UF(i, 2) * z2, UF(i, 0));
+        Z[i * K + j] = zi;
+        z2 = z1;
+        z1 = zi;
+        mx = max(mx, fabs(zi));
+      }
+      const T inv = mx > (T)0 ? (T)1 / mx : (T)1;
+      for (int i = 0; i < m; ++i) Z[i * K + j] *= inv;
+    }
+    __syncthreads();
+    RR_INV(0, tinv);
+    bool ok = true;
+    for (int pass = 0; pass < 2 && ok; ++pass) {
+      // Gram Z'Z (lower triangle), one thread per entry, four accumulators
+      for (int p = tid; p < K * K; p += NT) {
+        const int a = p / K, b = p % K;
+        if (b > a) continue;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int r = 0;
+        for (; r + 3 < m; r += 4) {
+          a0 = fma(Z[r * K + a], Z[r * K + b], a0);
+          a1 = fma(Z[(r + 1) * K + a], Z[(r + 1) * K + b], a1);
+          a2 = fma(Z[(r + 2) * K + a], Z[(r + 2) * K + b], a2);
+          a3 = fma(Z[(r + 3) * K + a], Z[(r + 3) * K + b], a3);
+        }
+        for (; r < m; ++r) a0 = fma(Z[r * K + a], Z[r * K + b], a0);
+        Gs[a * K + b] = (a0 + a1) + (a2 + a3);
+      }
+      __syncthreads();
+      RR_INV(1, tinv);
+      for (int a = tid; a < K; a += NT) wv[a] = rsqrt(max(Gs[a * K + a], Lim<T>::tiny()));
+      __syncthreads();
+      for (int p = tid; p < K * K; p += NT) {
+        const int a = p / K, b = p % K;
+        if (b <= a) Gs[a * K + b] *= wv[a] * wv[b];
+      }
+      __syncthreads();
+      const int fc = blk_ldl_inv<T>(K, Gs, K, dd, cbuf, (T)(sizeof(T) == 4 ? 1e-6 : 1e-14));
+      __syncthreads();
+      RR_INV(2, tinv);
+      if (fc >= 0) {
+        ok = false;
+        break;
+      }
+      for (int a = tid; a < K; a += NT) cbuf[a] = rsqrt(dd[a]);
+      if (tid == 0) {
+        T mind = (T)1;
+        for (int a = 0; a < K; ++a) mind = min(mind, dd[a]);
+        red[RS + 3] = mind;
+      }
+      // L^-1 transposed into the (unused) upper triangle: Gs[a][b] = (L^-1)_ba for a < b,
+      // so lanes that own consecutive output columns b read consecutive addresses
+      for (int p = tid; p < K * K; p += NT) {
+        const int a = p / K, b = p % K;
+        if (b > a) Gs[a * K + b] = Gs[b * K + a];
+      }
+      __syncthreads();
+      // Z <- Z diag(wv) L^-T D^-1/2: out_b = d_b^-1/2 sum_{a <= b} z_a wv_a (L^-1)_ba; a warp
+      // per row, lanes own output columns (kept in registers until the row has been read)
+      for (int r = warp; r < m; r += NW) {
+        T* zr = Z + r * K;
+        T out[16];
+        const int nq = (K + 31) >> 5;  // uniform
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q >= nq) break;
+          const int b = lane + 32 * q;
+          T acc = 0;
+          if (b < K) {
+            for (int a = 0; a < b; ++a) acc = fma(zr[a] * wv[a], Gs[a * K + b], acc);
+            acc = (acc + zr[b] * wv[b]) * cbuf[b];
+          }
+          out[q] = acc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q >= nq) break;
+          const int b = lane + 32 * q;
+          if (b < K) zr[b] = out[q];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      RR_INV(3, tinv);
+      if (red[RS + 3] > (T)0.5) break;  // nearly orthonormal input: one pass was enough
+    }
+    if (!ok) {
+      // in-order modified Gram-Schmidt (tight clusters)
+      for (int j = 0; j < K; ++j) {
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int q = warp; q < j; q += NW) {
+            T acc = 0;
+            for (int i = lane; i < m; i += 32) acc += Z[i * K + q] * Z[i * K + j];
+            acc = warp_sum(acc);
+            if (lane == 0) coef[q] = acc;
+          }
+          __syncthreads();
+          for (int i = tid; i < m; i += NT) {
+            T acc = 0;
+            for (int q = 0; q < j; ++q) acc += coef[q] * Z[i * K + q];
+            Z[i * K + j] -= acc;
+          }
+          __syncthreads();
+        }
+        if (warp == 0) {
+          T part = 0;
+          for (int i = lane; i < m; i += 32) part += Z[i * K + j] * Z[i * K + j];
+          part = warp_sum(part);
+          if (lane == 0) red[RS + 4] = part > (T)0 ? (T)1 / sqrt(part) : (T)0;
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += NT) Z[i * K + j] *= red[RS + 4];
+        __syncthreads();
+      }
+    }
+  }
+#undef UF
+  RR_MARK(4);
+
+  // ---- 4. back-transformation Y = H_0 ... H_{m-3} Z, two columns per warp in registers
+  for (int j0 = 2 * warp; j0 < K; j0 += 2 * NW) {
+    const int j1 = j0 + 1;
+    const bool two = j1 < K;  // uniform in the warp
+    T za[NS], zb[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int i = lane + 32 * u;
+      za[u] = i < m ? Z[i * K + j0] : (T)0;
+      zb[u] = (i < m && two) ? Z[i * K + j1] : (T)0;
+    }
+    for (int kr = m - 3; kr >= 0; --kr) {
+      const T bet = beta[kr];
+      if (bet == (T)0) continue;  // uniform
+      const int k1 = kr + 1;
+      const T* vk = A + kr * m;
+      T cv[NS];
+      T sa = 0, sb = 0;
+#pragma unroll
+      for (int u = 0; u < NS; ++u) {
+        const int i = lane + 32 * u;
+        cv[u] = (i == k1) ? (T)1 : ((i > k1 && i < m) ? vk[i] : (T)0);
+        sa = fma(cv[u], za[u], sa);
+        sb = fma(cv[u], zb[u], sb);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(FULL, sa, o);
+        sb += __shfl_xor_sync(FULL, sb, o);
+      }
+      sa *= bet;
+      sb *= bet;
+#pragma unroll
+      for (int u = 0; u < NS; ++u) {
+        za[u] = fma(-sa, cv[u], za[u]);
+        zb[u] = fma(-sb, cv[u], zb[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int i = lane + 32 * u;
+      if (i < m_full) {
+        Y[(long long)i * K + j0] = i < m ? za[u] : (T)0;
+        if (two) Y[(long long)i * K + j1] = i < m ? zb[u] : (T)0;
+      }
+    }
+  }
+  RR_MARK(5);
+  for (int j = tid; j < K; j += NT) theta[j] = (double)lam[j];
+  if (pflag && tid == 0) {
+    if (*pflag == 0 && nfallback) *nfallback += 1;
+    *pflag = 1;  // re-armed for the next pass
+  }
+  RR_MARK(6);
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
                      int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag) {
-  size_t base = sizeof(T) * (2 * (size_t)ka);
-  size_t wbytes = sizeof(T) * (size_t)ka * ka * 2;
+  size_t base = sizeof(T) * (4 * (size_t)ka);
+  size_t wbytes = sizeof(T) * (size_t)ka * ka;
   int in_smem = base + wbytes <= 200 * 1024;
   size_t sm = base + (in_smem ? wbytes : 0);
   T* Wg = nullptr;
   if (!in_smem) {
-    Wg = al.get<T>((size_t)ka * ka * 2);
+    Wg = al.get<T>((size_t)ka * ka);
     if (!Wg) return cudaErrorMemoryAllocation;
   }
   auto kern = in_smem ? k_chol_inv<T, true> : k_chol_inv<T, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   ProfScope ps(st, "chol_inv");
-  kern<<<1, 256, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag);
+  kern<<<1, 512, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag);
   note_launch();
   e = cudaGetLastError();
   al.put(Wg);
+  return e;
+}
+
+// Register-slot Rayleigh-Ritz: shared-memory sizes and launch for one (NS, NW) shape.
+template <typename T, int NS, int NW>
+cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
+                       double* theta, T* Y, int* d_status, int* pflag, int mP, int* nfallback) {
+  const size_t base = sizeof(T) * ((size_t)8 * m + 7 * (size_t)K + 3 * NW + 8);
+  const size_t big = sizeof(T) * ((size_t)m * m + 4 * (size_t)m * K + (size_t)K * K);
+  constexpr bool can_sm = sizeof(T) == 4 && NS == 5;  // the only shape whose blocks fit
+  const bool insm = can_sm && base + big <= 220 * 1024;
+  const size_t sm = base + (insm ? big : 0);
+  T* Ag = nullptr;
+  if (!insm) {
+    Ag = al.get<T>((size_t)m * m + 4 * (size_t)m * K + (size_t)K * K);
+    if (!Ag) return cudaErrorMemoryAllocation;
+  }
+  T* Zg = insm ? nullptr : Ag + (size_t)m * m;
+  T* Ug = insm ? nullptr : Zg + (size_t)m * K;
+  T* Gsg = insm ? nullptr : Ug + (size_t)3 * m * K;
+  auto kern = k_rr_eig_reg<T, NS, NW, false>;
+  if constexpr (can_sm) {
+    if (insm) kern = k_rr_eig_reg<T, NS, NW, true>;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) {
+    ProfScope ps(st, "rr_eig");
+    kern<<<1, NW * 32, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, d_status, pflag, mP,
+                                 nfallback);
+    note_launch();
+    e = cudaGetLastError();
+  }
+  al.put(Ag);
   return e;
 }
 
@@ -716,6 +1337,17 @@ template <typename T>
 cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
                    double* theta, T* Y, int* d_status, int* pflag, int mP, int* nfallback) {
   if (m < 1 || K < 1 || K > m) return cudaErrorInvalidValue;
+  // m <= 480: register-slot kernel (m = 3K up to K = 160)
+  if (m <= 160) {
+    if constexpr (sizeof(T) == 4)
+      return rr_eig_reg<T, 5, 32>(st, al, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+    else
+      return rr_eig_reg<T, 5, 16>(st, al, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+  }
+  if (m <= 320)
+    return rr_eig_reg<T, 10, 16>(st, al, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+  if (m <= 480)
+    return rr_eig_reg<T, 15, 16>(st, al, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
   size_t base = sizeof(T) * ((size_t)6 * m + K + 128);
   size_t abytes = sizeof(T) * (size_t)m * m;
   size_t zbytes = sizeof(T) * (size_t)m * K;

@@ -46,15 +46,15 @@ __device__ inline void map_cols(const Cat3<T>& M, int c0, ColMap* cm) {
 
 template <typename T>
 __global__ void __launch_bounds__(NT)
-    k_gram(long long n, Cat3<T> A, Cat3<T> B, const int2* __restrict__ tiles, int nch,
-           int ntiles, long long rows_per_chunk, double* __restrict__ part) {
+    k_gram(long long n, Cat3<T> A, Cat3<T> B, int nb, int sym, int nch, int ntiles,
+           long long rows_per_chunk, double* __restrict__ part) {
   using AT = typename Acc<T>::type;
   __shared__ __align__(16) T As[RB][TB];
   __shared__ __align__(16) T Bs[RB][TB];
   __shared__ ColMap cma[TB], cmb[TB];
   const int tile = blockIdx.x / nch;
   const int chunk = blockIdx.x % nch;
-  const int2 tl = tiles[tile];
+  const int2 tl = tile_coord(tile, nb, sym);
   const int ti = tl.x, tj = tl.y;
   map_cols(A, ti * TB, cma);
   map_cols(B, tj * TB, cmb);
@@ -107,15 +107,14 @@ __global__ void __launch_bounds__(NT)
 
 // C[tile element] = sum over chunks in chunk order; one thread per tile element, so the
 // chunk loop reads consecutive addresses across a warp.
-__global__ void k_gram_reduce(const double* __restrict__ part, int nch, int ntiles,
-                              const int2* __restrict__ tiles, int a, int b, double* C, int ldc,
-                              int sym) {
+__global__ void k_gram_reduce(const double* __restrict__ part, int nch, int ntiles, int nb,
+                              int a, int b, double* C, int ldc, int sym) {
   long long tot = (long long)ntiles * TB * TB;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot;
        g += (long long)gridDim.x * blockDim.x) {
     int tile = (int)(g / (TB * TB));
     int e = (int)(g % (TB * TB));
-    int2 tl = tiles[tile];
+    int2 tl = tile_coord(tile, nb, sym);
     int gi = tl.x * TB + e / TB, gj = tl.y * TB + e % TB;
     if (gi >= a || gj >= b) continue;
     double s = 0.0;
@@ -135,12 +134,8 @@ cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, cons
   if (a == 0 || b == 0) return cudaSuccess;
   if (n == 0) return cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * b, a, st);
   int na = (a + TB - 1) / TB, nb = (b + TB - 1) / TB;
-  int2 tl_host[64 * 64];
-  int nt = 0;
-  for (int i = 0; i < na; ++i)
-    for (int j = 0; j < nb; ++j)
-      if (!sym || i <= j) tl_host[nt++] = make_int2(i, j);
-  if (nt > 64 * 64) return cudaErrorInvalidValue;
+  if (sym && na != nb) return cudaErrorInvalidValue;
+  const int nt = sym ? na * (na + 1) / 2 : na * nb;
   // Row chunks: enough CTAs to fill the GPU twice, but at least 512 rows per chunk so the
   // FP64 partial tiles stay small next to the rows they summarise.
   long long target = 152LL * 2;
@@ -152,25 +147,21 @@ cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, cons
   rpc = (rpc + RB - 1) / RB * RB;
   nch = (n + rpc - 1) / rpc;
   if (nch < 1) nch = 1;
-  int2* tiles = al.get<int2>(nt);
   double* part = al.get<double>((size_t)nt * nch * TB * TB);
   cudaError_t e = cudaSuccess;
-  if (!tiles || !part) {
+  if (!part) {
     e = cudaErrorMemoryAllocation;
   } else {
-    cudaMemcpyAsync(tiles, tl_host, sizeof(int2) * nt, cudaMemcpyHostToDevice, st);
-    {
-      ProfScope ps(st, "gram");
-      k_gram<T><<<(unsigned)(nt * nch), NT, 0, st>>>(n, A, B, tiles, (int)nch, nt, rpc, part);
-      note_launch();
-      long long tot = (long long)nt * TB * TB;
-      unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
-      k_gram_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, tiles, a, b, C, ldc, sym ? 1 : 0);
-      note_launch();
-    }
+    ProfScope ps(st, "gram");
+    k_gram<T><<<(unsigned)(nt * nch), NT, 0, st>>>(n, A, B, nb, sym ? 1 : 0, (int)nch, nt, rpc,
+                                                   part);
+    note_launch();
+    long long tot = (long long)nt * TB * TB;
+    unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
+    k_gram_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, nb, a, b, C, ldc, sym ? 1 : 0);
+    note_launch();
     e = cudaGetLastError();
   }
-  al.put(tiles);
   al.put(part);
   return e;
 }
@@ -183,9 +174,9 @@ template cudaError_t gram<double>(cudaStream_t, Alloc&, long long, const Cat3<do
 }  // namespace sc
 
 // ---- Gram without allocation --------------------------------------------------------------
-// The split-K partials and the tile list of sc_gram_static live in this fixed device array
-// instead of memory allocated per call.  8 MiB: 64 x 64-tile partials for up to 256 tile-
-// chunk pairs plus the tile list.  Every GPU that loads the library keeps it until exit.
+// The split-K partials of sc_gram_static live in this fixed device array instead of memory
+// allocated per call.  8 MiB: 64 x 64-tile partials for up to 256 tile-chunk pairs.  Every
+// GPU that loads the library keeps it until exit.
 #include <mutex>
 
 #include "../../include/sc.h"
@@ -193,7 +184,6 @@ template cudaError_t gram<double>(cudaStream_t, Alloc&, long long, const Cat3<do
 namespace sc {
 namespace {
 constexpr size_t GRAM_STATIC_DOUBLES = (size_t)1 << 20;  // 8 MiB
-constexpr int GRAM_STATIC_TILES = 256;                    // tile list at the end
 static __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
 
 // Device address of g_gram_static for the current device, looked up once per device (the
@@ -212,12 +202,6 @@ double* gram_static_addr(int dev) {
     addr[dev] = (double*)p;
   }
   return addr[dev];
-}
-
-// The (row tile, column tile) list of an na x nb tile grid, written on the device so the
-// call needs no host-to-device copy.
-__global__ void k_tile_list(int2* tiles, int na, int nb) {
-  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) tiles[t] = make_int2(t / nb, t % nb);
 }
 }  // namespace
 }  // namespace sc
@@ -241,7 +225,7 @@ extern "C" int sc_gram_static(int64_t n, int a, int b, const float* A, int64_t l
   const int na = (a + TB - 1) / TB, nb = (b + TB - 1) / TB;
   const int nt = na * nb;  // <= 16 x 16 = 256 tiles
   // chunks: fill the GPU, at least 512 rows each, and fit the partials in the array
-  const long long cap_pairs = (long long)(GRAM_STATIC_DOUBLES - GRAM_STATIC_TILES) / (TB * TB);
+  const long long cap_pairs = (long long)GRAM_STATIC_DOUBLES / (TB * TB);
   long long nch = (152LL * 2 + nt - 1) / nt;
   long long maxch = (n + 511) / 512;
   if (nch > maxch) nch = maxch;
@@ -250,18 +234,15 @@ extern "C" int sc_gram_static(int64_t n, int a, int b, const float* A, int64_t l
   long long rpc = (n + nch - 1) / nch;
   rpc = (rpc + RB - 1) / RB * RB;
   nch = (n + rpc - 1) / rpc;
-  int2* tiles = (int2*)(scratch + (GRAM_STATIC_DOUBLES - GRAM_STATIC_TILES));
   double* part = scratch;
-  // the tile list is rewritten on every call (the array keeps the previous call's contents);
-  // the partials need no clearing: every entry the reduction reads is written by this call
-  k_tile_list<<<1, 256, 0, st>>>(tiles, na, nb);
-  note_launch();
+  // the partials need no clearing (the array keeps the previous call's contents): every entry
+  // the reduction reads is written by this call
   Cat3<float> ca = cat<float>(A, lda, a), cb = cat<float>(B, ldb, b);
-  k_gram<float><<<(unsigned)(nt * nch), NT, 0, st>>>(n, ca, cb, tiles, (int)nch, nt, rpc, part);
+  k_gram<float><<<(unsigned)(nt * nch), NT, 0, st>>>(n, ca, cb, nb, 0, (int)nch, nt, rpc, part);
   note_launch();
   long long tot = (long long)nt * TB * TB;
   unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
-  k_gram_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, tiles, a, b, C, b, 0);
+  k_gram_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, nb, a, b, C, b, 0);
   note_launch();
   return cudaGetLastError() == cudaSuccess ? SC_OK : SC_ECUDA;
 }

@@ -155,8 +155,8 @@ __device__ inline void convert_stage(const float* stage, uint8_t* big, uint8_t* 
 
 __global__ void __launch_bounds__(NTH, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              long long n, const int2* __restrict__ tiles, int nch, int ntiles,
-              long long rows_per_chunk, int a, int b, double* __restrict__ part, int* status) {
+              long long n, int nbt, int sym, int nch, int ntiles, long long rows_per_chunk,
+              int a, int b, double* __restrict__ part, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled operands
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(NTH, 1)
   __shared__ int abort_flag;
 
   const int tile = blockIdx.x / nch, chunk = blockIdx.x % nch;
-  const int2 tl = tiles[tile];
+  const int2 tl = tile_coord(tile, nbt, sym);
   const int ca = tl.x * TM, cb = tl.y * TN;
   const long long r0 = (long long)chunk * rows_per_chunk;
   long long r1 = r0 + rows_per_chunk;
@@ -306,23 +306,47 @@ __global__ void __launch_bounds__(NTH, 1)
   }
 }
 
-__global__ void k_gram_tc_reduce(const double* __restrict__ part, int nch, int ntiles,
-                                 const int2* __restrict__ tiles, int a, int b, SegMap ma,
-                                 SegMap mb, double* C, int ldc, int sym) {
-  long long tot = (long long)ntiles * TM * TN;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot;
-       g += (long long)gridDim.x * blockDim.x) {
-    int tile = (int)(g / (TM * TN));
-    int e = (int)(g % (TM * TN));
-    int2 tl = tiles[tile];
-    int gi = tl.x * TM + e / TN, gj = tl.y * TN + e % TN;
-    if (gi >= a || gj >= b) continue;
-    int oi = seg_index(ma, gi), oj = seg_index(mb, gj);
-    if (oi < 0 || oj < 0) continue;
-    double s = 0.0;
-    for (int c = 0; c < nch; ++c) s += part[((long long)c * ntiles + tile) * TM * TN + e];
-    C[(long long)oi * ldc + oj] = s;
-    if (sym && tl.x != tl.y) C[(long long)oj * ldc + oi] = s;
+// C = the sum of the chunk partials of each tile, in a fixed order.  One CTA per tile row:
+// warp w sums chunks w, w + 8, w + 16, ... (in increasing order) for 32 consecutive columns,
+// and the 8 warp sums are added in warp order.  Rows and columns past the output are skipped.
+__global__ void __launch_bounds__(256)
+    k_gram_tc_reduce(const double* __restrict__ part, int nch, int ntiles, int nbt, int a, int b,
+                     SegMap ma, SegMap mb, double* C, int ldc, int sym) {
+  __shared__ double ps[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tile = blockIdx.x / TM, er = blockIdx.x % TM;
+  const int2 tl = tile_coord(tile, nbt, sym);
+  const int gi = tl.x * TM + er;
+  if (gi >= a) return;  // uniform in the CTA
+  const int oi = seg_index(ma, gi);
+  const int ncol = min(TN, b - tl.y * TN);
+  const double* src = part + (long long)tile * TM * TN + (long long)er * TN;
+  const long long cstride = (long long)ntiles * TM * TN;
+  for (int j0 = 0; j0 < ncol; j0 += 32) {
+    const int j = j0 + lane;
+    double s0 = 0.0, s1 = 0.0;
+    if (j < ncol) {
+      int c = w;
+      for (; c + 8 < nch; c += 16) {
+        s0 += src[(long long)c * cstride + j];
+        s1 += src[(long long)(c + 8) * cstride + j];
+      }
+      if (c < nch) s0 += src[(long long)c * cstride + j];
+    }
+    ps[w][lane] = s0 + s1;
+    __syncthreads();
+    if (w == 0 && j < ncol) {
+      double t = ps[0][lane];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) t += ps[q][lane];
+      const int gj = tl.y * TN + j;
+      const int oj = seg_index(mb, gj);
+      if (oi >= 0 && oj >= 0) {
+        C[(long long)oi * ldc + oj] = t;
+        if (sym && tl.x != tl.y) C[(long long)oj * ldc + oi] = t;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -385,42 +409,35 @@ cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, lon
   if (!make_map(&mapA, A, n, a, lda, TM) || !make_map(&mapB, B, n, b, ldb, TN))
     return cudaErrorNotSupported;
   const int na = (a + TM - 1) / TM, nb = (b + TN - 1) / TN;
-  int2 tl_host[144];
-  int nt = 0;
-  for (int i = 0; i < na; ++i)
-    for (int j = 0; j < nb; ++j)
-      if (!sym || i <= j) tl_host[nt++] = make_int2(i, j);
+  if (sym && na != nb) return cudaErrorInvalidValue;
+  const int nt = sym ? na * (na + 1) / 2 : na * nb;
   long long nch = std::max<long long>(1, (152 + nt - 1) / nt);
   long long maxch = (n + 4 * BK - 1) / (4 * BK);  // at least 4 stages per CTA
   if (nch > maxch) nch = maxch;
   long long rpc = (n + nch - 1) / nch;
   rpc = (rpc + BK - 1) / BK * BK;
   nch = (n + rpc - 1) / rpc;
-  int2* tiles = al.get<int2>(nt);
   double* part = al.get<double>((size_t)nt * nch * TM * TN);
   cudaError_t e = cudaSuccess;
-  if (!tiles || !part) {
+  if (!part) {
     e = cudaErrorMemoryAllocation;
   } else {
-    cudaMemcpyAsync(tiles, tl_host, sizeof(int2) * nt, cudaMemcpyHostToDevice, st);
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
       cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     });
     {
       ProfScope ps(st, "gram_tc");
-      k_gram_tc<<<(unsigned)(nt * nch), NTH, SMEM_BYTES, st>>>(mapA, mapB, n, tiles, (int)nch, nt,
-                                                               rpc, a, b, part, d_status);
+      k_gram_tc<<<(unsigned)(nt * nch), NTH, SMEM_BYTES, st>>>(mapA, mapB, n, nb, sym ? 1 : 0,
+                                                               (int)nch, nt, rpc, a, b, part,
+                                                               d_status);
       note_launch();
-      long long tot = (long long)nt * TM * TN;
-      unsigned rb = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 8);
-      k_gram_tc_reduce<<<rb, 256, 0, st>>>(part, (int)nch, nt, tiles, a, b, ma, mb, C, ldc,
-                                           sym ? 1 : 0);
+      k_gram_tc_reduce<<<(unsigned)(nt * TM), 256, 0, st>>>(part, (int)nch, nt, nb, a, b, ma, mb,
+                                                            C, ldc, sym ? 1 : 0);
       note_launch();
     }
     e = cudaGetLastError();
   }
-  al.put(tiles);
   al.put(part);
   return e;
 }

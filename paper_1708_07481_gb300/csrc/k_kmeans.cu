@@ -21,7 +21,7 @@
 namespace sc {
 namespace {
 
-constexpr int PB = 1024;  // rows per seeding block
+constexpr int PB = 256;  // rows per seeding block (one CTA each; the pick CTA has PB threads)
 
 __device__ double block_sum_d(double v, double* sh) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -201,7 +201,9 @@ template <int D>
 __global__ void __launch_bounds__(256)
     k_assign(int n, int d, int k, const float* __restrict__ E, long long lde,
              const float* __restrict__ C32, const float* __restrict__ cn,
-             const double* __restrict__ C64, int* labels, int* changes, int first, double tie) {
+             const double* __restrict__ C64, int* labels, int* changes, int first, double tie,
+             const int* ctl) {
+  if (ctl[0]) return;  // converged in an earlier round (uniform: written by an earlier kernel)
   extern __shared__ float csm[];  // ACH * D
   __shared__ int nchg;
   if (threadIdx.x == 0) nchg = 0;
@@ -243,20 +245,38 @@ __global__ void __launch_bounds__(256)
   if (i < n) {
     if (k > 1 && second - best < (float)tie) {
       // near tie: re-decide among the centroids within the margin, with direct FP64
-      // distances ||e - c||^2 to the FP64 centroids (ties -> lowest index)
+      // distances ||e - c||^2 to the FP64 centroids (ties -> lowest index).  The FP32
+      // distances are recomputed exactly as above (same order), from the centroids still in
+      // shared memory when they all fit in one chunk.
       double bd = 1e300;
       int bb = 0;
       for (int j = 0; j < k; ++j) {
         float dot = 0.f;
-        const float* cj = C32 + (long long)j * d;
-        for (int q = 0; q < d; ++q) dot = fmaf(E[i * lde + q], cj[q], dot);
+        if (k <= ACH) {
+          const float4* c4 = reinterpret_cast<const float4*>(csm + j * D);
+#pragma unroll
+          for (int q = 0; q < D / 4; ++q) {
+            float4 cv = c4[q];
+            dot = fmaf(ev[4 * q], cv.x, dot);
+            dot = fmaf(ev[4 * q + 1], cv.y, dot);
+            dot = fmaf(ev[4 * q + 2], cv.z, dot);
+            dot = fmaf(ev[4 * q + 3], cv.w, dot);
+          }
+        } else {
+          const float* cj = C32 + (long long)j * d;
+#pragma unroll
+          for (int q = 0; q < D; ++q) dot = fmaf(ev[q], q < d ? cj[q] : 0.f, dot);
+        }
         float dist = fmaf(-2.f, dot, cn[j]);
         if (dist - best >= (float)tie) continue;
         const double* c = C64 + (long long)j * d;
         double acc = 0.0;
-        for (int q = 0; q < d; ++q) {
-          double df = (double)E[i * lde + q] - c[q];
-          acc = fma(df, df, acc);
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          if (q < d) {
+            double df = (double)ev[q] - c[q];
+            acc = fma(df, df, acc);
+          }
         }
         if (acc < bd) {
           bd = acc;
@@ -274,7 +294,7 @@ __global__ void __launch_bounds__(256)
 }
 
 using AssignFn = void (*)(int, int, int, const float*, long long, const float*, const float*,
-                          const double*, int*, int*, int, double);
+                          const double*, int*, int*, int, double, const int*);
 
 inline AssignFn assign_for(int d, int* D) {
   if (d <= 16) { *D = 16; return k_assign<16>; }
@@ -288,22 +308,38 @@ inline AssignFn assign_for(int d, int* D) {
   return k_assign<512>;
 }
 
-// Per-CTA FP64 cluster sums in row order; thread c owns column c (and thread 0 the counts).
+// Per-CTA FP64 cluster sums over a contiguous row range, accumulated in row order (thread c
+// owns column c, thread 0 the counts).  Rows pass through shared memory in chunks of CR (the
+// labels and the d columns, loaded coalesced), so the ordered accumulation itself reads only
+// shared memory.
+constexpr int CR = 32;
+
 __global__ void k_cent_partial(int n, int d, int k, const float* __restrict__ E, long long lde,
                                const int* __restrict__ labels, long long rows_per_cta,
-                               double* part, int* pcnt, int use_smem) {
-  extern __shared__ double acc_sm[];  // k*d (when use_smem)
+                               double* part, int* pcnt, int use_smem, const int* ctl,
+                               const int* chg, int it) {
+  if (ctl[0] || (it > 0 && *chg == 0)) return;  // no update this round
+  extern __shared__ double acc_sm[];  // k*d (when use_smem), then CR x d floats, CR labels
   double* acc = use_smem ? acc_sm : part + (long long)blockIdx.x * k * d;
+  float* stg = reinterpret_cast<float*>(acc_sm + (use_smem ? (size_t)k * d : 0));
+  int* lab = reinterpret_cast<int*>(stg + CR * d);
   int* cnt = pcnt + (long long)blockIdx.x * k;
   for (long long q = threadIdx.x; q < (long long)k * d; q += blockDim.x) acc[q] = 0.0;
   for (int j = threadIdx.x; j < k; j += blockDim.x) cnt[j] = 0;
-  __syncthreads();
-  long long r0 = blockIdx.x * rows_per_cta, r1 = min((long long)n, r0 + rows_per_cta);
-  for (long long r = r0; r < r1; ++r) {
-    int l = labels[r];
-    for (int c = threadIdx.x; c < d; c += blockDim.x)
-      acc[(long long)l * d + c] += (double)E[r * lde + c];
-    if (threadIdx.x == 0) cnt[l] += 1;
+  const long long r0 = blockIdx.x * rows_per_cta, r1 = min((long long)n, r0 + rows_per_cta);
+  for (long long r = r0; r < r1; r += CR) {
+    const int nr = (int)min((long long)CR, r1 - r);
+    __syncthreads();  // the previous chunk has been consumed
+    for (int q = threadIdx.x; q < nr * d; q += blockDim.x)
+      stg[q] = E[(r + q / d) * lde + q % d];
+    for (int q = threadIdx.x; q < nr; q += blockDim.x) lab[q] = labels[r + q];
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+      const int l = lab[rr];
+      for (int c = threadIdx.x; c < d; c += blockDim.x)
+        acc[(long long)l * d + c] += (double)stg[rr * d + c];
+      if (threadIdx.x == 0) cnt[l] += 1;
+    }
   }
   __syncthreads();
   if (use_smem)
@@ -311,11 +347,26 @@ __global__ void k_cent_partial(int n, int d, int k, const float* __restrict__ E,
       part[(long long)blockIdx.x * k * d + q] = acc[q];
 }
 
-__global__ void k_cent_reduce(int d, int k, int nct, const double* __restrict__ part,
-                              const int* __restrict__ pcnt, double* C64, float* C32, float* cn) {
-  int j = blockIdx.x;
+// Centroid j = (sum of the CTA partials) / count, empty clusters kept.  Warp w of the CTA sums
+// the partials w, w + 8, ... (two accumulators, even and odd steps) for 32 columns at a time;
+// the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256)
+    k_cent_reduce(int d, int k, int nct, const double* __restrict__ part,
+                  const int* __restrict__ pcnt, double* C64, float* C32, float* cn, int* ctl,
+                  const int* chg, int it) {
+  const int j = blockIdx.x;
+  // a round without label changes ends the iteration (before any centroid update); ctl[0]
+  // is only ever set on that path, where every CTA returns without writing
+  if (ctl[0]) return;
+  if (it > 0 && *chg == 0) {
+    if (j == 0 && threadIdx.x == 0) ctl[0] = 1;
+    return;
+  }
+  if (j == 0 && threadIdx.x == 0) ctl[1] = it + 1;  // rounds with a centroid update
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __shared__ long long tot;
-  __shared__ float red[32];
+  __shared__ double ps[8][33];
+  __shared__ float red[8];
   if (threadIdx.x == 0) tot = 0;
   __syncthreads();
   {
@@ -325,32 +376,39 @@ __global__ void k_cent_reduce(int d, int k, int nct, const double* __restrict__ 
   }
   __syncthreads();
   float s = 0.f;
-  for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    if (tot > 0) {
-      // fixed-order sum over the CTA partials, 8 independent loads in flight per step
-      double t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int q = 0;
-      for (; q + 8 <= nct; q += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) t[u] += part[((long long)(q + u) * k + j) * d + c];
+  for (int c0 = 0; c0 < d; c0 += 32) {
+    const int c = c0 + lane;
+    double t0 = 0.0, t1 = 0.0;
+    if (tot > 0 && c < d) {
+      int q = w;
+      for (; q + 8 < nct; q += 16) {
+        t0 += part[((long long)q * k + j) * d + c];
+        t1 += part[((long long)(q + 8) * k + j) * d + c];
       }
-      for (; q < nct; ++q) t[0] += part[((long long)q * k + j) * d + c];
-      double v = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
-      double m = v / (double)tot;
-      C64[(long long)j * d + c] = m;
-      C32[(long long)j * d + c] = (float)m;
+      if (q < nct) t0 += part[((long long)q * k + j) * d + c];
     }
-    float f = C32[(long long)j * d + c];
-    s = fmaf(f, f, s);
+    ps[w][lane] = t0 + t1;
+    __syncthreads();
+    if (w == 0 && c < d) {
+      if (tot > 0) {
+        double v = ps[0][lane];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) v += ps[q][lane];
+        const double mval = v / (double)tot;
+        C64[(long long)j * d + c] = mval;
+        C32[(long long)j * d + c] = (float)mval;
+      }
+      const float f = C32[(long long)j * d + c];
+      s = fmaf(f, f, s);
+    }
+    __syncthreads();
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    cn[j] = t;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) cn[j] = s;
   }
+  (void)red;
 }
 
 __global__ void k_inertia(int n, int d, const float* __restrict__ E, long long lde,
@@ -415,7 +473,7 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
                   int* iters_run, double* inertia) {
   float* C32 = al.get<float>((size_t)k * d);
   float* cn = al.get<float>(k);
-  int* changes = al.get<int>(1);
+  int* changes = al.get<int>((size_t)iters + 2);  // per-round change counts, then stop / done
   long long nct = 152 * 2;
   if (nct > n) nct = n > 0 ? n : 1;
   long long rpc = (n + nct - 1) / nct;
@@ -440,35 +498,43 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
       e = cudaFuncSetAttribute(afn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_bytes);
       if (e != cudaSuccess) goto out;
     }
+    const size_t stg_bytes = sizeof(float) * (size_t)CR * d + sizeof(int) * CR;
     size_t psm = sizeof(double) * (size_t)k * d;
-    int use_smem = psm <= 160 * 1024;
-    if (use_smem && psm > 48 * 1024) {
+    int use_smem = psm + stg_bytes <= 160 * 1024;
+    psm = (use_smem ? psm : 0) + stg_bytes;
+    if (psm > 48 * 1024) {
       e = cudaFuncSetAttribute(k_cent_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)psm);
       if (e != cudaSuccess) goto out;
     }
     unsigned ab = (unsigned)((n + 255) / 256);
+    int* ctl = changes + iters;
+    cudaMemsetAsync(changes, 0, sizeof(int) * ((size_t)iters + 2), st);
+    // Rounds are issued without waiting: a round that changes no label sets the stop flag on
+    // the device and every later kernel returns at once; the host looks every 4 rounds.
     for (int it = 0; it < iters; ++it) {
-      cudaMemsetAsync(changes, 0, sizeof(int), st);
-      ProfScope ps(st, "kmeans_assign");
-      // FP32 distances of unit rows to centroids of norm <= 1 carry at most ~2.5e-7 d of
-      // rounding each; margins below twice that (plus slack) are re-decided in FP64
-      afn<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes, it == 0,
-                                       2e-5 + 5e-7 * d);
-      note_launch();
-      if (it > 0) {
-        int h = 0;
-        cudaMemcpyAsync(&h, changes, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) goto out;
-        if (h == 0) break;
+      {
+        ProfScope ps(st, "kmeans_assign");
+        // FP32 distances of unit rows to centroids of norm <= 1 carry at most ~2.5e-7 d of
+        // rounding each; margins below twice that (plus slack) are re-decided in FP64
+        afn<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes + it,
+                                         it == 0, 2e-5 + 5e-7 * d, ctl);
+        note_launch();
       }
-      k_cent_partial<<<(unsigned)nct, 64, use_smem ? psm : 0, st>>>(n, d, k, E, lde, labels, rpc,
-                                                                    part, pcnt, use_smem);
+      k_cent_partial<<<(unsigned)nct, 64, psm, st>>>(n, d, k, E, lde, labels, rpc, part, pcnt,
+                                                     use_smem, ctl, changes + it, it);
       note_launch();
-      k_cent_reduce<<<k, 128, 0, st>>>(d, k, (int)nct, part, pcnt, C64, C32, cn);
+      k_cent_reduce<<<k, 256, 0, st>>>(d, k, (int)nct, part, pcnt, C64, C32, cn, ctl,
+                                       changes + it, it);
       note_launch();
-      ++done;
+      if ((it + 1) % 4 == 0 && it + 1 < iters) {
+        int h = 0;
+        cudaMemcpyAsync(&h, ctl, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) goto out;
+        if (h) break;
+      }
     }
+    cudaMemcpyAsync(&done, ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     k_inertia<<<152, 256, 0, st>>>(n, d, E, lde, labels, C64, ipart);
     note_launch();
     double hp[152];

@@ -166,7 +166,7 @@ def _sym_with_spectrum(m, ev, seed):
     return (Q * ev) @ Q.T
 
 
-@pytest.mark.parametrize("m,K", [(1, 1), (2, 1), (33, 11), (132, 44), (480, 160)])
+@pytest.mark.parametrize("m,K", [(1, 1), (2, 1), (33, 11), (132, 44), (200, 60), (480, 160), (500, 100)])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_rr_solve(sc, ctx, m, K, prec):
     rng = np.random.default_rng(m)
