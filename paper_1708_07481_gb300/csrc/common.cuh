@@ -137,7 +137,27 @@ cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, lon
 // Tall GEMM: out (n x b, ldo) = beta * Cin + A (n x a) W (a x b, row-major ldw, type T).
 template <typename T>
 cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W, int ldw,
-                      int b, T* out, long long ldo, const T* Cin, long long ldc, T beta);
+                      int b, T* out, long long ldo, const T* Cin, long long ldc, T beta,
+                      int* d_status = nullptr);
+// One output segment of a tall update: columns go to out (stride ldo), plus beta * Cin,
+// computed with the W block (stride ldw) whose rows start at row wskip of the concatenated A
+// (the rows before it are zero for this segment).
+template <typename T>
+struct TallSeg {
+  T* out;
+  long long ldo;
+  const T* Cin;
+  long long ldc;
+  const T* W;
+  int ldw;
+  int wskip;
+  int b;
+};
+// [out_0 | out_1] = beta [Cin_0 | Cin_1] + A [W_0 | W_1] in one pass over A
+template <typename T>
+cudaError_t tall_gemm2(cudaStream_t st, long long n, const Cat3<T>& A, const TallSeg<T>& s0,
+                       const TallSeg<T>& s1, T beta, int* d_status = nullptr);
+
 
 // Residual: R = LX - X diag(theta); rho2[j] = sum_i R_ij^2 (FP64).  Workspace from `al`.
 template <typename T>

@@ -185,7 +185,7 @@ __device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol) {
 // are returned, the rest zeroed, and *pflag cleared.
 // SM = the matrix lives in shared memory.
 template <typename T, bool SM>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
     k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
                int* status, int* fail_col, double pivot_tol, int keep, int* pflag) {
   extern __shared__ __align__(16) unsigned char craw[];
@@ -303,6 +303,9 @@ __device__ long long g_rr_inv[4];
 #endif
 
 constexpr int RR_NT = 1024;
+#ifndef RR_SWEEPS
+#define RR_SWEEPS 2  // inverse-iteration sweeps of the register-slot Rayleigh-Ritz
+#endif
 
 // Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of the symmetric
 // m x m matrix G (FP64 in, arithmetic in T), one CTA of 1024 threads.
@@ -839,10 +842,11 @@ __global__ void __launch_bounds__(NW * 32)
     sg = warp_sum(sg);
     T bet = 0, iv0 = 0, ek = x0;
     if (sg != (T)0) {
+      // v0 = x0 - mu without cancellation; beta = 2 v0^2 / (sigma + v0^2) = 2 / (1 + sigma / v0^2)
       const T mu = sqrt(x0 * x0 + sg);
       const T v0 = (x0 <= (T)0) ? x0 - mu : -sg / (x0 + mu);
-      bet = (T)2 * v0 * v0 / (sg + v0 * v0);
       iv0 = (T)1 / v0;
+      bet = (T)2 / ((T)1 + sg * iv0 * iv0);
       ek = mu;
     }
 #pragma unroll
@@ -1065,7 +1069,7 @@ __global__ void __launch_bounds__(NW * 32)
   const T small_piv = Lim<T>::eps() * tnorm + pivmin;
 #define UF(i, a) U[((i) * 3 + (a)) * K + j]
   long long tinv = clock64();
-  for (int sweep = 0; sweep < 2; ++sweep) {
+  for (int sweep = 0; sweep < RR_SWEEPS; ++sweep) {
     for (int j = tid; j < K; j += NT) {
       // LU with partial pivoting of T - s I, the right-hand side eliminated alongside
       const T sj = shift[j];
@@ -1278,8 +1282,20 @@ __global__ void __launch_bounds__(NW * 32)
 }  // namespace
 
 template <typename T>
+cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
+                        int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
+                        int nthreads);
+
+template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
                      int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag) {
+  return chol_inv_nt<T>(st, al, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, 512);
+}
+
+template <typename T>
+cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
+                        int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
+                        int nthreads) {
   size_t base = sizeof(T) * (4 * (size_t)ka);
   size_t wbytes = sizeof(T) * (size_t)ka * ka;
   int in_smem = base + wbytes <= 200 * 1024;
@@ -1293,7 +1309,7 @@ cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ld
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   ProfScope ps(st, "chol_inv");
-  kern<<<1, 512, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag);
+  kern<<<1, nthreads, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag);
   note_launch();
   e = cudaGetLastError();
   al.put(Wg);

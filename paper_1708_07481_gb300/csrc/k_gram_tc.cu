@@ -7,7 +7,7 @@
 //
 // CTA = one 128 x 128 output tile over one chunk of rows.  Per stage of 32 rows:
 //   TMA (cp.async.bulk.tensor.2d) brings the FP32 row blocks of A and B into shared memory
-//   (double-buffered, mbarrier complete_tx); all 256 threads split them into big/small TF32
+//   (three staging slots, mbarrier complete_tx); all 256 threads split them into big/small TF32
 //   operands written in the K-major 128-byte-swizzled layout the MMA reads (the transpose
 //   from row-major to K-major happens here, for free); one thread issues 4 K-steps x 3
 //   products of tcgen05.mma 128x128x8 into a TMEM accumulator and commits to an mbarrier
@@ -15,13 +15,10 @@
 //   tile's FP64 partial; a second kernel sums the partials over chunks in fixed order.
 // Every wait is bounded: on a timeout the CTA records ST_TIMEOUT, waits (bounded) for its
 // own outstanding copies and MMAs, frees its tensor memory and returns.
-#include <cuda.h>
-
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
-#include "common.cuh"
+#include "tc.cuh"
 
 namespace sc {
 namespace {
@@ -29,10 +26,8 @@ namespace {
 constexpr int TM = 128, TN = 128, BK = 32, NTH = 256;
 constexpr int STAGE_BYTES = BK * TM * 4;     // 16 KB: FP32 rows of one operand
 constexpr int OP_BYTES = TM * BK * 4;        // 16 KB: one TF32 operand tile
-constexpr int SMEM_BYTES = 2 * 2 * STAGE_BYTES + 2 * 4 * OP_BYTES + 1024 + 256;
-constexpr long long SPIN_LIMIT = 1LL << 26;  // bounded waits (~ seconds)
-constexpr int ST_TIMEOUT = 32;
-
+constexpr int NSTG = 3;                      // FP32 staging slots (copies in flight)
+constexpr int SMEM_BYTES = NSTG * 2 * STAGE_BYTES + 2 * 4 * OP_BYTES + 1024 + 256;
 struct SegMap {
   int start[3];
   int count[3];
@@ -48,63 +43,6 @@ __device__ inline int seg_index(const SegMap& s, int c) {
   return -1;
 }
 
-__device__ inline uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ inline void mbar_init(uint64_t* bar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for phase `parity` of an mbarrier; returns false on timeout.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < SPIN_LIMIT; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (it > 64) __nanosleep(64);
-  }
-  return false;
-}
-
-__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                   uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ inline uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ inline uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
-  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                          // layout: SWIZZLE_128B
-  return d;
-}
-
 // Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128.
 __host__ __device__ constexpr uint32_t idesc_tf32() {
   return (1u << 4)                 // c_format F32
@@ -114,30 +52,12 @@ __host__ __device__ constexpr uint32_t idesc_tf32() {
          | ((uint32_t)(TM >> 4) << 24);
 }
 
-__device__ inline void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ inline void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// Byte offset of TF32 element (row r, k) in a K-major SW128 tile of TM rows x BK=32 values.
-__device__ inline uint32_t sw128_off(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7))) << 4) + (k & 3) * 4);
-}
-
-// Split one FP32 stage (BK rows x TM columns, row-major) into big/small K-major operands.
-__device__ inline void convert_stage(const float* stage, uint8_t* big, uint8_t* small) {
+// Split one FP32 stage (BK rows x TM columns, row-major) into big/small K-major operands;
+// only the first ncols columns (operand rows) are needed.
+__device__ inline void convert_stage(const float* stage, uint8_t* big, uint8_t* small,
+                                     int ncols) {
   const int r = threadIdx.x & (TM - 1);  // operand row = column of the block
+  if (r >= ncols) return;
   for (int kc = threadIdx.x >> 7; kc < BK / 4; kc += NTH / TM) {
     uint32_t bg[4], sm[4];
 #pragma unroll
@@ -163,16 +83,25 @@ __global__ void __launch_bounds__(NTH, 1)
   uint8_t* opA = base;                           // [buf][big/small] 16 KB each
   uint8_t* opB = opA + 4 * OP_BYTES;
   float* stA = (float*)(opB + 4 * OP_BYTES);     // [slot] 16 KB
-  float* stB = stA + 2 * (STAGE_BYTES / 4);
-  uint64_t* bars = (uint64_t*)(stB + 2 * (STAGE_BYTES / 4));
-  uint64_t* full = bars;         // [2] TMA landed
-  uint64_t* mdone = bars + 2;    // [2] MMAs of a buffer finished
-  uint32_t* tmem_slot = (uint32_t*)(bars + 4);
+  float* stB = stA + NSTG * (STAGE_BYTES / 4);
+  uint64_t* bars = (uint64_t*)(stB + NSTG * (STAGE_BYTES / 4));
+  uint64_t* full = bars;            // [NSTG] TMA landed
+  uint64_t* mdone = bars + NSTG;    // [2] MMAs of an operand buffer finished
+  uint32_t* tmem_slot = (uint32_t*)(bars + NSTG + 2);
   __shared__ int abort_flag;
 
   const int tile = blockIdx.x / nch, chunk = blockIdx.x % nch;
   const int2 tl = tile_coord(tile, nbt, sym);
   const int ca = tl.x * TM, cb = tl.y * TN;
+  // The MMA's M side is always 128 wide; its N side is trimmed to the valid width of the
+  // narrower block (rounded up to 16).  When A's side of the tile is the narrower one the
+  // tile is computed transposed (B columns as M) and written back transposed.
+  const int va = min(TM, a - ca), vb = min(TN, b - cb);
+  const bool swp = !sym && va < vb;
+  const int nn = ((swp ? va : vb) + 15) & ~15;
+  const CUtensorMap* mapM = swp ? &mapB : &mapA;
+  const CUtensorMap* mapN = swp ? &mapA : &mapB;
+  const int xm = swp ? cb : ca, xn = swp ? ca : cb;
   const long long r0 = (long long)chunk * rows_per_chunk;
   long long r1 = r0 + rows_per_chunk;
   if (r1 > n) r1 = n;
@@ -181,7 +110,7 @@ __global__ void __launch_bounds__(NTH, 1)
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int q = 0; q < 4; ++q) mbar_init(&bars[q], 1);
+    for (int q = 0; q < NSTG + 2; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
@@ -198,24 +127,28 @@ __global__ void __launch_bounds__(NTH, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t IDESC = idesc_tf32();
+  const uint32_t IDESC = (idesc_tf32() & ~(0x3Fu << 17)) | ((uint32_t)(nn >> 3) << 17);
 
-  // prologue: stages 0 and 1 in flight
+  // prologue: stages 0 .. NSTG - 1 in flight
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2 && s < nst; ++s) {
+    for (int s = 0; s < NSTG && s < nst; ++s) {
       mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
       int y = (int)(r0 + (long long)s * BK);
-      tma_load_2d(stA + s * (STAGE_BYTES / 4), &mapA, ca, y, &full[s]);
-      tma_load_2d(stB + s * (STAGE_BYTES / 4), &mapB, cb, y, &full[s]);
+      tma_load_2d(stA + s * (STAGE_BYTES / 4), mapM, xm, y, &full[s]);
+      tma_load_2d(stB + s * (STAGE_BYTES / 4), mapN, xn, y, &full[s]);
     }
   }
   int issued_commits[2] = {0, 0};
-  int loads_issued[2] = {nst > 0 ? 1 : 0, nst > 1 ? 1 : 0};  // thread 0's bookkeeping
-  int loads_done[2] = {0, 0};
+  int loads_issued[NSTG], loads_done[NSTG];  // thread 0's bookkeeping
+  for (int q = 0; q < NSTG; ++q) {
+    loads_issued[q] = q < nst ? 1 : 0;
+    loads_done[q] = 0;
+  }
   for (int s = 0; s < nst; ++s) {
-    const int slot = s & 1;
-    bool ok = mbar_wait(&full[slot], (uint32_t)((s >> 1) & 1));
-    if (ok) loads_done[slot] += 1;
+    const int ss = s % NSTG;  // staging slot
+    const int slot = s & 1;   // operand buffer
+    bool ok = mbar_wait(&full[ss], (uint32_t)((s / NSTG) & 1));
+    if (ok) loads_done[ss] += 1;
     if (ok && s >= 2) ok = mbar_wait(&mdone[slot], (uint32_t)(((s - 2) >> 1) & 1));
     if (!ok) atomicExch(&abort_flag, 1);
     __syncthreads();
@@ -224,8 +157,8 @@ __global__ void __launch_bounds__(NTH, 1)
     uint8_t* aS = aB + OP_BYTES;
     uint8_t* bB = opB + (slot * 2) * OP_BYTES;
     uint8_t* bS = bB + OP_BYTES;
-    convert_stage(stA + slot * (STAGE_BYTES / 4), aB, aS);
-    convert_stage(stB + slot * (STAGE_BYTES / 4), bB, bS);
+    convert_stage(stA + ss * (STAGE_BYTES / 4), aB, aS, TM);
+    convert_stage(stB + ss * (STAGE_BYTES / 4), bB, bS, nn);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -241,13 +174,13 @@ __global__ void __launch_bounds__(NTH, 1)
       }
       mma_commit(&mdone[slot]);
       issued_commits[slot] += 1;
-      // the staging slot was consumed by the conversion above: refill it with stage s + 2
-      if (s + 2 < nst) {
-        loads_issued[slot] += 1;
-        mbar_expect_tx(&full[slot], 2 * STAGE_BYTES);
-        int y = (int)(r0 + (long long)(s + 2) * BK);
-        tma_load_2d(stA + slot * (STAGE_BYTES / 4), &mapA, ca, y, &full[slot]);
-        tma_load_2d(stB + slot * (STAGE_BYTES / 4), &mapB, cb, y, &full[slot]);
+      // the staging slot was consumed by the conversion above: refill it with stage s + NSTG
+      if (s + NSTG < nst) {
+        loads_issued[ss] += 1;
+        mbar_expect_tx(&full[ss], 2 * STAGE_BYTES);
+        int y = (int)(r0 + (long long)(s + NSTG) * BK);
+        tma_load_2d(stA + ss * (STAGE_BYTES / 4), mapM, xm, y, &full[ss]);
+        tma_load_2d(stB + ss * (STAGE_BYTES / 4), mapN, xn, y, &full[ss]);
       }
     }
   }
@@ -259,7 +192,7 @@ __global__ void __launch_bounds__(NTH, 1)
       if (issued_commits[q] > 0)
         ok = mbar_wait(&mdone[q], (uint32_t)((issued_commits[q] - 1) & 1)) && ok;
     // after an abort, copies may still be in flight: wait (bounded) for the latest one
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < NSTG; ++q)
       if (loads_issued[q] > loads_done[q])
         ok = mbar_wait(&full[q], (uint32_t)((loads_issued[q] - 1) & 1)) && ok;
     last_ok = ok ? 1 : 0;
@@ -267,13 +200,14 @@ __global__ void __launch_bounds__(NTH, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (last_ok && nst > 0) {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32, columns 64 (w / 4) .. +64
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 (M index), columns 64 (w / 4) ..
+    // +64 (N index, up to nn); element (M, N) is tile entry (M, N), or (N, M) when swapped
     const int lrow = 32 * (warp & 3) + lane;
     const int cbase = 64 * (warp >> 2);
     double* dst = part + ((long long)chunk * ntiles + tile) * TM * TN;
-    const int gi = ca + lrow;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
+      if (cbase + 32 * h >= nn) break;  // uniform in the warp
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(cbase + 32 * h);
       asm volatile(
@@ -287,12 +221,11 @@ __global__ void __launch_bounds__(NTH, 1)
             "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (gi < a) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          int j = cbase + 32 * h + q;
-          if (cb + j < b) dst[(long long)lrow * TN + j] = (double)__uint_as_float(v[q]);
-        }
+      for (int q = 0; q < 32; ++q) {
+        const int jn = cbase + 32 * h + q;  // N index
+        const int ti = swp ? jn : lrow, tj = swp ? lrow : jn;
+        if (ti < va && tj < vb) dst[(long long)ti * TN + tj] = (double)__uint_as_float(v[q]);
       }
     }
   } else if (!last_ok && threadIdx.x == 0) {
@@ -348,26 +281,6 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
   }
-}
-
-// ---- host: tensor maps through the driver entry point (no -lcuda link dependency) ---------
-using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeFn encoder() {
-  static EncodeFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeFn)p;
-  });
-  return fn;
 }
 
 bool make_map(CUtensorMap* m, const float* ptr, long long rows, int cols, long long ld,

@@ -495,10 +495,14 @@ struct LobRun : RunBase {
   double pivot_tol;
   std::vector<void*> bufs;
   T *S = nullptr, *LS = nullptr, *S2 = nullptr, *LS2 = nullptr, *T1 = nullptr, *W1 = nullptr,
-    *W2 = nullptr, *Q1 = nullptr, *LQ1 = nullptr, *Tm = nullptr, *Y = nullptr;
+    *W2 = nullptr, *Q1 = nullptr, *LQ1 = nullptr, *Tm = nullptr, *TmA = nullptr, *TmB = nullptr,
+    *Y = nullptr;
   double *G = nullptr, *theta = nullptr, *rho2 = nullptr;
   int *dcols = nullptr, *dfail = nullptr, *dP = nullptr, *dfb = nullptr, *dstatus = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // second stream for the L-image updates, which overlap the X/R/P side of the pass
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t evf = nullptr, evj = nullptr;
   uint64_t l0 = 0;
   int it = 0, done_passes = 0, converged = 0;
   bool haveP = false, over = false;
@@ -517,10 +521,23 @@ struct LobRun : RunBase {
     hth.assign(K, 0.0);
   }
   ~LobRun() override {
+    if (st2) cudaStreamSynchronize(st2);
     for (void* p : bufs) al.put(p);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (evf) cudaEventDestroy(evf);
+    if (evj) cudaEventDestroy(evj);
     cudaStreamSynchronize(st);
+    if (st2) cudaStreamDestroy(st2);
+  }
+  // st2 continues from everything issued on st so far / st waits for everything on st2
+  void fork() {
+    cudaEventRecord(evf, st);
+    cudaStreamWaitEvent(st2, evf, 0);
+  }
+  void join() {
+    cudaEventRecord(evj, st2);
+    cudaStreamWaitEvent(st, evj, 0);
   }
   bool finished() const override { return over; }
   cudaStream_t stream() const override { return st; }
@@ -592,7 +609,7 @@ struct LobRun : RunBase {
     if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
     *failed = (hs & (ST_CHOL_FAIL | ST_NONFINITE)) != 0;
     if (*failed) return SC_OK;
-    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0, dstatus), "tall");
     return SC_OK;
   }
 
@@ -600,6 +617,9 @@ struct LobRun : RunBase {
     if (!ev0) {
       cudaEventCreate(&ev0);
       cudaEventCreate(&ev1);
+      cudaEventCreateWithFlags(&evf, cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&evj, cudaEventDisableTiming);
+      CK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking), "stream");
     }
     const int mmax = 3 * K;
     S = get<T>((size_t)n * ld3, true);
@@ -613,6 +633,8 @@ struct LobRun : RunBase {
     LQ1 = get<T>((size_t)n * 2 * kp, true);
     G = get<double>((size_t)mmax * mmax);
     Tm = get<T>((size_t)mmax * mmax);
+    TmA = get<T>((size_t)mmax * mmax);
+    TmB = get<T>((size_t)mmax * mmax);
     Y = get<T>((size_t)mmax * K);
     theta = get<double>(K);
     rho2 = get<double>(K);
@@ -621,7 +643,8 @@ struct LobRun : RunBase {
     dP = get<int>(1);
     dfb = get<int>(1);
     dstatus = get<int>(1, true);
-    if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !Y ||
+    if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !TmA ||
+        !TmB || !Y ||
         !theta || !rho2 || !dcols || !dfail || !dP || !dfb || !dstatus)
       return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
     {
@@ -672,8 +695,8 @@ struct LobRun : RunBase {
     CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
     CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, false), "gram");
     CK(rr_eig<T>(st, al, K, K, G, K, theta, Y, dstatus), "rr");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus), "tall");
     std::swap(S, S2);
     std::swap(LS, LS2);
     CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
@@ -746,10 +769,15 @@ struct LobRun : RunBase {
     else
       CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}}, G, w, false), "gram");
     CK(cast_mat<T>(st, K, w, G, w, Tm, w, -1.0), "cast");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, w, ka, WR, ldw, WR, ldw, (T)1), "tall");
-    if (haveP) {
-      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm + ka, w, ka, WP, ldw, WP, ldw, (T)1), "tall");
-      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm + ka, w, ka, WLP, ldw, WLP, ldw, (T)1), "tall");
+    if (haveP) {  // LP_a -= LX F_P on the second stream, beside the R/P side
+      fork();
+      CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Tm + ka, w, ka, WLP, ldw, WLP, ldw, (T)1, dstatus), "tall");
+    }
+    {
+      // [R_a P_a] -= X [F_R F_P] in one pass over X
+      TallSeg<T> sr{WR, ldw, WR, ldw, Tm, w, 0, ka};
+      TallSeg<T> sp{WP, ldw, WP, ldw, Tm + ka, w, 0, haveP ? ka : 0};
+      CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus), "tall");
     }
     // (2) LR_a = L R_a: the one multiplication by L of the pass (Sec. III)
     T* WLR = all ? LRslot : W2;
@@ -768,17 +796,22 @@ struct LobRun : RunBase {
         CK(gram_seg(WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
       else
         CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, al, wq, G, wq, Tm, dstatus, pivot_tol, dfail, ka, pf), "chol");
-      CK(tall_gemm<T>(st, n, Vw, Tm, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
-      CK(tall_gemm<T>(st, n, LVw, Tm, wq, wq, LQ1, 2 * kp, nullptr, 0, (T)0), "tall");
+      CK(chol_inv<T>(st, al, wq, G, wq, TmA, dstatus, pivot_tol, dfail, ka, pf), "chol");
+      CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus), "tall");
+      if (haveP) join();  // LP_a is ready
+      fork();             // LQ1 on the second stream, beside the second Gram and Cholesky
+      CK(tall_gemm<T>(st2, n, LVw, TmA, wq, wq, LQ1, 2 * kp, nullptr, 0, (T)0, dstatus), "tall");
       CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, al, wq, G, wq, Tm, dstatus, pivot_tol, dfail, ka, pf), "chol");
-      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), Tm, wq, ka, Rslot, ld3, nullptr, 0, (T)0), "tall");
-      CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, ka), Tm, wq, ka, LRslot, ld3, nullptr, 0, (T)0), "tall");
-      if (haveP) {
-        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), Tm + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0), "tall");
-        CK(tall_gemm<T>(st, n, cat<T>(LQ1, 2 * kp, wq), Tm + ka, wq, ka, LPslot, ld3, nullptr, 0, (T)0), "tall");
-      }
+      CK(chol_inv<T>(st, al, wq, G, wq, TmB, dstatus, pivot_tol, dfail, ka, pf), "chol");
+      fork();  // TmB is ready for the L-images
+      // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
+      CK(tall_gemm<T>(st2, n, cat<T>(LQ1, 2 * kp, ka), TmB, wq, ka, LRslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
+      if (haveP)
+        CK(tall_gemm<T>(st2, n, cat<T>(LQ1, 2 * kp, wq), TmB + ka, wq, ka, LPslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
+      if (haveP)
+        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
+      join();
     }
     // (4) Rayleigh-Ritz on S = [X R_a P_a]
     const bool useP = haveP;
@@ -792,10 +825,12 @@ struct LobRun : RunBase {
     const T* Yrp = Y + (size_t)K * K;
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
     Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);
-    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1), "tall");
-    CK(tall_gemm<T>(st, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1), "tall");
+    fork();  // the L-images on the second stream
+    CK(tall_gemm<T>(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus), "tall");
+    CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1, dstatus), "tall");
+    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1, dstatus), "tall");
+    join();
     std::swap(S, S2);
     std::swap(LS, LS2);
     haveP = true;
