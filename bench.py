@@ -256,6 +256,15 @@ def run_ours(args):
                                "launches": cnt, "avg_launch_us": avg_s * 1e6,
                                "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x max clock"}
     res["cpu_baseline"] = cpu_baseline(g)
+    if args.configs:
+        extra = {}
+        if "3" in args.configs:
+            extra["cfg3_large"] = cfg_large(sc, W, ctx)
+        if "4" in args.configs:
+            extra["cfg4_stream"] = cfg_stream(sc, W, ctx)
+        if "5" in args.configs:
+            extra["cfg5_serve"] = cfg_serve(sc, W, ctx)
+        res["other_workloads"] = extra
     return res
 
 
@@ -274,6 +283,151 @@ def cpu_baseline(g, passes=3):
             "sample": f"oracle (NumPy/SciPy FP64) LOBPCG, {passes} passes after the start "
                       f"Rayleigh-Ritz on the full n={g.n} K={K} graph; Laplacian build "
                       f"{t1 - t0:.2f} s not counted"}
+
+
+# ---- other workloads (opt-in: --configs 3,4,5) -------------------------------------------------
+
+
+def lambda_max(sc, ctx, G, n, steps=60):
+    """||L||_2 by power iteration through sc_lap_apply (FP64 vectors on the device)."""
+    import torch
+
+    v = torch.ones((n, 1), dtype=torch.float64, device="cuda")
+    v[::2] = -1.0
+    v /= v.norm()
+    lam = 0.0
+    for _ in range(steps):
+        w = sc.sc_lap_apply(ctx, G, v, prec=sc.SC_PREC_FP64)
+        lam = float((v * w).sum())
+        v = w / w.norm()
+    return lam
+
+
+def cfg_large(sc, W, ctx, n=2_000_000, K=160, fp64_passes=3):
+    """n = 2M, K = 160: mixed LOBPCG to max residual <= 1e-2 lambda_max; plain FP64 per pass."""
+    import torch
+
+    t0 = time.perf_counter()
+    g = W.dcsbm(n, K, seed=SEED)
+    gen_s = time.perf_counter() - t0
+    G = sc.sc_build_laplacian(ctx, n, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda())
+    lmax = lambda_max(sc, ctx, G, n)
+    tol = 1e-2 * lmax
+    ctx.bytes_peak()
+    out = {"n": n, "K": K, "m": int(g.m), "nnz": int(sc.sc_graph_info(G)[1]),
+           "lambda_max": lmax, "tol": tol, "gen_s": gen_s}
+    try:
+        _, resid, _, inf = sc.sc_lobpcg(ctx, G, K, iters=400, tol_abs=tol, prec=sc.SC_PREC_MIXED,
+                                       seed=SEED, cold=1, want_X=False)
+        out["mixed"] = {"ms": inf["ms"], "iters": inf["iters_done"], "max_resid": float(resid.max()),
+                        "converged": inf["converged"], "ms_per_pass": inf["ms"] / max(inf["iters_done"], 1)}
+    except sc.ScError as e:
+        out["mixed"] = {"error": str(e)}
+    out["hbm_peak_gb"] = ctx.bytes_peak() / 1e9
+    try:
+        _, resid, _, inf = sc.sc_lobpcg(ctx, G, K, iters=fp64_passes, prec=sc.SC_PREC_FP64,
+                                       seed=SEED, cold=1, want_X=False)
+        per = inf["ms"] / max(inf["iters_done"], 1)
+        out["fp64"] = {"ms": inf["ms"], "iters": inf["iters_done"], "ms_per_pass": per,
+                       "note": f"{fp64_passes} passes timed; time to the residual not run"}
+        if "iters" in out.get("mixed", {}):
+            out["fp64"]["projected_ms_at_mixed_iters"] = per * out["mixed"]["iters"]
+    except sc.ScError as e:
+        out["fp64"] = {"error": str(e)}
+    out["hbm_peak_gb_fp64"] = ctx.bytes_peak() / 1e9
+    G.close()
+    return out
+
+
+def cfg_stream(sc, W, ctx, n=50000, K=44, stages=10, cap=200):
+    """Emerging-edge stream: stage 1 cold 20 passes sets rho*; stages 2.. run warm (resident
+    block) and cold (fresh graph) to max residual <= rho*, then k-means on the warm block."""
+    from paper_1708_07481_gb300.metrics import pm_pr_pp
+
+    g = W.dcsbm(n, K, seed=SEED)
+    deltas = W.emerging_deltas(g, stages)
+    G = sc.sc_build_laplacian(ctx, n, g.src[deltas[0]], g.dst[deltas[0]])
+    _, resid, _, inf = sc.sc_lobpcg(ctx, G, K, iters=20, seed=SEED, cold=1, want_X=False)
+    rho = float(resid.max())
+    rows = [{"stage": 1, "cold_iters": inf["iters_done"], "cold_ms": inf["ms"]}]
+    for s in range(1, stages):
+        sc.sc_stream_update(ctx, G, n, g.src[deltas[s]], g.dst[deltas[s]])
+        row = {"stage": s + 1}
+        for name, cold, graph in (("warm", 0, G), ("cold", 1, None)):
+            Gc = graph
+            if Gc is None:
+                upto = np.concatenate(deltas[: s + 1])
+                Gc = sc.sc_build_laplacian(ctx, n, g.src[upto], g.dst[upto])
+            try:
+                _, resid, _, inf = sc.sc_lobpcg(ctx, Gc, K, iters=cap, tol_abs=rho, seed=SEED,
+                                               cold=cold, want_X=False)
+                row[name + "_iters"], row[name + "_ms"] = inf["iters_done"], inf["ms"]
+            except sc.ScError as e:
+                row[name + "_iters"] = getattr(e, "info", {}).get("iters_done")
+                row[name + "_error"] = str(e)
+            if graph is None:
+                Gc.close()
+        labels, _ = sc.sc_partition(ctx, G, K, K, iters=0, seed=SEED, cold=0)
+        row["pm"], row["pr"], row["pp"] = pm_pr_pp(g.truth, labels)
+        rows.append(row)
+    warm = [r.get("warm_iters") or 0 for r in rows[1:]]
+    cold = [r.get("cold_iters") or 0 for r in rows[1:]]
+    G.close()
+    return {"n": n, "K": K, "rho_star": rho, "stages": rows,
+            "iters_saved_total": int(sum(cold) - sum(warm)),
+            "warm_over_cold_iters": (sum(warm) / sum(cold)) if sum(cold) else None}
+
+
+def cfg_serve(sc, W, ctx, count=128, rate=200.0, fp64_sample=6):
+    """Poisson arrivals (seeded) of cold graphs and emerging-edge deltas of the most recent
+    cold graph through the partition server; p50/p99 latency and partitions/s, next to the
+    same requests one at a time in plain FP64 on a bounded sample."""
+    reqs = W.serving_requests(count, rate, seed=SEED)
+    graphs, payload = {}, []
+    for i, r in enumerate(reqs):
+        if r["cold"]:
+            g = W.dcsbm(r["n"], r["K"], seed=r["seed"])
+            d = W.emerging_deltas(g, 10)
+            graphs[i] = (g, d, 1)
+            payload.append((sc.SC_REQ_COLD, i, g.n, g.src[d[0]], g.dst[d[0]], g.K))
+        else:
+            j = max(k for k in graphs if k < i)
+            g, d, nxt = graphs[j]
+            graphs[j] = (g, d, nxt + 1)
+            payload.append((sc.SC_REQ_DELTA, j, g.n, g.src[d[nxt]], g.dst[d[nxt]], g.K))
+    srv = sc.sc_server_create(ctx, max_slots=16, queue_cap=count)
+    t0 = time.perf_counter()
+    tickets = []
+    for r, (kind, gid, n, s_, d_, K) in zip(reqs, payload):
+        wait = r["t"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append((srv.submit(kind, gid, n, s_, d_, K, K, iters=20 if kind == sc.SC_REQ_COLD else 8), n))
+    lat, ok = [], 0
+    for t, n in tickets:
+        rc, _, _, l = srv.wait(t, n)
+        ok += rc == sc.SC_OK
+        lat.append(l)
+    wall = time.perf_counter() - t0
+    srv.close()
+    # one at a time, plain FP64, first cold requests of the same stream
+    t1 = time.perf_counter()
+    done = 0
+    for kind, gid, n, s_, d_, K in payload:
+        if kind != sc.SC_REQ_COLD:
+            continue
+        G = sc.sc_build_laplacian(ctx, n, s_, d_)
+        sc.sc_partition(ctx, G, K, K, iters=20, prec=sc.SC_PREC_FP64, seed=SEED)
+        G.close()
+        done += 1
+        if done >= fp64_sample:
+            break
+    fp64_rate = done / (time.perf_counter() - t1)
+    return {"requests": count, "rate_per_s": rate, "ok": ok,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "partitions_per_s": count / wall, "wall_s": wall,
+            "fp64_one_at_a_time_partitions_per_s": fp64_rate,
+            "fp64_sample": f"first {done} cold requests, sc_partition in SC_PREC_FP64, one at a time"}
 
 
 def run_reference(args):
@@ -314,6 +468,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--configs", default="", help="also run other workloads: 3 (n=2M, K=160 to "
+                    "residual), 4 (emerging-edge stream), 5 (serving); e.g. --configs 3,4,5")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -73,6 +73,9 @@ void sc_ctx_destroy(sc_ctx* ctx);
 const char* sc_last_error(const sc_ctx* ctx);
 /* Bytes currently held on the device by this context and its graphs. */
 size_t sc_ctx_bytes_in_use(const sc_ctx* ctx);
+/* High-water mark of the device bytes the context held since the previous call (or since
+ * creation); the mark is reset to the current use.  Not thread-safe (like the context). */
+size_t sc_ctx_bytes_peak(sc_ctx* ctx);
 /* Number of kernels the library has launched so far in this process (launch accounting). */
 uint64_t sc_ctx_kernel_launches(const sc_ctx* ctx);
 /* Kernel timing: between sc_profile_begin and sc_profile_end, every launch of a kernel
@@ -196,6 +199,8 @@ int sc_stream_update(sc_ctx* ctx, sc_graph* g, int32_t n_new, int64_t m_delta,
  *   SC_REQ_DELTA -- add the edges to graph graph_id, grow it to n vertices (new vertices
  *                   numbered last) and partition it warm-started from its resident block
  *                   (zero rows for new vertices, Sec. III).
+ * Requests on one graph_id run one at a time in submission order (a later request on a
+ * graph waits while an earlier one is queued or running); requests on other graphs proceed.
  * Edge arrays are copied by sc_server_submit.  Results are identical to running the same
  * request alone.  A request whose estimated footprint exceeds the budget fails SC_ENOMEM.
  * The server functions are thread-safe. */

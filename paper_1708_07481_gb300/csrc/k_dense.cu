@@ -798,7 +798,8 @@ __global__ void __launch_bounds__(NW * 32)
   T* red = coef + K;    // 3 NW per-warp parts, then scalar slots RS ..
   T* nxt = red + 3 * NW + 8;
   T* A = SM ? nxt : Ag;                             // m x m (row stride m)
-  T* Z = SM ? A + (size_t)m * m : Zg;               // m x K
+  const int lda = m;  // row stride of the matrix
+  T* Z = SM ? A + (size_t)m * lda : Zg;             // m x K
   T* U = SM ? Z + (size_t)m * K : Ug;               // 3 m K
   T* Gs = SM ? U + (size_t)3 * m * K : Gsg;         // K x K
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(NW * 32)
 
   for (int i = warp; i < m; i += NW)
     for (int j = lane; j < m; j += 32)
-      A[i * m + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+      A[i * lda + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
   __syncthreads();
   RR_MARK(0);
 
@@ -883,8 +884,8 @@ __global__ void __launch_bounds__(NW * 32)
       for (int i = k1 + off; i < m; i += 2 * NWR) {
         const int i2 = i + NWR;
         const bool has2 = i2 < m;  // uniform in the warp
-        const T* __restrict__ ra = A + i * m;
-        const T* __restrict__ rb = A + (has2 ? i2 : i) * m;
+        const T* __restrict__ ra = A + i * lda;
+        const T* __restrict__ rb = A + (has2 ? i2 : i) * lda;
         T sa = 0, sb = 0;
 #pragma unroll
         for (int u = 0; u < NS; ++u) {
@@ -926,8 +927,8 @@ __global__ void __launch_bounds__(NW * 32)
       // the next row (row k1 with this step's update; no warp updates row k1) and the
       // reflector of step k, kept in row k for the back-transformation
       const T wk1 = Pb[k1] - kc;
-      const T* r1 = A + k1 * m;
-      T* rk = A + k * m;
+      const T* r1 = A + k1 * lda;
+      T* rk = A + k * lda;
 #pragma unroll
       for (int u = 0; u < NS; ++u) {
         const int j = lane + 32 * u;
@@ -945,8 +946,8 @@ __global__ void __launch_bounds__(NW * 32)
         const bool has2 = i2 < m;
         const T via = vk[i], wia = Pb[i] - kc * via;
         const T vib = has2 ? vk[i2] : (T)0, wib = has2 ? Pb[i2] - kc * vib : (T)0;
-        T* __restrict__ ra = A + i * m;
-        T* __restrict__ rb = A + (has2 ? i2 : i) * m;
+        T* __restrict__ ra = A + i * lda;
+        T* __restrict__ rb = A + (has2 ? i2 : i) * lda;
         T na[NS], nb[NS];
 #pragma unroll
         for (int u = 0; u < NS; ++u) {
@@ -979,7 +980,7 @@ __global__ void __launch_bounds__(NW * 32)
       d[k] = xa;
       if (m >= 2) {
         e[k] = xb;
-        d[m - 1] = A[(m - 1) * m + (m - 1)];
+        d[m - 1] = A[(m - 1) * lda + (m - 1)];
       }
       e[m - 1] = 0;
     }
@@ -1238,7 +1239,7 @@ __global__ void __launch_bounds__(NW * 32)
       const T bet = beta[kr];
       if (bet == (T)0) continue;  // uniform
       const int k1 = kr + 1;
-      const T* vk = A + kr * m;
+      const T* vk = A + kr * lda;
       T cv[NS];
       T sa = 0, sb = 0;
 #pragma unroll

@@ -336,6 +336,7 @@ __global__ void k_cent_partial(int n, int d, int k, const float* __restrict__ E,
     __syncthreads();
     for (int rr = 0; rr < nr; ++rr) {
       const int l = lab[rr];
+      if ((unsigned)l >= (unsigned)k) continue;  // never written by an assignment: skip
       for (int c = threadIdx.x; c < d; c += blockDim.x)
         acc[(long long)l * d + c] += (double)stg[rr * d + c];
       if (threadIdx.x == 0) cnt[l] += 1;
@@ -411,14 +412,16 @@ __global__ void __launch_bounds__(256)
   (void)red;
 }
 
-__global__ void k_inertia(int n, int d, const float* __restrict__ E, long long lde,
+__global__ void k_inertia(int n, int d, int k, const float* __restrict__ E, long long lde,
                           const int* __restrict__ labels, const double* __restrict__ C64,
                           double* part) {
   __shared__ double sh[40];
   double v = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const double* c = C64 + (long long)labels[i] * d;
+    const int l = labels[i];
+    if ((unsigned)l >= (unsigned)k) continue;
+    const double* c = C64 + (long long)l * d;
     for (int q = 0; q < d; ++q) {
       double df = (double)E[i * lde + q] - c[q];
       v = fma(df, df, v);
@@ -494,7 +497,9 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
     int Dp = 0;
     AssignFn afn = assign_for(d, &Dp);
     size_t asm_bytes = sizeof(float) * (size_t)ACH * Dp;
-    if (asm_bytes > 48 * 1024) {
+    // opt in above 40 KB: the kernel's static shared memory comes on top of the dynamic part,
+    // and the two together may not exceed the 48 KB default without the attribute
+    if (asm_bytes > 40 * 1024) {
       e = cudaFuncSetAttribute(afn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_bytes);
       if (e != cudaSuccess) goto out;
     }
@@ -502,7 +507,7 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
     size_t psm = sizeof(double) * (size_t)k * d;
     int use_smem = psm + stg_bytes <= 160 * 1024;
     psm = (use_smem ? psm : 0) + stg_bytes;
-    if (psm > 48 * 1024) {
+    if (psm > 40 * 1024) {
       e = cudaFuncSetAttribute(k_cent_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)psm);
       if (e != cudaSuccess) goto out;
@@ -521,12 +526,15 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
                                          it == 0, 2e-5 + 5e-7 * d, ctl);
         note_launch();
       }
+      // a launch that did not start leaves the labels unwritten: stop here
+      if ((e = cudaGetLastError()) != cudaSuccess) goto out;
       k_cent_partial<<<(unsigned)nct, 64, psm, st>>>(n, d, k, E, lde, labels, rpc, part, pcnt,
                                                      use_smem, ctl, changes + it, it);
       note_launch();
       k_cent_reduce<<<k, 256, 0, st>>>(d, k, (int)nct, part, pcnt, C64, C32, cn, ctl,
                                        changes + it, it);
       note_launch();
+      if ((e = cudaGetLastError()) != cudaSuccess) goto out;
       if ((it + 1) % 4 == 0 && it + 1 < iters) {
         int h = 0;
         cudaMemcpyAsync(&h, ctl, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -535,7 +543,7 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
       }
     }
     cudaMemcpyAsync(&done, ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
-    k_inertia<<<152, 256, 0, st>>>(n, d, E, lde, labels, C64, ipart);
+    k_inertia<<<152, 256, 0, st>>>(n, d, k, E, lde, labels, C64, ipart);
     note_launch();
     double hp[152];
     cudaMemcpyAsync(hp, ipart, sizeof(hp), cudaMemcpyDeviceToHost, st);

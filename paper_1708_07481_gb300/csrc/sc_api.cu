@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/sc.h"
@@ -80,6 +81,7 @@ struct sc_ctx {
   bool own_stream = false;
   size_t budget = 0;
   size_t in_use = 0;
+  size_t peak = 0;  // high-water mark of in_use
   std::unordered_map<void*, size_t> sizes;
   std::string err;
   int* d_status = nullptr;
@@ -107,6 +109,7 @@ static void* ctx_alloc(void* self, size_t bytes) {
   }
   c->sizes[p] = bytes;
   c->in_use += bytes;
+  if (c->in_use > c->peak) c->peak = c->in_use;
   return p;
 }
 static void ctx_free(void* self, void* p) {
@@ -220,6 +223,12 @@ void sc_ctx_destroy(sc_ctx* c) {
 const char* sc_last_error(const sc_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 size_t sc_ctx_bytes_in_use(const sc_ctx* c) { return c ? c->in_use : 0; }
+size_t sc_ctx_bytes_peak(sc_ctx* c) {
+  if (!c) return 0;
+  const size_t p = c->peak;
+  c->peak = c->in_use;
+  return p;
+}
 uint64_t sc_ctx_kernel_launches(const sc_ctx*) { return launches_total(); }
 
 int sc_profile_begin(sc_ctx* c, const char* kernels) {
@@ -449,6 +458,7 @@ void* run_alloc(void* self, size_t bytes) {
   }
   c->sizes[p] = bytes;
   c->in_use += bytes;
+  if (c->in_use > c->peak) c->peak = c->in_use;
   return p;
 }
 void run_free(void* self, void* p) {
@@ -1361,23 +1371,35 @@ static void srv_loop(sc_server* s) {
                             [&] { return s->stop || !s->queue.empty(); });
       if (s->stop && s->queue.empty() && s->active.empty()) break;
       const size_t budget = s->c->budget;
-      while (!s->queue.empty() && (int)(s->active.size() + admit.size()) < s->max_slots) {
-        size_t est = footprint(s->queue.front().r);
+      // Requests on one graph run one at a time, in arrival order: a graph that is being
+      // solved (or has an earlier request still queued) must not be rebuilt or merged into
+      // while kernels of the running solve read its CSR and resident block.
+      std::unordered_set<int> busy;
+      for (const SrvSlot& sl : s->active) busy.insert(sl.req.r.graph_id);
+      for (auto it = s->queue.begin(); it != s->queue.end() &&
+                                       (int)(s->active.size() + admit.size()) < s->max_slots;) {
+        const int gid = it->r.graph_id;
+        if (busy.count(gid)) {
+          ++it;  // stays queued, and keeps later requests on the same graph behind it
+          continue;
+        }
+        busy.insert(gid);
+        size_t est = footprint(it->r);
         if (budget && est > budget) {  // can never fit: reject
           SrvResult res;
           res.status = SC_ENOMEM;
-          s->results[s->queue.front().ticket] = std::move(res);
+          s->results[it->ticket] = std::move(res);
           s->completed++;
-          s->queue.pop_front();
+          it = s->queue.erase(it);
           s->cv_done.notify_all();
           continue;
         }
         if (budget && s->c->in_use + s->reserved + est > budget && !(s->active.empty() && admit.empty()))
           break;  // wait for memory to free up
         s->reserved += est;
-        admit.push_back(std::move(s->queue.front()));
+        admit.push_back(std::move(*it));
         admit.back().r.src = nullptr;
-        s->queue.pop_front();
+        it = s->queue.erase(it);
       }
     }
     for (auto& rq : admit) {

@@ -77,6 +77,7 @@ def lib():
         "sc_ctx_destroy": ([vp], None),
         "sc_last_error": ([vp], C.c_char_p),
         "sc_ctx_bytes_in_use": ([vp], C.c_size_t),
+        "sc_ctx_bytes_peak": ([vp], C.c_size_t),
         "sc_ctx_kernel_launches": ([vp], u64),
         "sc_profile_begin": ([vp, C.c_char_p], C.c_int),
         "sc_profile_end": ([vp, C.c_char_p, C.c_size_t], C.c_int),
@@ -169,6 +170,10 @@ class Ctx:
     @property
     def bytes_in_use(self):
         return lib().sc_ctx_bytes_in_use(self.h)
+
+    def bytes_peak(self):
+        """High-water mark since the previous call (then reset to the current use)."""
+        return lib().sc_ctx_bytes_peak(self.h)
 
     @property
     def launches(self):

@@ -103,6 +103,35 @@ def test_server_results_equal_standalone(sc, ctx):
         srv_ctx.close()
 
 
+def test_server_back_to_back_requests_on_one_graph(sc):
+    # a cold request and two deltas of the same graph submitted without waiting: the server
+    # runs them one after the other on that graph, as the standalone sequence does
+    g = W.dcsbm(6000, 9, seed=41)
+    deltas = W.emerging_deltas(g, stages=3)
+    ref_ctx = sc.sc_ctx_create(0)
+    try:
+        G = sc.sc_build_laplacian(ref_ctx, g.n, g.src[deltas[0]], g.dst[deltas[0]])
+        ref = [sc.sc_partition(ref_ctx, G, 9, 9, iters=15, seed=5, cold=1)[0]]
+        for s_ in (1, 2):
+            sc.sc_stream_update(ref_ctx, G, g.n, g.src[deltas[s_]], g.dst[deltas[s_]])
+            ref.append(sc.sc_partition(ref_ctx, G, 9, 9, iters=8, seed=5, cold=0)[0])
+    finally:
+        ref_ctx.close()
+    srv_ctx = sc.sc_ctx_create(0)
+    srv = sc.sc_server_create(srv_ctx, max_slots=4, queue_cap=16)
+    try:
+        t = [srv.submit(sc.SC_REQ_COLD, 3, g.n, g.src[deltas[0]], g.dst[deltas[0]], 9, 9, iters=15, seed=5)]
+        for s_ in (1, 2):
+            t.append(srv.submit(sc.SC_REQ_DELTA, 3, g.n, g.src[deltas[s_]], g.dst[deltas[s_]], 9, 9,
+                                iters=8, seed=5))
+        for q, tk in enumerate(t):
+            rc, lab, _, _ = srv.wait(tk, g.n)
+            assert rc == sc.SC_OK and np.array_equal(lab, ref[q]), q
+    finally:
+        srv.close()
+        srv_ctx.close()
+
+
 def test_server_admission_and_queue_limits(sc):
     small = W.dcsbm(2000, 5, seed=30)
     ctx = sc.sc_ctx_create(0, budget=64 << 20)

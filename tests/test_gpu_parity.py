@@ -282,7 +282,7 @@ def _clustered(n, d, k, seed, spread=0.05):
     return O.embed_rows(E).astype(np.float32), lab
 
 
-@pytest.mark.parametrize("n,d,k", [(1000, 11, 11), (50000, 44, 44), (3001, 5, 1)])
+@pytest.mark.parametrize("n,d,k", [(1000, 11, 11), (50000, 44, 44), (3001, 5, 1), (3000, 100, 70), (3000, 156, 150), (2000, 200, 40)])
 def test_kmeans_seeds_and_labels_bit_exact(sc, ctx, n, d, k):
     E, _ = _clustered(n, d, max(k, 2), n)
     u = W.kmeans_uniforms(5, k)
@@ -318,6 +318,21 @@ def test_partition_matches_oracle_labels(sc, ctx):
     rl, res, E, idx = O.partition(L, X0, 11, W.kmeans_uniforms(0, 11), 20, 50)
     assert O.partition_metrics(rl, labels)[0] == 1.0  # identical up to a permutation
     assert O.partition_metrics(g.truth, labels)[0] == 1.0
+
+
+@pytest.mark.parametrize("n,K", [(3000, 50), (4000, 70), (5000, 140)])
+def test_partition_wide_blocks(sc, ctx, n, K):
+    # block widths of the serving workload: Rayleigh-Ritz sizes 3K from 150 to 420 and
+    # k-means in d = K dimensions with k = K clusters
+    g = W.dcsbm(n, K, seed=K)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=6, seed=1, cold=1)
+    ref = O.lobpcg(L, W.start_block(1, g.n, K).astype(np.float32).astype(np.float64), 6)
+    lmax = 2 * L.deg.max()
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
+    labels, info = sc.sc_partition(ctx, G, K, K, iters=6, seed=1)
+    assert labels.min() >= 0 and labels.max() < K
 
 
 # ------------------------------------------------------------------ a12: streaming
