@@ -135,6 +135,9 @@ typedef struct {
   double resid[SC_MAX_K];  /* ||L x_j - lambda_j x_j||_2 of the returned pairs     */
   float ms;            /* device time of the call (CUDA events on the ctx stream) */
   uint64_t kernels;    /* kernels launched by the call                           */
+  int dropped;         /* residual columns dropped from a pass's trial basis
+                          (Cholesky pivot below tolerance: the column had sunk to
+                          rounding noise in the span of X and the other columns)  */
 } sc_eig_info;
 
 /* sc_lobpcg: the K smallest eigenpairs of the graph's Laplacian.

@@ -12,6 +12,7 @@ from .spectral import (  # noqa: F401
     BreakdownError,
     LobpcgResult,
     cholqr,
+    cholqr_drop,
     embed_rows,
     kmeans,
     kmeanspp_seed,

@@ -111,6 +111,11 @@ class BreakdownError(RuntimeError):
 # breakdown of the trial basis.
 PIVOT_TOL = 1e-14
 
+# A direction column p_j (X unit) whose norm after projection against X is at or below this
+# rounding level is left out of the pass (64 units of roundoff of float64); a residual column
+# at or below DIR_FLOOR times the Gershgorin bound 2 max_i d_i on ||L|| likewise.
+DIR_FLOOR = 64.0 * 2.0 ** -53
+
 
 def _chol_lower(G: np.ndarray) -> np.ndarray:
     """Lower Cholesky factor of a symmetric matrix with unit-ish diagonal, or breakdown."""
@@ -139,6 +144,40 @@ def cholqr(V: np.ndarray):
     Cs = _chol_lower(G * s[:, None] * s[None, :])
     Q = sla.solve_triangular(Cs, (V * s[None, :]).T, lower=True).T
     return Q, Cs / s[:, None]
+
+
+def cholqr_drop(V: np.ndarray, tol: float = PIVOT_TOL):
+    """Cholesky-QR of the columns of V that are independent to working accuracy.
+
+    Column k is kept when its pivot in the Cholesky factorization of the scaled Gram
+    diag(s) V'V diag(s) restricted to the kept columns before it and k itself exceeds tol,
+    i.e. when the part of v_k / ||v_k|| orthogonal to the kept columns has squared norm
+    above tol; a zero column is never kept.  Returns (Q, kept) with Q = CholQR(V[:, kept]).
+    Used for the residual block, whose converged columns sink to rounding noise that need
+    not be independent (the block is rank-deficient to working accuracy).
+
+    Pinned by: exactly dependent columns dropped, independent ones kept, span preserved.
+    """
+    G = V.T @ V
+    G = 0.5 * (G + G.T)
+    d = np.diag(G).copy()
+    kept = []
+    for k in range(V.shape[1]):
+        if d[k] <= 0:
+            continue
+        idx = kept + [k]
+        s = 1.0 / np.sqrt(d[idx])
+        Gs = G[np.ix_(idx, idx)] * s[:, None] * s[None, :]
+        try:
+            C = np.linalg.cholesky(Gs)
+        except np.linalg.LinAlgError:
+            continue
+        if C[-1, -1] ** 2 > tol:
+            kept.append(k)
+    if not kept:
+        return V[:, :0].copy(), kept
+    Q, _ = cholqr(V[:, kept])
+    return Q, kept
 
 
 def rayleigh_ritz(GA: np.ndarray, GB: np.ndarray, K: int):
@@ -176,6 +215,7 @@ class LobpcgResult:
     iters: int  # loop passes performed after the initial Rayleigh-Ritz
     fallbacks: int  # iterations where the direction block P had to be dropped
     history: list = field(default_factory=list)  # per pass: (lam, resid-before-update)
+    dropped: int = 0  # residual columns dropped as dependent (cholqr_drop), summed over passes
 
 
 def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: float = 0.0,
@@ -186,9 +226,15 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
     Each pass i = 1..iters:
       R = LX - X diag(lam), rho_j = ||r_j||; active = {j : rho_j > tol_lock} (soft locking,
       Sec. IV); stop when nothing is active or max rho <= tol_abs.
-      R_a <- R_a - X (X' R_a); R_a <- CholQR(R_a); LR_a = L R_a.
+      R_a <- R_a - X (X' R_a); columns at the rounding floor (norm <= DIR_FLOOR * 2 max d)
+      are left out, which soft-locks pairs that cannot improve; R_a <- CholQR of its
+      columns independent to working accuracy (cholqr_drop: residuals of converged columns
+      sink to rounding noise, which need not be independent); LR_a = L R_a.
       For i > 1: P_a <- P_a - [X R_a] F with F = [X R_a]' P_a, then CholQR(P_a); LP_a is
-      transformed alike (the orthonormal trial basis of Hetmaniuk & Lehoucq 2006).
+      transformed alike (the orthonormal trial basis of Hetmaniuk & Lehoucq 2006).  Columns
+      of P_a whose part orthogonal to X is at rounding level (DIR_FLOOR) are left out of
+      the pass: past convergence the step sinks to roundoff, and the implicitly carried
+      image LP would otherwise be normalized noise that derails the iteration.
       S = [X R_a P_a], LS = [LX LR_a LP_a]; Rayleigh-Ritz on (S' LS, S' S), K smallest.
       With Y = [Y_X; Y_R; Y_P]: P = R_a Y_R + P_a Y_P, X = X Y_X + P (LX, LP alike).
       A breakdown of the Cholesky of P's Gram (P inside span{X, R}) or of the trial basis
@@ -218,7 +264,9 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
     P = LP = None
     hist = []
     fallbacks = 0
+    dropped = 0
     done = 0
+    res_floor = DIR_FLOOR * 2.0 * float(np.max(L.deg, initial=0.0))
     for _ in range(iters):
         R = LX - X * lam[None, :]
         rho = np.linalg.norm(R, axis=0)
@@ -229,25 +277,38 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
             break
         Ra = R[:, act]
         Ra = Ra - X @ (X.T @ Ra)
-        Ra, _ = cholqr(Ra)
+        # a residual at the rounding floor cannot improve its Ritz pair: leave it out (this
+        # soft-locks the pair at the accuracy the arithmetic allows)
+        Ra = Ra[:, np.linalg.norm(Ra, axis=0) > res_floor]
+        Ra, kept_r = cholqr_drop(Ra)
+        dropped += int(act.sum()) - len(kept_r)
         LRa = lap_apply(L, Ra)
         blocks = [(X, LX), (Ra, LRa)]
         if P is not None:
             Pa, LPa = P[:, act], LP[:, act]
-            XR = np.concatenate([X, Ra], axis=1)
-            LXR = np.concatenate([LX, LRa], axis=1)
-            F = XR.T @ Pa
-            Pa = Pa - XR @ F
-            LPa = LPa - LXR @ F
-            try:
-                Pa, Cp = cholqr(Pa)
-                if explicit:
-                    LPa = lap_apply(L, Pa)
-                else:
-                    LPa = sla.solve_triangular(Cp, LPa.T, lower=True).T
-                blocks.append((Pa, LPa))
-            except BreakdownError:
-                fallbacks += 1
+            # against X first; a column whose part orthogonal to X has sunk to rounding
+            # level (norm <= DIR_FLOOR, X unit) is left out: it carries no step, and its
+            # implicitly updated image would be amplified noise once normalized
+            F = X.T @ Pa
+            Pa = Pa - X @ F
+            LPa = LPa - LX @ F
+            live = np.linalg.norm(Pa, axis=0) > DIR_FLOOR
+            dropped += int((~live).sum())
+            Pa, LPa = Pa[:, live], LPa[:, live]
+            # then against R_a (orthogonal to X, so the two steps project against [X R_a])
+            F = Ra.T @ Pa
+            Pa = Pa - Ra @ F
+            LPa = LPa - LRa @ F
+            if Pa.shape[1] > 0:
+                try:
+                    Pa, Cp = cholqr(Pa)
+                    if explicit:
+                        LPa = lap_apply(L, Pa)
+                    else:
+                        LPa = sla.solve_triangular(Cp, LPa.T, lower=True).T
+                    blocks.append((Pa, LPa))
+                except BreakdownError:
+                    fallbacks += 1
         try:
             theta, Y = _rr_blocks(blocks, K)
         except BreakdownError:
@@ -271,7 +332,7 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
         done += 1
     R = LX - X * lam[None, :]
     return LobpcgResult(lam=lam, X=X, resid=np.linalg.norm(R, axis=0), iters=done,
-                        fallbacks=fallbacks, history=hist)
+                        fallbacks=fallbacks, history=hist, dropped=dropped)
 
 
 def _rr_blocks(blocks, K):

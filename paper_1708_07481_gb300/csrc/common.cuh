@@ -183,15 +183,22 @@ cudaError_t rownorm(cudaStream_t st, long long n, int K, const T* X, long long l
 // Tm is ka x ka upper triangular (row-major, T).  Status bit ST_CHOL_FAIL on breakdown.
 // With pflag != null and a breakdown at a column >= keep, the transform of the leading keep
 // columns is returned (zeros elsewhere) and *pflag is cleared instead of reporting failure.
+// A column whose norm is at or below its floor (rfloor for columns < keep, pfloor for the
+// rest) counts as zero.  With ndrop > 0, a breakdown at a column < ndrop, or a zero column
+// anywhere, drops that column alone (zero column of Tm) and adds one to *ndropped (if given).
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
                      int* d_status, double pivot_tol, int* fail_col = nullptr, int keep = 0,
-                     int* pflag = nullptr);
+                     int* pflag = nullptr, int ndrop = 0, int* ndropped = nullptr,
+                     double rfloor = 0.0, double pfloor = 0.0);
 
 // Rayleigh-Ritz in an orthonormal basis: K smallest eigenpairs of symmetric m x m G (FP64).
 // theta[K] FP64 (device), Y (m x K, T, row-major).  Arithmetic in T.
 // pflag (optional, device): 0 = the trailing mP basis columns were dropped; the solve then
 // uses the leading m - mP block, zeroes the rest of Y, bumps *nfallback and re-arms *pflag.
+// A basis column i >= K with G_ii exactly 0 (a column the Cholesky-QR dropped: its row of G
+// is zero) gets a diagonal above the Gershgorin bound of G, so its spurious eigenvalue is
+// never among the K smallest.
 template <typename T>
 cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
                    double* theta, T* Y, int* d_status, int* pflag = nullptr, int mP = 0,

@@ -145,10 +145,15 @@ __device__ void blk_tri_inv(int ka, const T* W, int ldw, const T* rdiag, T* Li, 
 // l_ik = W_ik / d_k, which updates its trailing part W_ij (j > k) with the pivot column and
 // its leading part (L^-1)_ic (c < k) with row k of L^-1).  On return M[i][c] (c < i) holds
 // (L^-1)_ic and dd[k] the pivot d_k.  One barrier per column: the pivot column is passed on
-// through the double buffer cb (2 n entries) by the rows that finish it.  Returns the first
-// k with d_k <= tol (rows and pivots before it are final), else -1.
+// through the double buffer cb (2 n entries) by the rows that finish it.  A pivot d_k <= tol
+// at k < ndrop, or an exactly zero pivot anywhere when zdrop is set (a zeroed column), drops
+// column k (it lies in the span of the columns before it, to working accuracy): dd[k] = 0,
+// column k of L^-1 below the diagonal is zero and the column takes no part in eliminating
+// the rows below.  Returns the first other k with d_k <= tol (rows and pivots before it are
+// final), else -1.
 template <typename T>
-__device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol) {
+__device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol, int ndrop = 0,
+                           bool zdrop = false) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int i = tid; i < n; i += nt) cb[i] = M[(long long)i * ldm];
   __syncthreads();
@@ -156,7 +161,16 @@ __device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol) {
     const T* cur = cb + (k & 1) * n;
     T* nxt = cb + ((k + 1) & 1) * n;
     const T dk = cur[k];
-    if (!(dk > tol)) return k;  // every thread read the same value
+    if (!(dk > tol)) {  // every thread read the same value
+      if (k >= ndrop && !(zdrop && dk == (T)0)) return k;
+      if (tid == 0) dd[k] = 0;
+      for (int i = k + 1 + tid; i < n; i += nt) {
+        M[(long long)i * ldm + k] = 0;
+        nxt[i] = M[(long long)i * ldm + k + 1];
+      }
+      __syncthreads();
+      continue;
+    }
     if (tid == 0) dd[k] = dk;
     const T invd = (T)1 / dk;
     const T* rowk = M + (long long)k * ldm;
@@ -179,15 +193,19 @@ __device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol) {
 // Cholesky-QR transform in the arithmetic of T: from the FP64 Gram G (accumulated in FP64
 // across CTAs), scale s = diag(G)^-1/2 in FP64, factor s G s = L D L' in T (with L^-1 formed
 // alongside), and write Tm = diag(s) L^-T D^-1/2 (ka x ka upper triangular) so that V Tm has
-// orthonormal columns.  A zero column has a zero pivot.  On a pivot <= pivot_tol:
-// ST_CHOL_FAIL in *status and the failing column in *fail_col, unless the failure lies in
-// the trailing columns >= keep (the direction block), in which case the leading keep columns
-// are returned, the rest zeroed, and *pflag cleared.
+// orthonormal columns.  A zero column has a zero pivot, and so has a column whose norm is at
+// or below its floor (rfloor for columns < keep, pfloor for the rest): it is zeroed.  With ndrop > 0, a pivot <= pivot_tol in the leading ndrop
+// columns, and a zero pivot anywhere, drops that column (its column of Tm is zero; the count
+// goes to *ndropped).  Any other pivot <= pivot_tol: ST_CHOL_FAIL in *status and the failing
+// column in *fail_col, unless the failure lies in the trailing columns >= keep (the
+// direction block), in which case the leading keep columns are returned, the rest zeroed,
+// and *pflag cleared.
 // SM = the matrix lives in shared memory.
 template <typename T, bool SM>
 __global__ void __launch_bounds__(1024)
     k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
-               int* status, int* fail_col, double pivot_tol, int keep, int* pflag) {
+               int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
+               int* ndropped, double rfloor, double pfloor) {
   extern __shared__ __align__(16) unsigned char craw[];
   T* s = (T*)craw;    // ka scale factors
   T* dd = s + ka;     // ka pivots
@@ -196,7 +214,8 @@ __global__ void __launch_bounds__(1024)
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < ka; i += nt) {
     double dgi = G[(long long)i * ldg + i];
-    s[i] = dgi > 0.0 ? (T)rsqrt(dgi) : (T)0;
+    const double fl = i < keep ? rfloor * rfloor : pfloor * pfloor;
+    s[i] = dgi > fl ? (T)rsqrt(dgi) : (T)0;
   }
   __syncthreads();
   for (int idx = tid; idx < ka * ka; idx += nt) {
@@ -206,8 +225,14 @@ __global__ void __launch_bounds__(1024)
     W[i * ka + j] = (T)g * s[i] * s[j];
   }
   __syncthreads();
-  const int fc = blk_ldl_inv<T>(ka, W, ka, dd, cb, (T)pivot_tol);
+  const int fc = blk_ldl_inv<T>(ka, W, ka, dd, cb, (T)pivot_tol, ndrop, ndrop > 0);
   __syncthreads();
+  if (ndropped && tid == 0) {
+    const int lim = fc >= 0 ? fc : ka;
+    int cnt = 0;
+    for (int k = 0; k < lim; ++k) cnt += dd[k] == (T)0;
+    if (cnt) atomicAdd(ndropped, cnt);
+  }
   int kk = ka;  // size of the leading block whose transform is returned
   if (fc >= 0) {
     if (pflag && keep > 0 && fc >= keep) {
@@ -221,7 +246,7 @@ __global__ void __launch_bounds__(1024)
       return;
     }
   }
-  for (int i = tid; i < kk; i += nt) cb[i] = rsqrt(dd[i]);
+  for (int i = tid; i < kk; i += nt) cb[i] = dd[i] > (T)0 ? rsqrt(dd[i]) : (T)0;
   __syncthreads();
   // Tm[r][c] = s_r (L^-1)_cr d_c^-1/2 for r <= c < kk
   for (int idx = tid; idx < ka * ka; idx += nt) {
@@ -230,6 +255,27 @@ __global__ void __launch_bounds__(1024)
     if (r <= c && c < kk) v = s[r] * (r == c ? (T)1 : W[c * ka + r]) * cb[c];
     Tm[(long long)r * ka + c] = v;
   }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Rayleigh-Ritz input guard: basis columns i >= K whose FP64 Gram diagonal is exactly zero
+// were dropped by the Cholesky-QR (their columns of S and LS are zero, so is their row of G).
+// Their diagonal is lifted above the Gershgorin bound (the largest of the nw per-warp row-sum
+// maxima in red), which puts their spurious eigenvalues above every genuine Ritz value.
+template <typename T>
+__device__ void lift_dropped(int m, int K, const double* __restrict__ G, int ldg, T* A,
+                             int lda, const T* red, int nw) {
+  T big = 0;
+  for (int w = 0; w < nw; ++w) big = fmax(big, red[w]);
+  big = big * (T)1.25 + (T)1;
+  for (int i = K + (int)threadIdx.x; i < m; i += blockDim.x)
+    if (G[(long long)i * ldg + i] == 0.0) A[(long long)i * lda + i] = big;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -341,10 +387,22 @@ __global__ void __launch_bounds__(RR_NT)
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = nt / 32;
 
-  for (int i = warp; i < m; i += nw)
-    for (int j = lane; j < m; j += 32)
-      A[(long long)i * m + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
-  __syncthreads();
+  {
+    T gmax = 0;  // Gershgorin bound of A: the largest row sum of |a_ij|
+    for (int i = warp; i < m; i += nw) {
+      T rs = 0;
+      for (int j = lane; j < m; j += 32) {
+        const T a = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+        A[(long long)i * m + j] = a;
+        rs += fabs(a);
+      }
+      gmax = fmax(gmax, warp_sum(rs));
+    }
+    if (lane == 0) red[warp] = gmax;
+    __syncthreads();
+    lift_dropped<T>(m, K, G, ldg, A, m, red, nw);
+    __syncthreads();
+  }
   RR_MARK(0);
   // ---- 1. tridiagonalization
   long long tsub = clock64();
@@ -369,11 +427,13 @@ __global__ void __launch_bounds__(RR_NT)
           bet = 0;
           ek = x0;
         } else {
+          // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
+          // v = x / v0 stays <= 1 however small sigma is (no cancellation, no overflow)
           T mu = sqrt(x0 * x0 + sigma);
-          T v0 = (x0 <= (T)0) ? x0 - mu : -sigma / (x0 + mu);
+          T v0 = x0 + copysign(mu, x0);
           bet = (T)2 * v0 * v0 / (sigma + v0 * v0);
           iv0 = (T)1 / v0;
-          ek = mu;
+          ek = -copysign(mu, x0);
         }
         beta[k] = bet;
         e[k] = ek;
@@ -767,13 +827,6 @@ __device__ __forceinline__ T slot_sel(const T (&a)[NS], int u) {
   return r;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 template <typename T, int NS, int NW, bool SM>
 __global__ void __launch_bounds__(NW * 32)
     k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
@@ -805,10 +858,22 @@ __global__ void __launch_bounds__(NW * 32)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int RS = 3 * NW;  // red[RS + 0..4]: lo, hi, max e^2, min pivot, MGS scale
 
-  for (int i = warp; i < m; i += NW)
-    for (int j = lane; j < m; j += 32)
-      A[i * lda + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
-  __syncthreads();
+  {
+    T gmax = 0;  // Gershgorin bound of A: the largest row sum of |a_ij|
+    for (int i = warp; i < m; i += NW) {
+      T rs = 0;
+      for (int j = lane; j < m; j += 32) {
+        const T a = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+        A[i * lda + j] = a;
+        rs += fabs(a);
+      }
+      gmax = fmax(gmax, warp_sum(rs));
+    }
+    if (lane == 0) red[warp] = gmax;
+    __syncthreads();
+    lift_dropped<T>(m, K, G, ldg, A, lda, red, NW);
+    __syncthreads();
+  }
   RR_MARK(0);
 
   // ---- 1. tridiagonalization
@@ -843,12 +908,13 @@ __global__ void __launch_bounds__(NW * 32)
     sg = warp_sum(sg);
     T bet = 0, iv0 = 0, ek = x0;
     if (sg != (T)0) {
-      // v0 = x0 - mu without cancellation; beta = 2 v0^2 / (sigma + v0^2) = 2 / (1 + sigma / v0^2)
+      // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
+      // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
       const T mu = sqrt(x0 * x0 + sg);
-      const T v0 = (x0 <= (T)0) ? x0 - mu : -sg / (x0 + mu);
+      const T v0 = x0 + copysign(mu, x0);
       iv0 = (T)1 / v0;
       bet = (T)2 / ((T)1 + sg * iv0 * iv0);
-      ek = mu;
+      ek = -copysign(mu, x0);
     }
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
@@ -1285,17 +1351,21 @@ __global__ void __launch_bounds__(NW * 32)
 template <typename T>
 cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
                         int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
+                        int ndrop, int* ndropped, double rfloor, double pfloor,
                         int nthreads);
 
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
-                     int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag) {
-  return chol_inv_nt<T>(st, al, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, 512);
+                     int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
+                     int ndrop, int* ndropped, double rfloor, double pfloor) {
+  return chol_inv_nt<T>(st, al, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
+                        ndropped, rfloor, pfloor, 512);
 }
 
 template <typename T>
 cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
                         int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
+                        int ndrop, int* ndropped, double rfloor, double pfloor,
                         int nthreads) {
   size_t base = sizeof(T) * (4 * (size_t)ka);
   size_t wbytes = sizeof(T) * (size_t)ka * ka;
@@ -1310,7 +1380,8 @@ cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   ProfScope ps(st, "chol_inv");
-  kern<<<1, nthreads, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag);
+  kern<<<1, nthreads, sm, st>>>(ka, G, ldg, Tm, Wg, d_status, fail_col, pivot_tol, keep, pflag,
+                                ndrop, ndropped, rfloor, pfloor);
   note_launch();
   e = cudaGetLastError();
   al.put(Wg);
@@ -1397,9 +1468,9 @@ cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, in
 }
 
 template cudaError_t chol_inv<float>(cudaStream_t, Alloc&, int, const double*, int, float*,
-                                     int*, double, int*, int, int*);
+                                     int*, double, int*, int, int*, int, int*, double, double);
 template cudaError_t chol_inv<double>(cudaStream_t, Alloc&, int, const double*, int, double*,
-                                      int*, double, int*, int, int*);
+                                      int*, double, int*, int, int*, int, int*, double, double);
 template cudaError_t rr_eig<float>(cudaStream_t, Alloc&, int, int, const double*, int, double*,
                                    float*, int*, int*, int, int*);
 template cudaError_t rr_eig<double>(cudaStream_t, Alloc&, int, int, const double*, int,

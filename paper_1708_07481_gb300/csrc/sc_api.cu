@@ -503,12 +503,20 @@ struct LobRun : RunBase {
   Alloc al;
   int use_tc;
   double pivot_tol;
+  // Rounding floors of the arithmetic T.  A residual column at or below res_floor (64 ulps of
+  // the Gershgorin bound 2 max_i d_i on ||L||) cannot improve its Ritz pair any further: it is
+  // left out of the pass, which soft-locks that pair on the device.  A direction column whose
+  // norm (X unit) has sunk to dir_floor carries no step, only rounding noise: it is left out
+  // too.
+  double res_floor, dir_floor;
+  static constexpr int kReorth = 16;
   std::vector<void*> bufs;
   T *S = nullptr, *LS = nullptr, *S2 = nullptr, *LS2 = nullptr, *T1 = nullptr, *W1 = nullptr,
-    *W2 = nullptr, *Q1 = nullptr, *LQ1 = nullptr, *Tm = nullptr, *TmA = nullptr, *TmB = nullptr,
+    *Q1 = nullptr, *Tm = nullptr, *TmA = nullptr, *TmB = nullptr,
     *Y = nullptr;
   double *G = nullptr, *theta = nullptr, *rho2 = nullptr;
-  int *dcols = nullptr, *dfail = nullptr, *dP = nullptr, *dfb = nullptr, *dstatus = nullptr;
+  int *dcols = nullptr, *dfail = nullptr, *dP = nullptr, *dfb = nullptr, *ddrop = nullptr,
+      *dstatus = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // second stream for the L-image updates, which overlap the X/R/P side of the pass
   cudaStream_t st2 = nullptr;
@@ -527,6 +535,8 @@ struct LobRun : RunBase {
     al = Alloc{run_alloc, run_free, &ra};
     use_tc = (sizeof(T) == 4 && o.prec == SC_PREC_MIXED) ? 1 : 0;
     pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-14;
+    dir_floor = 64.0 * (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53);
+    res_floor = dir_floor * 2.0 * g->csr.deg_max;
     hrho.assign(K, 0.0);
     hth.assign(K, 0.0);
   }
@@ -638,9 +648,7 @@ struct LobRun : RunBase {
     LS2 = get<T>((size_t)n * ld3, true);
     T1 = get<T>((size_t)n * kp, true);
     W1 = get<T>((size_t)n * 2 * kp, true);
-    W2 = get<T>((size_t)n * 2 * kp, true);
     Q1 = get<T>((size_t)n * 2 * kp, true);
-    LQ1 = get<T>((size_t)n * 2 * kp, true);
     G = get<double>((size_t)mmax * mmax);
     Tm = get<T>((size_t)mmax * mmax);
     TmA = get<T>((size_t)mmax * mmax);
@@ -652,15 +660,17 @@ struct LobRun : RunBase {
     dfail = get<int>(1);
     dP = get<int>(1);
     dfb = get<int>(1);
+    ddrop = get<int>(1);
     dstatus = get<int>(1, true);
-    if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !W2 || !Q1 || !LQ1 || !G || !Tm || !TmA ||
+    if (!S || !LS || !S2 || !LS2 || !T1 || !W1 || !Q1 || !G || !Tm || !TmA ||
         !TmB || !Y ||
-        !theta || !rho2 || !dcols || !dfail || !dP || !dfb || !dstatus)
+        !theta || !rho2 || !dcols || !dfail || !dP || !dfb || !ddrop || !dstatus)
       return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
     {
       int one = 1, zero = 0;
       CK(cudaMemcpyAsync(dP, &one, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
       CK(cudaMemcpyAsync(dfb, &zero, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
+      CK(cudaMemcpyAsync(ddrop, &zero, sizeof(int), cudaMemcpyHostToDevice, st), "flags");
     }
     // ---- start block: given X0 (top x0_rows rows, zero fill below), the resident block of
     //      the previous call (warm start), or a seeded Gaussian block generated on the device
@@ -723,8 +733,14 @@ struct LobRun : RunBase {
     const bool watch = o.tol_abs > 0 || o.tol_lock > 0;
     std::vector<int> act;
     if (watch) {
+      int hs = 0;
       CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "rho");
+      CK(cudaMemcpyAsync(&hs, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st), "rho");
       CK(cudaStreamSynchronize(st), "rho");
+      if (hs) {  // a breakdown or a timed-out wait: stop here, finish() reports it
+        over = true;
+        return SC_OK;
+      }
       double mx = 0.0;
       for (int j = 0; j < K; ++j) {
         double r = std::sqrt(std::max(hrho[j], 0.0));
@@ -752,10 +768,9 @@ struct LobRun : RunBase {
     T* Pslot = S + 2 * kp;
     T* LPslot = LS + 2 * kp;
     // Working copies of the active R and P columns: the S slots themselves when every column
-    // is active; otherwise gathered into W1 = [R_a | P_a] and W2 = [LR_a | LP_a] (n x 2kp).
+    // is active; otherwise gathered into W1 = [R_a | P_a] (n x 2kp).
     T* WR = Rslot;
     T* WP = Pslot;
-    T* WLP = LPslot;
     long long ldw = ld3;
     const int offP = kp;
     if (!all) {
@@ -764,64 +779,58 @@ struct LobRun : RunBase {
       WR = W1;
       WP = W1 + kp;
       ldw = 2 * kp;
-      if (haveP) {
-        CK(gather_cols<T>(st, n, Pslot, ld3, WP, ldw, dcols, ka), "gather");
-        CK(gather_cols<T>(st, n, LPslot, ld3, W2 + kp, ldw, dcols, ka), "gather");
-        WLP = W2 + kp;
-      }
+      if (haveP) CK(gather_cols<T>(st, n, Pslot, ld3, WP, ldw, dcols, ka), "gather");
       // the gathered column list must stay valid until the copy ran
       CK(cudaStreamSynchronize(st), "cols");
     }
     const int w = haveP ? 2 * ka : ka;
-    // (1) project [R_a P_a] against X: F = X'[R_a P_a]; R_a -= X F_R, P_a -= X F_P, LP_a -= LX F_P
+    // (1) project [R_a P_a] against X: F = X'[R_a P_a]; [R_a P_a] -= X F in one pass over X
     if (haveP)
       CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, false), "gram");
     else
       CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}}, G, w, false), "gram");
     CK(cast_mat<T>(st, K, w, G, w, Tm, w, -1.0), "cast");
-    if (haveP) {  // LP_a -= LX F_P on the second stream, beside the R/P side
-      fork();
-      CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Tm + ka, w, ka, WLP, ldw, WLP, ldw, (T)1, dstatus), "tall");
-    }
     {
-      // [R_a P_a] -= X [F_R F_P] in one pass over X
       TallSeg<T> sr{WR, ldw, WR, ldw, Tm, w, 0, ka};
       TallSeg<T> sp{WP, ldw, WP, ldw, Tm + ka, w, 0, haveP ? ka : 0};
       CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus), "tall");
     }
-    // (2) LR_a = L R_a: the one multiplication by L of the pass (Sec. III)
-    T* WLR = all ? LRslot : W2;
-    CK(spmm_lap<T>(st, g->csr, WR, ldw, WLR, ldw, ka), "spmm");
-    // (3) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too),
-    //     with [LR_a LP_a] transformed alike.  A breakdown inside the P columns is handled on
-    //     the device: the kernel keeps the R transform, zeroes P's, and clears *dP, which the
-    //     Rayleigh-Ritz step reads to solve without P.  A breakdown inside R goes to the
-    //     status word.
+    // (2) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too), into
+    //     the R and P slots.  A breakdown inside the P columns is handled on the device: the
+    //     kernel keeps the R transform, zeroes P's, and clears *dP, which the Rayleigh-Ritz
+    //     step reads to solve without P.  A residual column whose pivot falls below the
+    //     tolerance (it lies in the span of X and the R columns before it, to working
+    //     accuracy: converged columns' residuals sink to rounding noise) is dropped from this
+    //     pass's basis, and so are residual and direction columns whose norms are at rounding
+    //     level (res_floor, dir_floor); their zero columns are kept out of the Rayleigh-Ritz
+    //     solve.
     {
       const int wq = w;
       int* pf = haveP ? dP : nullptr;
       Cat3<T> Vw = haveP ? cat<T>(WR, ldw, ka, WP, ldw, ka) : cat<T>(WR, ldw, ka);
-      Cat3<T> LVw = haveP ? cat<T>(WLR, ldw, ka, WLP, ldw, ka) : cat<T>(WLR, ldw, ka);
       if (haveP)
         CK(gram_seg(WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
       else
         CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, al, wq, G, wq, TmA, dstatus, pivot_tol, dfail, ka, pf), "chol");
+      CK(chol_inv<T>(st, al, wq, G, wq, TmA, dstatus, pivot_tol, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
       CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus), "tall");
-      if (haveP) join();  // LP_a is ready
-      fork();             // LQ1 on the second stream, beside the second Gram and Cholesky
-      CK(tall_gemm<T>(st2, n, LVw, TmA, wq, wq, LQ1, 2 * kp, nullptr, 0, (T)0, dstatus), "tall");
       CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, al, wq, G, wq, TmB, dstatus, pivot_tol, dfail, ka, pf), "chol");
-      fork();  // TmB is ready for the L-images
+      CK(chol_inv<T>(st, al, wq, G, wq, TmB, dstatus, pivot_tol, dfail, ka, pf, ka, nullptr), "chol");
       // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
-      CK(tall_gemm<T>(st2, n, cat<T>(LQ1, 2 * kp, ka), TmB, wq, ka, LRslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
-      if (haveP)
-        CK(tall_gemm<T>(st2, n, cat<T>(LQ1, 2 * kp, wq), TmB + ka, wq, ka, LPslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
       CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
       if (haveP)
         CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
-      join();
+    }
+    // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken
+    //     on the orthonormalized block so that its images are products with L rather than
+    //     images carried through the Cholesky factors (in FP32 those lose accuracy as fast as
+    //     the factors grow ill-conditioned near convergence).  With every column active the
+    //     R and P slots are adjacent (R slot padding is zero) and one SpMM covers both.
+    if (haveP && all) {
+      CK(spmm_lap<T>(st, g->csr, Rslot, ld3, LRslot, ld3, kp + ka), "spmm");
+    } else {
+      CK(spmm_lap<T>(st, g->csr, Rslot, ld3, LRslot, ld3, ka), "spmm");
+      if (haveP) CK(spmm_lap<T>(st, g->csr, Pslot, ld3, LPslot, ld3, ka), "spmm");
     }
     // (4) Rayleigh-Ritz on S = [X R_a P_a]
     const bool useP = haveP;
@@ -844,6 +853,20 @@ struct LobRun : RunBase {
     std::swap(S, S2);
     std::swap(LS, LS2);
     haveP = true;
+    // Every kReorth passes X is re-orthonormalized by Cholesky-QR, LX transformed alike.  In
+    // exact arithmetic X stays orthonormal and the transform is the identity; in FP32 its
+    // departure from orthonormality grows pass by pass, and with a basis that is not
+    // orthonormal the standard Rayleigh-Ritz solve lets Ritz vectors merge.
+    if ((done_passes + 1) % kReorth == 0) {
+      CK(gram_seg(S, ld3, {{0, K}}, S, ld3, {{0, K}}, G, K, true), "gram");
+      CK(chol_inv<T>(st, al, K, G, K, Tm, dstatus, pivot_tol), "chol");
+      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus), "tall");
+      CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, T1, sizeof(T) * kp, sizeof(T) * K, n,
+                           cudaMemcpyDeviceToDevice, st), "reorth");
+      CK(cudaMemcpy2DAsync(LS, sizeof(T) * ld3, W1, sizeof(T) * kp, sizeof(T) * K, n,
+                           cudaMemcpyDeviceToDevice, st), "reorth");
+    }
     CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
     ++done_passes;
     if (++it >= o.iters) over = true;
@@ -859,8 +882,9 @@ struct LobRun : RunBase {
     if (st_final & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
     if (st_final & ST_NONFINITE) return fail(c, SC_EBREAKDOWN, "non-finite values in Rayleigh-Ritz");
     if (st_final & ST_CHOL_FAIL) return fail(c, SC_EBREAKDOWN, "residual block lost rank");
-    int fallbacks = 0;
+    int fallbacks = 0, dropped = 0;
     CK(cudaMemcpyAsync(&fallbacks, dfb, sizeof(int), cudaMemcpyDeviceToHost, st), "out");
+    CK(cudaMemcpyAsync(&dropped, ddrop, sizeof(int), cudaMemcpyDeviceToHost, st), "out");
     CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
     CK(cudaMemcpyAsync(hth.data(), theta, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "out");
     // resident block (float, n x K) for warm starts and the embedding
@@ -893,6 +917,7 @@ struct LobRun : RunBase {
       info->K = K;
       info->iters_done = done_passes;
       info->fallbacks = fallbacks;
+      info->dropped = dropped;
       info->converged = converged;
       for (int j = 0; j < K; ++j) {
         info->lambda[j] = hth[j];

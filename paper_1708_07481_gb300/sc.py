@@ -51,13 +51,15 @@ SC_REQ_COLD, SC_REQ_DELTA = 0, 1
 class EigInfo(C.Structure):
     _fields_ = [("K", C.c_int), ("iters_done", C.c_int), ("fallbacks", C.c_int),
                 ("converged", C.c_int), ("lambda_", C.c_double * SC_MAX_K),
-                ("resid", C.c_double * SC_MAX_K), ("ms", C.c_float), ("kernels", C.c_uint64)]
+                ("resid", C.c_double * SC_MAX_K), ("ms", C.c_float), ("kernels", C.c_uint64),
+                ("dropped", C.c_int)]
 
     def as_dict(self):
         K = self.K
         return dict(K=K, iters_done=self.iters_done, fallbacks=self.fallbacks,
                     converged=self.converged, lam=np.array(self.lambda_[:K]),
-                    resid=np.array(self.resid[:K]), ms=float(self.ms), kernels=int(self.kernels))
+                    resid=np.array(self.resid[:K]), ms=float(self.ms), kernels=int(self.kernels),
+                    dropped=int(self.dropped))
 
 
 _lib = None

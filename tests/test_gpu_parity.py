@@ -253,6 +253,81 @@ def test_lobpcg_soft_locking_converges(sc, ctx):
     assert resid.max() <= tol
 
 
+def test_lobpcg_fp64_far_past_convergence(sc, ctx):
+    """400 fixed FP64 passes with no locking: the columns reach roundoff long before the
+    end.  Dropped residual/direction columns keep the one-product-per-pass iteration at the
+    solution instead of letting normalized noise derail it (Sec. II.B, Sec. IV)."""
+    g = W.dcsbm(2000, 6, seed=9)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 6, iters=400, prec=2, seed=4)
+    assert info["iters_done"] == 400 and info["dropped"] > 0
+    assert np.max(np.abs(lam - ev[:6])) <= 1e-11 * ev[-1]
+    assert resid.max() <= 1e-10 * ev[-1]
+    R = O.lap_apply(L, X.astype(np.float64)) - X.astype(np.float64) * lam
+    assert np.linalg.norm(R, axis=0).max() <= 1e-6 * ev[-1]  # X returned as float32
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lobpcg_fp32_far_past_convergence(sc, ctx, prec):
+    """400 FP32 passes with no locking: residual columns sink to FP32 rounding noise within
+    about 60 passes.  The pass must stay at the solution: exact L-images of the
+    orthonormalized trial block, dropped noise columns and the periodic re-orthonormalization
+    of X keep Ritz vectors from drifting or merging."""
+    g = W.dcsbm(2000, 6, seed=9)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 6, iters=400, prec=prec, seed=4)
+    assert info["iters_done"] == 400
+    assert np.max(np.abs(lam - ev[:6])) <= 2e-5 * ev[-1]
+    assert resid.max() <= 1e-4 * ev[-1]
+    Xd = X.astype(np.float64)
+    assert np.max(np.abs(Xd.T @ Xd - np.eye(6))) <= 1e-4
+    R = O.lap_apply(L, Xd) - Xd * lam
+    assert np.linalg.norm(R, axis=0).max() <= 1e-4 * ev[-1]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lobpcg_fp32_soft_locked_long_run(sc, ctx, prec):
+    """FP32 run with a 400-pass budget and soft locking at 1e-4 lambda_max (Sec. IV): every
+    column locks once it reaches the tolerance, and the result is the converged spectrum."""
+    g = W.dcsbm(2000, 6, seed=9)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    tl = 1e-4 * ev[-1]
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 6, iters=400, tol_lock=tl, prec=prec, seed=4)
+    assert info["iters_done"] < 400
+    assert np.max(np.abs(lam - ev[:6])) <= 2e-5 * ev[-1]
+    assert resid.max() <= tl
+
+
+@pytest.mark.parametrize("m,K", [(132, 44), (264, 44), (500, 100)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_rr_solve_skips_dropped_columns(sc, ctx, m, K, prec):
+    """Zero rows of G beyond the first K (columns the Cholesky-QR dropped) take no part:
+    the K smallest eigenpairs are those of G with those rows and columns removed."""
+    rng = np.random.default_rng(m + K)
+    keep = np.ones(m, bool)
+    keep[rng.choice(np.arange(K, m), size=max(3, (m - K) // 5), replace=False)] = False
+    mk = int(keep.sum())
+    ev = np.sort(rng.uniform(0, 100, mk))
+    ev[0] = 0.0  # a zero eigenvalue: must not be confused with the dropped columns
+    Gk = _sym_with_spectrum(mk, ev, m)
+    G = np.zeros((m, m))
+    G[np.ix_(keep, keep)] = Gk
+    p = sc.SC_PREC_FP64 if prec == "fp64" else sc.SC_PREC_FP32
+    th, Y = sc.sc_rr_solve(ctx, G, K, p)
+    tol = (1e-11 if prec == "fp64" else 2e-5) * 100
+    assert np.max(np.abs(th - ev[:K])) <= tol
+    Yk = Y[keep]
+    res = np.linalg.norm(Gk @ Yk - Yk * th, axis=0)
+    assert res.max() <= (1e-9 if prec == "fp64" else 1e-3) * 100
+    np.testing.assert_allclose(Yk.T @ Yk, np.eye(K), atol=1e-9 if prec == "fp64" else 1e-4)
+
+
 def test_lobpcg_rejects_bad_sizes(sc, ctx):
     G = sc.sc_build_laplacian(ctx, 10, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
     with pytest.raises(sc.ScError) as e:
@@ -336,6 +411,27 @@ def test_partition_wide_blocks(sc, ctx, n, K):
 
 
 # ------------------------------------------------------------------ a12: streaming
+
+
+def test_stream_warm_starts_through_the_component_merge(sc, ctx):
+    """Emerging edges at n = 50,000, K = 44: stage 1 cold sets rho*; stages 2-8 run warm to
+    max residual <= rho* with soft locking at rho* (Sec. IV), across the stage where the last
+    isolated vertices join the graph."""
+    n, K = 50000, 44
+    g = W.dcsbm(n, K, seed=0)
+    deltas = W.emerging_deltas(g, 10)
+    G = sc.sc_build_laplacian(ctx, n, g.src[deltas[0]], g.dst[deltas[0]])
+    _, resid, _, _ = sc.sc_lobpcg(ctx, G, K, iters=20, seed=0, cold=1, want_X=False)
+    rho = float(resid.max())
+    for s_ in range(1, 8):
+        sc.sc_stream_update(ctx, G, n, g.src[deltas[s_]], g.dst[deltas[s_]])
+        lam, resid, _, info = sc.sc_lobpcg(ctx, G, K, iters=300, tol_abs=rho, tol_lock=rho,
+                                           seed=0, cold=0, want_X=False)
+        assert info["converged"] == 1, s_
+        assert resid.max() <= rho
+        assert np.all(np.isfinite(lam)) and np.all(np.diff(lam) >= -1e-6 * lam[-1])
+        assert lam[0] >= -1e-4 and lam[-1] <= 2 * 205
+    G.close()
 
 
 def test_stream_emerging_matches_rebuild(sc, ctx):

@@ -275,6 +275,37 @@ def test_cholqr():
     np.testing.assert_allclose(Q @ C.T, V, atol=1e-12)
 
 
+def test_cholqr_drop_keeps_independent_columns_only():
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((80, 3))
+    V = np.column_stack([A[:, 0], A[:, 1], A[:, 0] - 2.0 * A[:, 1], np.zeros(80), A[:, 2],
+                         3.0 * A[:, 2]])
+    Q, kept = O.cholqr_drop(V)
+    assert kept == [0, 1, 4]
+    np.testing.assert_allclose(Q.T @ Q, np.eye(3), atol=1e-13)
+    # every column of V lies in span(Q)
+    np.testing.assert_allclose(Q @ (Q.T @ V), V, atol=1e-12)
+    Q2, kept2 = O.cholqr_drop(A)
+    assert kept2 == [0, 1, 2]
+    Q3, _ = O.cholqr(A)
+    np.testing.assert_allclose(Q2, Q3, atol=1e-13)
+
+
+def test_lobpcg_stays_at_the_solution_far_past_convergence():
+    """400 passes, no locking: columns reach roundoff around pass 150; the direction floor
+    keeps the implicitly carried images from derailing the iteration afterwards (without it
+    this run ends with Ritz values off by O(lambda_max))."""
+    g = W.dcsbm(300, 4, seed=16)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    res = O.lobpcg(L, W.start_block(0, g.n, 4), 400)
+    assert res.iters == 400 and res.dropped > 0
+    np.testing.assert_allclose(res.lam, ev[:4], rtol=0, atol=1e-13 * ev[-1])
+    assert res.resid.max() <= 1e-13 * ev[-1]
+    R = O.lap_apply(L, res.X) - res.X * res.lam
+    assert np.linalg.norm(R, axis=0).max() <= 1e-13 * ev[-1]
+
+
 def test_soft_locking_freezes_converged_columns():
     g = W.dcsbm(400, 4, seed=15)
     L = O.laplacian_csr(g.n, g.src, g.dst)
