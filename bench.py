@@ -2,8 +2,9 @@
 
 Workload (the configuration the headline metric is quoted on): directed degree-corrected
 SBM, n = 50,000 vertices, K = 44 blocks, ~1M edges, seed 0; symmetrized Laplacian; LOBPCG
-with K = 44 vectors, 20 passes, mixed precision (FP32 blocks/SpMM, FP64 K x K Cholesky,
-FP32 Rayleigh-Ritz); unit rows; k-means++ (seed 0) + 50 Lloyd rounds.
+with K = 44 vectors, 20 passes, mixed precision (FP32 blocks and SpMM, 3xTF32 tensor-core
+Gram matrices accumulated in FP64, FP32 Cholesky and Rayleigh-Ritz); unit rows; k-means++
+(seed 0) + 50 Lloyd rounds.
 
 One step = one pass of the whole path over the graph: Laplacian build from the device-
 resident edge list, LOBPCG, embedding, k-means, labels to the host.  value = LOBPCG passes
@@ -96,10 +97,16 @@ def dist_env():
     return r, w, lr
 
 
+# DRAM bytes (read + write) per launch from one ncu --set full capture of each kernel on this
+# workload; to be cleared whenever the kernel changes after the capture.
+NCU_TRAFFIC = {"rr_eig": 216576, "spmm": 32049920, "gram": 23421952, "tall_gemm": 14492160,
+               "chol_inv": 89344}
+
+
 def algorithmic_bytes(kernel, n, K, nnz, m_rr):
     """Algorithmic bytes (or flops) per launch of the kernels on this workload."""
-    if kernel == "spmm":  # row_ptr + col_idx + deg + V read + Y write (FP32), active = all K
-        return 4 * (n + 1) + 4 * nnz + 4 * n + 8 * n * K, "hbm"
+    if kernel == "spmm":  # row_ptr + col_idx + deg + [R P] read + images write (FP32, 2K cols)
+        return 4 * (n + 1) + 4 * nnz + 4 * n + 2 * 4 * n * 2 * K, "hbm"
     if kernel == "gram":  # dominant Gram [X R P]'[LX LR LP]: both n x 3K operands read once
         return 2 * 4 * n * 3 * K, "hbm"
     if kernel == "tall_gemm":  # the update kernels: read n x 2K (or n x 3K) inputs, write n x K
@@ -244,7 +251,8 @@ def run_ours(args):
             peak = pk.get("hbm_gbs", 6800.0)
             ach = alg / avg_s / 1e9
             res["roofline"] = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": peak,
-                               "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                               "unit": "GB/s", "frac": ach / peak,
+                               "traffic": NCU_TRAFFIC.get(dominant),
                                "launches": cnt, "avg_launch_us": avg_s * 1e6,
                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
         elif alg is not None:
@@ -252,7 +260,8 @@ def run_ours(args):
             peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             ach = alg / avg_s / 1e12
             res["roofline"] = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": peak,
-                               "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                               "unit": "TFLOP/s", "frac": ach / peak,
+                               "traffic": NCU_TRAFFIC.get(dominant),
                                "launches": cnt, "avg_launch_us": avg_s * 1e6,
                                "peak_source": "derived: 152 SM x 128 FP32 FMA/clk x 2 x max clock"}
     res["cpu_baseline"] = cpu_baseline(g)

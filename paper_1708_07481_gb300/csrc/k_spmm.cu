@@ -7,6 +7,8 @@
 // 16-byte vectors.  TL is picked from the block width so idle lanes stay few.
 // HBM/L2-bound: per row, 4 bytes of index per neighbour plus k * sizeof(T) bytes of the
 // neighbour's row (served from L2 when the block fits there), and the row's own V/Y rows.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sc {
@@ -140,7 +142,14 @@ cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv
   constexpr int W = Vec<T>::W;
   if (ldv % W || ldy % W) return cudaErrorInvalidValue;
   int nvec = (k + W - 1) / W;
-  if (nvec > 32 * MAXC) return cudaErrorInvalidValue;
+  if (nvec > 32 * MAXC) {  // wider blocks: column chunks of the widest kernel shape
+    const int kc = 32 * MAXC * W;
+    for (int c0 = 0; c0 < k; c0 += kc) {
+      cudaError_t e = spmm_lap<T>(st, g, V + c0, ldv, Y + c0, ldy, std::min(kc, k - c0));
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   const T* deg;
   if constexpr (sizeof(T) == 4) deg = (const T*)g.degf;
   else deg = (const T*)g.degd;

@@ -429,7 +429,9 @@ static int lap_apply_t(sc_ctx* c, sc_graph* g, int k, const T* V, T* Y, int on_d
 }
 
 int sc_lap_apply(sc_ctx* c, sc_graph* g, int k, int prec, const void* V, void* Y, int on_device) {
-  if (!c || !g || !V || !Y || k < 1 || k > SC_MAX_K) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (!g || !V || !Y || k < 1 || k > SC_MAX_K)
+    return fail(c, SC_EINVAL, "sc_lap_apply: invalid argument (null pointer or size out of range)");
   cudaSetDevice(c->device);
   if (prec == SC_PREC_FP64) return lap_apply_t<double>(c, g, k, (const double*)V, (double*)Y, on_device);
   return lap_apply_t<float>(c, g, k, (const float*)V, (float*)Y, on_device);
@@ -939,7 +941,9 @@ RunBase* make_run(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, cudaSt
 }
 
 int check_lobpcg_args(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o) {
-  if (!c || !g || !o || K < 1 || K > SC_MAX_K || o->iters < 0) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (!g || !o || K < 1 || K > SC_MAX_K || o->iters < 0)
+    return fail(c, SC_EINVAL, "sc_lobpcg: invalid argument (null pointer or size out of range)");
   if ((int64_t)3 * K > g->csr.n) return fail(c, SC_EINVAL, "sc_lobpcg: need 3K <= n");
   if (o->prec < SC_PREC_MIXED || o->prec > SC_PREC_FP64) return fail(c, SC_EINVAL, "bad precision");
   return SC_OK;
@@ -964,7 +968,9 @@ int sc_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const floa
 // kernels -- in particular the one-CTA small dense solves -- overlap on the device.
 int sc_lobpcg_batch(sc_ctx* c, int count, sc_graph* const* graphs, const int* K,
                     const sc_lobpcg_opts* opts, sc_eig_info* infos) {
-  if (!c || count < 0 || (count > 0 && (!graphs || !K || !opts))) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (count < 0 || (count > 0 && (!graphs || !K || !opts)))
+    return fail(c, SC_EINVAL, "sc_lobpcg_batch: invalid argument (null pointer or size out of range)");
   for (int q = 0; q < count; ++q) {
     int rc = check_lobpcg_args(c, graphs[q], K[q], &opts[q]);
     if (rc != SC_OK) return rc;
@@ -1000,7 +1006,9 @@ int sc_lobpcg_batch(sc_ctx* c, int count, sc_graph* const* graphs, const int* K,
 }
 
 int sc_embed_rows(sc_ctx* c, const float* X, int32_t n, int K, float* E, int on_device) {
-  if (!c || !X || !E || n < 1 || K < 1) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (!X || !E || n < 1 || K < 1)
+    return fail(c, SC_EINVAL, "sc_embed_rows: invalid argument (null pointer or size out of range)");
   cudaSetDevice(c->device);
   Alloc al = alloc_of(c);
   const float* dx = X;
@@ -1073,7 +1081,9 @@ static int kmeans_dev(sc_ctx* c, const float* dE, int32_t n, int d, int k, int i
 int sc_kmeans(sc_ctx* c, const float* E, int32_t n, int d, int k, int iters, uint64_t seed,
               const int32_t* init_idx, int on_device, int32_t* labels_out, float* centroids_out,
               int32_t* seeds_out, double* inertia, int* iters_run) {
-  if (!c || !E || !labels_out || n < 1 || d < 1 || k < 1 || k > n || iters < 0) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (!E || !labels_out || n < 1 || d < 1 || k < 1 || k > n || iters < 0)
+    return fail(c, SC_EINVAL, "sc_kmeans: invalid argument (null pointer or size out of range)");
   cudaSetDevice(c->device);
   Alloc al = alloc_of(c);
   const float* dE = E;
@@ -1093,7 +1103,9 @@ int sc_kmeans(sc_ctx* c, const float* E, int32_t n, int d, int k, int iters, uin
 
 int sc_partition(sc_ctx* c, sc_graph* g, int K, int k, const sc_lobpcg_opts* o, int kmeans_iters,
                  int32_t* labels_out, sc_eig_info* info) {
-  if (!c || !g || !o || !labels_out || k < 1 || k > g->csr.n) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (!g || !o || !labels_out || k < 1 || k > g->csr.n)
+    return fail(c, SC_EINVAL, "sc_partition: invalid argument (null pointer or size out of range)");
   int rc = sc_lobpcg(c, g, K, o, nullptr, 0, nullptr, info);
   if (rc != SC_OK) return rc;
   Alloc al = alloc_of(c);
@@ -1228,7 +1240,9 @@ static int rr_t(sc_ctx* c, int m, int K, const double* G, double* theta, double*
 }
 
 int sc_rr_solve(sc_ctx* c, int prec, int m, int K, const double* G, double* theta, double* Y) {
-  if (!c || !G || !theta || !Y || m < 1 || K < 1 || K > m || m > 3 * SC_MAX_K) return SC_EINVAL;
+  if (!c) return SC_EINVAL;
+  if (!G || !theta || !Y || m < 1 || K < 1 || K > m || m > 3 * SC_MAX_K)
+    return fail(c, SC_EINVAL, "sc_rr_solve: invalid argument (null pointer or size out of range)");
   cudaSetDevice(c->device);
   if (prec == SC_PREC_FP64) return rr_t<double>(c, m, K, G, theta, Y);
   return rr_t<float>(c, m, K, G, theta, Y);

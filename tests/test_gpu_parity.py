@@ -88,7 +88,7 @@ def test_laplacian_long_rows_and_edge_cases(sc, ctx):
 # ------------------------------------------------------------------ a4: SpMM
 
 
-@pytest.mark.parametrize("k", [1, 3, 11, 44, 160])
+@pytest.mark.parametrize("k", [1, 3, 11, 44, 160, 300, 512])
 def test_spmm_fp32_and_fp64(sc, ctx, k):
     g = W.dcsbm(3001, 7, seed=5)
     L = O.laplacian_csr(g.n, g.src, g.dst)
@@ -227,6 +227,16 @@ def test_lobpcg_fp32_bench_size(sc, ctx):
     assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-3
 
 
+def test_lobpcg_fp64_wide_block(sc, ctx):
+    """K = 140 in FP64: the pass's SpMM covers [R P] = 280 columns, wider than one launch of
+    the SpMM kernel takes, so it runs in column chunks."""
+    g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 3000, 140, 4, prec=2)
+    lmax = 2 * L.deg.max()
+    assert info["iters_done"] == ref.iters == 4
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-10
+    np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
+
+
 def test_lobpcg_ragged_sizes(sc, ctx):
     # K = 1, K not a multiple of 4, n = 3K exactly
     for n, K in [(300, 1), (61, 7), (36, 12)]:
@@ -333,6 +343,9 @@ def test_lobpcg_rejects_bad_sizes(sc, ctx):
     with pytest.raises(sc.ScError) as e:
         sc.sc_lobpcg(ctx, G, 4, iters=1)
     assert e.value.code == sc.SC_EINVAL
+    with pytest.raises(sc.ScError) as e:
+        sc.sc_lap_apply(ctx, G, np.zeros((10, 513), np.float32))
+    assert e.value.code == sc.SC_EINVAL and "sc_lap_apply" in str(e.value)
 
 
 # ------------------------------------------------------------------ a8: embedding
