@@ -108,8 +108,9 @@ class BreakdownError(RuntimeError):
 
 
 # A Cholesky pivot below this (relative to the unit diagonal after scaling) counts as a
-# breakdown of the trial basis.
-PIVOT_TOL = 1e-14
+# breakdown of the trial basis: a column whose part orthogonal to the columns before it is
+# below 1e-5 of its norm would be normalized with its rounding error amplified 1e5-fold.
+PIVOT_TOL = 1e-10
 
 # A direction column p_j (X unit) whose norm after projection against X is at or below this
 # rounding level is left out of the pass (64 units of roundoff of float64); a residual column

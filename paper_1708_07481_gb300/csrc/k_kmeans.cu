@@ -308,44 +308,57 @@ inline AssignFn assign_for(int d, int* D) {
   return k_assign<512>;
 }
 
-// Per-CTA FP64 cluster sums over a contiguous row range, accumulated in row order (thread c
-// owns column c, thread 0 the counts).  Rows pass through shared memory in chunks of CR (the
-// labels and the d columns, loaded coalesced), so the ordered accumulation itself reads only
-// shared memory.
-constexpr int CR = 32;
+// Per-CTA FP64 cluster sums over a contiguous row range.  Rows pass through shared memory in
+// chunks of CR (the labels and the d columns, loaded coalesced).  The CTA's threads form `sub`
+// groups; group g accumulates rows g, g + sub, ... of each chunk in row order into its own
+// shared accumulator (one thread per column), and the sub accumulators are added in group
+// order at the end, so the summation order depends only on n, d and the launch shape.
+// Counts are integers (shared atomics; any order gives the same total).
+constexpr int CR = 64;
 
 __global__ void k_cent_partial(int n, int d, int k, const float* __restrict__ E, long long lde,
                                const int* __restrict__ labels, long long rows_per_cta,
-                               double* part, int* pcnt, int use_smem, const int* ctl,
+                               double* part, int* pcnt, int use_smem, int sub, const int* ctl,
                                const int* chg, int it) {
   if (ctl[0] || (it > 0 && *chg == 0)) return;  // no update this round
-  extern __shared__ double acc_sm[];  // k*d (when use_smem), then CR x d floats, CR labels
-  double* acc = use_smem ? acc_sm : part + (long long)blockIdx.x * k * d;
-  float* stg = reinterpret_cast<float*>(acc_sm + (use_smem ? (size_t)k * d : 0));
+  extern __shared__ double acc_sm[];  // sub x k*d (when use_smem), then CR x d floats, CR
+                                      // labels, k counts
+  const long long kd = (long long)k * d;
+  double* acc = use_smem ? acc_sm : part + (long long)blockIdx.x * kd;  // sub == 1 unless smem
+  float* stg = reinterpret_cast<float*>(acc_sm + (use_smem ? (size_t)sub * kd : 0));
   int* lab = reinterpret_cast<int*>(stg + CR * d);
-  int* cnt = pcnt + (long long)blockIdx.x * k;
-  for (long long q = threadIdx.x; q < (long long)k * d; q += blockDim.x) acc[q] = 0.0;
+  int* cnt = lab + CR;
+  const int gs = blockDim.x / sub, grp = threadIdx.x / gs, gt = threadIdx.x % gs;
+  double* mine = acc + grp * kd;
+  for (long long q = threadIdx.x; q < (long long)sub * kd; q += blockDim.x) acc[q] = 0.0;
   for (int j = threadIdx.x; j < k; j += blockDim.x) cnt[j] = 0;
   const long long r0 = blockIdx.x * rows_per_cta, r1 = min((long long)n, r0 + rows_per_cta);
   for (long long r = r0; r < r1; r += CR) {
     const int nr = (int)min((long long)CR, r1 - r);
     __syncthreads();  // the previous chunk has been consumed
-    for (int q = threadIdx.x; q < nr * d; q += blockDim.x)
-      stg[q] = E[(r + q / d) * lde + q % d];
+    for (int q = threadIdx.x; q < nr * d; q += blockDim.x) {
+      const int rr = q / d;
+      stg[q] = E[(r + rr) * lde + (q - rr * d)];
+    }
     for (int q = threadIdx.x; q < nr; q += blockDim.x) lab[q] = labels[r + q];
     __syncthreads();
-    for (int rr = 0; rr < nr; ++rr) {
-      const int l = lab[rr];
-      if ((unsigned)l >= (unsigned)k) continue;  // never written by an assignment: skip
-      for (int c = threadIdx.x; c < d; c += blockDim.x)
-        acc[(long long)l * d + c] += (double)stg[rr * d + c];
-      if (threadIdx.x == 0) cnt[l] += 1;
+    if (grp < sub) {
+      for (int rr = grp; rr < nr; rr += sub) {
+        const int l = lab[rr];
+        if ((unsigned)l >= (unsigned)k) continue;  // never written by an assignment: skip
+        for (int c = gt; c < d; c += gs) mine[(long long)l * d + c] += (double)stg[rr * d + c];
+        if (gt == 0) atomicAdd(&cnt[l], 1);
+      }
     }
   }
   __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) pcnt[(long long)blockIdx.x * k + j] = cnt[j];
   if (use_smem)
-    for (long long q = threadIdx.x; q < (long long)k * d; q += blockDim.x)
-      part[(long long)blockIdx.x * k * d + q] = acc[q];
+    for (long long q = threadIdx.x; q < kd; q += blockDim.x) {
+      double v = acc[q];
+      for (int g = 1; g < sub; ++g) v += acc[g * kd + q];
+      part[(long long)blockIdx.x * kd + q] = v;
+    }
 }
 
 // Centroid j = (sum of the CTA partials) / count, empty clusters kept.  Warp w of the CTA sums
@@ -503,10 +516,13 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
       e = cudaFuncSetAttribute(afn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_bytes);
       if (e != cudaSuccess) goto out;
     }
-    const size_t stg_bytes = sizeof(float) * (size_t)CR * d + sizeof(int) * CR;
-    size_t psm = sizeof(double) * (size_t)k * d;
-    int use_smem = psm + stg_bytes <= 160 * 1024;
-    psm = (use_smem ? psm : 0) + stg_bytes;
+    const size_t stg_bytes = sizeof(float) * (size_t)CR * d + sizeof(int) * ((size_t)CR + k);
+    const size_t kdb = sizeof(double) * (size_t)k * d;
+    int sub = 4;
+    while (sub > 1 && sub * kdb + stg_bytes > 160 * 1024) sub /= 2;
+    int use_smem = sub * kdb + stg_bytes <= 160 * 1024;
+    if (!use_smem) sub = 1;
+    size_t psm = (use_smem ? sub * kdb : 0) + stg_bytes;
     if (psm > 40 * 1024) {
       e = cudaFuncSetAttribute(k_cent_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)psm);
@@ -528,8 +544,9 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
       }
       // a launch that did not start leaves the labels unwritten: stop here
       if ((e = cudaGetLastError()) != cudaSuccess) goto out;
-      k_cent_partial<<<(unsigned)nct, 64, psm, st>>>(n, d, k, E, lde, labels, rpc, part, pcnt,
-                                                     use_smem, ctl, changes + it, it);
+      k_cent_partial<<<(unsigned)nct, 64 * sub, psm, st>>>(n, d, k, E, lde, labels, rpc, part,
+                                                           pcnt, use_smem, sub, ctl, changes + it,
+                                                           it);
       note_launch();
       k_cent_reduce<<<k, 256, 0, st>>>(d, k, (int)nct, part, pcnt, C64, C32, cn, ctl,
                                        changes + it, it);

@@ -536,7 +536,7 @@ struct LobRun : RunBase {
     ra = RunAlloc{c, st};
     al = Alloc{run_alloc, run_free, &ra};
     use_tc = (sizeof(T) == 4 && o.prec == SC_PREC_MIXED) ? 1 : 0;
-    pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-14;
+    pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-10;
     dir_floor = 64.0 * (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53);
     res_floor = dir_floor * 2.0 * g->csr.deg_max;
     hrho.assign(K, 0.0);
@@ -715,7 +715,8 @@ struct LobRun : RunBase {
     if (rc != SC_OK) return rc;
     if (bad) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
     CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
-    CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, false), "gram");
+    // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
+    CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, true), "gram");
     CK(rr_eig<T>(st, al, K, K, G, K, theta, Y, dstatus), "rr");
     CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus), "tall");
     CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus), "tall");
@@ -837,10 +838,11 @@ struct LobRun : RunBase {
     // (4) Rayleigh-Ritz on S = [X R_a P_a]
     const bool useP = haveP;
     const int m = K + ka + (useP ? ka : 0);
+    // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
     if (useP)
-      CK(gram_seg(S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, false), "gram");
+      CK(gram_seg(S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, true), "gram");
     else
-      CK(gram_seg(S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, false), "gram");
+      CK(gram_seg(S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, true), "gram");
     CK(rr_eig<T>(st, al, m, K, G, m, theta, Y, dstatus, useP ? dP : nullptr, ka, dfb), "rr");
     // (5) update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike); R = LX - X theta
     const T* Yrp = Y + (size_t)K * K;
