@@ -239,14 +239,16 @@ __global__ void __launch_bounds__(NTH, 1)
   }
 }
 
-// C = the sum of the chunk partials of each tile, in a fixed order.  One CTA per tile row:
-// warp w sums chunks w, w + 8, w + 16, ... (in increasing order) for 32 consecutive columns,
-// and the 8 warp sums are added in warp order.  Rows and columns past the output are skipped.
+// C = the sum of the chunk partials of each tile, in a fixed order.  One CTA per tile row and
+// one thread per column and half of the chunks: thread (j, h) sums chunks h, h + 2, h + 4, ...
+// into eight accumulators (chunk h + 2(8q + u) goes to accumulator u), so eight independent
+// loads are in flight per thread; the accumulators are added pairwise and the two halves in
+// order h = 0, 1.  Rows and columns past the output are skipped.
+static_assert(TN == 128, "the reduction maps one thread to each of 128 tile columns");
 __global__ void __launch_bounds__(256)
     k_gram_tc_reduce(const double* __restrict__ part, int nch, int ntiles, int nbt, int a, int b,
                      SegMap ma, SegMap mb, double* C, int ldc, int sym) {
-  __shared__ double ps[8][33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ double hs[TN];
   const int tile = blockIdx.x / TM, er = blockIdx.x % TM;
   const int2 tl = tile_coord(tile, nbt, sym);
   const int gi = tl.x * TM + er;
@@ -255,31 +257,31 @@ __global__ void __launch_bounds__(256)
   const int ncol = min(TN, b - tl.y * TN);
   const double* src = part + (long long)tile * TM * TN + (long long)er * TN;
   const long long cstride = (long long)ntiles * TM * TN;
-  for (int j0 = 0; j0 < ncol; j0 += 32) {
-    const int j = j0 + lane;
-    double s0 = 0.0, s1 = 0.0;
-    if (j < ncol) {
-      int c = w;
-      for (; c + 8 < nch; c += 16) {
-        s0 += src[(long long)c * cstride + j];
-        s1 += src[(long long)(c + 8) * cstride + j];
-      }
-      if (c < nch) s0 += src[(long long)c * cstride + j];
-    }
-    ps[w][lane] = s0 + s1;
-    __syncthreads();
-    if (w == 0 && j < ncol) {
-      double t = ps[0][lane];
+  const int j = threadIdx.x & (TN - 1), h = threadIdx.x >> 7;
+  double s[8];
 #pragma unroll
-      for (int q = 1; q < 8; ++q) t += ps[q][lane];
-      const int gj = tl.y * TN + j;
-      const int oj = seg_index(mb, gj);
-      if (oi >= 0 && oj >= 0) {
-        C[(long long)oi * ldc + oj] = t;
-        if (sym && tl.x != tl.y) C[(long long)oj * ldc + oi] = t;
-      }
+  for (int u = 0; u < 8; ++u) s[u] = 0.0;
+  if (j < ncol) {
+    int c = h;
+    for (; c + 14 < nch; c += 16) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[u] += src[(long long)(c + 2 * u) * cstride + j];
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c + 2 * u < nch) s[u] += src[(long long)(c + 2 * u) * cstride + j];
+  }
+  double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+  if (h == 1) hs[j] = t;
+  __syncthreads();
+  if (h == 0 && j < ncol) {
+    t += hs[j];
+    const int gj = tl.y * TN + j;
+    const int oj = seg_index(mb, gj);
+    if (oi >= 0 && oj >= 0) {
+      C[(long long)oi * ldc + oj] = t;
+      if (sym && tl.x != tl.y) C[(long long)oj * ldc + oi] = t;
+    }
   }
 }
 
