@@ -97,6 +97,23 @@ def dist_env():
     return r, w, lr
 
 
+def max_over_ranks(vals, world, device):
+    """Each value's maximum over all ranks (one all-reduce); the identity for one rank."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_step, steps, world, seconds):
+    """Units processed by all ranks (replicas, weak scaling) per second of the slowest rank."""
+    return units_per_step * steps * world / seconds
+
+
 # DRAM bytes (read + write) per launch from one ncu --set full capture of each kernel on this
 # workload; to be cleared whenever the kernel changes after the capture.
 NCU_TRAFFIC = {"rr_eig": 216576, "spmm": 32049920, "gram": 23421952, "tall_gemm": 14492160,
@@ -184,12 +201,7 @@ def run_ours(args):
         times, prof, launches = timed(True, dominant)
     e2e_times, _, _ = timed(False)
 
-    total = sum(times) / 1e3
-    e2e_total = sum(e2e_times) / 1e3
-    if world > 1:
-        t = torch.tensor([total, e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total, e2e_total = float(t[0]), float(t[1])
+    total, e2e_total = max_over_ranks([sum(times) / 1e3, sum(e2e_times) / 1e3], world, "cuda")
 
     # equal-residual comparison, FP32 (mixed) vs plain FP64, outside the timed region
     G = sc.sc_build_laplacian(ctx, N, src_d, dst_d)
@@ -208,7 +220,7 @@ def run_ours(args):
     if rank != 0:
         return None
     n_steps = args.steps * world
-    iters_per_s = ITERS * n_steps / total
+    iters_per_s = whole_job_rate(ITERS, args.steps, world, total)
     m = g.m
     res = {
         "metric": METRIC,
@@ -235,7 +247,8 @@ def run_ours(args):
         "equal_residual": {"tol": tol, "norm": "2 * max degree (Gershgorin bound on ||L||)",
                            **eq, "speedup": (eq.get("fp64", {}).get("ms", 0) / eq["mixed"]["ms"])
                            if "ms" in eq.get("mixed", {}) and "ms" in eq.get("fp64", {}) else None},
-        "e2e": {"value": ITERS * n_steps / e2e_total, "unit": "LOBPCG iters/s",
+        "e2e": {"value": whole_job_rate(ITERS, args.steps, world, e2e_total),
+                "unit": "LOBPCG iters/s",
                 "h2d_bytes_per_step": int(2 * 4 * m), "d2h_bytes_per_step": int(4 * N)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
