@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(NTH, 1)
   const int ca = tl.x * TM, cb = tl.y * TN;
   // The MMA's M side is always 128 wide; its N side is trimmed to the valid width of the
   // narrower block (rounded up to 16).  When A's side of the tile is the narrower one the
-  // tile is computed transposed (B columns as M) and written back transposed.
+  // tile is computed transposed (B columns as M); the reduction maps it back.
   const int va = min(TM, a - ca), vb = min(TN, b - cb);
   const bool swp = !sym && va < vb;
   const int nn = ((swp ? va : vb) + 15) & ~15;
@@ -221,11 +221,14 @@ __global__ void __launch_bounds__(NTH, 1)
             "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // partials are stored N-major (element (M, N) at N * TM + M), so the 32 lanes (32
+      // consecutive M) of each store write one contiguous 256-byte run
+      const int mcount = swp ? vb : va, ncount = swp ? va : vb;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int jn = cbase + 32 * h + q;  // N index
-        const int ti = swp ? jn : lrow, tj = swp ? lrow : jn;
-        if (ti < va && tj < vb) dst[(long long)ti * TN + tj] = (double)__uint_as_float(v[q]);
+        if (lrow < mcount && jn < ncount)
+          dst[(long long)jn * TM + lrow] = (double)__uint_as_float(v[q]);
       }
     }
   } else if (!last_ok && threadIdx.x == 0) {
@@ -239,45 +242,47 @@ __global__ void __launch_bounds__(NTH, 1)
   }
 }
 
-// C = the sum of the chunk partials of each tile, in a fixed order.  One CTA per tile row and
-// one thread per column and half of the chunks: thread (j, h) sums chunks h, h + 2, h + 4, ...
-// into eight accumulators (chunk h + 2(8q + u) goes to accumulator u), so eight independent
-// loads are in flight per thread; the accumulators are added pairwise and the two halves in
-// order h = 0, 1.  Rows and columns past the output are skipped.
-static_assert(TN == 128, "the reduction maps one thread to each of 128 tile columns");
+// C = the sum of the chunk partials of each tile, in a fixed order.  One CTA per N index of a
+// tile (the partials are N-major) and one thread per M index and half of the chunks: thread
+// (M, h) sums chunks h, h + 2, h + 4, ... into eight accumulators (chunk h + 2(8q + u) goes to
+// accumulator u), so eight independent loads are in flight per thread; the accumulators are
+// added pairwise and the two halves in order h = 0, 1.  Element (M, N) is tile entry (M, N),
+// or (N, M) when the kernel swapped the operand roles.  Entries past the output are skipped.
+static_assert(TM == 128 && TN == 128, "the reduction maps one thread to each of 128 M indices");
 __global__ void __launch_bounds__(256)
     k_gram_tc_reduce(const double* __restrict__ part, int nch, int ntiles, int nbt, int a, int b,
                      SegMap ma, SegMap mb, double* C, int ldc, int sym) {
-  __shared__ double hs[TN];
-  const int tile = blockIdx.x / TM, er = blockIdx.x % TM;
+  __shared__ double hs[TM];
+  const int tile = blockIdx.x / TN, jn = blockIdx.x % TN;
   const int2 tl = tile_coord(tile, nbt, sym);
-  const int gi = tl.x * TM + er;
-  if (gi >= a) return;  // uniform in the CTA
-  const int oi = seg_index(ma, gi);
-  const int ncol = min(TN, b - tl.y * TN);
-  const double* src = part + (long long)tile * TM * TN + (long long)er * TN;
+  const int ca = tl.x * TM, cb = tl.y * TN;
+  const int va = min(TM, a - ca), vb = min(TN, b - cb);
+  const bool swp = !sym && va < vb;  // the same choice as the Gram kernel
+  const int mcount = swp ? vb : va, ncount = swp ? va : vb;
+  if (jn >= ncount) return;  // uniform in the CTA
+  const int mi = threadIdx.x & (TM - 1), h = threadIdx.x >> 7;
+  const double* src = part + (long long)tile * TM * TN + (long long)jn * TM;
   const long long cstride = (long long)ntiles * TM * TN;
-  const int j = threadIdx.x & (TN - 1), h = threadIdx.x >> 7;
   double s[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) s[u] = 0.0;
-  if (j < ncol) {
+  if (mi < mcount) {
     int c = h;
     for (; c + 14 < nch; c += 16) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s[u] += src[(long long)(c + 2 * u) * cstride + j];
+      for (int u = 0; u < 8; ++u) s[u] += src[(long long)(c + 2 * u) * cstride + mi];
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      if (c + 2 * u < nch) s[u] += src[(long long)(c + 2 * u) * cstride + j];
+      if (c + 2 * u < nch) s[u] += src[(long long)(c + 2 * u) * cstride + mi];
   }
   double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-  if (h == 1) hs[j] = t;
+  if (h == 1) hs[mi] = t;
   __syncthreads();
-  if (h == 0 && j < ncol) {
-    t += hs[j];
-    const int gj = tl.y * TN + j;
-    const int oj = seg_index(mb, gj);
+  if (h == 0 && mi < mcount) {
+    t += hs[mi];
+    const int ti = swp ? jn : mi, tj = swp ? mi : jn;
+    const int oi = seg_index(ma, ca + ti), oj = seg_index(mb, cb + tj);
     if (oi >= 0 && oj >= 0) {
       C[(long long)oi * ldc + oj] = t;
       if (sym && tl.x != tl.y) C[(long long)oj * ldc + oi] = t;
@@ -347,7 +352,7 @@ cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, lon
                                                                (int)nch, nt, rpc, a, b, part,
                                                                d_status);
       note_launch();
-      k_gram_tc_reduce<<<(unsigned)(nt * TM), 256, 0, st>>>(part, (int)nch, nt, nb, a, b, ma, mb,
+      k_gram_tc_reduce<<<(unsigned)(nt * TN), 256, 0, st>>>(part, (int)nch, nt, nb, a, b, ma, mb,
                                                             C, ldc, sym ? 1 : 0);
       note_launch();
     }
