@@ -116,7 +116,12 @@ int sc_lap_apply(sc_ctx* ctx, sc_graph* g, int k, int prec, const void* V, void*
  * prec:     sc_precision.
  * seed:     seed of the Gaussian start block when one is generated.
  * cold:     1 = ignore a resident block and start cold.
- * max_iters_for_tol: when tol_abs > 0, cap on passes (SC_ENOTCONV if not reached). */
+ * precond:  sc_precond.  SC_PRECOND_NONE is the unpreconditioned iteration the paper ran
+ *           (Sec. III); SC_PRECOND_JACOBI applies T = D^-1 (rows of isolated vertices
+ *           unscaled) to the residual block before it enters the trial basis (the optional
+ *           preconditioner T of LOBPCG, Sec. II.B).  Residual norms, tolerances and locking
+ *           always refer to the unpreconditioned residual. */
+enum { SC_PRECOND_NONE = 0, SC_PRECOND_JACOBI = 1 };
 typedef struct {
   int iters;
   double tol_abs;
@@ -124,6 +129,7 @@ typedef struct {
   int prec;
   uint64_t seed;
   int cold;
+  int precond;
 } sc_lobpcg_opts;
 
 typedef struct {

@@ -220,7 +220,8 @@ class LobpcgResult:
 
 
 def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: float = 0.0,
-           keep_history: bool = False, explicit: bool = False) -> LobpcgResult:
+           keep_history: bool = False, explicit: bool = False,
+           precond: str | None = None) -> LobpcgResult:
     """Unpreconditioned block LOBPCG for the K smallest eigenpairs of L (Sec. II.B, III).
 
     Start: X = CholQR(CholQR(X0)); LX = L X; Rayleigh-Ritz on span(X).
@@ -240,6 +241,10 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
       With Y = [Y_X; Y_R; Y_P]: P = R_a Y_R + P_a Y_P, X = X Y_X + P (LX, LP alike).
       A breakdown of the Cholesky of P's Gram (P inside span{X, R}) or of the trial basis
       drops P for that pass; a breakdown without P is raised.
+    ``precond="jacobi"`` applies the preconditioner T = D^-1 (rows of isolated vertices
+    unscaled) to R_a before the projection: the trial basis is [X, T R_a, P_a] (the optional T
+    of preconditioned LOBPCG, Sec. II.B); the rounding floor for R_a is divided by max d.
+    Residual norms, the tolerance and locking refer to the unpreconditioned R.
     One multiplication by L per pass (Sec. III): LP and LX are carried along implicitly.
     ``explicit=True`` recomputes LX, LR_a and LP_a as products with L instead -- the same
     iteration in exact arithmetic, stable when a direction column sinks to rounding level
@@ -267,7 +272,15 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
     fallbacks = 0
     dropped = 0
     done = 0
-    res_floor = DIR_FLOOR * 2.0 * float(np.max(L.deg, initial=0.0))
+    dmax = float(np.max(L.deg, initial=0.0))
+    res_floor = DIR_FLOOR * 2.0 * dmax
+    if precond not in (None, "jacobi"):
+        raise ValueError(precond)
+    tinv = None
+    if precond == "jacobi":
+        tinv = np.where(L.deg > 0, L.deg, 1.0)
+        if dmax > 0:
+            res_floor /= dmax
     for _ in range(iters):
         R = LX - X * lam[None, :]
         rho = np.linalg.norm(R, axis=0)
@@ -277,6 +290,8 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
         if not act.any() or rho.max() <= tol_abs:
             break
         Ra = R[:, act]
+        if tinv is not None:
+            Ra = Ra / tinv[:, None]
         Ra = Ra - X @ (X.T @ Ra)
         # a residual at the rounding floor cannot improve its Ritz pair: leave it out (this
         # soft-locks the pair at the accuracy the arithmetic allows)
@@ -431,9 +446,10 @@ def kmeans(E: np.ndarray, k: int, u: np.ndarray, iters: int = 50, init_idx=None)
 
 
 def partition(L: Csr, X0: np.ndarray, k: int, u: np.ndarray, iters: int = 20,
-              kmeans_iters: int = 50, tol_abs: float = 0.0, tol_lock: float = 0.0):
+              kmeans_iters: int = 50, tol_abs: float = 0.0, tol_lock: float = 0.0,
+              precond: str | None = None):
     """Spectral partition: LOBPCG block -> unit rows -> k-means (Sec. II.A)."""
-    res = lobpcg(L, X0, iters, tol_abs=tol_abs, tol_lock=tol_lock)
+    res = lobpcg(L, X0, iters, tol_abs=tol_abs, tol_lock=tol_lock, precond=precond)
     E = embed_rows(res.X)
     labels, C, idx, inertia = kmeans(E, k, u, kmeans_iters)
     return labels, res, E, idx

@@ -159,10 +159,13 @@ cudaError_t tall_gemm2(cudaStream_t st, long long n, const Cat3<T>& A, const Tal
                        const TallSeg<T>& s1, T beta, int* d_status = nullptr);
 
 
-// Residual: R = LX - X diag(theta); rho2[j] = sum_i R_ij^2 (FP64).  Workspace from `al`.
+// Residual: R = LX - X diag(theta); rho2[j] = sum_i R_ij^2 (FP64).  With deg non-null the
+// block stored is D^-1 R (rows with d_i = 0 unscaled: the Jacobi preconditioner), while rho2
+// stays the norms of R.  Workspace from `al`.
 template <typename T>
 cudaError_t residual(cudaStream_t st, Alloc& al, long long n, int K, const T* X, const T* LX,
-                     long long ld, const double* theta, T* R, double* rho2);
+                     long long ld, const double* theta, T* R, double* rho2,
+                     const T* deg = nullptr);
 
 // Gather / scatter of a column subset (cols[j] -> j).
 template <typename T>

@@ -383,11 +383,18 @@ __global__ void __launch_bounds__(16 * NCG)
 // below the rounding of R itself), the row groups of a CTA and the CTA partials are added in
 // FP64 in fixed orders; the last CTA to finish (ticket) sums the partials with 8 warps
 // (warp w takes partials w, w + 8, ...) and adds the 8 warp sums in warp order.
+// Jacobi preconditioner entry: r / d, or r itself for an isolated vertex (d = 0).
+template <typename T>
+__device__ __forceinline__ T jacobi(T r, T d) {
+  return d > (T)0 ? r / d : r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_residual(long long n, int K, const T* __restrict__ X, const T* __restrict__ LX,
                long long ld, const double* __restrict__ theta, T* __restrict__ R,
-               long long rows_per_cta, double* part, int* ticket, double* rho2) {
+               long long rows_per_cta, double* part, int* ticket, double* rho2,
+               const T* __restrict__ deg) {
   extern __shared__ double sred[];  // [rp][kc], reused as [8][K] by the last CTA
   __shared__ int last;
   const int kc = K < 256 ? K : 256;
@@ -405,14 +412,14 @@ __global__ void __launch_bounds__(256)
       for (; r + rp < r1; r += 2 * rp) {
         const T v0 = LX[r * ld + j] - X[r * ld + j] * th;
         const T v1 = LX[(r + rp) * ld + j] - X[(r + rp) * ld + j] * th;
-        R[r * ld + j] = v0;
-        R[(r + rp) * ld + j] = v1;
+        R[r * ld + j] = deg ? jacobi(v0, deg[r]) : v0;
+        R[(r + rp) * ld + j] = deg ? jacobi(v1, deg[r + rp]) : v1;
         s0 = fma(v0, v0, s0);
         s1 = fma(v1, v1, s1);
       }
       if (r < r1) {
         const T v0 = LX[r * ld + j] - X[r * ld + j] * th;
-        R[r * ld + j] = v0;
+        R[r * ld + j] = deg ? jacobi(v0, deg[r]) : v0;
         s0 = fma(v0, v0, s0);
       }
     }
@@ -667,7 +674,7 @@ cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W
 
 template <typename T>
 cudaError_t residual(cudaStream_t st, Alloc& al, long long n, int K, const T* X, const T* LX,
-                     long long ld, const double* theta, T* R, double* rho2) {
+                     long long ld, const double* theta, T* R, double* rho2, const T* deg) {
   long long nct = cap_grid((n + 255) / 256, 152 * 2);
   long long rpc = (n + nct - 1) / nct;
   if (rpc < 1) rpc = 1;
@@ -686,7 +693,7 @@ cudaError_t residual(cudaStream_t st, Alloc& al, long long n, int K, const T* X,
   size_t sm = sizeof(double) * std::max<size_t>((size_t)rp * kc, 8 * 32);
   ProfScope ps(st, "residual");
   k_residual<T><<<(unsigned)nct, 256, sm, st>>>(n, K, X, LX, ld, theta, R, rpc, part, ticket,
-                                                 rho2);
+                                                 rho2, deg);
   note_launch();
   cudaError_t e = cudaGetLastError();
   al.put(part);
@@ -745,7 +752,7 @@ cudaError_t cast_mat(cudaStream_t st, int rows, int cols, const double* src, int
   template cudaError_t tall_gemm2<T>(cudaStream_t, long long, const Cat3<T>&,                \
                                      const TallSeg<T>&, const TallSeg<T>&, T, int*);         \
   template cudaError_t residual<T>(cudaStream_t, Alloc&, long long, int, const T*, const T*, \
-                                   long long, const double*, T*, double*);                   \
+                                   long long, const double*, T*, double*, const T*);         \
   template cudaError_t gather_cols<T>(cudaStream_t, long long, const T*, long long, T*,      \
                                       long long, const int*, int);                           \
   template cudaError_t rownorm<T>(cudaStream_t, long long, int, const T*, long long, float*, \

@@ -511,6 +511,7 @@ struct LobRun : RunBase {
   // norm (X unit) has sunk to dir_floor carries no step, only rounding noise: it is left out
   // too.
   double res_floor, dir_floor;
+  const T* pdeg = nullptr;  // degrees for the Jacobi preconditioner, or null
   static constexpr int kReorth = 16;
   std::vector<void*> bufs;
   T *S = nullptr, *LS = nullptr, *S2 = nullptr, *LS2 = nullptr, *T1 = nullptr, *W1 = nullptr,
@@ -539,6 +540,12 @@ struct LobRun : RunBase {
     pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-10;
     dir_floor = 64.0 * (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53);
     res_floor = dir_floor * 2.0 * g->csr.deg_max;
+    if (o.precond == SC_PRECOND_JACOBI) {
+      // the residual slot holds D^-1 R: a column with ||r|| above the floor keeps
+      // ||D^-1 r|| >= ||r|| / max_i d_i above res_floor / max_i d_i
+      pdeg = sizeof(T) == 4 ? (const T*)g->csr.degf : (const T*)g->csr.degd;
+      if (g->csr.deg_max > 0) res_floor /= g->csr.deg_max;
+    }
     hrho.assign(K, 0.0);
     hth.assign(K, 0.0);
   }
@@ -722,7 +729,7 @@ struct LobRun : RunBase {
     CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus), "tall");
     std::swap(S, S2);
     std::swap(LS, LS2);
-    CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
+    CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2, pdeg), "residual");
     it = 0;
     over = o.iters <= 0;
     return SC_OK;
@@ -871,7 +878,7 @@ struct LobRun : RunBase {
       CK(cudaMemcpy2DAsync(LS, sizeof(T) * ld3, W1, sizeof(T) * kp, sizeof(T) * K, n,
                            cudaMemcpyDeviceToDevice, st), "reorth");
     }
-    CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2), "residual");
+    CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2, pdeg), "residual");
     ++done_passes;
     if (++it >= o.iters) over = true;
     return SC_OK;
@@ -948,6 +955,8 @@ int check_lobpcg_args(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o) {
     return fail(c, SC_EINVAL, "sc_lobpcg: invalid argument (null pointer or size out of range)");
   if ((int64_t)3 * K > g->csr.n) return fail(c, SC_EINVAL, "sc_lobpcg: need 3K <= n");
   if (o->prec < SC_PREC_MIXED || o->prec > SC_PREC_FP64) return fail(c, SC_EINVAL, "bad precision");
+  if (o->precond != SC_PRECOND_NONE && o->precond != SC_PRECOND_JACOBI)
+    return fail(c, SC_EINVAL, "sc_lobpcg: unknown preconditioner");
   return SC_OK;
 }
 
@@ -1392,7 +1401,8 @@ static int srv_start(sc_server* s, SrvSlot& sl) {
                           sl.req.dst.data(), nullptr, 0);
     if (rc != SC_OK) return rc;
   }
-  sc_lobpcg_opts o{r.iters, r.tol_abs, 0.0, r.prec, r.seed, r.kind == SC_REQ_COLD ? 1 : 0};
+  sc_lobpcg_opts o{r.iters, r.tol_abs, 0.0, r.prec, r.seed, r.kind == SC_REQ_COLD ? 1 : 0,
+                   SC_PRECOND_NONE};
   rc = check_lobpcg_args(c, sl.g, r.K, &o);
   if (rc != SC_OK) return rc;
   if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess)

@@ -35,7 +35,10 @@ class ScError(RuntimeError):
 
 class LobpcgOpts(C.Structure):
     _fields_ = [("iters", C.c_int), ("tol_abs", C.c_double), ("tol_lock", C.c_double),
-                ("prec", C.c_int), ("seed", C.c_uint64), ("cold", C.c_int)]
+                ("prec", C.c_int), ("seed", C.c_uint64), ("cold", C.c_int), ("precond", C.c_int)]
+
+
+SC_PRECOND_NONE, SC_PRECOND_JACOBI = 0, 1
 
 
 class Request(C.Structure):
@@ -260,8 +263,8 @@ def sc_lap_apply(ctx: Ctx, g: Graph, V, prec=SC_PREC_FP32):
 
 
 def sc_lobpcg(ctx: Ctx, g: Graph, K, iters=20, tol_abs=0.0, tol_lock=0.0, prec=SC_PREC_MIXED,
-              seed=0, cold=0, X0=None, x0_rows=0, want_X=True):
-    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold)
+              seed=0, cold=0, X0=None, x0_rows=0, want_X=True, precond=SC_PRECOND_NONE):
+    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold, precond)
     info = EigInfo()
     n = sc_graph_info(g)[0]
     X = np.empty((n, K), np.float32) if want_X else None
@@ -304,8 +307,8 @@ def sc_kmeans(ctx: Ctx, E, k, iters=50, seed=0, init_idx=None):
 
 
 def sc_partition(ctx: Ctx, g: Graph, K, k, iters=20, kmeans_iters=50, prec=SC_PREC_MIXED,
-                 seed=0, tol_abs=0.0, tol_lock=0.0, cold=1):
-    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold)
+                 seed=0, tol_abs=0.0, tol_lock=0.0, cold=1, precond=SC_PRECOND_NONE):
+    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold, precond)
     info = EigInfo()
     n = sc_graph_info(g)[0]
     labels = np.empty(n, np.int32)
@@ -349,7 +352,7 @@ def sc_lobpcg_batch(ctx: Ctx, graphs, K, iters=20, tol_abs=0.0, prec=SC_PREC_MIX
     Ks = (C.c_int * cnt)(*([K] * cnt if isinstance(K, int) else K))
     hs = (C.c_void_p * cnt)(*[g.h.value for g in graphs])
     seeds = seeds or [0] * cnt
-    opts = (LobpcgOpts * cnt)(*[LobpcgOpts(iters, tol_abs, 0.0, prec, s, cold) for s in seeds])
+    opts = (LobpcgOpts * cnt)(*[LobpcgOpts(iters, tol_abs, 0.0, prec, s, cold, 0) for s in seeds])
     infos = (EigInfo * cnt)()
     ctx.check(lib().sc_lobpcg_batch(ctx.h, cnt, hs, Ks, opts, infos))
     return [infos[q].as_dict() for q in range(cnt)]
@@ -364,7 +367,7 @@ def sc_partition_batch(ctx: Ctx, graphs, K, k, iters=20, kmeans_iters=50, prec=S
     outs = [np.empty(sc_graph_info(g)[0], np.int32) for g in graphs]
     lp = (C.c_void_p * cnt)(*[o.ctypes.data for o in outs])
     hs = (C.c_void_p * cnt)(*[g.h.value for g in graphs])
-    opts = (LobpcgOpts * cnt)(*[LobpcgOpts(iters, 0.0, 0.0, prec, s, 1) for s in seeds])
+    opts = (LobpcgOpts * cnt)(*[LobpcgOpts(iters, 0.0, 0.0, prec, s, 1, 0) for s in seeds])
     infos = (EigInfo * cnt)()
     ctx.check(lib().sc_partition_batch(ctx.h, cnt, hs, (C.c_int * cnt)(*Kl), (C.c_int * cnt)(*kl),
                                        opts, kmeans_iters, lp, infos))

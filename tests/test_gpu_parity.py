@@ -237,6 +237,38 @@ def test_lobpcg_fp64_wide_block(sc, ctx):
     np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_lobpcg_jacobi_matches_oracle(sc, ctx, prec):
+    """The Jacobi-preconditioned iteration (T = D^-1 on the residual block, Sec. II.B) against
+    the oracle's, 20 passes from the same start block."""
+    g = W.dcsbm(3000, 11, seed=23)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    X0 = W.start_block(5, g.n, 11)
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 11, iters=20, prec=prec, X0=X0,
+                                       precond=sc.SC_PRECOND_JACOBI)
+    ref = O.lobpcg(L, X0.astype(np.float32).astype(np.float64), 20, precond="jacobi")
+    lmax = 2 * L.deg.max()
+    tol = 1e-10 if prec == 2 else 1e-5
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= tol
+    assert O.sin_theta(ref.X, X.astype(np.float64)) <= (1e-6 if prec == 2 else 1e-3)
+    np.testing.assert_allclose(resid, ref.resid, rtol=1e-3 if prec != 2 else 1e-6,
+                               atol=(1e-10 if prec == 2 else 1e-5) * lmax)
+
+
+def test_lobpcg_jacobi_reaches_tolerance_in_fewer_passes(sc, ctx):
+    g = W.dcsbm(20000, 22, seed=24)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    tol = 1e-3 * 2 * sc.sc_graph_info(G)[2]
+    runs = {}
+    for pc in (sc.SC_PRECOND_NONE, sc.SC_PRECOND_JACOBI):
+        _, resid, _, info = sc.sc_lobpcg(ctx, G, 22, iters=400, tol_abs=tol, seed=6, cold=1,
+                                         want_X=False, precond=pc)
+        assert info["converged"] == 1 and resid.max() <= tol
+        runs[pc] = info["iters_done"]
+    assert runs[sc.SC_PRECOND_JACOBI] * 2 <= runs[sc.SC_PRECOND_NONE], runs
+
+
 def test_lobpcg_ragged_sizes(sc, ctx):
     # K = 1, K not a multiple of 4, n = 3K exactly
     for n, K in [(300, 1), (61, 7), (36, 12)]:
@@ -346,6 +378,10 @@ def test_lobpcg_rejects_bad_sizes(sc, ctx):
     with pytest.raises(sc.ScError) as e:
         sc.sc_lap_apply(ctx, G, np.zeros((10, 513), np.float32))
     assert e.value.code == sc.SC_EINVAL and "sc_lap_apply" in str(e.value)
+    G2 = sc.sc_build_laplacian(ctx, 30, np.arange(29, dtype=np.int32), np.arange(1, 30, dtype=np.int32))
+    with pytest.raises(sc.ScError) as e:
+        sc.sc_lobpcg(ctx, G2, 4, iters=1, precond=7)
+    assert e.value.code == sc.SC_EINVAL and "preconditioner" in str(e.value)
 
 
 # ------------------------------------------------------------------ a8: embedding

@@ -306,6 +306,58 @@ def test_lobpcg_stays_at_the_solution_far_past_convergence():
     assert np.linalg.norm(R, axis=0).max() <= 1e-13 * ev[-1]
 
 
+def test_jacobi_first_pass_is_rayleigh_ritz_on_x_and_dinv_r():
+    """Pass 1 with precond="jacobi" is Rayleigh-Ritz on span{X, D^-1 R} (T = D^-1), built here
+    directly: orthonormal basis by a dense QR, then eigh of the projected L."""
+    g = W.dcsbm(400, 5, seed=22)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    Ld = O.laplacian_dense(L)
+    K = 5
+    X0 = W.start_block(3, g.n, K)
+    Q0, _ = np.linalg.qr(X0)
+    w0, V0 = np.linalg.eigh(Q0.T @ Ld @ Q0)
+    X = Q0 @ V0
+    R = Ld @ X - X * w0
+    B, _ = np.linalg.qr(np.concatenate([X, R / L.deg[:, None]], axis=1))
+    want = np.linalg.eigvalsh(B.T @ Ld @ B)[:K]
+    res = O.lobpcg(L, X0, 1, precond="jacobi")
+    np.testing.assert_allclose(res.lam, want, rtol=0, atol=1e-10 * 2 * L.deg.max())
+    other = O.lobpcg(L, X0, 1)  # T = I gives a different first pass
+    assert np.max(np.abs(other.lam - want)) > 1e-6
+
+
+def test_jacobi_preconditioned_lobpcg_converges_faster_to_dense_eigenpairs():
+    g = W.dcsbm(1500, 6, seed=21)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev, V = np.linalg.eigh(O.laplacian_dense(L))
+    X0 = W.start_block(0, g.n, 6)
+    pre = O.lobpcg(L, X0, 25, precond="jacobi")
+    plain = O.lobpcg(L, X0, 25)
+    err_pre = np.max(np.abs(pre.lam - ev[:6])) / ev[-1]
+    err_plain = np.max(np.abs(plain.lam - ev[:6])) / ev[-1]
+    assert err_pre <= 1e-7 and err_pre < 1e-3 * err_plain
+    full = O.lobpcg(L, X0, 80, precond="jacobi")
+    np.testing.assert_allclose(full.lam, ev[:6], rtol=0, atol=1e-12 * ev[-1])
+    assert O.sin_theta(V[:, :6], full.X) <= 1e-8
+
+
+def test_jacobi_leaves_isolated_vertices_unscaled():
+    # two triangles and two isolated vertices: D has zeros, the preconditioned run still
+    # reaches the dense eigenpairs (zero eigenvalue of multiplicity 4)
+    src = np.array([0, 1, 2, 3, 4, 5], np.int64)
+    dst = np.array([1, 2, 0, 4, 5, 3], np.int64)
+    n = 12
+    rng = np.random.default_rng(7)
+    extra_s = rng.integers(6, 10, 12)
+    extra_d = rng.integers(6, 10, 12)
+    L = O.laplacian_csr(n, np.concatenate([src, extra_s]), np.concatenate([dst, extra_d]))
+    assert np.sum(L.deg == 0) == 2
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    res = O.lobpcg(L, W.start_block(1, n, 4), 30, precond="jacobi")
+    assert np.all(np.isfinite(res.lam))
+    np.testing.assert_allclose(res.lam, ev[:4], rtol=0, atol=1e-10 * max(ev[-1], 1.0))
+
+
 def test_soft_locking_freezes_converged_columns():
     g = W.dcsbm(400, 4, seed=15)
     L = O.laplacian_csr(g.n, g.src, g.dst)
