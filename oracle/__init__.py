@@ -13,6 +13,8 @@ from .spectral import (  # noqa: F401
     LobpcgResult,
     cholqr,
     cholqr_drop,
+    cpqr_assign,
+    cpqr_pivots,
     embed_rows,
     kmeans,
     kmeanspp_seed,

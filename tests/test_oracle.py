@@ -475,3 +475,30 @@ def test_planted_partition_fully_recovered():
     L = O.laplacian_csr(g.n, g.src, g.dst)
     labels, res, E, idx = O.partition(L, W.start_block(0, g.n, 4), 4, W.kmeans_uniforms(0, 4), 20, 50)
     assert O.partition_metrics(g.truth, labels) == (1.0, 1.0, 1.0)
+
+
+# ---------------------------------------------------------------- CPQR assignment (Sec. II.A)
+
+
+def test_cpqr_pivots_match_lapack_on_generic_input():
+    import scipy.linalg as sla2
+
+    Y = np.random.default_rng(31).standard_normal((300, 9))
+    piv = O.cpqr_pivots(Y, 9)
+    _, _, P = sla2.qr(Y.T, pivoting=True, mode="economic")
+    assert piv == [int(p) for p in P[:9]]
+
+
+def test_cpqr_recovers_planted_blocks_and_ignores_column_signs():
+    rng = np.random.default_rng(32)
+    k, n = 5, 400
+    truth = rng.integers(0, k, n)
+    basis, _ = np.linalg.qr(rng.standard_normal((k, k)))  # any rotation of the indicators
+    Y = np.eye(k)[truth] @ basis + 0.05 * rng.standard_normal((n, k))
+    labels, piv = O.cpqr_assign(Y, k)
+    assert len(set(truth[piv])) == k  # one pivot per block
+    pm, _, _ = O.partition_metrics(truth, labels)
+    assert pm == 1.0
+    D = np.diag([1.0, -1.0, 1.0, -1.0, -1.0])
+    labels2, piv2 = O.cpqr_assign(Y @ D, k)
+    assert piv2 == piv and np.array_equal(labels2, labels)
