@@ -184,6 +184,19 @@ int sc_lobpcg_batch(sc_ctx* ctx, int count, sc_graph* const* graphs, const int* 
 int sc_partition(sc_ctx* ctx, sc_graph* g, int K, int k, const sc_lobpcg_opts* opts,
                  int kmeans_iters, int32_t* labels_out, sc_eig_info* info);
 
+/* sc_cpqr_assign: cluster labels from an eigenvector block by QR with column pivoting, the
+ * assignment the paper names beside k-means++ (Sec. II.A; Damle, Minden & Ying, arXiv
+ * 1609.08251).  The K pivot rows of Y are chosen greedily (the row of the current residual
+ * with the largest norm, lowest index on ties, then every residual row is projected off its
+ * direction); Q is the polar factor of C = Y'[:, pivots]; label_i = argmax_j |(Y Q)_ij|
+ * (lowest j on ties).  One cluster per column: k = K.  Arithmetic in FP64.
+ * Y: n x K FP32 row-major, on the device when on_device = 1, else host (copied).
+ * labels_out: n int32 (host).  pivots_out: K int32 (host) or NULL.
+ * Errors: SC_EINVAL (null pointer, K < 1, K > n or K > SC_MAX_K), SC_ENOMEM, SC_ECUDA,
+ * SC_EBREAKDOWN (non-finite polar factor). */
+int sc_cpqr_assign(sc_ctx* ctx, const float* Y, int32_t n, int K, int on_device,
+                   int32_t* labels_out, int32_t* pivots_out);
+
 /* sc_partition_batch: sc_partition over `count` graphs with batched LOBPCG (labels_out[q]
  * has n_q entries; host). */
 int sc_partition_batch(sc_ctx* ctx, int count, sc_graph* const* graphs, const int* K,

@@ -483,8 +483,8 @@ def cpqr_pivots(Y: np.ndarray, k: int) -> list:
         j = int(np.argmax(norms))
         piv.append(j)
         nj = np.sqrt(norms[j])
-        if nj == 0.0:
-            break
+        if nj == 0.0:  # the remaining columns are zero: nothing left to project off
+            continue
         q = A[:, j] / nj
         A -= np.outer(q, q @ A)
     return piv

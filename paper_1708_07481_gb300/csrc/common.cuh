@@ -207,6 +207,12 @@ cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, in
                    double* theta, T* Y, int* d_status, int* pflag = nullptr, int mP = 0,
                    int* nfallback = nullptr);
 
+// Cluster assignment by QR with column pivoting (FP64): piv (K, device) = the pivot rows of
+// Y (n x K FP32, stride ldy), labels (n, device) = argmax_j |(Y Q)_ij| with Q the polar factor
+// of Y'[:, piv].
+cudaError_t cpqr_assign(cudaStream_t st, Alloc& al, long long n, int K, const float* Y,
+                        long long ldy, int* piv, int* labels, int* d_status);
+
 // k-means.
 cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
                      long long lde, const double* u_host, int* seeds_dev);

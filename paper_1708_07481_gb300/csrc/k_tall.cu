@@ -389,7 +389,7 @@ __device__ __forceinline__ T jacobi(T r, T d) {
   return d > (T)0 ? r / d : r;
 }
 
-template <typename T>
+template <typename T, bool PRE>
 __global__ void __launch_bounds__(256)
     k_residual(long long n, int K, const T* __restrict__ X, const T* __restrict__ LX,
                long long ld, const double* __restrict__ theta, T* __restrict__ R,
@@ -412,14 +412,14 @@ __global__ void __launch_bounds__(256)
       for (; r + rp < r1; r += 2 * rp) {
         const T v0 = LX[r * ld + j] - X[r * ld + j] * th;
         const T v1 = LX[(r + rp) * ld + j] - X[(r + rp) * ld + j] * th;
-        R[r * ld + j] = deg ? jacobi(v0, deg[r]) : v0;
-        R[(r + rp) * ld + j] = deg ? jacobi(v1, deg[r + rp]) : v1;
+        R[r * ld + j] = PRE ? jacobi(v0, deg[r]) : v0;
+        R[(r + rp) * ld + j] = PRE ? jacobi(v1, deg[r + rp]) : v1;
         s0 = fma(v0, v0, s0);
         s1 = fma(v1, v1, s1);
       }
       if (r < r1) {
         const T v0 = LX[r * ld + j] - X[r * ld + j] * th;
-        R[r * ld + j] = deg ? jacobi(v0, deg[r]) : v0;
+        R[r * ld + j] = PRE ? jacobi(v0, deg[r]) : v0;
         s0 = fma(v0, v0, s0);
       }
     }
@@ -692,8 +692,12 @@ cudaError_t residual(cudaStream_t st, Alloc& al, long long n, int K, const T* X,
   int rp = 256 / kc;
   size_t sm = sizeof(double) * std::max<size_t>((size_t)rp * kc, 8 * 32);
   ProfScope ps(st, "residual");
-  k_residual<T><<<(unsigned)nct, 256, sm, st>>>(n, K, X, LX, ld, theta, R, rpc, part, ticket,
-                                                 rho2, deg);
+  if (deg)
+    k_residual<T, true><<<(unsigned)nct, 256, sm, st>>>(n, K, X, LX, ld, theta, R, rpc, part,
+                                                        ticket, rho2, deg);
+  else
+    k_residual<T, false><<<(unsigned)nct, 256, sm, st>>>(n, K, X, LX, ld, theta, R, rpc, part,
+                                                         ticket, rho2, deg);
   note_launch();
   cudaError_t e = cudaGetLastError();
   al.put(part);

@@ -1112,6 +1112,52 @@ int sc_kmeans(sc_ctx* c, const float* E, int32_t n, int d, int k, int iters, uin
   return rc;
 }
 
+int sc_cpqr_assign(sc_ctx* c, const float* Y, int32_t n, int K, int on_device,
+                   int32_t* labels_out, int32_t* pivots_out) {
+  if (!c) return SC_EINVAL;
+  if (!Y || !labels_out || n < 1 || K < 1 || K > n || K > SC_MAX_K)
+    return fail(c, SC_EINVAL, "sc_cpqr_assign: invalid argument (null pointer or size out of range)");
+  cudaSetDevice(c->device);
+  Alloc al = alloc_of(c);
+  const float* dY = Y;
+  float* tY = nullptr;
+  int* dl = al.get<int>((size_t)n);
+  int* dp = al.get<int>((size_t)K);
+  if (!dl || !dp) {
+    al.put(dl);
+    al.put(dp);
+    return fail(c, SC_ENOMEM, "sc_cpqr_assign");
+  }
+  if (!on_device) {
+    tY = al.get<float>((size_t)n * K);
+    if (!tY) {
+      al.put(dl);
+      al.put(dp);
+      return fail(c, SC_ENOMEM, "sc_cpqr_assign");
+    }
+    CK(cudaMemcpyAsync(tY, Y, sizeof(float) * (size_t)n * K, cudaMemcpyHostToDevice, c->stream), "cpqr");
+    dY = tY;
+  }
+  int rc = SC_OK;
+  cudaError_t e = cpqr_assign(c->stream, al, n, K, dY, K, dp, dl, c->d_status);
+  if (e != cudaSuccess) rc = fail(c, SC_ECUDA, std::string("cpqr: ") + cudaGetErrorString(e));
+  if (rc == SC_OK) {
+    CK(cudaMemcpyAsync(labels_out, dl, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, c->stream), "cpqr");
+    if (pivots_out)
+      CK(cudaMemcpyAsync(pivots_out, dp, sizeof(int) * (size_t)K, cudaMemcpyDeviceToHost, c->stream), "cpqr");
+    CK(cudaStreamSynchronize(c->stream), "cpqr");
+    int hs = 0;
+    rc = read_status(c, &hs);
+    if (rc == SC_OK && (hs & ST_NONFINITE)) rc = fail(c, SC_EBREAKDOWN, "cpqr: non-finite polar factor");
+  } else {
+    cudaStreamSynchronize(c->stream);
+  }
+  al.put(tY);
+  al.put(dl);
+  al.put(dp);
+  return rc;
+}
+
 int sc_partition(sc_ctx* c, sc_graph* g, int K, int k, const sc_lobpcg_opts* o, int kmeans_iters,
                  int32_t* labels_out, sc_eig_info* info) {
   if (!c) return SC_EINVAL;

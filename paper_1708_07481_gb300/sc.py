@@ -95,6 +95,7 @@ def lib():
         "sc_embed_rows": ([vp, vp, i32, C.c_int, vp, C.c_int], C.c_int),
         "sc_kmeans": ([vp, vp, i32, C.c_int, C.c_int, C.c_int, u64, vp, C.c_int, vp, vp, vp,
                        C.POINTER(dbl), C.POINTER(C.c_int)], C.c_int),
+        "sc_cpqr_assign": ([vp, vp, i32, C.c_int, C.c_int, vp, vp], C.c_int),
         "sc_partition": ([vp, vp, C.c_int, C.c_int, C.POINTER(LobpcgOpts), C.c_int, vp,
                           C.POINTER(EigInfo)], C.c_int),
         "sc_stream_update": ([vp, vp, i32, i64, vp, vp, vp, C.c_int], C.c_int),
@@ -304,6 +305,17 @@ def sc_kmeans(ctx: Ctx, E, k, iters=50, seed=0, init_idx=None):
     ctx.check(lib().sc_kmeans(ctx.h, pe, n, d, k, iters, seed, _ptr(init)[0], dev, _ptr(labels)[0],
                               _ptr(cent)[0], _ptr(seeds)[0], C.byref(inertia), C.byref(ran)))
     return labels, cent, seeds, inertia.value, ran.value
+
+
+def sc_cpqr_assign(ctx: Ctx, Y):
+    """Labels and pivot rows of the eigenvector block Y (n x K) by QR with column pivoting."""
+    Y = _np(Y, np.float32)
+    n, K = int(Y.shape[0]), int(Y.shape[1])
+    labels = np.empty(n, np.int32)
+    piv = np.empty(K, np.int32)
+    py, dev = _ptr(Y)
+    ctx.check(lib().sc_cpqr_assign(ctx.h, py, n, K, dev, _ptr(labels)[0], _ptr(piv)[0]))
+    return labels, piv
 
 
 def sc_partition(ctx: Ctx, g: Graph, K, k, iters=20, kmeans_iters=50, prec=SC_PREC_MIXED,

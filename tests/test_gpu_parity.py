@@ -514,3 +514,40 @@ def test_stream_snowball_grows_and_warm_starts(sc, ctx):
         ref = O.lobpcg(O.laplacian_csr(cur.n, cur.src, cur.dst), Xw, 10)
         lmax = 2 * ref.lam.max() + 1
         assert np.max(np.abs(lam - ref.lam)) <= 1e-8 * max(lmax, 1)
+
+
+# ------------------------------------------------------------------ CPQR assignment (f2)
+
+
+def _planted_block(n, k, seed, noise=0.05):
+    rng = np.random.default_rng(seed)
+    truth = rng.integers(0, k, n)
+    basis, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    return truth, (np.eye(k)[truth] @ basis + noise * rng.standard_normal((n, k))).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (7, 7), (1000, 5), (20001, 44)])
+def test_cpqr_assign_matches_oracle(sc, ctx, n, k):
+    truth, Y = _planted_block(n, k, n + k)
+    labels, piv = sc.sc_cpqr_assign(ctx, Y)
+    ref_labels, ref_piv = O.cpqr_assign(Y.astype(np.float64), k)
+    assert list(piv) == list(ref_piv)
+    assert np.array_equal(labels, ref_labels)
+    if n >= 1000:
+        pm, _, _ = O.partition_metrics(truth, labels)
+        assert pm == 1.0
+
+
+def test_cpqr_assign_on_spectral_embedding(sc, ctx):
+    """The paper's use: assignment from the LOBPCG eigenvector block of a DC-SBM graph."""
+    g = W.dcsbm(5000, 11, seed=1)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    _, _, X, _ = sc.sc_lobpcg(ctx, G, 11, iters=60, prec=sc.SC_PREC_FP64, seed=2,
+                              precond=sc.SC_PRECOND_JACOBI)
+    labels, piv = sc.sc_cpqr_assign(ctx, X)
+    ref_labels, ref_piv = O.cpqr_assign(X.astype(np.float64), 11)
+    assert list(piv) == list(ref_piv)
+    assert np.mean(labels == ref_labels) >= 0.999
+    pm, _, _ = O.partition_metrics(g.truth, labels)
+    pm_ref, _, _ = O.partition_metrics(g.truth, ref_labels)
+    assert abs(pm - pm_ref) <= 2e-3
