@@ -216,6 +216,21 @@ def run_ours(args):
             eq[name] = {"ms": inf["ms"], "iters": inf["iters_done"], "max_resid": float(resid.max())}
         except sc.ScError as e:
             eq[name] = {"error": str(e)}
+    # partition quality of the step's k-means labels against the planted blocks, and the
+    # other assignment of Sec. II.A (QR with column pivoting) on the same 20-pass block
+    from paper_1708_07481_gb300.metrics import pm_pr_pp
+
+    assign = {"kmeans_pm_pr_pp": list(pm_pr_pp(g.truth, labels))}
+    try:
+        _, _, X20, _ = sc.sc_lobpcg(ctx, G, K, iters=ITERS, prec=sc.SC_PREC_MIXED, seed=SEED,
+                                    cold=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cl, _ = sc.sc_cpqr_assign(ctx, X20)
+        assign["cpqr_ms_host_block"] = 1e3 * (time.perf_counter() - t0)
+        assign["cpqr_pm_pr_pp"] = list(pm_pr_pp(g.truth, cl))
+    except sc.ScError as e:
+        assign["cpqr_error"] = str(e)
     G.close()
 
     if rank != 0:
@@ -245,6 +260,7 @@ def run_ours(args):
         "partitions_per_s": n_steps / total,
         "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
         "lobpcg_only_ms": info["ms"],
+        "assignment": assign,
         "equal_residual": {"tol": tol, "norm": "2 * max degree (Gershgorin bound on ||L||)",
                            **eq, "speedup": (eq.get("fp64", {}).get("ms", 0) / eq["mixed"]["ms"])
                            if "ms" in eq.get("mixed", {}) and "ms" in eq.get("fp64", {}) else None},
