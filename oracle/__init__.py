@@ -23,6 +23,7 @@ from .spectral import (  # noqa: F401
     laplacian_dense,
     lloyd,
     lobpcg,
+    lobpcg_blocks,
     partition,
     partition_metrics,
     rayleigh_ritz,

@@ -221,7 +221,7 @@ class LobpcgResult:
 
 def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: float = 0.0,
            keep_history: bool = False, explicit: bool = False,
-           precond: str | None = None) -> LobpcgResult:
+           precond: str | None = None, constraint: np.ndarray | None = None) -> LobpcgResult:
     """Unpreconditioned block LOBPCG for the K smallest eigenpairs of L (Sec. II.B, III).
 
     Start: X = CholQR(CholQR(X0)); LX = L X; Rayleigh-Ritz on span(X).
@@ -245,6 +245,9 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
     unscaled) to R_a before the projection: the trial basis is [X, T R_a, P_a] (the optional T
     of preconditioned LOBPCG, Sec. II.B); the rounding floor for R_a is divided by max d.
     Residual norms, the tolerance and locking refer to the unpreconditioned R.
+    ``constraint`` (n x c, orthonormal columns) runs the iteration in its orthogonal
+    complement (hard locking, Sec. IV): the start block and every (preconditioned) residual
+    block are projected off it before anything else, so X and P stay in the complement.
     One multiplication by L per pass (Sec. III): LP and LX are carried along implicitly.
     ``explicit=True`` recomputes LX, LR_a and LP_a as products with L instead -- the same
     iteration in exact arithmetic, stable when a direction column sinks to rounding level
@@ -259,6 +262,10 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
     """
     X0 = np.asarray(X0, dtype=np.float64)
     n, K = X0.shape
+    Yc = None
+    if constraint is not None and np.asarray(constraint).shape[1] > 0:
+        Yc = np.asarray(constraint, dtype=np.float64)
+        X0 = X0 - Yc @ (Yc.T @ X0)
     X, _ = cholqr(X0)
     X, _ = cholqr(X)
     LX = lap_apply(L, X)
@@ -292,6 +299,8 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
         Ra = R[:, act]
         if tinv is not None:
             Ra = Ra / tinv[:, None]
+        if Yc is not None:
+            Ra = Ra - Yc @ (Yc.T @ Ra)
         Ra = Ra - X @ (X.T @ Ra)
         # a residual at the rounding floor cannot improve its Ritz pair: leave it out (this
         # soft-locks the pair at the accuracy the arithmetic allows)
@@ -349,6 +358,34 @@ def lobpcg(L: Csr, X0: np.ndarray, iters: int, tol_abs: float = 0.0, tol_lock: f
     R = LX - X * lam[None, :]
     return LobpcgResult(lam=lam, X=X, resid=np.linalg.norm(R, axis=0), iters=done,
                         fallbacks=fallbacks, history=hist, dropped=dropped)
+
+
+def lobpcg_blocks(L: Csr, X0: np.ndarray, nb: int, iters: int, tol_abs: float = 0.0,
+                  precond: str | None = None) -> LobpcgResult:
+    """Hard locking (Sec. IV): the K = X0.shape[1] smallest eigenpairs computed nb columns at a
+    time.  Block b starts from columns [b nb, (b + 1) nb) of X0 and runs lobpcg in the
+    orthogonal complement of the Ritz vectors of the blocks before it; the blocks' Ritz
+    vectors, values and residual norms are concatenated in order.
+
+    Pinned by: converged block runs reproduce the dense eigenpairs; a block constrained by
+    exact eigenvectors finds the next eigenvalues.
+    """
+    X0 = np.asarray(X0, dtype=np.float64)
+    n, K = X0.shape
+    Yc = np.zeros((n, 0))
+    lams, res = [], []
+    done = fb = drop = 0
+    for b0 in range(0, K, nb):
+        r = lobpcg(L, X0[:, b0:b0 + nb], iters, tol_abs=tol_abs, precond=precond,
+                   constraint=Yc)
+        Yc = np.concatenate([Yc, r.X], axis=1)
+        lams.extend(r.lam.tolist())
+        res.extend(r.resid.tolist())
+        done += r.iters
+        fb += r.fallbacks
+        drop += r.dropped
+    return LobpcgResult(lam=np.array(lams), X=Yc, resid=np.array(res), iters=done,
+                        fallbacks=fb, dropped=drop)
 
 
 def _rr_blocks(blocks, K):

@@ -502,3 +502,26 @@ def test_cpqr_recovers_planted_blocks_and_ignores_column_signs():
     D = np.diag([1.0, -1.0, 1.0, -1.0, -1.0])
     labels2, piv2 = O.cpqr_assign(Y @ D, k)
     assert piv2 == piv and np.array_equal(labels2, labels)
+
+
+# ---------------------------------------------------------------- hard locking (Sec. IV)
+
+
+def test_constrained_lobpcg_finds_the_next_eigenpairs():
+    g = W.dcsbm(600, 5, seed=41)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev, V = np.linalg.eigh(O.laplacian_dense(L))
+    res = O.lobpcg(L, W.start_block(4, g.n, 3), 200, constraint=V[:, :3])
+    np.testing.assert_allclose(res.lam, ev[3:6], rtol=0, atol=1e-10 * ev[-1])
+    assert np.max(np.abs(V[:, :3].T @ res.X)) <= 1e-8
+
+
+def test_block_hard_locking_reproduces_dense_eigenpairs():
+    g = W.dcsbm(600, 6, seed=42)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev, V = np.linalg.eigh(O.laplacian_dense(L))
+    X0 = W.start_block(5, g.n, 6)
+    res = O.lobpcg_blocks(L, X0, 2, 300)
+    np.testing.assert_allclose(res.lam, ev[:6], rtol=0, atol=1e-9 * ev[-1])
+    np.testing.assert_allclose(res.X.T @ res.X, np.eye(6), atol=1e-8)
+    assert O.sin_theta(V[:, :6], res.X) <= 1e-6
