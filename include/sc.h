@@ -170,6 +170,19 @@ int sc_kmeans(sc_ctx* ctx, const float* E, int32_t n, int d, int k, int iters,
               uint64_t seed, const int32_t* init_idx, int on_device, int32_t* labels_out,
               float* centroids_out, int32_t* seeds_out, double* inertia, int* iters_run);
 
+/* sc_lobpcg_blocks: hard locking (Sec. IV) -- the K smallest eigenpairs computed nb columns
+ * at a time: block b (columns b nb ...) runs sc_lobpcg in the orthogonal complement of the
+ * Ritz vectors of the blocks before it (its start block and every residual block are
+ * projected off them).  The device holds one block's workspace (3 nb columns wide) plus the
+ * n x K result instead of a 3K-wide workspace.  Start blocks are the columns of X0 (host,
+ * n x K FP32) when given, else seeded Gaussian blocks (seed + b); opts->cold is ignored and
+ * opts->iters / tol_abs / tol_lock / precond apply to every block.  X_out (host n x K FP32)
+ * may be NULL.  info: lambda and resid of all K pairs in block order; iters_done, fallbacks,
+ * dropped, ms and kernels summed over blocks; converged = every block converged.  The result
+ * becomes the graph's resident block.  Needs 1 <= nb <= K <= SC_MAX_K and 3 nb <= n. */
+int sc_lobpcg_blocks(sc_ctx* ctx, sc_graph* g, int K, int nb, const sc_lobpcg_opts* opts,
+                     const float* X0, float* X_out, sc_eig_info* info);
+
 /* sc_lobpcg_batch: sc_lobpcg (seeded start block, or the resident block when !cold) for
  * `count` graphs at once.  Each solve runs on its own stream and the passes of all solves
  * are issued in turn, so their kernels overlap on the device -- in particular the one-CTA

@@ -512,6 +512,13 @@ struct LobRun : RunBase {
   // too.
   double res_floor, dir_floor;
   const T* pdeg = nullptr;  // degrees for the Jacobi preconditioner, or null
+  // Hard locking (Sec. IV): an orthonormal constraint block Yc (n x kc, stride ldyc) whose
+  // complement the iteration runs in; x0_pitch = row stride (floats) of a host start block.
+  const T* Yc = nullptr;
+  int kc = 0;
+  long long ldyc = 0, x0_pitch = 0;
+  double* Gy = nullptr;
+  T* Ty = nullptr;
   static constexpr int kReorth = 16;
   std::vector<void*> bufs;
   T *S = nullptr, *LS = nullptr, *S2 = nullptr, *LS2 = nullptr, *T1 = nullptr, *W1 = nullptr,
@@ -628,6 +635,15 @@ struct LobRun : RunBase {
     return gram<T>(st, al, n, ca, cb, C, ldc, sym, 0);
   }
 
+  // V (n x cols, stride ldv) <- V - Yc (Yc' V): the part of V in the complement of Yc.
+  cudaError_t project_off(T* V, long long ldv, int cols) {
+    cudaError_t e = gram_seg(Yc, ldyc, {{0, kc}}, V, ldv, {{0, cols}}, Gy, cols, false);
+    if (e == cudaSuccess) e = cast_mat<T>(st, kc, cols, Gy, cols, Ty, cols, -1.0);
+    if (e == cudaSuccess)
+      e = tall_gemm<T>(st, n, cat<T>(Yc, ldyc, kc), Ty, cols, cols, V, ldv, V, ldv, (T)1, dstatus);
+    return e;
+  }
+
   // Cholesky-QR of V (n x kc, stride ldv) into out (stride ldo); failure -> *failed.
   int cholqr_step(const T* V, long long ldv, int kc, T* out, long long ldo, bool* failed) {
     CK(gram_seg(V, ldv, {{0, kc}}, V, ldv, {{0, kc}}, G, kc, true), "gram");
@@ -697,13 +713,17 @@ struct LobRun : RunBase {
     if (!src) {
       CK(gauss_block<T>(st, n, K, stream_key(o.seed, 1, 0), S, ld3), "x0");
     } else if (sizeof(T) == 4) {
-      CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, src, sizeof(float) * K, sizeof(float) * K, rows,
+      const long long sp = (!dev_src && x0_pitch > 0) ? x0_pitch : K;
+      CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, src, sizeof(float) * sp, sizeof(float) * K, rows,
                            dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "x0");
     } else {
       std::vector<float> hf((size_t)rows * K);
       if (dev_src) {
         CK(cudaMemcpyAsync(hf.data(), src, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, st), "x0");
         CK(cudaStreamSynchronize(st), "x0");
+      } else if (x0_pitch > 0) {
+        for (int r = 0; r < rows; ++r)
+          std::memcpy(hf.data() + (size_t)r * K, src + (size_t)r * x0_pitch, sizeof(float) * K);
       } else {
         std::memcpy(hf.data(), src, sizeof(float) * hf.size());
       }
@@ -714,6 +734,12 @@ struct LobRun : RunBase {
     CK(cudaStreamSynchronize(st), "x0");
     CK(cudaEventRecord(ev0, st), "event");
     l0 = launches_total();
+    if (kc > 0) {
+      Gy = get<double>((size_t)kc * 2 * kp);
+      Ty = get<T>((size_t)kc * 2 * kp);
+      if (!Gy || !Ty) return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
+      CK(project_off(S, ld3, K), "constraint");
+    }
     // X <- CholQR(CholQR(X0)):  X slot -> T1 -> X slot
     bool bad = false;
     int rc = cholqr_step(S, ld3, K, T1, kp, &bad);
@@ -794,6 +820,9 @@ struct LobRun : RunBase {
       CK(cudaStreamSynchronize(st), "cols");
     }
     const int w = haveP ? 2 * ka : ka;
+    // (0) hard locking: the residual block leaves the span of the constraint block (P and X
+    //     stay in its complement as combinations of blocks that are)
+    if (kc > 0) CK(project_off(WR, ldw, ka), "constraint");
     // (1) project [R_a P_a] against X: F = X'[R_a P_a]; [R_a P_a] -= X F in one pass over X
     if (haveP)
       CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, false), "gram");
@@ -961,6 +990,97 @@ int check_lobpcg_args(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o) {
 }
 
 }  // namespace
+
+namespace {
+
+// Hard locking (Sec. IV): blocks of nb columns, each solved by a LobRun constrained to the
+// complement of the Ritz vectors of the blocks before it (held in Yc, n x K).
+template <typename T>
+int lobpcg_blocks_t(sc_ctx* c, sc_graph* g, int K, int nb, const sc_lobpcg_opts* o,
+                    const float* X0, float* X_out, sc_eig_info* info) {
+  const int n = g->csr.n;
+  Alloc al = alloc_of(c);
+  const long long ldy = (K + 3) & ~3;  // 16-byte rows for the tensor-map Gram
+  T* Yc = al.get<T>((size_t)n * ldy);
+  if (!Yc) return fail(c, SC_ENOMEM, "sc_lobpcg_blocks: out of device memory or HBM budget");
+  CK(cudaMemsetAsync(Yc, 0, sizeof(T) * (size_t)n * ldy, c->stream), "blocks");
+  sc_eig_info acc{};
+  acc.K = K;
+  acc.converged = 1;
+  int rc = SC_OK;
+  for (int b0 = 0, b = 0; b0 < K && rc == SC_OK; b0 += nb, ++b) {
+    const int kb = std::min(nb, K - b0);
+    sc_lobpcg_opts ob = *o;
+    ob.cold = 1;
+    ob.seed = o->seed + (uint64_t)b;  // a distinct seeded start block for each block
+    LobRun<T> r(c, g, kb, &ob, c->stream);
+    r.Yc = Yc;
+    r.kc = b0;
+    r.ldyc = ldy;
+    r.x0_pitch = X0 ? K : 0;
+    rc = r.setup(X0 ? X0 + b0 : nullptr, 0);
+    while (rc == SC_OK && !r.finished()) rc = r.pass();
+    sc_eig_info bi{};
+    if (rc == SC_OK) rc = r.finish(nullptr, &bi);
+    if (rc != SC_OK) break;
+    CK(cudaMemcpy2DAsync(Yc + b0, sizeof(T) * ldy, r.S, sizeof(T) * r.ld3, sizeof(T) * kb, n,
+                         cudaMemcpyDeviceToDevice, c->stream), "blocks");
+    for (int j = 0; j < kb; ++j) {
+      acc.lambda[b0 + j] = bi.lambda[j];
+      acc.resid[b0 + j] = bi.resid[j];
+    }
+    acc.iters_done += bi.iters_done;
+    acc.fallbacks += bi.fallbacks;
+    acc.dropped += bi.dropped;
+    acc.converged = acc.converged && bi.converged;
+    acc.ms += bi.ms;
+    acc.kernels += bi.kernels;
+  }
+  if (rc == SC_OK) {
+    // the n x K result as FP32: the graph's resident block and X_out
+    std::vector<float> hf;
+    if (g->X) ctx_free(c, g->X);
+    g->X = (float*)ctx_alloc(c, sizeof(float) * (size_t)n * K);
+    g->K = g->X ? K : 0;
+    if (!g->X) {
+      rc = fail(c, SC_ENOMEM, "sc_lobpcg_blocks: resident block");
+    } else if (sizeof(T) == 4) {
+      CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, Yc, sizeof(T) * ldy, sizeof(float) * K, n,
+                           cudaMemcpyDeviceToDevice, c->stream), "blocks");
+      if (X_out)
+        CK(cudaMemcpyAsync(X_out, g->X, sizeof(float) * (size_t)n * K, cudaMemcpyDeviceToHost,
+                           c->stream), "blocks");
+    } else {
+      std::vector<double> hd((size_t)n * K);
+      CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, Yc, sizeof(T) * ldy, sizeof(double) * K,
+                           n, cudaMemcpyDeviceToHost, c->stream), "blocks");
+      CK(cudaStreamSynchronize(c->stream), "blocks");
+      hf.assign(hd.begin(), hd.end());
+      CK(cudaMemcpyAsync(g->X, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice,
+                         c->stream), "blocks");
+      if (X_out) std::memcpy(X_out, hf.data(), sizeof(float) * hf.size());
+    }
+    CK(cudaStreamSynchronize(c->stream), "blocks");
+  }
+  al.put(Yc);
+  cudaStreamSynchronize(c->stream);
+  if (info && rc == SC_OK) *info = acc;
+  return rc;
+}
+
+}  // namespace
+
+int sc_lobpcg_blocks(sc_ctx* c, sc_graph* g, int K, int nb, const sc_lobpcg_opts* o,
+                     const float* X0, float* X_out, sc_eig_info* info) {
+  if (!c) return SC_EINVAL;
+  if (!g || !o || K < 1 || K > SC_MAX_K || nb < 1 || nb > K || K > g->csr.n)
+    return fail(c, SC_EINVAL, "sc_lobpcg_blocks: invalid argument (null pointer or size out of range)");
+  int rc = check_lobpcg_args(c, g, nb, o);
+  if (rc != SC_OK) return rc;
+  cudaSetDevice(c->device);
+  if (o->prec == SC_PREC_FP64) return lobpcg_blocks_t<double>(c, g, K, nb, o, X0, X_out, info);
+  return lobpcg_blocks_t<float>(c, g, K, nb, o, X0, X_out, info);
+}
 
 int sc_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const float* X0,
               int32_t x0_rows, float* X_out, sc_eig_info* info) {

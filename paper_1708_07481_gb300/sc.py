@@ -102,6 +102,8 @@ def lib():
         "sc_gram": ([vp, C.c_int, i64, C.c_int, C.c_int, vp, i64, vp, i64, vp, C.c_int], C.c_int),
         "sc_rr_solve": ([vp, C.c_int, C.c_int, C.c_int, vp, vp, vp], C.c_int),
         "sc_lobpcg_batch": ([vp, C.c_int, vp, vp, vp, vp], C.c_int),
+        "sc_lobpcg_blocks": ([vp, vp, C.c_int, C.c_int, C.POINTER(LobpcgOpts), vp, vp,
+                              C.POINTER(EigInfo)], C.c_int),
         "sc_partition_batch": ([vp, C.c_int, vp, vp, vp, vp, C.c_int, vp, vp], C.c_int),
         "sc_server_create": ([vp, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
         "sc_server_submit": ([vp, C.POINTER(Request), C.POINTER(u64)], C.c_int),
@@ -355,6 +357,20 @@ def sc_rr_solve(ctx: Ctx, G, K, prec=SC_PREC_FP32):
     Y = np.empty((m, K), np.float64)
     ctx.check(lib().sc_rr_solve(ctx.h, prec, m, K, _ptr(G)[0], _ptr(th)[0], _ptr(Y)[0]))
     return th, Y
+
+
+def sc_lobpcg_blocks(ctx: Ctx, g: Graph, K, nb, iters=20, tol_abs=0.0, tol_lock=0.0,
+                     prec=SC_PREC_MIXED, seed=0, X0=None, precond=SC_PRECOND_NONE):
+    """Hard locking: the K smallest eigenpairs nb at a time; returns (lam, resid, X, info)."""
+    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, 1, precond)
+    info = EigInfo()
+    n = sc_graph_info(g)[0]
+    X = np.empty((n, K), np.float32)
+    x0 = None if X0 is None else np.ascontiguousarray(X0, dtype=np.float32)
+    ctx.check(lib().sc_lobpcg_blocks(ctx.h, g.h, K, nb, C.byref(o), _ptr(x0)[0], _ptr(X)[0],
+                                     C.byref(info)))
+    d = info.as_dict()
+    return d["lam"], d["resid"], X, d
 
 
 def sc_lobpcg_batch(ctx: Ctx, graphs, K, iters=20, tol_abs=0.0, prec=SC_PREC_MIXED, seeds=None,

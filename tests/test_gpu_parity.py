@@ -551,3 +551,46 @@ def test_cpqr_assign_on_spectral_embedding(sc, ctx):
     pm, _, _ = O.partition_metrics(g.truth, labels)
     pm_ref, _, _ = O.partition_metrics(g.truth, ref_labels)
     assert abs(pm - pm_ref) <= 2e-3
+
+
+# ------------------------------------------------------------------ hard locking (f4)
+
+
+def test_lobpcg_blocks_matches_oracle_fp64(sc, ctx):
+    g = W.dcsbm(2000, 9, seed=51)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    X0 = W.start_block(7, g.n, 9)
+    lam, resid, X, info = sc.sc_lobpcg_blocks(ctx, G, 9, 3, iters=20, prec=sc.SC_PREC_FP64,
+                                              X0=X0)
+    ref = O.lobpcg_blocks(L, X0.astype(np.float32).astype(np.float64), 3, 20)
+    lmax = 2 * L.deg.max()
+    assert info["iters_done"] == ref.iters == 60
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-9
+    np.testing.assert_allclose(resid, ref.resid, rtol=1e-5, atol=1e-9 * lmax)
+    Xd = X.astype(np.float64)
+    np.testing.assert_allclose(Xd.T @ Xd, np.eye(9), atol=1e-5)
+
+
+def test_lobpcg_blocks_converges_and_saves_memory(sc, ctx):
+    g = W.dcsbm(3000, 12, seed=52)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    tol = 1e-4 * ev[-1]
+    lam, resid, X, info = sc.sc_lobpcg_blocks(ctx, G, 12, 4, iters=400, tol_abs=tol, seed=3,
+                                              precond=sc.SC_PRECOND_JACOBI)
+    assert info["converged"] == 1 and resid.max() <= tol
+    np.testing.assert_allclose(np.sort(lam), ev[:12], rtol=0, atol=2e-5 * ev[-1])
+    # one block's workspace instead of the whole block's
+    n, K = 200000, 96
+    gb = W.dcsbm(n, K, seed=53)
+    Gb = sc.sc_build_laplacian(ctx, n, gb.src, gb.dst)
+    base = ctx.bytes_in_use
+    ctx.bytes_peak()  # reset
+    sc.sc_lobpcg(ctx, Gb, K, iters=2, seed=1, cold=1, want_X=False)
+    whole = ctx.bytes_peak() - base
+    base2 = ctx.bytes_in_use
+    sc.sc_lobpcg_blocks(ctx, Gb, K, 24, iters=2, seed=1)
+    blocks = ctx.bytes_peak() - base2
+    assert blocks < 0.6 * whole, (blocks, whole)
