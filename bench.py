@@ -116,7 +116,8 @@ def whole_job_rate(units_per_step, steps, world, seconds):
 
 # DRAM bytes (read + write) per launch from one ncu --set full capture of each kernel on this
 # workload; to be cleared whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"rr_eig": 216576, "spmm": 32049920, "tall_gemm": 14492160, "chol_inv": 89344}
+NCU_TRAFFIC = {"rr_eig": 216576, "spmm": 32049920, "tall_gemm": 14492160, "chol_inv": 89344,
+               "gram": 23246592}
 
 
 def algorithmic_bytes(kernel, n, K, nnz, m_rr):
@@ -426,7 +427,7 @@ def cfg_stream(sc, W, ctx, n=50000, K=44, stages=10, cap=200):
             "warm_over_cold_iters": (sum(warm) / sum(cold)) if sum(cold) else None}
 
 
-def cfg_serve(sc, W, ctx, count=128, rate=200.0, fp64_sample=6):
+def cfg_serve(sc, W, ctx, count=512, rate=200.0, fp64_sample=6):
     """Poisson arrivals (seeded) of cold graphs and emerging-edge deltas of the most recent
     cold graph through the partition server; p50/p99 latency and partitions/s, next to the
     same requests one at a time in plain FP64 on a bounded sample."""
