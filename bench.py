@@ -427,7 +427,7 @@ def cfg_stream(sc, W, ctx, n=50000, K=44, stages=10, cap=200):
             "warm_over_cold_iters": (sum(warm) / sum(cold)) if sum(cold) else None}
 
 
-def cfg_serve(sc, W, ctx, count=512, rate=200.0, fp64_sample=6):
+def cfg_serve(sc, W, ctx, count=512, rate=200.0, fp64_sample=6, slots=64):
     """Poisson arrivals (seeded) of cold graphs and emerging-edge deltas of the most recent
     cold graph through the partition server; p50/p99 latency and partitions/s, next to the
     same requests one at a time in plain FP64 on a bounded sample."""
@@ -444,7 +444,7 @@ def cfg_serve(sc, W, ctx, count=512, rate=200.0, fp64_sample=6):
             g, d, nxt = graphs[j]
             graphs[j] = (g, d, nxt + 1)
             payload.append((sc.SC_REQ_DELTA, j, g.n, g.src[d[nxt]], g.dst[d[nxt]], g.K))
-    srv = sc.sc_server_create(ctx, max_slots=16, queue_cap=count)
+    srv = sc.sc_server_create(ctx, max_slots=slots, queue_cap=count)
     t0 = time.perf_counter()
     tickets = []
     for r, (kind, gid, n, s_, d_, K) in zip(reqs, payload):
