@@ -51,12 +51,20 @@ typedef enum {
 } sc_status;
 
 /* Arithmetic of the LOBPCG path.
- *  SC_PREC_MIXED: FP32 blocks and SpMM; Gram products on tcgen05 tensor cores as
- *                 3-term split-TF32 products, FP32 accumulation in tensor memory and FP64
- *                 sums across CTAs; FP64 Cholesky of the K x K Grams; FP32 Rayleigh-Ritz.
- *  SC_PREC_FP32:  as MIXED, but Gram products on FP32 CUDA cores (FP64 cross-CTA sums).
- *  SC_PREC_FP64:  every step in FP64 (the plain form and the 1e-10 check mode). */
-typedef enum { SC_PREC_MIXED = 0, SC_PREC_FP32 = 1, SC_PREC_FP64 = 2 } sc_precision;
+ *  SC_PREC_MIXED:    FP32 blocks and SpMM; Gram products on tcgen05 tensor cores as
+ *                    3-term split-TF32 products, FP32 accumulation in tensor memory and FP64
+ *                    sums across CTAs (the Gram matrices are FP64); the small dense solves
+ *                    (Cholesky-QR factors, Rayleigh-Ritz eigenproblem) in FP32.
+ *  SC_PREC_FP32:     as MIXED, but Gram products on FP32 CUDA cores (FP64 cross-CTA sums).
+ *  SC_PREC_FP64:     every step in FP64 (the plain form and the 1e-10 check mode).
+ *  SC_PREC_MIXED_DD: as MIXED, with the small dense solves in FP64 (results cast to FP32
+ *                    for the tall updates). */
+typedef enum {
+  SC_PREC_MIXED = 0,
+  SC_PREC_FP32 = 1,
+  SC_PREC_FP64 = 2,
+  SC_PREC_MIXED_DD = 3
+} sc_precision;
 
 /* Symmetrization W <- W + W' (Sec. II.A): logical sum (unweighted, duplicates merged,
  * every stored weight 1) or algebraic sum (weights added, duplicates accumulate). */

@@ -504,6 +504,8 @@ struct LobRun : RunBase {
   RunAlloc ra;
   Alloc al;
   int use_tc;
+  bool dense64 = false;      // small dense solves in FP64, results cast to T
+  double *Gd = nullptr, *Yd = nullptr;  // FP64 results of those solves
   double pivot_tol;
   // Rounding floors of the arithmetic T.  A residual column at or below res_floor (64 ulps of
   // the Gershgorin bound 2 max_i d_i on ||L||) cannot improve its Ritz pair any further: it is
@@ -543,7 +545,8 @@ struct LobRun : RunBase {
     ld3 = 3LL * kp;
     ra = RunAlloc{c, st};
     al = Alloc{run_alloc, run_free, &ra};
-    use_tc = (sizeof(T) == 4 && o.prec == SC_PREC_MIXED) ? 1 : 0;
+    use_tc = (sizeof(T) == 4 && (o.prec == SC_PREC_MIXED || o.prec == SC_PREC_MIXED_DD)) ? 1 : 0;
+    dense64 = sizeof(T) == 4 && o.prec == SC_PREC_MIXED_DD;
     pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-10;
     dir_floor = 64.0 * (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53);
     res_floor = dir_floor * 2.0 * g->csr.deg_max;
@@ -635,6 +638,26 @@ struct LobRun : RunBase {
     return gram<T>(st, al, n, ca, cb, C, ldc, sym, 0);
   }
 
+  // The small dense solves, in T or (dense64) in FP64 with the result cast to T.
+  cudaError_t chol(int ka, const double* Gm, T* out, int* fail_col = nullptr, int keep = 0,
+                   int* pflag = nullptr, int ndrop = 0, int* ndropped = nullptr,
+                   double rfloor = 0.0, double pfloor = 0.0) {
+    if (!dense64)
+      return chol_inv<T>(st, al, ka, Gm, ka, out, dstatus, pivot_tol, fail_col, keep, pflag, ndrop,
+                         ndropped, rfloor, pfloor);
+    cudaError_t e = chol_inv<double>(st, al, ka, Gm, ka, Gd, dstatus, pivot_tol, fail_col, keep,
+                                     pflag, ndrop, ndropped, rfloor, pfloor);
+    if (e == cudaSuccess) e = cast_mat<T>(st, ka, ka, Gd, ka, out, ka, 1.0);
+    return e;
+  }
+  cudaError_t rr(int m, const double* Gm, int* pflag = nullptr, int mP = 0,
+                 int* nfallback = nullptr) {
+    if (!dense64) return rr_eig<T>(st, al, m, K, Gm, m, theta, Y, dstatus, pflag, mP, nfallback);
+    cudaError_t e = rr_eig<double>(st, al, m, K, Gm, m, theta, Yd, dstatus, pflag, mP, nfallback);
+    if (e == cudaSuccess) e = cast_mat<T>(st, m, K, Yd, K, Y, K, 1.0);
+    return e;
+  }
+
   // V (n x cols, stride ldv) <- V - Yc (Yc' V): the part of V in the complement of Yc.
   cudaError_t project_off(T* V, long long ldv, int cols) {
     cudaError_t e = gram_seg(Yc, ldyc, {{0, kc}}, V, ldv, {{0, cols}}, Gy, cols, false);
@@ -647,7 +670,7 @@ struct LobRun : RunBase {
   // Cholesky-QR of V (n x kc, stride ldv) into out (stride ldo); failure -> *failed.
   int cholqr_step(const T* V, long long ldv, int kc, T* out, long long ldo, bool* failed) {
     CK(gram_seg(V, ldv, {{0, kc}}, V, ldv, {{0, kc}}, G, kc, true), "gram");
-    CK(chol_inv<T>(st, al, kc, G, kc, Tm, dstatus, pivot_tol), "chol");
+    CK(chol(kc, G, Tm), "chol");
     int hs = 0;
     int rc = read_status(&hs);
     if (rc != SC_OK) return rc;
@@ -675,6 +698,11 @@ struct LobRun : RunBase {
     W1 = get<T>((size_t)n * 2 * kp, true);
     Q1 = get<T>((size_t)n * 2 * kp, true);
     G = get<double>((size_t)mmax * mmax);
+    if (dense64) {
+      Gd = get<double>((size_t)mmax * mmax);
+      Yd = get<double>((size_t)mmax * K);
+      if (!Gd || !Yd) return fail(c, SC_ENOMEM, "sc_lobpcg: out of device memory or HBM budget");
+    }
     Tm = get<T>((size_t)mmax * mmax);
     TmA = get<T>((size_t)mmax * mmax);
     TmB = get<T>((size_t)mmax * mmax);
@@ -750,7 +778,7 @@ struct LobRun : RunBase {
     CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
     // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
     CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, true), "gram");
-    CK(rr_eig<T>(st, al, K, K, G, K, theta, Y, dstatus), "rr");
+    CK(rr(K, G), "rr");
     CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus), "tall");
     CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus), "tall");
     std::swap(S, S2);
@@ -851,10 +879,10 @@ struct LobRun : RunBase {
         CK(gram_seg(WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
       else
         CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, al, wq, G, wq, TmA, dstatus, pivot_tol, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
+      CK(chol(wq, G, TmA, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
       CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus), "tall");
       CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
-      CK(chol_inv<T>(st, al, wq, G, wq, TmB, dstatus, pivot_tol, dfail, ka, pf, ka, nullptr), "chol");
+      CK(chol(wq, G, TmB, dfail, ka, pf, ka, nullptr), "chol");
       // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
       CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
       if (haveP)
@@ -879,7 +907,7 @@ struct LobRun : RunBase {
       CK(gram_seg(S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, true), "gram");
     else
       CK(gram_seg(S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, true), "gram");
-    CK(rr_eig<T>(st, al, m, K, G, m, theta, Y, dstatus, useP ? dP : nullptr, ka, dfb), "rr");
+    CK(rr(m, G, useP ? dP : nullptr, ka, dfb), "rr");
     // (5) update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike); R = LX - X theta
     const T* Yrp = Y + (size_t)K * K;
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
@@ -899,7 +927,7 @@ struct LobRun : RunBase {
     // orthonormal the standard Rayleigh-Ritz solve lets Ritz vectors merge.
     if ((done_passes + 1) % kReorth == 0) {
       CK(gram_seg(S, ld3, {{0, K}}, S, ld3, {{0, K}}, G, K, true), "gram");
-      CK(chol_inv<T>(st, al, K, G, K, Tm, dstatus, pivot_tol), "chol");
+      CK(chol(K, G, Tm), "chol");
       CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus), "tall");
       CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus), "tall");
       CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, T1, sizeof(T) * kp, sizeof(T) * K, n,
@@ -983,7 +1011,7 @@ int check_lobpcg_args(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o) {
   if (!g || !o || K < 1 || K > SC_MAX_K || o->iters < 0)
     return fail(c, SC_EINVAL, "sc_lobpcg: invalid argument (null pointer or size out of range)");
   if ((int64_t)3 * K > g->csr.n) return fail(c, SC_EINVAL, "sc_lobpcg: need 3K <= n");
-  if (o->prec < SC_PREC_MIXED || o->prec > SC_PREC_FP64) return fail(c, SC_EINVAL, "bad precision");
+  if (o->prec < SC_PREC_MIXED || o->prec > SC_PREC_MIXED_DD) return fail(c, SC_EINVAL, "bad precision");
   if (o->precond != SC_PRECOND_NONE && o->precond != SC_PRECOND_JACOBI)
     return fail(c, SC_EINVAL, "sc_lobpcg: unknown preconditioner");
   return SC_OK;

@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "sc.h")
 
 SC_OK, SC_EINVAL, SC_ENOMEM, SC_EBREAKDOWN, SC_ENOTCONV, SC_ETIMEOUT, SC_ECUDA, SC_EAGAIN = (
     0, -1, -2, -3, -4, -5, -6, -7)
-SC_PREC_MIXED, SC_PREC_FP32, SC_PREC_FP64 = 0, 1, 2
+SC_PREC_MIXED, SC_PREC_FP32, SC_PREC_FP64, SC_PREC_MIXED_DD = 0, 1, 2, 3
 SC_SYM_LOGICAL, SC_SYM_ALGEBRAIC = 0, 1
 SC_MAX_K = 512
 _NAMES = {0: "SC_OK", -1: "SC_EINVAL", -2: "SC_ENOMEM", -3: "SC_EBREAKDOWN", -4: "SC_ENOTCONV",

@@ -211,7 +211,7 @@ def test_lobpcg_fp64_check_mode_small(sc, ctx):
     np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_lobpcg_fp32_small(sc, ctx, prec):
     g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 1000, 11, 20, prec=prec)
     lmax = 2 * L.deg.max()
@@ -220,8 +220,9 @@ def test_lobpcg_fp32_small(sc, ctx, prec):
     assert info["fallbacks"] == ref.fallbacks == 0
 
 
-def test_lobpcg_fp32_bench_size(sc, ctx):
-    g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 50000, 44, 20)
+@pytest.mark.parametrize("prec", [0, 3])
+def test_lobpcg_fp32_bench_size(sc, ctx, prec):
+    g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 50000, 44, 20, prec=prec)
     lmax = 2 * L.deg.max()
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
     assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-3
@@ -237,7 +238,7 @@ def test_lobpcg_fp64_wide_block(sc, ctx):
     np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_lobpcg_jacobi_matches_oracle(sc, ctx, prec):
     """The Jacobi-preconditioned iteration (T = D^-1 on the residual block, Sec. II.B) against
     the oracle's, 20 passes from the same start block."""
@@ -311,7 +312,7 @@ def test_lobpcg_fp64_far_past_convergence(sc, ctx):
     assert np.linalg.norm(R, axis=0).max() <= 1e-6 * ev[-1]  # X returned as float32
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_lobpcg_fp32_far_past_convergence(sc, ctx, prec):
     """400 FP32 passes with no locking: residual columns sink to FP32 rounding noise within
     about 60 passes.  The pass must stay at the solution: exact L-images of the
