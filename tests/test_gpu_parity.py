@@ -595,3 +595,22 @@ def test_lobpcg_blocks_converges_and_saves_memory(sc, ctx):
     sc.sc_lobpcg_blocks(ctx, Gb, K, 24, iters=2, seed=1)
     blocks = ctx.bytes_peak() - base2
     assert blocks < 0.6 * whole, (blocks, whole)
+
+
+def test_lobpcg_blocks_ragged_last_block_and_device_cpqr(sc, ctx):
+    """K = 10 in blocks of 4 (4 + 4 + 2), mixed precision against the FP64 oracle's block
+    driver from the same start block; then CPQR on the device-resident copy of the block."""
+    torch = pytest.importorskip("torch")
+    g = W.dcsbm(2500, 10, seed=54)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    X0 = W.start_block(8, g.n, 10)
+    lam, resid, X, info = sc.sc_lobpcg_blocks(ctx, G, 10, 4, iters=20, X0=X0)
+    ref = O.lobpcg_blocks(L, X0.astype(np.float32).astype(np.float64), 4, 20)
+    lmax = 2 * L.deg.max()
+    assert info["iters_done"] == ref.iters == 60 and len(lam) == 10
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
+    Xd = torch.from_numpy(X).cuda()
+    labels_d, piv_d = sc.sc_cpqr_assign(ctx, Xd)
+    labels_h, piv_h = sc.sc_cpqr_assign(ctx, X)
+    assert np.array_equal(labels_d, labels_h) and np.array_equal(piv_d, piv_h)
