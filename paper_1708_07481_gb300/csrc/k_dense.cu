@@ -804,14 +804,10 @@ __global__ void __launch_bounds__(RR_NT)
 // ---------------------------------------------------------------------------------------
 // Rayleigh-Ritz, register-slot form for m <= 32 NS: the same four steps as k_rr_eig with
 // less synchronization.
-//  1. Tridiagonalization, one barrier per Householder step.  Warp w owns rows i = w + NW t,
-//     so row i's entry of a vector held as lane (i & 31), slot (i >> 5) is reachable with a
-//     compile-time slot index.  Every warp keeps the reflector v, the vector w and the next
-//     row x in registers (columns j = lane + 32 u), forms the next reflector itself from x
-//     (no barrier), computes p = beta A v on its own rows, and after the one barrier (which
-//     publishes p and the per-warp parts of p'v) forms w, the next row x (row k+1 with the
-//     two-sided update applied, computed by every warp from the not-yet-updated row) and the
-//     rank-2 update of its own rows.  The reflector of step k is stored in row k.
+//  1. Tridiagonalization with a few threads per row and two barriers per Householder step:
+//     the owners of a row form its entries of p = beta A v and apply the rank-2 update to
+//     them; the reflector scalars are formed by every thread from one block sum.  The
+//     reflector of step k is stored in row k.
 //  2. Multisection on Sturm counts as in k_rr_eig, converged to eps ||T|| (the accuracy the
 //     reduction itself has).
 //  3. Inverse iteration: LU with partial pivoting of T - sigma I fused with the forward
@@ -827,6 +823,26 @@ __device__ __forceinline__ T slot_sel(const T (&a)[NS], int u) {
   return r;
 }
 
+// Threads per row in the tridiagonalization of an m x m matrix by nt threads: the largest
+// of 8, 4, 2, 1 with m * tpr <= nt.
+__host__ __device__ inline int rr_tpr(int m, int nt) {
+  int t = 8;
+  while (t > 1 && m * t > nt) t >>= 1;
+  return t;
+}
+// Row stride of the matrix: a multiple of tpr, at least m, with an odd quotient, so that the
+// tpr parts of 32 / tpr consecutive rows fall in distinct shared-memory banks.  At most
+// m + 2 tpr - 1 <= m + 15.
+__host__ __device__ inline int rr_lda(int m, int tpr) {
+  int l = (m + tpr - 1) / tpr * tpr;
+  if ((l / tpr) % 2 == 0) l += tpr;
+  return l;
+}
+// Barrier 1 over the first n threads of the block (n a multiple of 32).
+__device__ __forceinline__ void rr_named_sync(int n) {
+  asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
 template <typename T, int NS, int NW, bool SM>
 __global__ void __launch_bounds__(NW * 32)
     k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
@@ -840,9 +856,8 @@ __global__ void __launch_bounds__(NW * 32)
   T* e = d + m;         // m
   T* beta = e + m;      // m
   T* e2 = beta + m;     // m
-  T* Pb = e2 + m;       // 2 m: p of the current step
-  T* Vsh = Pb + 2 * m;  // 2 m: the reflector of the current step (double-buffered)
-  T* lam = Vsh + 2 * m; // K
+  T* Pb = e2 + m;       // 2 m: p of the current step (double-buffered)
+  T* lam = Pb + 2 * m;  // K
   T* shift = lam + K;   // K
   T* dd = shift + K;    // K pivots of the block Cholesky
   T* cbuf = dd + K;     // 2 K
@@ -851,7 +866,7 @@ __global__ void __launch_bounds__(NW * 32)
   T* red = coef + K;    // 3 NW per-warp parts, then scalar slots RS ..
   T* nxt = red + 3 * NW + 8;
   T* A = SM ? nxt : Ag;                             // m x m (row stride m)
-  const int lda = m;  // row stride of the matrix
+  const int lda = rr_lda(m, rr_tpr(m, NT));  // row stride of the matrix
   T* Z = SM ? A + (size_t)m * lda : Zg;             // m x K
   T* U = SM ? Z + (size_t)m * K : Ug;               // 3 m K
   T* Gs = SM ? U + (size_t)3 * m * K : Gsg;         // K x K
@@ -876,179 +891,122 @@ __global__ void __launch_bounds__(NW * 32)
   }
   RR_MARK(0);
 
-  // ---- 1. tridiagonalization
-  // Warp 0 forms the reflectors: from x = row k (with the updates of the steps before k) it
-  // writes v_k to a double-buffered shared vector; after the first barrier the worker warps
-  // form p = beta A v on the rows they own (row class i mod NWR), two rows at a time; after
-  // the second barrier the workers form w = p - (beta/2)(p'v) v and apply the rank-2 update
-  // to their rows while warp 0 computes the next row x and the next reflector.  Warps that
-  // share warp 0's scheduler (warp % 4 == 0) own no rows, so the reflector's dependent chain
-  // is not starved of issue slots by the update.
-  constexpr int NWR = NW - NW / 4;  // row-owning warps: warp % 4 != 0
-  const int wk = (warp & 3) ? warp - (warp >> 2) - 1 : -1;  // worker index
-  T x[NS];
-  if (warp == 0) {
-#pragma unroll
-    for (int u = 0; u < NS; ++u) {
-      const int j = lane + 32 * u;
-      x[u] = j < m ? A[j] : (T)0;  // row 0
-    }
-  }
-  // warp 0: reflector of step kk from x into vbuf, plus d, e, beta
-  auto reflector = [&](int kk, T* vbuf) {
-    const int k1 = kk + 1;
-    const T x0 = __shfl_sync(FULL, slot_sel(x, k1 >> 5), k1 & 31);
-    const T xk = __shfl_sync(FULL, slot_sel(x, kk >> 5), kk & 31);
-    T sg = 0;
-#pragma unroll
-    for (int u = 0; u < NS; ++u) {
-      const int j = lane + 32 * u;
-      if (j > k1 && j < m) sg = fma(x[u], x[u], sg);
-    }
-    sg = warp_sum(sg);
-    T bet = 0, iv0 = 0, ek = x0;
-    if (sg != (T)0) {
-      // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
-      // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
-      const T mu = sqrt(x0 * x0 + sg);
-      const T v0 = x0 + copysign(mu, x0);
-      iv0 = (T)1 / v0;
-      bet = (T)2 / ((T)1 + sg * iv0 * iv0);
-      ek = -copysign(mu, x0);
-    }
-#pragma unroll
-    for (int u = 0; u < NS; ++u) {
-      const int j = lane + 32 * u;
-      if (j < m) vbuf[j] = (j == k1) ? (T)1 : ((j > k1) ? x[u] * iv0 : (T)0);
-    }
-    if (lane == 0) {
-      d[kk] = xk;
-      e[kk] = ek;
-      beta[kk] = bet;
-    }
-  };
-  if (warp == 0 && m > 2) reflector(0, Vsh);
-  int k = 0;
-  long long tsub = clock64();
-  for (; k + 2 < m; ++k) {
-    const int k1 = k + 1;
-    const T* __restrict__ vk = Vsh + (k & 1) * m;
-    __syncthreads();
-    RR_SUB(0, tsub);
-    const T bet = beta[k];
-    const int umin = k1 >> 5;
-    T vr[NS];
-#pragma unroll
-    for (int u = 0; u < NS; ++u) {
-      const int j = lane + 32 * u;
-      vr[u] = j < m ? vk[j] : (T)0;
-    }
-    // p_i = beta (A v)_i on this warp's rows i >= k1, two rows at a time
-    if (wk >= 0) {
-      int off = (wk - k1) % NWR;
-      if (off < 0) off += NWR;
-      for (int i = k1 + off; i < m; i += 2 * NWR) {
-        const int i2 = i + NWR;
-        const bool has2 = i2 < m;  // uniform in the warp
-        const T* __restrict__ ra = A + i * lda;
-        const T* __restrict__ rb = A + (has2 ? i2 : i) * lda;
-        T sa = 0, sb = 0;
-#pragma unroll
-        for (int u = 0; u < NS; ++u) {
-          const int j = lane + 32 * u;
-          if (u >= umin && j < m) {
-            sa = fma(ra[j], vr[u], sa);
-            sb = fma(rb[j], vr[u], sb);
+  // ---- 1. tridiagonalization (Golub & Van Loan Alg. 8.3.1), two barriers per step
+  // tpr threads per row: thread t < ntri owns row i = t / tpr and, of the columns j that step
+  // k touches, those with j = k + 1 + q (mod tpr), q = t % tpr.  Step k:
+  //  (a) the owners of rows j > k publish x_j = a_jk (their own entry) and per-warp sums of
+  //      x_j^2 over j > k + 1;
+  //  (b) every thread forms the reflector scalars (mu, v0, beta, e_k) from sigma^2 and x_{k+1};
+  //      v = e_{k+1} + x / v0 on j > k + 1 goes to row k for the back-transformation;
+  //  (c) p_i = beta (A v)_i on the owned rows (parts over q combined by shuffles), published
+  //      with per-warp sums of p_i v_i;
+  //  (d) w = p - (beta / 2)(p'v) v and the rank-2 update A -= v w' + w v' of the owned
+  //      entries, with v_j and w_j formed on the fly from x_j and p_j.
+  // The entry a_j,k+1 that row j's owner reads in the next step's (a) is updated by that same
+  // thread in (d), so no barrier separates (d) from the next (a).
+  {
+    const int tpr = rr_tpr(m, NT);
+    const int ntri = (m * tpr + 31) / 32 * 32;
+    const int nwt = ntri / 32;
+    const int ri = tid / tpr, q = tid % tpr;
+    const bool own = tid < ntri && ri < m;
+    T* __restrict__ pvec = e2;  // p of the current step (e2 is free until step 2)
+    if (tid < ntri) {
+      for (int k = 0; k + 2 < m; ++k) {
+        const int k1 = k + 1;
+        T* __restrict__ xs = Pb + (k & 1) * m;  // x of this step (double-buffered)
+        // (a)
+        T xi = 0, s2 = 0;
+        if (own && q == 0) {
+          if (ri >= k1) {
+            xi = A[ri * lda + k];
+            xs[ri] = xi;
+            if (ri > k1) s2 = xi * xi;
+          } else if (ri == k) {
+            d[k] = A[k * lda + k];
           }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          sa += __shfl_xor_sync(FULL, sa, o);
-          sb += __shfl_xor_sync(FULL, sb, o);
+        s2 = warp_sum(s2);
+        if (lane == 0) red[warp] = s2;
+        rr_named_sync(ntri);
+        // (b)
+        const T sg = warp_sum(lane < nwt ? red[lane] : (T)0);
+        const T x0 = xs[k1];
+        T bet = 0, iv0 = 0, ek = x0;
+        if (sg != (T)0) {
+          // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
+          // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
+          const T mu = sqrt(x0 * x0 + sg);
+          const T v0 = x0 + copysign(mu, x0);
+          iv0 = (T)1 / v0;
+          bet = (T)2 / ((T)1 + sg * iv0 * iv0);
+          ek = -copysign(mu, x0);
         }
-        if (lane == 0) {
-          Pb[i] = bet * sa;
-          if (has2) Pb[i2] = bet * sb;
+        if (tid == 0) {
+          e[k] = ek;
+          beta[k] = bet;
         }
-      }
-    }
-    RR_SUB(1, tsub);
-    __syncthreads();
-    RR_SUB(2, tsub);
-    if (warp != 0 && wk < 0) continue;  // idle warps: straight to the next step's barrier
-    // w = p - (beta/2)(p'v) v (every warp forms p'v itself, same order everywhere)
-    T wr[NS];
-    T pv = 0;
-#pragma unroll
-    for (int u = 0; u < NS; ++u) {
-      const int j = lane + 32 * u;
-      wr[u] = (j >= k1 && j < m) ? Pb[j] : (T)0;
-      pv = fma(wr[u], vr[u], pv);
-    }
-    pv = warp_sum(pv);
-    const T kc = bet * (T)0.5 * pv;
-#pragma unroll
-    for (int u = 0; u < NS; ++u) wr[u] = fma(-kc, vr[u], wr[u]);
-    if (warp == 0) {
-      // the next row (row k1 with this step's update; no warp updates row k1) and the
-      // reflector of step k, kept in row k for the back-transformation
-      const T wk1 = Pb[k1] - kc;
-      const T* r1 = A + k1 * lda;
-      T* rk = A + k * lda;
-#pragma unroll
-      for (int u = 0; u < NS; ++u) {
-        const int j = lane + 32 * u;
-        x[u] = (j >= k1 && j < m) ? r1[j] - wr[u] - wk1 * vr[u] : (T)0;
-        if (j > k1 && j < m) rk[j] = vr[u];
-      }
-      if (k1 + 2 < m) reflector(k1, Vsh + (k1 & 1) * m);
-    } else {
-      // rank-2 update of this warp's rows i > k1, two rows at a time
-      const int r0 = k1 + 1;
-      int off = (wk - r0) % NWR;
-      if (off < 0) off += NWR;
-      for (int i = r0 + off; i < m; i += 2 * NWR) {
-        const int i2 = i + NWR;
-        const bool has2 = i2 < m;
-        const T via = vk[i], wia = Pb[i] - kc * via;
-        const T vib = has2 ? vk[i2] : (T)0, wib = has2 ? Pb[i2] - kc * vib : (T)0;
-        T* __restrict__ ra = A + i * lda;
-        T* __restrict__ rb = A + (has2 ? i2 : i) * lda;
-        T na[NS], nb[NS];
-#pragma unroll
-        for (int u = 0; u < NS; ++u) {
-          const int j = lane + 32 * u;
-          if (u >= umin && j < m) {
-            na[u] = ra[j] - (via * wr[u] + wia * vr[u]);
-            nb[u] = rb[j] - (vib * wr[u] + wib * vr[u]);
+        if (own && q == 0 && ri > k1) A[k * lda + ri] = xi * iv0;
+        // (c)
+        const bool act = own && ri >= k1;
+        T sacc = 0;
+        if (act) {
+          const T* __restrict__ ra = A + ri * lda;
+          T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+          int j = k1 + 1 + q;
+          for (; j + 3 * tpr < m; j += 4 * tpr) {
+            s0 = fma(ra[j], xs[j], s0);
+            s1 = fma(ra[j + tpr], xs[j + tpr], s1);
+            s2 = fma(ra[j + 2 * tpr], xs[j + 2 * tpr], s2);
+            s3 = fma(ra[j + 3 * tpr], xs[j + 3 * tpr], s3);
+          }
+          for (; j < m; j += tpr) s0 = fma(ra[j], xs[j], s0);
+          sacc = (s0 + s1) + (s2 + s3);
+        }
+        for (int o = 1; o < tpr; o <<= 1) sacc += __shfl_xor_sync(FULL, sacc, o);
+        T pi = 0, vi = 0, pvp = 0;
+        if (act) {
+          pi = bet * (A[ri * lda + k1] + iv0 * sacc);
+          vi = ri == k1 ? (T)1 : xs[ri] * iv0;
+          if (q == 0) {
+            pvec[ri] = pi;
+            pvp = pi * vi;
           }
         }
-#pragma unroll
-        for (int u = 0; u < NS; ++u) {
-          const int j = lane + 32 * u;
-          if (u >= umin && j < m) {
-            ra[j] = na[u];
-            if (has2) rb[j] = nb[u];
+        pvp = warp_sum(pvp);
+        if (lane == 0) red[NW + warp] = pvp;
+        rr_named_sync(ntri);
+        // (d)
+        const T pv = warp_sum(lane < nwt ? red[NW + lane] : (T)0);
+        const T kc = bet * (T)0.5 * pv;
+        if (act) {
+          const T wi = pi - kc * vi;
+          T* __restrict__ ra = A + ri * lda;
+          int j = k1 + q;
+          if (q == 0) {  // column k + 1, where v_j = 1
+            ra[k1] = ra[k1] - vi * (pvec[k1] - kc) - wi;
+            j += tpr;
+          }
+#pragma unroll 4
+          for (; j < m; j += tpr) {
+            const T vj = xs[j] * iv0;
+            const T wj = pvec[j] - kc * vj;
+            ra[j] = ra[j] - vi * wj - wi * vj;
           }
         }
       }
-    }
-    RR_SUB(3, tsub);
-  }
-  (void)tsub;
-  __syncthreads();  // the last row's diagonal was updated by its owner
-  if (warp == 0) {
-    // x = row k (k = m - 2, or 0 when m == 1)
-    const T xa = __shfl_sync(FULL, slot_sel(x, k >> 5), k & 31);
-    const int k1 = k + 1 < m ? k + 1 : k;
-    const T xb = __shfl_sync(FULL, slot_sel(x, k1 >> 5), k1 & 31);
-    if (lane == 0) {
-      d[k] = xa;
-      if (m >= 2) {
-        e[k] = xb;
-        d[m - 1] = A[(m - 1) * lda + (m - 1)];
+      rr_named_sync(ntri);
+      if (tid == 0) {
+        // the trailing 2 x 2 block of T (or the 1 x 1 matrix)
+        if (m >= 2) {
+          d[m - 2] = A[(m - 2) * lda + (m - 2)];
+          e[m - 2] = A[(m - 1) * lda + (m - 2)];
+          d[m - 1] = A[(m - 1) * lda + (m - 1)];
+        } else {
+          d[0] = A[0];
+        }
+        e[m - 1] = 0;
       }
-      e[m - 1] = 0;
     }
   }
   __syncthreads();
@@ -1392,17 +1350,19 @@ cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int
 template <typename T, int NS, int NW>
 cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
                        double* theta, T* Y, int* d_status, int* pflag, int mP, int* nfallback) {
-  const size_t base = sizeof(T) * ((size_t)8 * m + 7 * (size_t)K + 3 * NW + 8);
-  const size_t big = sizeof(T) * ((size_t)m * m + 4 * (size_t)m * K + (size_t)K * K);
+  const size_t base = sizeof(T) * ((size_t)6 * m + 7 * (size_t)K + 3 * NW + 8);
+  if (m > NW * 32) return cudaErrorInvalidValue;
+  // the matrix rows are padded to rr_lda(m', tpr) <= m' + 15 for the m' <= m the kernel solves
+  const size_t big = sizeof(T) * ((size_t)m * (m + 16) + 4 * (size_t)m * K + (size_t)K * K);
   constexpr bool can_sm = sizeof(T) == 4 && NS == 5;  // the only shape whose blocks fit
   const bool insm = can_sm && base + big <= 220 * 1024;
   const size_t sm = base + (insm ? big : 0);
   T* Ag = nullptr;
   if (!insm) {
-    Ag = al.get<T>((size_t)m * m + 4 * (size_t)m * K + (size_t)K * K);
+    Ag = al.get<T>((size_t)m * (m + 16) + 4 * (size_t)m * K + (size_t)K * K);
     if (!Ag) return cudaErrorMemoryAllocation;
   }
-  T* Zg = insm ? nullptr : Ag + (size_t)m * m;
+  T* Zg = insm ? nullptr : Ag + (size_t)m * (m + 16);
   T* Ug = insm ? nullptr : Zg + (size_t)m * K;
   T* Gsg = insm ? nullptr : Ug + (size_t)3 * m * K;
   auto kern = k_rr_eig_reg<T, NS, NW, false>;
