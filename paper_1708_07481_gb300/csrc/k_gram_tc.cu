@@ -243,16 +243,17 @@ __global__ void __launch_bounds__(NTH, 1)
 }
 
 // C = the sum of the chunk partials of each tile, in a fixed order.  One CTA per N index of a
-// tile (the partials are N-major) and one thread per M index and half of the chunks: thread
-// (M, h) sums chunks h, h + 2, h + 4, ... into eight accumulators (chunk h + 2(8q + u) goes to
-// accumulator u), so eight independent loads are in flight per thread; the accumulators are
-// added pairwise and the two halves in order h = 0, 1.  Element (M, N) is tile entry (M, N),
-// or (N, M) when the kernel swapped the operand roles.  Entries past the output are skipped.
+// tile (the partials are N-major) and one thread per M index and chunk group: thread (M, h)
+// sums chunks h, h + RH, h + 2 RH, ... into four accumulators (chunk h + RH (4q + u) goes to
+// accumulator u), which are added pairwise; the RH group sums are added in order h = 0 .. RH-1.
+// Element (M, N) is tile entry (M, N), or (N, M) when the kernel swapped the operand roles.
+// Entries past the output are skipped.
 static_assert(TM == 128 && TN == 128, "the reduction maps one thread to each of 128 M indices");
-__global__ void __launch_bounds__(256)
+constexpr int RH = 8;  // chunk groups of the reduction: thread (mi, h) sums chunks c = h (mod RH)
+__global__ void __launch_bounds__(TM * RH)
     k_gram_tc_reduce(const double* __restrict__ part, int nch, int ntiles, int nbt, int a, int b,
                      SegMap ma, SegMap mb, double* C, int ldc, int sym) {
-  __shared__ double hs[TM];
+  __shared__ double hs[RH][TM];
   const int tile = blockIdx.x / TN, jn = blockIdx.x % TN;
   const int2 tl = tile_coord(tile, nbt, sym);
   const int ca = tl.x * TM, cb = tl.y * TN;
@@ -260,27 +261,26 @@ __global__ void __launch_bounds__(256)
   const bool swp = !sym && va < vb;  // the same choice as the Gram kernel
   const int mcount = swp ? vb : va, ncount = swp ? va : vb;
   if (jn >= ncount) return;  // uniform in the CTA
-  const int mi = threadIdx.x & (TM - 1), h = threadIdx.x >> 7;
+  const int mi = threadIdx.x & (TM - 1), h = threadIdx.x / TM;
   const double* src = part + (long long)tile * TM * TN + (long long)jn * TM;
   const long long cstride = (long long)ntiles * TM * TN;
-  double s[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) s[u] = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   if (mi < mcount) {
     int c = h;
-    for (; c + 14 < nch; c += 16) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s[u] += src[(long long)(c + 2 * u) * cstride + mi];
+    for (; c + 3 * RH < nch; c += 4 * RH) {
+      s0 += src[(long long)c * cstride + mi];
+      s1 += src[(long long)(c + RH) * cstride + mi];
+      s2 += src[(long long)(c + 2 * RH) * cstride + mi];
+      s3 += src[(long long)(c + 3 * RH) * cstride + mi];
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (c + 2 * u < nch) s[u] += src[(long long)(c + 2 * u) * cstride + mi];
+    for (; c < nch; c += RH) s0 += src[(long long)c * cstride + mi];
   }
-  double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-  if (h == 1) hs[mi] = t;
+  hs[h][mi] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (h == 0 && mi < mcount) {
-    t += hs[mi];
+    double t = hs[0][mi];
+#pragma unroll
+    for (int q = 1; q < RH; ++q) t += hs[q][mi];
     const int ti = swp ? jn : mi, tj = swp ? mi : jn;
     const int oi = seg_index(ma, ca + ti), oj = seg_index(mb, cb + tj);
     if (oi >= 0 && oj >= 0) {
@@ -352,7 +352,7 @@ cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, lon
                                                                (int)nch, nt, rpc, a, b, part,
                                                                d_status);
       note_launch();
-      k_gram_tc_reduce<<<(unsigned)(nt * TN), 256, 0, st>>>(part, (int)nch, nt, nb, a, b, ma, mb,
+      k_gram_tc_reduce<<<(unsigned)(nt * TN), TM * RH, 0, st>>>(part, (int)nch, nt, nb, a, b, ma, mb,
                                                             C, ldc, sym ? 1 : 0);
       note_launch();
     }
