@@ -21,8 +21,6 @@
 namespace sc {
 namespace {
 
-constexpr int NT = 1024;
-
 template <typename T> struct Lim;
 template <> struct Lim<float> {
   __device__ static float eps() { return FLT_EPSILON; }
