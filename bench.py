@@ -116,7 +116,7 @@ def whole_job_rate(units_per_step, steps, world, seconds):
 
 # DRAM bytes (read + write) per launch from one ncu --set full capture of each kernel on this
 # workload; to be cleared whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"rr_eig": None, "spmm": 32049920, "tall_gemm": 14492160, "chol_inv": 89344,
+NCU_TRAFFIC = {"rr_eig": 217088, "spmm": 32049920, "tall_gemm": 14492160, "chol_inv": 89344,
                "gram": 23246592}
 
 
