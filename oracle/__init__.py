@@ -15,6 +15,7 @@ from .spectral import (  # noqa: F401
     cholqr_drop,
     cpqr_assign,
     cpqr_pivots,
+    eigengap_k,
     embed_rows,
     kmeans,
     kmeanspp_seed,

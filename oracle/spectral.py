@@ -546,6 +546,34 @@ def cpqr_assign(Y: np.ndarray, k: int):
     return np.argmax(scores, axis=1).astype(np.int64), piv
 
 
+def eigengap_k(lam, ratio: float = 4.0, floor: float = 0.0) -> int:
+    """Number of clusters from the gap in the smallest Laplacian eigenvalues (Sec. II.A).
+
+    The paper compares the increments of the ascending eigenvalues and takes the first
+    significantly large one; the eigenvalues below it count the clusters, and no such
+    increment means no reliable multi-way partition.  Reading used here: with
+    d_i = lam_{i+1} - lam_i (ascending lam, i = 0 .. l-2), increments at or below ``floor``
+    (the accuracy of the eigenvalues) count as zero; the first i >= 1 with
+    d_i > ratio * max(d_0 .. d_{i-1}) and d_i > 0 gives k = i + 1.  The first increment has no
+    earlier one to be compared with, so k = 1 is never returned; 0 means no gap.
+
+    Pinned by: disjoint cliques (closed-form spectrum: c zeros, then the clique size) give
+    k = c; a path graph's smooth spectrum gives no gap; planted blocks with a strong
+    within/between contrast give k = number of blocks (dense spectrum).
+    """
+    lam = np.sort(np.asarray(lam, dtype=np.float64))
+    if lam.size < 3:
+        return 0
+    d = np.diff(lam)
+    d = np.where(d > floor, d, 0.0)
+    prev = d[0]
+    for i in range(1, d.size):
+        if d[i] > 0.0 and d[i] > ratio * prev:
+            return i + 1
+        prev = max(prev, d[i])
+    return 0
+
+
 def partition_metrics(truth, found):
     """(PM, PR, PP): optimal partition matching, pairwise recall, pairwise precision.
 

@@ -525,3 +525,67 @@ def test_block_hard_locking_reproduces_dense_eigenpairs():
     np.testing.assert_allclose(res.lam, ev[:6], rtol=0, atol=1e-9 * ev[-1])
     np.testing.assert_allclose(res.X.T @ res.X, np.eye(6), atol=1e-8)
     assert O.sin_theta(V[:, :6], res.X) <= 1e-6
+
+
+# ------------------------------------------------------------------ eigengap cluster count (f1)
+
+
+def _clique_union(c, s):
+    src, dst = [], []
+    for b in range(c):
+        for i in range(s):
+            for j in range(i + 1, s):
+                src.append(b * s + i)
+                dst.append(b * s + j)
+    return c * s, np.array(src, np.int32), np.array(dst, np.int32)
+
+
+@pytest.mark.parametrize("c,s", [(2, 4), (3, 5), (5, 7)])
+def test_eigengap_counts_disjoint_cliques(c, s):
+    """c disjoint cliques K_s: Laplacian spectrum 0 (c times) then s (c(s-1) times)."""
+    n, src, dst = _clique_union(c, s)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(O.laplacian_csr(n, src, dst)))
+    closed = np.array([0.0] * c + [float(s)] * (c * (s - 1)))
+    np.testing.assert_allclose(ev, closed, atol=1e-9)
+    assert O.eigengap_k(ev[:c + 3], floor=1e-9) == c
+    assert O.eigengap_k(closed[:c + 3]) == c
+
+
+def test_eigengap_none_on_a_path():
+    """Path P_n: lam_j = 2 - 2 cos(pi j / n); increments grow by at most 3x (j = 1), so no
+    increment is 4x the ones before it."""
+    n = 60
+    src = np.arange(n - 1, dtype=np.int32)
+    dst = src + 1
+    ev = np.linalg.eigvalsh(O.laplacian_dense(O.laplacian_csr(n, src, dst)))
+    closed = 2 - 2 * np.cos(np.pi * np.arange(n) / n)
+    np.testing.assert_allclose(ev, closed, atol=1e-12)
+    assert O.eigengap_k(ev[:20], floor=1e-12) == 0
+    assert O.eigengap_k(ev[:20], ratio=2.9, floor=1e-12) == 2  # the 3x step at j = 1
+
+
+def test_eigengap_counts_strong_planted_blocks():
+    rng = np.random.default_rng(5)
+    K, s = 6, 40
+    truth = np.repeat(np.arange(K), s)
+    n = K * s
+    iu = np.triu_indices(n, 1)
+    p = np.where(truth[iu[0]] == truth[iu[1]], 0.5, 0.004)
+    keep = rng.random(p.size) < p
+    ev = np.linalg.eigvalsh(O.laplacian_dense(
+        O.laplacian_csr(n, iu[0][keep].astype(np.int32), iu[1][keep].astype(np.int32))))
+    assert O.eigengap_k(ev[:K + 4], floor=1e-9) == K
+
+
+def test_eigengap_reading_edge_cases():
+    # fewer than three values, or no increments: no gap
+    assert O.eigengap_k([0.0, 5.0]) == 0
+    assert O.eigengap_k(np.zeros(6)) == 0
+    # the first increment is never a gap by itself (it has nothing to be compared with)
+    assert O.eigengap_k([0.0, 10.0, 10.1, 10.2]) == 0
+    # strict comparison: an increment exactly ratio times the largest before it is no gap
+    assert O.eigengap_k([0.0, 1.0, 5.0], ratio=4.0) == 0
+    assert O.eigengap_k([0.0, 1.0, 5.0 + 1e-9], ratio=4.0) == 2
+    # increments at or below the floor count as zero; input order does not matter
+    assert O.eigengap_k([3.0, 1e-12, 0.0, 2e-12], floor=1e-9) == 3
+    assert O.eigengap_k([3.0, 1e-12, 0.0, 2e-12], floor=0.0) == 3
