@@ -218,6 +218,18 @@ int sc_partition(sc_ctx* ctx, sc_graph* g, int K, int k, const sc_lobpcg_opts* o
 int sc_cpqr_assign(sc_ctx* ctx, const float* Y, int32_t n, int K, int on_device,
                    int32_t* labels_out, int32_t* pivots_out);
 
+/* sc_eigengap: the number of clusters read off the smallest Laplacian eigenvalues (Sec. II.A:
+ * the eigenvalues below the first significantly large increment count the clusters, and no
+ * such increment means no reliable multi-way partition).  lam: l eigenvalues (host, any
+ * order; sorted internally), e.g. sc_eig_info.lambda of an sc_lobpcg run with l slightly
+ * above the expected count.  With d_i = lam_{i+1} - lam_i of the ascending values and
+ * increments <= floor taken as 0 (floor: the accuracy of the eigenvalues), *k_out is i + 1
+ * for the first i >= 1 with d_i > 0 and d_i > ratio * max(d_0 .. d_{i-1}), else 0.  Host
+ * arithmetic in FP64, no device work.
+ * Errors: SC_EINVAL (null pointer, l < 0 or l > SC_MAX_K, ratio <= 1, floor < 0 or not
+ * finite, a non-finite eigenvalue). */
+int sc_eigengap(const double* lam, int l, double ratio, double floor, int* k_out);
+
 /* sc_partition_batch: sc_partition over `count` graphs with batched LOBPCG (labels_out[q]
  * has n_q entries; host). */
 int sc_partition_batch(sc_ctx* ctx, int count, sc_graph* const* graphs, const int* K,

@@ -1260,6 +1260,34 @@ int sc_kmeans(sc_ctx* c, const float* E, int32_t n, int d, int k, int iters, uin
   return rc;
 }
 
+int sc_eigengap(const double* lam, int l, double ratio, double floor, int* k_out) {
+  if (!k_out || (l > 0 && !lam) || l < 0 || l > SC_MAX_K || !(ratio > 1.0) ||
+      !(floor >= 0.0) || !std::isfinite(floor) || !std::isfinite(ratio))
+    return SC_EINVAL;
+  double v[SC_MAX_K];
+  for (int i = 0; i < l; ++i) {
+    if (!std::isfinite(lam[i])) return SC_EINVAL;
+    v[i] = lam[i];
+  }
+  std::sort(v, v + l);
+  *k_out = 0;
+  if (l < 3) return SC_OK;
+  auto inc = [&](int i) {
+    const double d = v[i + 1] - v[i];
+    return d > floor ? d : 0.0;
+  };
+  double prev = inc(0);
+  for (int i = 1; i + 1 < l; ++i) {
+    const double d = inc(i);
+    if (d > 0.0 && d > ratio * prev) {
+      *k_out = i + 1;
+      return SC_OK;
+    }
+    prev = std::max(prev, d);
+  }
+  return SC_OK;
+}
+
 int sc_cpqr_assign(sc_ctx* c, const float* Y, int32_t n, int K, int on_device,
                    int32_t* labels_out, int32_t* pivots_out) {
   if (!c) return SC_EINVAL;

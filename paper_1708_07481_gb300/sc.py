@@ -96,6 +96,7 @@ def lib():
         "sc_kmeans": ([vp, vp, i32, C.c_int, C.c_int, C.c_int, u64, vp, C.c_int, vp, vp, vp,
                        C.POINTER(dbl), C.POINTER(C.c_int)], C.c_int),
         "sc_cpqr_assign": ([vp, vp, i32, C.c_int, C.c_int, vp, vp], C.c_int),
+        "sc_eigengap": ([vp, C.c_int, dbl, dbl, C.POINTER(C.c_int)], C.c_int),
         "sc_partition": ([vp, vp, C.c_int, C.c_int, C.POINTER(LobpcgOpts), C.c_int, vp,
                           C.POINTER(EigInfo)], C.c_int),
         "sc_stream_update": ([vp, vp, i32, i64, vp, vp, vp, C.c_int], C.c_int),
@@ -318,6 +319,17 @@ def sc_cpqr_assign(ctx: Ctx, Y):
     py, dev = _ptr(Y)
     ctx.check(lib().sc_cpqr_assign(ctx.h, py, n, K, dev, _ptr(labels)[0], _ptr(piv)[0]))
     return labels, piv
+
+
+def sc_eigengap(lam, ratio=4.0, floor=0.0):
+    """Cluster count from the first significantly large increment of the eigenvalues lam
+    (host arithmetic in the library); 0 when there is no such increment."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    k = C.c_int(0)
+    rc = lib().sc_eigengap(_ptr(lam)[0], int(lam.size), float(ratio), float(floor), C.byref(k))
+    if rc != SC_OK:
+        raise ScError(rc, "sc_eigengap: invalid argument")
+    return k.value
 
 
 def sc_partition(ctx: Ctx, g: Graph, K, k, iters=20, kmeans_iters=50, prec=SC_PREC_MIXED,
