@@ -380,7 +380,6 @@ __global__ void __launch_bounds__(256)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __shared__ long long tot;
   __shared__ double ps[8][33];
-  __shared__ float red[8];
   if (threadIdx.x == 0) tot = 0;
   __syncthreads();
   {
@@ -422,7 +421,6 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) cn[j] = s;
   }
-  (void)red;
 }
 
 __global__ void k_inertia(int n, int d, int k, const float* __restrict__ E, long long lde,
