@@ -37,3 +37,32 @@ def test_binding_names_match_header():
                  "sc_server_stats", "sc_server_destroy"):
             continue  # methods of Ctx / Graph / Server
         assert hasattr(sc, s), s
+
+
+def test_eigengap_host_rule_matches_oracle(built):
+    """sc_eigengap is host arithmetic in the library (no device work), so its parity with the
+    oracle's count is checked here, on random, clustered and rounded spectra."""
+    import numpy as np
+
+    import oracle as O
+
+    rng = np.random.default_rng(12)
+    for t in range(4000):
+        l = int(rng.integers(0, 48))
+        kind = t % 4
+        if kind == 0:
+            lam = rng.random(l) * 10
+        elif kind == 1:
+            c = int(rng.integers(1, 9))
+            lam = np.concatenate([rng.random(min(c, l)) * 1e-9, 5 + rng.random(max(l - c, 0))])
+        elif kind == 2:
+            lam = np.cumsum(rng.random(l) ** 3)
+        else:
+            lam = np.round(rng.random(l) * 4, 1)
+        ratio = float(rng.choice([1.5, 2.0, 3.0, 4.0, 10.0]))
+        floor = float(rng.choice([0.0, 1e-9, 1e-3]))
+        assert sc.sc_eigengap(lam, ratio, floor) == O.eigengap_k(lam, ratio, floor)
+    for bad in (([np.nan, 1.0, 2.0], 4.0, 0.0), ([0.0, 1.0, 2.0], 1.0, 0.0),
+                ([0.0, 1.0, 2.0], 4.0, -1.0), (np.zeros(600), 4.0, 0.0)):
+        with pytest.raises(sc.ScError):
+            sc.sc_eigengap(*bad)

@@ -619,31 +619,6 @@ def test_lobpcg_blocks_ragged_last_block_and_device_cpqr(sc, ctx):
 # ------------------------------------------------------------------ eigengap cluster count (f1)
 
 
-def test_eigengap_matches_oracle(sc):
-    """The library's count agrees with the oracle's on random, clustered and rounded
-    spectra (FP64 decisions on the same values, so exactly)."""
-    rng = np.random.default_rng(11)
-    for t in range(2000):
-        l = int(rng.integers(0, 40))
-        kind = t % 4
-        if kind == 0:
-            lam = rng.random(l) * 10
-        elif kind == 1:
-            c = int(rng.integers(1, 8))
-            lam = np.concatenate([rng.random(min(c, l)) * 1e-9, 5 + rng.random(max(l - c, 0))])
-        elif kind == 2:
-            lam = np.cumsum(rng.random(l) ** 3)
-        else:
-            lam = np.round(rng.random(l) * 4, 1)
-        ratio = float(rng.choice([1.5, 2.0, 3.0, 4.0, 10.0]))
-        floor = float(rng.choice([0.0, 1e-9, 1e-3]))
-        assert sc.sc_eigengap(lam, ratio, floor) == O.eigengap_k(lam, ratio, floor)
-    for bad in (([np.nan, 1.0, 2.0], 4.0, 0.0), ([0.0, 1.0, 2.0], 1.0, 0.0),
-                ([0.0, 1.0, 2.0], 4.0, -1.0)):
-        with pytest.raises(sc.ScError):
-            sc.sc_eigengap(*bad)
-
-
 def test_eigengap_on_lobpcg_ritz_values_of_disjoint_cliques(sc, ctx):
     """End to end: 4 disjoint 30-cliques (spectrum 0 x4, then 30), LOBPCG for K = 7, then
     the count read off the Ritz values is 4."""
