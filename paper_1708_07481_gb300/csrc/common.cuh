@@ -177,6 +177,12 @@ template <typename T>
 cudaError_t cast_mat(cudaStream_t st, int rows, int cols, const double* src, int lds, T* dst,
                      int ldd, double scale);
 
+// dst (rows x cols, To, row stride ldd) = src (Ti, row stride lds), element by element
+// (FP32 <-> FP64).
+template <typename Ti, typename To>
+cudaError_t convert_mat(cudaStream_t st, long long rows, int cols, const Ti* src, long long lds,
+                        To* dst, long long ldd);
+
 // Row normalization E_i = X_i / ||X_i||.
 template <typename T>
 cudaError_t rownorm(cudaStream_t st, long long n, int K, const T* X, long long ldx, float* E,

@@ -507,6 +507,19 @@ __global__ void k_cast(int rows, int cols, const double* __restrict__ src, int l
   }
 }
 
+// dst (rows x cols, To, row stride ldd) = src (rows x cols, Ti, row stride lds), converted.
+template <typename Ti, typename To>
+__global__ void k_convert(long long rows, int cols, const Ti* __restrict__ src, long long lds,
+                          To* __restrict__ dst, long long ldd) {
+  const long long total = rows * cols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx / cols;
+    const int j = (int)(idx - i * cols);
+    dst[i * ldd + j] = (To)src[i * lds + j];
+  }
+}
+
 __device__ inline unsigned long long d_sm64(unsigned long long key, unsigned long long i) {
   unsigned long long z = key + (i + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -745,6 +758,20 @@ cudaError_t cast_mat(cudaStream_t st, int rows, int cols, const double* src, int
   note_launch();
   return cudaGetLastError();
 }
+
+template <typename Ti, typename To>
+cudaError_t convert_mat(cudaStream_t st, long long rows, int cols, const Ti* src, long long lds,
+                        To* dst, long long ldd) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const long long blocks = (rows * cols + 255) / 256;
+  k_convert<Ti, To><<<cap_grid(blocks, 4 * 152), 256, 0, st>>>(rows, cols, src, lds, dst, ldd);
+  note_launch();
+  return cudaGetLastError();
+}
+template cudaError_t convert_mat<float, double>(cudaStream_t, long long, int, const float*,
+                                                long long, double*, long long);
+template cudaError_t convert_mat<double, float>(cudaStream_t, long long, int, const double*,
+                                                long long, float*, long long);
 
 #define SC_INST(T)                                                                          \
   template cudaError_t gauss_block<T>(cudaStream_t, long long, int, unsigned long long, T*,  \

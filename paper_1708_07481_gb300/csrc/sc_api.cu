@@ -740,24 +740,25 @@ struct LobRun : RunBase {
     }
     if (!src) {
       CK(gauss_block<T>(st, n, K, stream_key(o.seed, 1, 0), S, ld3), "x0");
-    } else if (sizeof(T) == 4) {
+    } else if constexpr (sizeof(T) == 4) {
       const long long sp = (!dev_src && x0_pitch > 0) ? x0_pitch : K;
       CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, src, sizeof(float) * sp, sizeof(float) * K, rows,
                            dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st), "x0");
     } else {
-      std::vector<float> hf((size_t)rows * K);
-      if (dev_src) {
-        CK(cudaMemcpyAsync(hf.data(), src, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, st), "x0");
-        CK(cudaStreamSynchronize(st), "x0");
-      } else if (x0_pitch > 0) {
-        for (int r = 0; r < rows; ++r)
-          std::memcpy(hf.data() + (size_t)r * K, src + (size_t)r * x0_pitch, sizeof(float) * K);
-      } else {
-        std::memcpy(hf.data(), src, sizeof(float) * hf.size());
+      // the FP32 start block widened to FP64 on the device (a host block is copied first)
+      const float* fsrc = src;
+      float* tmp = nullptr;
+      if (!dev_src) {
+        tmp = al.get<float>((size_t)rows * K);
+        if (!tmp) return fail(c, SC_ENOMEM, "sc_lobpcg: start block");
+        const long long sp = x0_pitch > 0 ? x0_pitch : K;
+        CK(cudaMemcpy2DAsync(tmp, sizeof(float) * K, src, sizeof(float) * sp, sizeof(float) * K,
+                             rows, cudaMemcpyHostToDevice, st), "x0");
+        fsrc = tmp;
       }
-      std::vector<double> hd(hf.begin(), hf.end());
-      CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, hd.data(), sizeof(double) * K, sizeof(double) * K,
-                           rows, cudaMemcpyHostToDevice, st), "x0");
+      CK((convert_mat<float, T>(st, rows, K, fsrc, K, S, ld3)), "x0");
+      CK(cudaStreamSynchronize(st), "x0");
+      al.put(tmp);
     }
     CK(cudaStreamSynchronize(st), "x0");
     CK(cudaEventRecord(ev0, st), "event");
@@ -962,17 +963,14 @@ struct LobRun : RunBase {
       g->K = g->X ? K : 0;
     }
     if (g->X) {
-      if (sizeof(T) == 4) {
+      if constexpr (sizeof(T) == 4) {
         CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
                              cudaMemcpyDeviceToDevice, st), "resident");
       } else {
-        std::vector<double> hd((size_t)n * K);
-        CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, S, sizeof(T) * ld3, sizeof(double) * K,
-                             n, cudaMemcpyDeviceToHost, st), "resident");
-        CK(cudaStreamSynchronize(st), "resident");
-        std::vector<float> hf(hd.begin(), hd.end());
-        CK(cudaMemcpyAsync(g->X, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, st), "resident");
-        if (X_out) std::memcpy(X_out, hf.data(), sizeof(float) * hf.size());
+        CK((convert_mat<T, float>(st, n, K, S, ld3, g->X, K)), "resident");
+        if (X_out)
+          CK(cudaMemcpyAsync(X_out, g->X, sizeof(float) * (size_t)n * K, cudaMemcpyDeviceToHost,
+                             st), "resident");
         CK(cudaStreamSynchronize(st), "resident");
       }
     }
@@ -1066,27 +1064,21 @@ int lobpcg_blocks_t(sc_ctx* c, sc_graph* g, int K, int nb, const sc_lobpcg_opts*
   }
   if (rc == SC_OK) {
     // the n x K result as FP32: the graph's resident block and X_out
-    std::vector<float> hf;
     if (g->X) ctx_free(c, g->X);
     g->X = (float*)ctx_alloc(c, sizeof(float) * (size_t)n * K);
     g->K = g->X ? K : 0;
     if (!g->X) {
       rc = fail(c, SC_ENOMEM, "sc_lobpcg_blocks: resident block");
-    } else if (sizeof(T) == 4) {
-      CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, Yc, sizeof(T) * ldy, sizeof(float) * K, n,
-                           cudaMemcpyDeviceToDevice, c->stream), "blocks");
+    } else {
+      if constexpr (sizeof(T) == 4) {
+        CK(cudaMemcpy2DAsync(g->X, sizeof(float) * K, Yc, sizeof(T) * ldy, sizeof(float) * K, n,
+                             cudaMemcpyDeviceToDevice, c->stream), "blocks");
+      } else {
+        CK((convert_mat<T, float>(c->stream, n, K, Yc, ldy, g->X, K)), "blocks");
+      }
       if (X_out)
         CK(cudaMemcpyAsync(X_out, g->X, sizeof(float) * (size_t)n * K, cudaMemcpyDeviceToHost,
                            c->stream), "blocks");
-    } else {
-      std::vector<double> hd((size_t)n * K);
-      CK(cudaMemcpy2DAsync(hd.data(), sizeof(double) * K, Yc, sizeof(T) * ldy, sizeof(double) * K,
-                           n, cudaMemcpyDeviceToHost, c->stream), "blocks");
-      CK(cudaStreamSynchronize(c->stream), "blocks");
-      hf.assign(hd.begin(), hd.end());
-      CK(cudaMemcpyAsync(g->X, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice,
-                         c->stream), "blocks");
-      if (X_out) std::memcpy(X_out, hf.data(), sizeof(float) * hf.size());
     }
     CK(cudaStreamSynchronize(c->stream), "blocks");
   }
