@@ -164,6 +164,16 @@ typedef struct {
 int sc_lobpcg(sc_ctx* ctx, sc_graph* g, int K, const sc_lobpcg_opts* opts, const float* X0,
               int32_t x0_rows, float* X_out, sc_eig_info* info);
 
+/* sc_lobpcg64: sc_lobpcg with the start block and the result block in FP64 (Sec. II.B; the
+ * FP64 form is the check mode whose Ritz vectors are compared with an FP64 reference).
+ * X0: host n x K double (row-major; its first x0_rows rows, zero fill below) or NULL (the
+ * resident or seeded Gaussian block, as sc_lobpcg).  X_out: host n x K double or NULL.  With
+ * SC_PREC_FP64 the start block, every step and X_out are FP64; with the other precisions X0
+ * is rounded to FP32 and X_out is the FP32 block widened.  The resident block kept for warm
+ * starts is FP32, as after sc_lobpcg.  Errors as sc_lobpcg. */
+int sc_lobpcg64(sc_ctx* ctx, sc_graph* g, int K, const sc_lobpcg_opts* opts, const double* X0,
+                int32_t x0_rows, double* X_out, sc_eig_info* info);
+
 /* sc_embed_rows: E_i = X_i / ||X_i||_2 (rows of norm < 1e-30 stay zero), n x K float. */
 int sc_embed_rows(sc_ctx* ctx, const float* X, int32_t n, int K, float* E, int on_device);
 
@@ -200,8 +210,11 @@ int sc_lobpcg_batch(sc_ctx* ctx, int count, sc_graph* const* graphs, const int* 
                     const sc_lobpcg_opts* opts, sc_eig_info* infos);
 
 /* ---- end to end ------------------------------------------------------------------------
- * sc_partition: LOBPCG (K vectors) -> unit rows -> k-means (k clusters, kmeans_iters
- * Lloyd rounds, k-means++ seeded by opts->seed) -> labels_out[n] (host). */
+ * sc_partition: the spectral partition of Sec. II.A -- LOBPCG for the K smallest eigenpairs
+ * of L (Sec. II.B) -> the rows of the eigenvector block scaled to unit length -> k-means (k
+ * clusters, kmeans_iters Lloyd rounds, k-means++ seeded by opts->seed) -> labels_out[n]
+ * (host).  The eigenvector block stays resident on the graph for a later warm start
+ * (Sec. III).  Errors: those of sc_lobpcg and sc_kmeans; SC_EINVAL for k < 1 or k > n. */
 int sc_partition(sc_ctx* ctx, sc_graph* g, int K, int k, const sc_lobpcg_opts* opts,
                  int kmeans_iters, int32_t* labels_out, sc_eig_info* info);
 
@@ -245,7 +258,10 @@ int sc_stream_update(sc_ctx* ctx, sc_graph* g, int32_t n_new, int64_t m_delta,
                      const int32_t* src, const int32_t* dst, const float* w, int on_device);
 
 /* ---- serving loop (continuous batching of partition requests) ----------------------------
- * A server owns a context (used only by its worker thread; its HBM budget is the admission
+ * The paper's streaming setting (Sec. III: a graph G is partitioned, then G + g as new edges
+ * and vertices arrive, each stage warm-started from the previous eigenvector block) served
+ * as a request loop; the loop itself (queueing, admission, batching) has no counterpart in
+ * the paper.  A server owns a context (used only by its worker thread; its HBM budget is the admission
  * limit).  Requests wait in a queue of queue_cap entries; up to max_slots solves run at once,
  * each advancing one LOBPCG pass per round on its own stream, and a request that arrives
  * while others run joins at the next pass boundary.  Graphs stay resident by graph_id:
@@ -313,8 +329,12 @@ int sc_rr_solve(sc_ctx* ctx, int prec, int m, int K, const double* G, double* th
  * latency-critical loop that must not enter the allocator.  A, B and C are device pointers on
  * the current device; work is issued on cuda_stream (NULL = the legacy default stream) and
  * the call returns without waiting for it.
- * Scratch: the split-K partials and the tile list live in one fixed 8 MiB device array that
- * the library defines (every GPU that loads the library holds it until the process exits).
+ * Scratch: the FP64 partial sums of the row chunks (split-K partials) live in one fixed
+ * 8 MiB device array that the library defines (every GPU that loads the library holds it
+ * until the process exits).  The array holds 256 chunk-tile partials of 64 x 64 entries, so
+ * when the output has more than 128 such tiles (ceil(a/64) ceil(b/64) > 128, e.g. a and b
+ * both above 704) every tile gets a single chunk: each entry is then one FP32 accumulation
+ * over all n rows, with an error that grows with n instead of with the chunk length.
  * The first call on a device looks up that array's device address; make that first call
  * before any stream capture.  All calls share the array and it keeps the previous call's
  * contents, so calls whose work overlaps on the GPU (other streams, other threads) race and

@@ -19,6 +19,7 @@ from .spectral import (  # noqa: F401
     embed_rows,
     kmeans,
     kmeanspp_seed,
+    lambda_max,
     lap_apply,
     laplacian_csr,
     laplacian_dense,

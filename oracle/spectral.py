@@ -98,6 +98,29 @@ def laplacian_dense(L: Csr) -> np.ndarray:
     return np.diag(L.deg) - L.W().toarray()
 
 
+def lambda_max(L: Csr, dense_below: int = 2000) -> float:
+    """||L||_2 = the largest eigenvalue of the positive semidefinite L = D - W (Sec. II.A):
+    the scale against which eigenvalue errors and residual norms are stated.
+
+    n <= dense_below: dense symmetric eigendecomposition of L.  Larger graphs: Lanczos
+    (ARPACK through scipy.sparse.linalg.eigsh) for the largest eigenvalue, to 1e-12 relative.
+
+    Pinned by: closed forms (complete graph K_n and star S_n: n; path P_n: 2 + 2 cos(pi / n);
+    hypercube Q_d: 2 d), the Lanczos branch equal to the dense one on a DC-SBM graph, and
+    lambda_max <= 2 max_i d_i (Gershgorin).
+    """
+    if L.n == 0:
+        return 0.0
+    if L.n <= dense_below:
+        return float(np.linalg.eigvalsh(laplacian_dense(L))[-1])
+    import scipy.sparse.linalg as ssla
+
+    A = (sp.diags(L.deg) - L.W()).tocsr()
+    v0 = np.ones(L.n) + np.arange(L.n) % 7  # fixed start vector: the result is deterministic
+    w = ssla.eigsh(A, k=1, which="LA", tol=1e-12, v0=v0, return_eigenvectors=False)
+    return float(w[0])
+
+
 # --------------------------------------------------------------------------------------
 # LOBPCG (Sec. II.B, Sec. III, Sec. IV; Knyazev 2001)
 # --------------------------------------------------------------------------------------

@@ -185,6 +185,12 @@ namespace sc {
 namespace {
 constexpr size_t GRAM_STATIC_DOUBLES = (size_t)1 << 20;  // 8 MiB
 static __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
+// the largest block pair (1024 x 1024 columns: 16 x 16 tiles) still gets one row chunk per
+// tile, which the chunk clamp below relies on
+static_assert((size_t)((SC_GRAM_STATIC_MAX_COLS + TB - 1) / TB) *
+                      ((SC_GRAM_STATIC_MAX_COLS + TB - 1) / TB) * TB * TB <=
+                  GRAM_STATIC_DOUBLES,
+              "static Gram scratch too small for one chunk per tile");
 
 // Device address of g_gram_static for the current device, looked up once per device (the
 // host-side name of the array is only a stand-in, never a device address).

@@ -519,6 +519,9 @@ struct LobRun : RunBase {
   const T* Yc = nullptr;
   int kc = 0;
   long long ldyc = 0, x0_pitch = 0;
+  // FP64 host start block (used instead of an FP32 one when set) and FP64 host result block
+  const double* X0d = nullptr;
+  double* Xout64 = nullptr;
   double* Gy = nullptr;
   T* Ty = nullptr;
   static constexpr int kReorth = 16;
@@ -730,7 +733,21 @@ struct LobRun : RunBase {
     const float* src = nullptr;
     int rows = 0;
     bool dev_src = false;
-    if (X0) {
+    if (X0d) {
+      // an FP64 host start block: staged on the device, then narrowed to T (or copied)
+      rows = x0_rows > 0 ? std::min(x0_rows, n) : n;
+      double* tmp = get<double>((size_t)rows * K);
+      if (!tmp) return fail(c, SC_ENOMEM, "sc_lobpcg: start block");
+      const long long sp = x0_pitch > 0 ? x0_pitch : K;
+      CK(cudaMemcpy2DAsync(tmp, sizeof(double) * K, X0d, sizeof(double) * sp, sizeof(double) * K,
+                           rows, cudaMemcpyHostToDevice, st), "x0");
+      if constexpr (sizeof(T) == 8) {
+        CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, tmp, sizeof(double) * K, sizeof(double) * K, rows,
+                             cudaMemcpyDeviceToDevice, st), "x0");
+      } else {
+        CK((convert_mat<double, T>(st, rows, K, tmp, K, S, ld3)), "x0");
+      }
+    } else if (X0) {
       src = X0;
       rows = x0_rows > 0 ? std::min(x0_rows, n) : n;
     } else if (g->X && g->K == K && !o.cold) {
@@ -738,7 +755,9 @@ struct LobRun : RunBase {
       rows = n;
       dev_src = true;
     }
-    if (!src) {
+    if (X0d) {
+      // staged above
+    } else if (!src) {
       CK(gauss_block<T>(st, n, K, stream_key(o.seed, 1, 0), S, ld3), "x0");
     } else if constexpr (sizeof(T) == 4) {
       const long long sp = (!dev_src && x0_pitch > 0) ? x0_pitch : K;
@@ -749,7 +768,7 @@ struct LobRun : RunBase {
       const float* fsrc = src;
       float* tmp = nullptr;
       if (!dev_src) {
-        tmp = al.get<float>((size_t)rows * K);
+        tmp = get<float>((size_t)rows * K);  // tracked: freed with the run on every path
         if (!tmp) return fail(c, SC_ENOMEM, "sc_lobpcg: start block");
         const long long sp = x0_pitch > 0 ? x0_pitch : K;
         CK(cudaMemcpy2DAsync(tmp, sizeof(float) * K, src, sizeof(float) * sp, sizeof(float) * K,
@@ -757,8 +776,6 @@ struct LobRun : RunBase {
         fsrc = tmp;
       }
       CK((convert_mat<float, T>(st, rows, K, fsrc, K, S, ld3)), "x0");
-      CK(cudaStreamSynchronize(st), "x0");
-      al.put(tmp);
     }
     CK(cudaStreamSynchronize(st), "x0");
     CK(cudaEventRecord(ev0, st), "event");
@@ -978,6 +995,18 @@ struct LobRun : RunBase {
       CK(cudaMemcpy2DAsync(X_out, sizeof(float) * K, S, sizeof(T) * ld3, sizeof(float) * K, n,
                            cudaMemcpyDeviceToHost, st), "xout");
     }
+    if (Xout64) {
+      if constexpr (sizeof(T) == 8) {
+        CK(cudaMemcpy2DAsync(Xout64, sizeof(double) * K, S, sizeof(T) * ld3, sizeof(double) * K, n,
+                             cudaMemcpyDeviceToHost, st), "xout");
+      } else {
+        double* tmp = get<double>((size_t)n * K);
+        if (!tmp) return fail(c, SC_ENOMEM, "sc_lobpcg64: result block");
+        CK((convert_mat<T, double>(st, n, K, S, ld3, tmp, K)), "xout");
+        CK(cudaMemcpyAsync(Xout64, tmp, sizeof(double) * (size_t)n * K, cudaMemcpyDeviceToHost,
+                           st), "xout");
+      }
+    }
     CK(cudaStreamSynchronize(st), "sync");
     if (info) {
       info->K = K;
@@ -1112,6 +1141,29 @@ int sc_lobpcg(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const floa
   while (rc == SC_OK && !r->finished()) rc = r->pass();
   if (rc == SC_OK) rc = r->finish(X_out, info);
   delete r;
+  return rc;
+}
+
+int sc_lobpcg64(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const double* X0,
+                int32_t x0_rows, double* X_out, sc_eig_info* info) {
+  int rc = check_lobpcg_args(c, g, K, o);
+  if (rc != SC_OK) return rc;
+  cudaSetDevice(c->device);
+  if (o->prec == SC_PREC_FP64) {
+    LobRun<double> r(c, g, K, o, c->stream);
+    r.X0d = X0;
+    r.Xout64 = X_out;
+    rc = r.setup(nullptr, x0_rows);
+    while (rc == SC_OK && !r.finished()) rc = r.pass();
+    if (rc == SC_OK) rc = r.finish(nullptr, info);
+    return rc;
+  }
+  LobRun<float> r(c, g, K, o, c->stream);
+  r.X0d = X0;
+  r.Xout64 = X_out;
+  rc = r.setup(nullptr, x0_rows);
+  while (rc == SC_OK && !r.finished()) rc = r.pass();
+  if (rc == SC_OK) rc = r.finish(nullptr, info);
   return rc;
 }
 

@@ -92,6 +92,7 @@ def lib():
         "sc_graph_destroy": ([vp], None),
         "sc_lap_apply": ([vp, vp, C.c_int, C.c_int, vp, vp, C.c_int], C.c_int),
         "sc_lobpcg": ([vp, vp, C.c_int, C.POINTER(LobpcgOpts), vp, i32, vp, C.POINTER(EigInfo)], C.c_int),
+        "sc_lobpcg64": ([vp, vp, C.c_int, C.POINTER(LobpcgOpts), vp, i32, vp, C.POINTER(EigInfo)], C.c_int),
         "sc_embed_rows": ([vp, vp, i32, C.c_int, vp, C.c_int], C.c_int),
         "sc_kmeans": ([vp, vp, i32, C.c_int, C.c_int, C.c_int, u64, vp, C.c_int, vp, vp, vp,
                        C.POINTER(dbl), C.POINTER(C.c_int)], C.c_int),
@@ -275,6 +276,25 @@ def sc_lobpcg(ctx: Ctx, g: Graph, K, iters=20, tol_abs=0.0, tol_lock=0.0, prec=S
     x0 = None if X0 is None else np.ascontiguousarray(X0, dtype=np.float32)
     rc = lib().sc_lobpcg(ctx.h, g.h, K, C.byref(o), _ptr(x0)[0], int(x0_rows), _ptr(X)[0],
                          C.byref(info))
+    d = info.as_dict()
+    if rc != SC_OK:
+        err = ScError(rc, lib().sc_last_error(ctx.h).decode())
+        err.info = d
+        raise err
+    return d["lam"], d["resid"], X, d
+
+
+def sc_lobpcg64(ctx: Ctx, g: Graph, K, iters=20, tol_abs=0.0, tol_lock=0.0,
+                prec=SC_PREC_FP64, seed=0, cold=0, X0=None, x0_rows=0, want_X=True,
+                precond=SC_PRECOND_NONE):
+    """sc_lobpcg with an FP64 start block and an FP64 result block (host arrays)."""
+    o = LobpcgOpts(iters, tol_abs, tol_lock, prec, seed, cold, precond)
+    info = EigInfo()
+    n = sc_graph_info(g)[0]
+    X = np.empty((n, K), np.float64) if want_X else None
+    x0 = None if X0 is None else np.ascontiguousarray(X0, dtype=np.float64)
+    rc = lib().sc_lobpcg64(ctx.h, g.h, K, C.byref(o), _ptr(x0)[0], int(x0_rows), _ptr(X)[0],
+                           C.byref(info))
     d = info.as_dict()
     if rc != SC_OK:
         err = ScError(rc, lib().sc_last_error(ctx.h).decode())
@@ -467,7 +487,7 @@ def sc_server_create(ctx: Ctx, max_slots=8, queue_cap=64) -> Server:
 def sc_gram_static(A, B, C_out, stream=None):
     """C_out = A' B without any device allocation (see include/sc.h): A (n x a), B (n x b) are
     float32 CUDA tensors, C_out an (a x b) float64 CUDA tensor; issued on `stream` (a
-    cudaStream_t handle, default stream when None) without waiting for it."""
+    cudaStream_t handle; None = torch's current stream) without waiting for it."""
     import torch
 
     if A.dtype != torch.float32 or B.dtype != torch.float32 or C_out.dtype != torch.float64:
@@ -481,6 +501,8 @@ def sc_gram_static(A, B, C_out, stream=None):
     if (A.stride(1) != 1 and a > 1) or (B.stride(1) != 1 and b > 1) or \
             tuple(C_out.shape) != (a, b) or not C_out.is_contiguous():
         raise ValueError("sc_gram_static: row-major A, B and a contiguous (a x b) C_out expected")
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device).cuda_stream
     rc = lib().sc_gram_static(n, a, b, C.c_void_p(A.data_ptr()), int(A.stride(0)),
                               C.c_void_p(B.data_ptr()), int(B.stride(0)),
                               C.c_void_p(C_out.data_ptr()), C.c_void_p(stream) if stream else None)

@@ -204,17 +204,40 @@ def _lobpcg_pair(sc, ctx, n, K, iters, seed=0, prec=None, **kw):
 
 def test_lobpcg_fp64_check_mode_small(sc, ctx):
     g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 1000, 11, 20, prec=2)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert info["iters_done"] == ref.iters == 20
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-10
-    assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-6  # X returned as float32
+    assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-6  # sc_lobpcg returns X as float32
     np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
+
+
+@pytest.mark.parametrize("n,K", [(1000, 11), (5003, 19)])
+def test_lobpcg_fp64_check_mode_fp64_block(sc, ctx, n, K):
+    """The FP64 check mode with an FP64 start block and FP64 result (sc_lobpcg64): Ritz
+    values to 1e-10 lambda_max and the block's subspace to sin-theta <= 1e-10 against the
+    oracle from the same start block."""
+    g = W.dcsbm(n, K, seed=1)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    X0 = W.start_block(3, g.n, K)
+    lam, resid, X, info = sc.sc_lobpcg64(ctx, G, K, iters=20, prec=sc.SC_PREC_FP64, X0=X0)
+    ref = O.lobpcg(L, X0, 20)
+    lmax = O.lambda_max(L)
+    assert X.dtype == np.float64 and info["iters_done"] == ref.iters == 20
+    assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-10
+    assert O.sin_theta(ref.X, X) <= 1e-10
+    np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
+    # the mixed form through the same entry point: FP32 arithmetic, widened result
+    lam32, _, X32, _ = sc.sc_lobpcg64(ctx, G, K, iters=20, prec=sc.SC_PREC_MIXED, X0=X0)
+    ref32 = O.lobpcg(L, X0.astype(np.float32).astype(np.float64), 20)
+    assert np.max(np.abs(lam32 - ref32.lam)) / lmax <= 1e-5
+    assert O.sin_theta(ref32.X, X32) <= 1e-3
 
 
 @pytest.mark.parametrize("prec", [0, 1, 3])
 def test_lobpcg_fp32_small(sc, ctx, prec):
     g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 1000, 11, 20, prec=prec)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
     assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-3
     assert info["fallbacks"] == ref.fallbacks == 0
@@ -223,7 +246,7 @@ def test_lobpcg_fp32_small(sc, ctx, prec):
 @pytest.mark.parametrize("prec", [0, 3])
 def test_lobpcg_fp32_bench_size(sc, ctx, prec):
     g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 50000, 44, 20, prec=prec)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
     assert O.sin_theta(ref.X, X.astype(np.float64)) <= 1e-3
 
@@ -232,7 +255,7 @@ def test_lobpcg_fp64_wide_block(sc, ctx):
     """K = 140 in FP64: the pass's SpMM covers [R P] = 280 columns, wider than one launch of
     the SpMM kernel takes, so it runs in column chunks."""
     g, L, lam, resid, X, info, ref = _lobpcg_pair(sc, ctx, 3000, 140, 4, prec=2)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert info["iters_done"] == ref.iters == 4
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-10
     np.testing.assert_allclose(resid, ref.resid, rtol=1e-6, atol=1e-10 * lmax)
@@ -249,7 +272,7 @@ def test_lobpcg_jacobi_matches_oracle(sc, ctx, prec):
     lam, resid, X, info = sc.sc_lobpcg(ctx, G, 11, iters=20, prec=prec, X0=X0,
                                        precond=sc.SC_PRECOND_JACOBI)
     ref = O.lobpcg(L, X0.astype(np.float32).astype(np.float64), 20, precond="jacobi")
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     tol = 1e-10 if prec == 2 else 1e-5
     assert np.max(np.abs(lam - ref.lam)) / lmax <= tol
     assert O.sin_theta(ref.X, X.astype(np.float64)) <= (1e-6 if prec == 2 else 1e-3)
@@ -279,7 +302,7 @@ def test_lobpcg_ragged_sizes(sc, ctx):
         X0 = W.start_block(2, n, K)
         lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=5, prec=2, X0=X0)
         ref = O.lobpcg(L, X0.astype(np.float32).astype(np.float64), 5)
-        lmax = 2 * L.deg.max()
+        lmax = O.lambda_max(L)
         assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-9, (n, K)
 
 
@@ -454,7 +477,7 @@ def test_partition_wide_blocks(sc, ctx, n, K):
     G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
     lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=6, seed=1, cold=1)
     ref = O.lobpcg(L, W.start_block(1, g.n, K).astype(np.float32).astype(np.float64), 6)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
     labels, info = sc.sc_partition(ctx, G, K, K, iters=6, seed=1)
     assert labels.min() >= 0 and labels.max() < K
@@ -512,9 +535,9 @@ def test_stream_snowball_grows_and_warm_starts(sc, ctx):
         Xw = np.zeros((cur.n, 8))
         Xw[: prev.n] = X
         lam, resid, X, info = sc.sc_lobpcg(ctx, G, 8, iters=10, prec=2)
-        ref = O.lobpcg(O.laplacian_csr(cur.n, cur.src, cur.dst), Xw, 10)
-        lmax = 2 * ref.lam.max() + 1
-        assert np.max(np.abs(lam - ref.lam)) <= 1e-8 * max(lmax, 1)
+        Lc = O.laplacian_csr(cur.n, cur.src, cur.dst)
+        ref = O.lobpcg(Lc, Xw, 10)
+        assert np.max(np.abs(lam - ref.lam)) <= 1e-10 * O.lambda_max(Lc)
 
 
 # ------------------------------------------------------------------ CPQR assignment (f2)
@@ -565,7 +588,7 @@ def test_lobpcg_blocks_matches_oracle_fp64(sc, ctx):
     lam, resid, X, info = sc.sc_lobpcg_blocks(ctx, G, 9, 3, iters=20, prec=sc.SC_PREC_FP64,
                                               X0=X0)
     ref = O.lobpcg_blocks(L, X0.astype(np.float32).astype(np.float64), 3, 20)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert info["iters_done"] == ref.iters == 60
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-9
     np.testing.assert_allclose(resid, ref.resid, rtol=1e-5, atol=1e-9 * lmax)
@@ -607,7 +630,7 @@ def test_lobpcg_blocks_ragged_last_block_and_device_cpqr(sc, ctx):
     X0 = W.start_block(8, g.n, 10)
     lam, resid, X, info = sc.sc_lobpcg_blocks(ctx, G, 10, 4, iters=20, X0=X0)
     ref = O.lobpcg_blocks(L, X0.astype(np.float32).astype(np.float64), 4, 20)
-    lmax = 2 * L.deg.max()
+    lmax = O.lambda_max(L)
     assert info["iters_done"] == ref.iters == 60 and len(lam) == 10
     assert np.max(np.abs(lam - ref.lam)) / lmax <= 1e-5
     Xd = torch.from_numpy(X).cuda()

@@ -589,3 +589,150 @@ def test_eigengap_reading_edge_cases():
     # increments at or below the floor count as zero; input order does not matter
     assert O.eigengap_k([3.0, 1e-12, 0.0, 2e-12], floor=1e-9) == 3
     assert O.eigengap_k([3.0, 1e-12, 0.0, 2e-12], floor=0.0) == 3
+
+
+# ---------------------------------------------------------------- lambda_max (the tolerance scale)
+
+
+def test_lambda_max_closed_forms_and_lanczos():
+    cases = [(_graph_complete(15), 15, 15.0), (_graph_star(20), 20, 20.0),
+             (_graph_path(30), 30, 2 + 2 * math.cos(math.pi / 30)),
+             (_graph_hypercube(5), 32, 10.0)]
+    for (src, dst), n, ref in cases:
+        L = O.laplacian_csr(n, src, dst)
+        assert abs(O.lambda_max(L) - ref) <= 1e-12 * ref
+        assert abs(O.lambda_max(L, dense_below=0) - ref) <= 1e-10 * ref  # Lanczos branch
+    g = W.dcsbm(1500, 9, seed=2)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    dense = O.lambda_max(L)
+    assert abs(O.lambda_max(L, dense_below=0) - dense) <= 1e-10 * dense
+    assert dense <= 2 * L.deg.max()
+
+
+# ---------------------------------------------------------------- LOBPCG trajectory vs SciPy
+
+
+def _scipy_history(L, X0, iters, M=None, Y=None):
+    """Ritz values of scipy.sparse.linalg.lobpcg (the implementation the paper ran, Sec. II.B)
+    before the loop and after each of `iters` passes, every column active (tol = 1e-300)."""
+    import warnings
+
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as ssla
+
+    A = (sp.diags(L.deg) - L.W()).tocsr()
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        _, _, lh, rh = ssla.lobpcg(A, X0.copy(), M=M, Y=Y, largest=False, tol=1e-300,
+                                   maxiter=iters, retLambdaHistory=True,
+                                   retResidualNormsHistory=True)
+    lams, rhos = [], []
+    for i in range(iters + 1):
+        o = np.argsort(np.asarray(lh[i]))
+        lams.append(np.asarray(lh[i])[o])
+        rhos.append(np.asarray(rh[i])[o] if i < iters else None)
+    return lams, rhos
+
+
+def _oracle_history(mod, L, X0, iters, **kw):
+    """Ritz values before the loop and after each pass; residual norms before each pass."""
+    res = mod.lobpcg(L, X0, iters, keep_history=True, **kw)
+    return [h[0] for h in res.history] + [res.lam], [h[1] for h in res.history] + [None]
+
+
+def _worst(ours, ref):
+    (la, ra), (lb, rb) = ours, ref
+    w = max(np.max(np.abs(a - b)) for a, b in zip(la, lb))
+    return max([w] + [np.max(np.abs(a - b)) for a, b in zip(ra, rb) if a is not None])
+
+
+def _trajectory_case(kind):
+    if kind == "plain":
+        g = W.dcsbm(2000, 11, seed=0)
+        L = O.laplacian_csr(g.n, g.src, g.dst)
+        return L, W.start_block(0, g.n, 11), {}, {}
+    g = W.dcsbm(1500, 9, seed=3)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    X0 = W.start_block(4, g.n, 9)
+    if kind == "jacobi":
+        import scipy.sparse.linalg as ssla
+
+        t = np.where(L.deg > 0, L.deg, 1.0)
+        M = ssla.LinearOperator((g.n, g.n), matvec=lambda v: v.reshape(g.n, -1)[:, 0] / t,
+                                matmat=lambda V: V / t[:, None], dtype=float)
+        return L, X0, {"precond": "jacobi"}, {"M": M}
+    Yc = np.linalg.eigh(O.laplacian_dense(L))[1][:, :3]  # hard locking against 3 eigenvectors
+    return L, X0[:, 3:], {"constraint": Yc}, {"Y": Yc}
+
+
+@pytest.mark.parametrize("kind", ["plain", "jacobi", "constraint"])
+def test_lobpcg_trajectory_matches_scipy_lobpcg(kind):
+    """Pass by pass, the oracle's Ritz values equal those of SciPy's lobpcg from the same
+    start block (unpreconditioned, Jacobi-preconditioned, and constrained to the complement
+    of exact eigenvectors), while the K/K+1 gap is open and nothing has converged: the
+    orthonormal-basis form spans the same trial subspaces as Knyazev's [X W P]."""
+    L, X0, kw, skw = _trajectory_case(kind)
+    lmax = O.lambda_max(L)
+    ev = np.linalg.eigvalsh(O.laplacian_dense(L))
+    K = X0.shape[1] + (3 if kind == "constraint" else 0)
+    assert ev[K] - ev[K - 1] > 1e-2  # the gap is open
+    ours = _oracle_history(O, L, X0, 10, **kw)
+    ref = _scipy_history(L, X0, 10, **skw)
+    assert len(ours[0]) == len(ref[0]) == 11
+    for i, (a, b) in enumerate(zip(ours[0], ref[0])):
+        assert np.max(np.abs(a - b)) <= 1e-10 * lmax, (kind, "lambda", i)
+    for i, (a, b) in enumerate(zip(ours[1][:10], ref[1][:10])):
+        assert np.max(np.abs(a - b)) <= 1e-10 * lmax, (kind, "residual norm", i)
+    assert np.max(ours[0][-1] - ev[3 if kind == "constraint" else 0:K]) > 1e-6 * lmax
+
+
+MUTATIONS = [
+    ("P drops P_a Y_P", "Pn = Pn + blocks[2][0] @ Yp", "Pn = Pn"),
+    ("X update without P", "X = X @ Yx + Pn", "X = X @ Yx + Ra @ Yr"),
+    ("LP image drops LP_a Y_P", "LPn = LPn + blocks[2][1] @ Yp", "LPn = LPn"),
+    ("residual sign", "R = LX - X * lam[None, :]\n        rho", "R = LX + X * lam[None, :]\n        rho"),
+    ("Y_R taken from the X rows", "Yx, Yr = Y[:K], Y[K:K + ka]", "Yx, Yr = Y[:K], Y[:ka]"),
+    ("largest Ritz pairs kept", "return theta[:K], Y", "return theta[-K:], Y"),
+    ("image of the unprojected residual", "LRa = lap_apply(L, Ra)",
+     "LRa = lap_apply(L, R[:, act]) if True else None"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_trajectory_pin_catches_planted_mistakes(name, old, new):
+    """A plausible mistake planted in a copy of the oracle's source (a dropped term, a sign,
+    a wrong block of Y, the wrong end of the spectrum, a missing back-transformation) makes
+    the pass-by-pass comparison with SciPy fail."""
+    import importlib
+    import sys
+    import types
+
+    src = open(importlib.import_module("oracle.spectral").__file__).read()
+    assert src.count(old) == 1, name
+    mod = types.ModuleType("oracle_mutant")
+    sys.modules["oracle_mutant"] = mod  # dataclasses look their module up while being built
+    try:
+        exec(compile(src.replace(old, new), "oracle_mutant", "exec"), mod.__dict__)
+    finally:
+        del sys.modules["oracle_mutant"]
+    L, X0, kw, skw = _trajectory_case("plain")
+    lmax = O.lambda_max(L)
+    ref = _scipy_history(L, X0, 10)
+    try:
+        ours = _oracle_history(mod, L, X0, 10, **kw)
+    except Exception:
+        return  # the mutant breaks down outright: caught
+    assert _worst(ours, ref) > 1e-10 * lmax, name
+
+
+@pytest.mark.parametrize("n,K", [(1000, 11), (50000, 44)])
+def test_rounding_safeguards_do_not_fire_on_the_parity_configs(n, K):
+    """The rounding-level safeguards (residual and direction columns at the rounding floor,
+    dependent residual columns dropped below PIVOT_TOL, the P block dropped on a Cholesky
+    breakdown) fire on no pass of the 20-pass runs the GPU parity tests compare: on these
+    inputs the oracle is exactly the textbook iteration."""
+    g = W.dcsbm(n, K, seed=0)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    X0 = W.start_block(0, g.n, K).astype(np.float32).astype(np.float64)
+    res = O.lobpcg(L, X0, 20)
+    assert res.iters == 20 and res.dropped == 0 and res.fallbacks == 0

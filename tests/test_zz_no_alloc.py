@@ -49,6 +49,26 @@ def test_static_gram_matches_sc_gram_twice_in_a_row(sc):
         ctx.close()
 
 
+def test_static_gram_allocates_nothing(sc):
+    """After a first call (which looks up the array's device address), further calls leave
+    the device's free memory and torch's reserved pool unchanged: no allocation happens."""
+    import torch
+
+    rng = np.random.default_rng(7)
+    A = torch.from_numpy(rng.standard_normal((20000, 40)).astype(np.float32)).cuda()
+    B = torch.from_numpy(rng.standard_normal((20000, 90)).astype(np.float32)).cuda()
+    Cd = torch.empty((40, 90), dtype=torch.float64, device="cuda")
+    sc.sc_gram_static(A, B, Cd)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    res0 = torch.cuda.memory_reserved()
+    for _ in range(5):
+        sc.sc_gram_static(A, B, Cd)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_reserved() == res0
+
+
 def test_static_gram_rejects_oversized_blocks(sc):
     import torch
 
