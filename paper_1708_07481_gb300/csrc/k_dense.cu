@@ -799,217 +799,20 @@ __global__ void __launch_bounds__(RR_NT)
 }
 
 
-// ---------------------------------------------------------------------------------------
-// Rayleigh-Ritz, register-slot form for m <= 32 NS: the same four steps as k_rr_eig with
-// less synchronization.
-//  1. Tridiagonalization with a few threads per row and two barriers per Householder step:
-//     the owners of a row form its entries of p = beta A v and apply the rank-2 update to
-//     them; the reflector scalars are formed by every thread from one block sum.  The
-//     reflector of step k is stored in row k.
-//  2. Multisection on Sturm counts as in k_rr_eig, converged to eps ||T|| (the accuracy the
-//     reduction itself has).
-//  3. Inverse iteration: LU with partial pivoting of T - sigma I fused with the forward
-//     elimination of the right-hand side (only U is stored), back substitution; two sweeps,
-//     each followed by a block Cholesky-QR through blk_ldl_inv.
-//  4. Back-transformation with one warp per column pair, no barriers.
-template <typename T, int NS>
-__device__ __forceinline__ T slot_sel(const T (&a)[NS], int u) {
-  T r = a[0];
-#pragma unroll
-  for (int q = 1; q < NS; ++q)
-    if (q == u) r = a[q];
-  return r;
-}
-
-// Threads per row in the tridiagonalization of an m x m matrix by nt threads: the largest
-// of 8, 4, 2, 1 with m * tpr <= nt.
-__host__ __device__ inline int rr_tpr(int m, int nt) {
-  int t = 8;
-  while (t > 1 && m * t > nt) t >>= 1;
-  return t;
-}
-// Row stride of the matrix: a multiple of tpr, at least m, with an odd quotient, so that the
-// tpr parts of 32 / tpr consecutive rows fall in distinct shared-memory banks.  At most
-// m + 2 tpr - 1 <= m + 15.
-__host__ __device__ inline int rr_lda(int m, int tpr) {
-  int l = (m + tpr - 1) / tpr * tpr;
-  if ((l / tpr) % 2 == 0) l += tpr;
-  return l;
-}
-// Barrier 1 over the first n threads of the block (n a multiple of 32).
-__device__ __forceinline__ void rr_named_sync(int n) {
-  asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
-}
-
-template <typename T, int NS, int NW, bool SM>
-__global__ void __launch_bounds__(NW * 32)
-    k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
-                 double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
-                 int* status, int* pflag, int mP, int* nfallback) {
-  constexpr int NT = NW * 32;
+// ---- phases 2 and 3 of the register-slot Rayleigh-Ritz kernels (shared) ------------------
+// Phase 2: Gershgorin bounds of the tridiagonal T = (d, e); the K smallest eigenvalues of T by
+// 17-point multisection on Sturm counts, 16 lanes per eigenvalue, into lam[K].  Outputs the
+// norm bound tnorm and the pivot floor pivmin that phase 3 uses.  NT threads take part; red
+// holds 3 NW per-warp slots followed by the scalar slots RS ...
+template <typename T, int NT>
+__device__ void rr_phase_eigvals(int m, int K, const T* __restrict__ d, const T* __restrict__ e,
+                                 T* __restrict__ e2, T* red, T* __restrict__ lam, int* status,
+                                 T& tnorm, T& pivmin) {
+  constexpr int NW = NT / 32;
   constexpr unsigned FULL = 0xffffffffu;
-  const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* d = (T*)smraw;     // m
-  T* e = d + m;         // m
-  T* beta = e + m;      // m
-  T* e2 = beta + m;     // m
-  T* Pb = e2 + m;       // 2 m: p of the current step (double-buffered)
-  T* lam = Pb + 2 * m;  // K
-  T* shift = lam + K;   // K
-  T* dd = shift + K;    // K pivots of the block Cholesky
-  T* cbuf = dd + K;     // 2 K
-  T* wv = cbuf + 2 * K; // K
-  T* coef = wv + K;     // K
-  T* red = coef + K;    // 3 NW per-warp parts, then scalar slots RS ..
-  T* nxt = red + 3 * NW + 8;
-  T* A = SM ? nxt : Ag;                             // m x m (row stride m)
-  const int lda = rr_lda(m, rr_tpr(m, NT));  // row stride of the matrix
-  T* Z = SM ? A + (size_t)m * lda : Zg;             // m x K
-  T* U = SM ? Z + (size_t)m * K : Ug;               // 3 m K
-  T* Gs = SM ? U + (size_t)3 * m * K : Gsg;         // K x K
+  constexpr int RS = 3 * NW;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int RS = 3 * NW;  // red[RS + 0..4]: lo, hi, max e^2, min pivot, MGS scale
-
-  {
-    T gmax = 0;  // Gershgorin bound of A: the largest row sum of |a_ij|
-    for (int i = warp; i < m; i += NW) {
-      T rs = 0;
-      for (int j = lane; j < m; j += 32) {
-        const T a = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
-        A[i * lda + j] = a;
-        rs += fabs(a);
-      }
-      gmax = fmax(gmax, warp_sum(rs));
-    }
-    if (lane == 0) red[warp] = gmax;
-    __syncthreads();
-    lift_dropped<T>(m, K, G, ldg, A, lda, red, NW);
-    __syncthreads();
-  }
-  RR_MARK(0);
-
-  // ---- 1. tridiagonalization (Golub & Van Loan Alg. 8.3.1), two barriers per step
-  // tpr threads per row: thread t < ntri owns row i = t / tpr and, of the columns j that step
-  // k touches, those with j = k + 1 + q (mod tpr), q = t % tpr.  Step k:
-  //  (a) the owners of rows j > k publish x_j = a_jk (their own entry) and per-warp sums of
-  //      x_j^2 over j > k + 1;
-  //  (b) every thread forms the reflector scalars (mu, v0, beta, e_k) from sigma^2 and x_{k+1};
-  //      v = e_{k+1} + x / v0 on j > k + 1 goes to row k for the back-transformation;
-  //  (c) p_i = beta (A v)_i on the owned rows (parts over q combined by shuffles), published
-  //      with per-warp sums of p_i v_i;
-  //  (d) w = p - (beta / 2)(p'v) v and the rank-2 update A -= v w' + w v' of the owned
-  //      entries, with v_j and w_j formed on the fly from x_j and p_j.
-  // The entry a_j,k+1 that row j's owner reads in the next step's (a) is updated by that same
-  // thread in (d), so no barrier separates (d) from the next (a).
-  {
-    const int tpr = rr_tpr(m, NT);
-    const int ntri = (m * tpr + 31) / 32 * 32;
-    const int nwt = ntri / 32;
-    const int ri = tid / tpr, q = tid % tpr;
-    const bool own = tid < ntri && ri < m;
-    T* __restrict__ pvec = e2;  // p of the current step (e2 is free until step 2)
-    if (tid < ntri) {
-      for (int k = 0; k + 2 < m; ++k) {
-        const int k1 = k + 1;
-        T* __restrict__ xs = Pb + (k & 1) * m;  // x of this step (double-buffered)
-        // (a)
-        T xi = 0, s2 = 0;
-        if (own && q == 0) {
-          if (ri >= k1) {
-            xi = A[ri * lda + k];
-            xs[ri] = xi;
-            if (ri > k1) s2 = xi * xi;
-          } else if (ri == k) {
-            d[k] = A[k * lda + k];
-          }
-        }
-        s2 = warp_sum(s2);
-        if (lane == 0) red[warp] = s2;
-        rr_named_sync(ntri);
-        // (b)
-        const T sg = warp_sum(lane < nwt ? red[lane] : (T)0);
-        const T x0 = xs[k1];
-        T bet = 0, iv0 = 0, ek = x0;
-        if (sg != (T)0) {
-          // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
-          // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
-          const T mu = sqrt(x0 * x0 + sg);
-          const T v0 = x0 + copysign(mu, x0);
-          iv0 = (T)1 / v0;
-          bet = (T)2 / ((T)1 + sg * iv0 * iv0);
-          ek = -copysign(mu, x0);
-        }
-        if (tid == 0) {
-          e[k] = ek;
-          beta[k] = bet;
-        }
-        if (own && q == 0 && ri > k1) A[k * lda + ri] = xi * iv0;
-        // (c)
-        const bool act = own && ri >= k1;
-        T sacc = 0;
-        if (act) {
-          const T* __restrict__ ra = A + ri * lda;
-          T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-          int j = k1 + 1 + q;
-          for (; j + 3 * tpr < m; j += 4 * tpr) {
-            s0 = fma(ra[j], xs[j], s0);
-            s1 = fma(ra[j + tpr], xs[j + tpr], s1);
-            s2 = fma(ra[j + 2 * tpr], xs[j + 2 * tpr], s2);
-            s3 = fma(ra[j + 3 * tpr], xs[j + 3 * tpr], s3);
-          }
-          for (; j < m; j += tpr) s0 = fma(ra[j], xs[j], s0);
-          sacc = (s0 + s1) + (s2 + s3);
-        }
-        for (int o = 1; o < tpr; o <<= 1) sacc += __shfl_xor_sync(FULL, sacc, o);
-        T pi = 0, vi = 0, pvp = 0;
-        if (act) {
-          pi = bet * (A[ri * lda + k1] + iv0 * sacc);
-          vi = ri == k1 ? (T)1 : xs[ri] * iv0;
-          if (q == 0) {
-            pvec[ri] = pi;
-            pvp = pi * vi;
-          }
-        }
-        pvp = warp_sum(pvp);
-        if (lane == 0) red[NW + warp] = pvp;
-        rr_named_sync(ntri);
-        // (d)
-        const T pv = warp_sum(lane < nwt ? red[NW + lane] : (T)0);
-        const T kc = bet * (T)0.5 * pv;
-        if (act) {
-          const T wi = pi - kc * vi;
-          T* __restrict__ ra = A + ri * lda;
-          int j = k1 + q;
-          if (q == 0) {  // column k + 1, where v_j = 1
-            ra[k1] = ra[k1] - vi * (pvec[k1] - kc) - wi;
-            j += tpr;
-          }
-#pragma unroll 4
-          for (; j < m; j += tpr) {
-            const T vj = xs[j] * iv0;
-            const T wj = pvec[j] - kc * vj;
-            ra[j] = ra[j] - vi * wj - wi * vj;
-          }
-        }
-      }
-      rr_named_sync(ntri);
-      if (tid == 0) {
-        // the trailing 2 x 2 block of T (or the 1 x 1 matrix)
-        if (m >= 2) {
-          d[m - 2] = A[(m - 2) * lda + (m - 2)];
-          e[m - 2] = A[(m - 1) * lda + (m - 2)];
-          d[m - 1] = A[(m - 1) * lda + (m - 1)];
-        } else {
-          d[0] = A[0];
-        }
-        e[m - 1] = 0;
-      }
-    }
-  }
-  __syncthreads();
-  RR_MARK(1);
-
+  (void)FULL;
   // ---- 2. Gershgorin bounds; 17-point multisection, 16 lanes per eigenvalue
   {
     T lo_p = (T)3e38, hi_p = (T)-3e38, emax = 0;
@@ -1046,8 +849,8 @@ __global__ void __launch_bounds__(NW * 32)
     }
     __syncthreads();
   }
-  const T tnorm = max(fabs(red[RS]), fabs(red[RS + 1]));
-  const T pivmin = Lim<T>::tiny() * max((T)1, red[RS + 2]);
+  tnorm = max(fabs(red[RS]), fabs(red[RS + 1]));
+  pivmin = Lim<T>::tiny() * max((T)1, red[RS + 2]);
   const T glo = red[RS] - (T)2 * Lim<T>::eps() * tnorm - pivmin;
   const T ghi = red[RS + 1] + (T)2 * Lim<T>::eps() * tnorm + pivmin;
   const T abstol = Lim<T>::eps() * tnorm;
@@ -1073,8 +876,21 @@ __global__ void __launch_bounds__(NW * 32)
     }
   }
   __syncthreads();
-  RR_MARK(2);
+}
 
+// Phase 3: eigenvectors of T for the eigenvalues lam[K] by inverse iteration into Z (m x K):
+// LU with partial pivoting of T - sigma I fused with the forward elimination, back
+// substitution, RR_SWEEPS sweeps, each followed by a block Cholesky-QR (in-order Gram-Schmidt
+// when a tight cluster breaks it).  U (3 m K), Gs (K x K), shift/dd/wv/coef (K), cbuf (2 K)
+// are scratch.
+template <typename T, int NT>
+__device__ void rr_phase_eigvecs(int m, int K, const T* __restrict__ d, const T* __restrict__ e,
+                                 const T* __restrict__ lam, T* __restrict__ shift, T* Z, T* U,
+                                 T* Gs, T* dd, T* cbuf, T* wv, T* coef, T* red, T tnorm,
+                                 T pivmin) {
+  constexpr int NW = NT / 32;
+  constexpr int RS = 3 * NW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // ---- 3. inverse iteration
   const T sep = (T)10 * Lim<T>::eps() * tnorm + pivmin;
   if (tid == 0) {
@@ -1244,6 +1060,225 @@ __global__ void __launch_bounds__(NW * 32)
     }
   }
 #undef UF
+}
+
+// ---------------------------------------------------------------------------------------
+// Rayleigh-Ritz, register-slot form for m <= 32 NS: the same four steps as k_rr_eig with
+// less synchronization.
+//  1. Tridiagonalization with a few threads per row and two barriers per Householder step:
+//     the owners of a row form its entries of p = beta A v and apply the rank-2 update to
+//     them; the reflector scalars are formed by every thread from one block sum.  The
+//     reflector of step k is stored in row k.
+//  2. Multisection on Sturm counts as in k_rr_eig, converged to eps ||T|| (the accuracy the
+//     reduction itself has).
+//  3. Inverse iteration: LU with partial pivoting of T - sigma I fused with the forward
+//     elimination of the right-hand side (only U is stored), back substitution; two sweeps,
+//     each followed by a block Cholesky-QR through blk_ldl_inv.
+//  4. Back-transformation with one warp per column pair, no barriers.
+template <typename T, int NS>
+__device__ __forceinline__ T slot_sel(const T (&a)[NS], int u) {
+  T r = a[0];
+#pragma unroll
+  for (int q = 1; q < NS; ++q)
+    if (q == u) r = a[q];
+  return r;
+}
+
+// Threads per row in the tridiagonalization of an m x m matrix by nt threads: the largest
+// of 8, 4, 2, 1 with m * tpr <= nt.
+__host__ __device__ inline int rr_tpr(int m, int nt) {
+  int t = 8;
+  while (t > 1 && m * t > nt) t >>= 1;
+  return t;
+}
+// Row stride of the matrix: a multiple of tpr, at least m, with an odd quotient, so that the
+// tpr parts of 32 / tpr consecutive rows fall in distinct shared-memory banks.  At most
+// m + 2 tpr - 1 <= m + 15.
+__host__ __device__ inline int rr_lda(int m, int tpr) {
+  int l = (m + tpr - 1) / tpr * tpr;
+  if ((l / tpr) % 2 == 0) l += tpr;
+  return l;
+}
+// Barrier 1 over the first n threads of the block (n a multiple of 32).
+__device__ __forceinline__ void rr_named_sync(int n) {
+  asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
+template <typename T, int NS, int NW, bool SM>
+__global__ void __launch_bounds__(NW * 32)
+    k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
+                 double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
+                 int* status, int* pflag, int mP, int* nfallback) {
+  constexpr int NT = NW * 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* d = (T*)smraw;     // m
+  T* e = d + m;         // m
+  T* beta = e + m;      // m
+  T* e2 = beta + m;     // m
+  T* Pb = e2 + m;       // 2 m: p of the current step (double-buffered)
+  T* lam = Pb + 2 * m;  // K
+  T* shift = lam + K;   // K
+  T* dd = shift + K;    // K pivots of the block Cholesky
+  T* cbuf = dd + K;     // 2 K
+  T* wv = cbuf + 2 * K; // K
+  T* coef = wv + K;     // K
+  T* red = coef + K;    // 3 NW per-warp parts, then scalar slots RS ..
+  T* nxt = red + 3 * NW + 8;
+  T* A = SM ? nxt : Ag;                             // m x m (row stride m)
+  const int lda = rr_lda(m, rr_tpr(m, NT));  // row stride of the matrix
+  T* Z = SM ? A + (size_t)m * lda : Zg;             // m x K
+  T* U = SM ? Z + (size_t)m * K : Ug;               // 3 m K
+  T* Gs = SM ? U + (size_t)3 * m * K : Gsg;         // K x K
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // red[3 NW + 0..4]: lo, hi, max e^2, min pivot, MGS scale (the shared phases use them)
+
+  {
+    T gmax = 0;  // Gershgorin bound of A: the largest row sum of |a_ij|
+    for (int i = warp; i < m; i += NW) {
+      T rs = 0;
+      for (int j = lane; j < m; j += 32) {
+        const T a = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+        A[i * lda + j] = a;
+        rs += fabs(a);
+      }
+      gmax = fmax(gmax, warp_sum(rs));
+    }
+    if (lane == 0) red[warp] = gmax;
+    __syncthreads();
+    lift_dropped<T>(m, K, G, ldg, A, lda, red, NW);
+    __syncthreads();
+  }
+  RR_MARK(0);
+
+  // ---- 1. tridiagonalization (Golub & Van Loan Alg. 8.3.1), two barriers per step
+  // tpr threads per row: thread t < ntri owns row i = t / tpr and, of the columns j that step
+  // k touches, those with j = k + 1 + q (mod tpr), q = t % tpr.  Step k:
+  //  (a) the owners of rows j > k publish x_j = a_jk (their own entry) and per-warp sums of
+  //      x_j^2 over j > k + 1;
+  //  (b) every thread forms the reflector scalars (mu, v0, beta, e_k) from sigma^2 and x_{k+1};
+  //      v = e_{k+1} + x / v0 on j > k + 1 goes to row k for the back-transformation;
+  //  (c) p_i = beta (A v)_i on the owned rows (parts over q combined by shuffles), published
+  //      with per-warp sums of p_i v_i;
+  //  (d) w = p - (beta / 2)(p'v) v and the rank-2 update A -= v w' + w v' of the owned
+  //      entries, with v_j and w_j formed on the fly from x_j and p_j.
+  // The entry a_j,k+1 that row j's owner reads in the next step's (a) is updated by that same
+  // thread in (d), so no barrier separates (d) from the next (a).
+  {
+    const int tpr = rr_tpr(m, NT);
+    const int ntri = (m * tpr + 31) / 32 * 32;
+    const int nwt = ntri / 32;
+    const int ri = tid / tpr, q = tid % tpr;
+    const bool own = tid < ntri && ri < m;
+    T* __restrict__ pvec = e2;  // p of the current step (e2 is free until step 2)
+    if (tid < ntri) {
+      for (int k = 0; k + 2 < m; ++k) {
+        const int k1 = k + 1;
+        T* __restrict__ xs = Pb + (k & 1) * m;  // x of this step (double-buffered)
+        // (a)
+        T xi = 0, s2 = 0;
+        if (own && q == 0) {
+          if (ri >= k1) {
+            xi = A[ri * lda + k];
+            xs[ri] = xi;
+            if (ri > k1) s2 = xi * xi;
+          } else if (ri == k) {
+            d[k] = A[k * lda + k];
+          }
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) red[warp] = s2;
+        rr_named_sync(ntri);
+        // (b)
+        const T sg = warp_sum(lane < nwt ? red[lane] : (T)0);
+        const T x0 = xs[k1];
+        T bet = 0, iv0 = 0, ek = x0;
+        if (sg != (T)0) {
+          // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
+          // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
+          const T mu = sqrt(x0 * x0 + sg);
+          const T v0 = x0 + copysign(mu, x0);
+          iv0 = (T)1 / v0;
+          bet = (T)2 / ((T)1 + sg * iv0 * iv0);
+          ek = -copysign(mu, x0);
+        }
+        if (tid == 0) {
+          e[k] = ek;
+          beta[k] = bet;
+        }
+        if (own && q == 0 && ri > k1) A[k * lda + ri] = xi * iv0;
+        // (c)
+        const bool act = own && ri >= k1;
+        T sacc = 0;
+        if (act) {
+          const T* __restrict__ ra = A + ri * lda;
+          T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+          int j = k1 + 1 + q;
+          for (; j + 3 * tpr < m; j += 4 * tpr) {
+            s0 = fma(ra[j], xs[j], s0);
+            s1 = fma(ra[j + tpr], xs[j + tpr], s1);
+            s2 = fma(ra[j + 2 * tpr], xs[j + 2 * tpr], s2);
+            s3 = fma(ra[j + 3 * tpr], xs[j + 3 * tpr], s3);
+          }
+          for (; j < m; j += tpr) s0 = fma(ra[j], xs[j], s0);
+          sacc = (s0 + s1) + (s2 + s3);
+        }
+        for (int o = 1; o < tpr; o <<= 1) sacc += __shfl_xor_sync(FULL, sacc, o);
+        T pi = 0, vi = 0, pvp = 0;
+        if (act) {
+          pi = bet * (A[ri * lda + k1] + iv0 * sacc);
+          vi = ri == k1 ? (T)1 : xs[ri] * iv0;
+          if (q == 0) {
+            pvec[ri] = pi;
+            pvp = pi * vi;
+          }
+        }
+        pvp = warp_sum(pvp);
+        if (lane == 0) red[NW + warp] = pvp;
+        rr_named_sync(ntri);
+        // (d)
+        const T pv = warp_sum(lane < nwt ? red[NW + lane] : (T)0);
+        const T kc = bet * (T)0.5 * pv;
+        if (act) {
+          const T wi = pi - kc * vi;
+          T* __restrict__ ra = A + ri * lda;
+          int j = k1 + q;
+          if (q == 0) {  // column k + 1, where v_j = 1
+            ra[k1] = ra[k1] - vi * (pvec[k1] - kc) - wi;
+            j += tpr;
+          }
+#pragma unroll 4
+          for (; j < m; j += tpr) {
+            const T vj = xs[j] * iv0;
+            const T wj = pvec[j] - kc * vj;
+            ra[j] = ra[j] - vi * wj - wi * vj;
+          }
+        }
+      }
+      rr_named_sync(ntri);
+      if (tid == 0) {
+        // the trailing 2 x 2 block of T (or the 1 x 1 matrix)
+        if (m >= 2) {
+          d[m - 2] = A[(m - 2) * lda + (m - 2)];
+          e[m - 2] = A[(m - 1) * lda + (m - 2)];
+          d[m - 1] = A[(m - 1) * lda + (m - 1)];
+        } else {
+          d[0] = A[0];
+        }
+        e[m - 1] = 0;
+      }
+    }
+  }
+  __syncthreads();
+  RR_MARK(1);
+
+  T tnorm, pivmin;
+  rr_phase_eigvals<T, NT>(m, K, d, e, e2, red, lam, status, tnorm, pivmin);
+  RR_MARK(2);
+
+  rr_phase_eigvecs<T, NT>(m, K, d, e, lam, shift, Z, U, Gs, dd, cbuf, wv, coef, red, tnorm,
+                          pivmin);
   RR_MARK(4);
 
   // ---- 4. back-transformation Y = H_0 ... H_{m-3} Z, two columns per warp in registers
@@ -1295,6 +1330,311 @@ __global__ void __launch_bounds__(NW * 32)
   }
   RR_MARK(5);
   for (int j = tid; j < K; j += NT) theta[j] = (double)lam[j];
+  if (pflag && tid == 0) {
+    if (*pflag == 0 && nfallback) *nfallback += 1;
+    *pflag = 1;  // re-armed for the next pass
+  }
+  RR_MARK(6);
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Rayleigh-Ritz with the matrix held in registers, m <= 32 RS, FP32, 16 warps.  Half-warp
+// g = 2 warp + lane / 16 (0..31) owns rows g + 32 r (r < RS); lane cl = lane % 16 of it owns
+// columns cl + 16 c (c < CS = 2 RS) of those rows.
+//  1. Householder tridiagonalization (Golub & Van Loan Alg. 8.3.1), two barriers per step.
+//     Step k has q = k / 16, the column slot of k, as a compile-time index: the slots r < q / 2
+//     and c < q hold rows and columns <= k only, which the step leaves alone, so they drop out
+//     of the loops as the trailing block shrinks.
+//      (a) the lanes owning column k publish x_i = a_ik (i > k) into row k of Vs and per
+//          half-warp sums of x_i^2 (i > k + 1); the owner of a_kk writes d_k;
+//      (b) every thread forms the reflector scalars (mu, v0, beta, e_k) from sigma^2 and
+//          x_{k+1}, and v = e_{k+1} + x / v0 on its rows and columns;
+//      (c) p_i = beta (A v)_i on the owned rows: register dot products over the owned columns
+//          and half-warp butterflies; p and per-half-warp sums of p_i v_i go to shared memory;
+//      (d) w = p - (beta / 2)(p'v) v and the rank-2 update A -= v w' + w v' of the owned
+//          entries.
+//     The lane that reads a_i,k+1 in the next step's (a) is the one that updated it in (d).
+//  2. and 3. as in k_rr_eig_reg (rr_phase_eigvals, rr_phase_eigvecs).
+//  4. Back-transformation Y = H_0 ... H_{m-3} Z with the reflectors of Vs (v_j = x_j / v0),
+//     CPW columns per warp held in registers, the next reflector loaded while the current
+//     one's dot products reduce.
+template <int N>
+__device__ __forceinline__ float halfwarp_sum(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int RT_NW = 16;
+constexpr int RT_NT = RT_NW * 32;
+
+__host__ __device__ inline int rt_ldv(int m) { return m | 1; }
+
+// Shared-memory floats of k_rr_eig_rt for an m x m problem with K wanted pairs.
+__host__ __device__ inline size_t rt_smem_floats(int m, int K) {
+  return (size_t)6 * m + 7 * (size_t)K + 3 * RT_NW + 8 + 64 + (size_t)m * rt_ldv(m) +
+         4 * (size_t)m * K + (size_t)K * K;
+}
+
+template <int RS>
+__global__ void __launch_bounds__(RT_NT, 1)
+    k_rr_eig_rt(int m_full, int K, const double* __restrict__ G, int ldg,
+                double* __restrict__ theta, float* __restrict__ Y, int* status, int* pflag,
+                int mP, int* nfallback) {
+  using T = float;
+  constexpr int CS = 2 * RS;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* d = (T*)smraw;       // m
+  T* e = d + m;           // m
+  T* beta = e + m;        // m
+  T* e2 = beta + m;       // m
+  T* ivs = e2 + m;        // m: 1 / v0 of each reflector
+  T* pvec = ivs + m;      // m: p of the current step
+  T* lam = pvec + m;      // K
+  T* shift = lam + K;     // K
+  T* dd = shift + K;      // K
+  T* cbuf = dd + K;       // 2 K
+  T* wv = cbuf + 2 * K;   // K
+  T* coef = wv + K;       // K
+  T* red = coef + K;      // 3 NW + 8 (the shared phases' slots)
+  T* rs2 = red + 3 * RT_NW + 8;  // 32 half-warp sums of x^2
+  T* rpv = rs2 + 32;             // 32 half-warp sums of p_i v_i
+  const int ldv = rt_ldv(m);
+  T* Vs = rpv + 32;              // m x ldv: row k = x of reflector k
+  T* Z = Vs + (size_t)m * ldv;   // m x K
+  T* U = Z + (size_t)m * K;      // 3 m K
+  T* Gs = U + (size_t)3 * m * K; // K x K
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = 2 * warp + (lane >> 4), cl = lane & 15;
+
+  // ---- load (symmetrized), Gershgorin bound, lift the diagonal of dropped columns
+  T A[RS][CS];
+  T gmax = 0;
+#pragma unroll
+  for (int r = 0; r < RS; ++r) {
+    const int i = g + 32 * r;
+    T rs = 0;
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      const int j = cl + 16 * c;
+      T a = 0;
+      if (i < m && j < m) a = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+      A[r][c] = a;
+      rs += fabsf(a);
+    }
+    gmax = fmaxf(gmax, halfwarp_sum<16>(rs));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(FULL, gmax, o));
+  if (lane == 0) red[warp] = gmax;
+  __syncthreads();
+  {
+    T big = 0;
+    for (int w = 0; w < RT_NW; ++w) big = fmaxf(big, red[w]);
+    big = big * (T)1.25 + (T)1;
+#pragma unroll
+    for (int r = 0; r < RS; ++r)
+#pragma unroll
+      for (int c = 0; c < CS; ++c) {
+        const int i = g + 32 * r, j = cl + 16 * c;
+        if (i == j && i >= K && i < m && G[(long long)i * ldg + i] == 0.0) A[r][c] = big;
+      }
+  }
+  __syncthreads();
+  RR_MARK(0);
+
+  // ---- 1. tridiagonalization
+  bool stop = false;
+#pragma unroll
+  for (int q = 0; q < CS; ++q) {
+    if (stop) break;
+    constexpr int dummy = 0;
+    (void)dummy;
+    const int r0 = q / 2;
+    for (int kw = 0; kw < 16; ++kw) {
+      const int k = 16 * q + kw;
+      if (k + 2 >= m) {
+        stop = true;
+        break;
+      }
+      const int k1 = k + 1;
+      T* __restrict__ xs = Vs + (size_t)k * ldv;
+      // (a)
+      if (cl == kw) {
+        T s2 = 0;
+#pragma unroll
+        for (int r = r0; r < RS; ++r) {
+          const int i = g + 32 * r;
+          const T x = A[r][q];
+          if (i > k && i < m) {
+            xs[i] = x;
+            if (i > k1) s2 = fmaf(x, x, s2);
+          }
+        }
+        rs2[g] = s2;
+        if (g == (k & 31)) d[k] = A[r0][q];
+      }
+      __syncthreads();
+      // (b)
+      T sg = rs2[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(FULL, sg, o);
+      const T x0 = xs[k1];
+      T bet = 0, iv0 = 0, ek = x0;
+      if (sg != (T)0) {
+        // x -> ek e1 with ek = -sign(x0) mu: v0 = x0 - ek has |v0| >= mu, so the tail of
+        // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
+        const T mu = sqrtf(x0 * x0 + sg);
+        const T v0 = x0 + copysignf(mu, x0);
+        iv0 = (T)1 / v0;
+        bet = (T)2 / ((T)1 + sg * iv0 * iv0);
+        ek = -copysignf(mu, x0);
+      }
+      if (tid == 0) {
+        e[k] = ek;
+        beta[k] = bet;
+        ivs[k] = iv0;
+      }
+      T vc[CS], vr[RS], pr[RS];
+#pragma unroll
+      for (int c = q; c < CS; ++c) {
+        const int j = cl + 16 * c;
+        vc[c] = j == k1 ? (T)1 : ((j > k1 && j < m) ? xs[j] * iv0 : (T)0);
+      }
+#pragma unroll
+      for (int r = r0; r < RS; ++r) {
+        const int i = g + 32 * r;
+        vr[r] = i == k1 ? (T)1 : ((i > k1 && i < m) ? xs[i] * iv0 : (T)0);
+      }
+      // (c)
+      T pvp = 0;
+#pragma unroll
+      for (int r = r0; r < RS; ++r) {
+        T sacc = 0;
+#pragma unroll
+        for (int c = q; c < CS; ++c) sacc = fmaf(A[r][c], vc[c], sacc);
+        sacc = halfwarp_sum<16>(sacc);
+        pr[r] = (g + 32 * r > k) ? bet * sacc : (T)0;
+        pvp = fmaf(pr[r], vr[r], pvp);
+      }
+      if (cl == 0) {
+        rpv[g] = pvp;
+#pragma unroll
+        for (int r = r0; r < RS; ++r) {
+          const int i = g + 32 * r;
+          if (i < m) pvec[i] = pr[r];
+        }
+      }
+      __syncthreads();
+      // (d)
+      T pv = rpv[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(FULL, pv, o);
+      const T kc = bet * (T)0.5 * pv;
+#pragma unroll
+      for (int c = q; c < CS; ++c) {
+        const int j = cl + 16 * c;
+        const T wj = (j > k && j < m) ? pvec[j] - kc * vc[c] : (T)0;
+#pragma unroll
+        for (int r = r0; r < RS; ++r) {
+          const T wi = pr[r] - kc * vr[r];
+          A[r][c] = fmaf(-vr[r], wj, fmaf(-wi, vc[c], A[r][c]));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the trailing 2 x 2 block of T (or the 1 x 1 matrix), from the owners of its entries
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      const int i = g + 32 * r, j = cl + 16 * c;
+      if (m >= 2) {
+        if (i == m - 2 && j == m - 2) d[m - 2] = A[r][c];
+        if (i == m - 1 && j == m - 2) e[m - 2] = A[r][c];
+        if (i == m - 1 && j == m - 1) d[m - 1] = A[r][c];
+      } else if (i == 0 && j == 0) {
+        d[0] = A[r][c];
+      }
+    }
+  if (tid == 0) e[m - 1] = 0;
+  __syncthreads();
+  RR_MARK(1);
+
+  // ---- 2. and 3.
+  T tnorm, pivmin;
+  rr_phase_eigvals<T, RT_NT>(m, K, d, e, e2, red, lam, status, tnorm, pivmin);
+  RR_MARK(2);
+  rr_phase_eigvecs<T, RT_NT>(m, K, d, e, lam, shift, Z, U, Gs, dd, cbuf, wv, coef, red, tnorm,
+                             pivmin);
+  RR_MARK(4);
+
+  // ---- 4. back-transformation Y = H_0 ... H_{m-3} Z, CPW columns per warp in registers
+  {
+    constexpr int CPW = 4;
+    for (int j0 = CPW * warp; j0 < K; j0 += CPW * RT_NW) {
+      T z[CPW][RS];
+#pragma unroll
+      for (int t = 0; t < CPW; ++t)
+#pragma unroll
+        for (int u = 0; u < RS; ++u) {
+          const int i = lane + 32 * u, j = j0 + t;
+          z[t][u] = (i < m && j < K) ? Z[i * K + j] : (T)0;
+        }
+      // reflector kr: v_i = 1 at i = kr + 1, x_i / v0 beyond, 0 before
+      auto load_v = [&](int kr, T (&cv)[RS]) {
+        const T* __restrict__ xk = Vs + (size_t)kr * ldv;
+        const T iv = ivs[kr];
+#pragma unroll
+        for (int u = 0; u < RS; ++u) {
+          const int i = lane + 32 * u;
+          cv[u] = i == kr + 1 ? (T)1 : ((i > kr + 1 && i < m) ? xk[i] * iv : (T)0);
+        }
+      };
+      T cv[RS], nv[RS];
+      int kr = m - 3;
+      if (kr >= 0) load_v(kr, cv);
+      for (; kr >= 0; --kr) {
+        const T bet = beta[kr];
+        if (kr > 0) load_v(kr - 1, nv);
+        if (bet != (T)0) {  // uniform
+          T sa[CPW];
+#pragma unroll
+          for (int t = 0; t < CPW; ++t) {
+            T acc = 0;
+#pragma unroll
+            for (int u = 0; u < RS; ++u) acc = fmaf(cv[u], z[t][u], acc);
+            sa[t] = acc;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int t = 0; t < CPW; ++t) sa[t] += __shfl_xor_sync(FULL, sa[t], o);
+#pragma unroll
+          for (int t = 0; t < CPW; ++t) {
+            const T f = bet * sa[t];
+#pragma unroll
+            for (int u = 0; u < RS; ++u) z[t][u] = fmaf(-f, cv[u], z[t][u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < RS; ++u) cv[u] = nv[u];
+      }
+#pragma unroll
+      for (int t = 0; t < CPW; ++t)
+#pragma unroll
+        for (int u = 0; u < RS; ++u) {
+          const int i = lane + 32 * u, j = j0 + t;
+          if (i < m_full && j < K) Y[(long long)i * K + j] = i < m ? z[t][u] : (T)0;
+        }
+    }
+  }
+  RR_MARK(5);
+  for (int j = tid; j < K; j += RT_NT) theta[j] = (double)lam[j];
   if (pflag && tid == 0) {
     if (*pflag == 0 && nfallback) *nfallback += 1;
     *pflag = 1;  // re-armed for the next pass
@@ -1379,10 +1719,36 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
   return e;
 }
 
+
+// Register-resident Rayleigh-Ritz (FP32, m <= 32 RS): launch with the whole working set in
+// shared memory.  Returns cudaErrorNotSupported when it does not fit (the caller falls back).
+template <int RS>
+cudaError_t rr_eig_rt(cudaStream_t st, int m, int K, const double* G, int ldg, double* theta,
+                      float* Y, int* d_status, int* pflag, int mP, int* nfallback) {
+  const size_t sm = sizeof(float) * rt_smem_floats(m, K);
+  if (m > 32 * RS || sm > 225 * 1024) return cudaErrorNotSupported;
+  auto kern = k_rr_eig_rt<RS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  ProfScope ps(st, "rr_eig");
+  kern<<<1, RT_NT, sm, st>>>(m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, int ldg,
                    double* theta, T* Y, int* d_status, int* pflag, int mP, int* nfallback) {
   if (m < 1 || K < 1 || K > m) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    // register-resident tridiagonalization when the working set fits in shared memory
+    cudaError_t e = cudaErrorNotSupported;
+    if (m <= 64) e = rr_eig_rt<2>(st, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+    else if (m <= 96) e = rr_eig_rt<3>(st, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+    else if (m <= 128) e = rr_eig_rt<4>(st, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+    else if (m <= 160) e = rr_eig_rt<5>(st, m, K, G, ldg, theta, Y, d_status, pflag, mP, nfallback);
+    if (e != cudaErrorNotSupported) return e;
+  }
   // m <= 480: register-slot kernel (m = 3K up to K = 160)
   if (m <= 160) {
     if constexpr (sizeof(T) == 4)

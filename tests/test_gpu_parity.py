@@ -468,6 +468,38 @@ def test_partition_matches_oracle_labels(sc, ctx):
     assert O.partition_metrics(g.truth, labels)[0] == 1.0
 
 
+@pytest.fixture(scope="module")
+def headline_oracle():
+    """The oracle's partition of the n = 50,000, K = 44 DC-SBM graph (seed 0): 20 LOBPCG
+    passes from the seeded start block, unit rows, k-means++ with the seed-0 uniforms and 50
+    Lloyd rounds."""
+    g = W.dcsbm(50000, 44, seed=0)
+    L = O.laplacian_csr(g.n, g.src, g.dst)
+    X0 = W.start_block(0, g.n, 44).astype(np.float32).astype(np.float64)
+    rl, res, E, idx = O.partition(L, X0, 44, W.kmeans_uniforms(0, 44), 20, 50)
+    return g, L, rl, res, idx
+
+
+@pytest.mark.parametrize("prec", [0, 3, 2])
+def test_partition_labels_match_oracle_at_headline_size(sc, ctx, headline_oracle, prec):
+    """sc_partition at n = 50,000, K = 44, seed 0: the labels are identical to the oracle's up to
+    a permutation of the cluster ids (matched fraction 1.0), and the k-means++ seeds drawn on the
+    library's embedding are the oracle's, in every precision."""
+    g, L, rl, res, idx = headline_oracle
+    G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+    labels, info = sc.sc_partition(ctx, G, 44, 44, iters=20, seed=0, prec=prec)
+    assert info["iters_done"] == 20
+    assert O.partition_metrics(rl, labels)[0] == 1.0
+    X0 = W.start_block(0, g.n, 44).astype(np.float32).astype(np.float64)
+    lam, _, X, _ = sc.sc_lobpcg64(ctx, G, 44, iters=20, prec=prec, X0=X0)
+    E = sc.sc_embed_rows(ctx, X.astype(np.float32))
+    _, _, seeds, _, _ = sc.sc_kmeans(ctx, E, 44, iters=50, seed=0)
+    assert np.array_equal(seeds, idx)
+    tol = 1e-10 if prec == 2 else 1e-5
+    assert np.max(np.abs(lam - res.lam)) / O.lambda_max(L) <= tol
+    G.close()
+
+
 @pytest.mark.parametrize("n,K", [(3000, 50), (4000, 70), (5000, 140)])
 def test_partition_wide_blocks(sc, ctx, n, K):
     # block widths of the serving workload: Rayleigh-Ritz sizes 3K from 150 to 420 and
