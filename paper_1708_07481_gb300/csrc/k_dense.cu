@@ -1451,8 +1451,6 @@ __global__ void __launch_bounds__(RT_NT, 1)
 #pragma unroll
   for (int q = 0; q < CS; ++q) {
     if (stop) break;
-    constexpr int dummy = 0;
-    (void)dummy;
     const int r0 = q / 2;
     for (int kw = 0; kw < 16; ++kw) {
       const int k = 16 * q + kw;
