@@ -1640,6 +1640,177 @@ __global__ void __launch_bounds__(RT_NT, 1)
   RR_MARK(6);
 }
 
+
+// Cholesky-QR transform with the matrix in registers, FP32, ka <= 32 RS, 16 warps: the same
+// arithmetic as k_chol_inv (scaled FP64 Gram, in-place LDL' with L^-1 formed alongside,
+// column drops, floors, the direction-block fallback), laid out like k_rr_eig_rt: half-warp
+// g owns rows g + 32 r, lane cl owns columns cl + 16 c.  Step k reads one shared buffer
+// (double-buffered by the parity of k) that holds row k of L^-1 in its entries c < k and the
+// current pivot column in its entries i >= k; the owners of column k + 1 and row k + 1 write
+// the next step's buffer right after their own update, so one barrier per column suffices.
+template <int RS>
+__global__ void __launch_bounds__(RT_NT, 1)
+    k_chol_inv_rt(int ka, const double* __restrict__ G, int ldg, float* __restrict__ Tm,
+                  int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
+                  int* ndropped, double rfloor, double pfloor) {
+  using T = float;
+  constexpr int CS = 2 * RS;
+  __shared__ T s[32 * RS];
+  __shared__ T dd[32 * RS];
+  __shared__ T buf[2][32 * RS];
+  __shared__ int sfc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = 2 * warp + (lane >> 4), cl = lane & 15;
+  for (int i = tid; i < ka; i += RT_NT) {
+    const double dgi = G[(long long)i * ldg + i];
+    const double fl = i < keep ? rfloor * rfloor : pfloor * pfloor;
+    s[i] = dgi > fl ? (T)rsqrt(dgi) : (T)0;
+  }
+  if (tid == 0) sfc = -1;
+  __syncthreads();
+  T M[RS][CS];
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      const int i = g + 32 * r, j = cl + 16 * c;
+      T v = 0;
+      if (i < ka && j <= i) {
+        const double gg = 0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]);
+        v = (T)gg * s[i] * s[j];
+      }
+      M[r][c] = v;
+    }
+  // the first step's buffer: column 0
+  if (cl == 0) {
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+      const int i = g + 32 * r;
+      if (i < ka) buf[0][i] = M[r][0];
+    }
+  }
+  __syncthreads();
+  const T tol = (T)pivot_tol;
+  const bool zdrop = ndrop > 0;
+  int fc = -1;
+  bool stop = false;
+#pragma unroll
+  for (int q = 0; q < CS; ++q) {
+    if (stop) break;
+    const int r0 = q / 2;
+    for (int kw = 0; kw < 16; ++kw) {
+      const int k = 16 * q + kw;
+      if (k >= ka) {
+        stop = true;
+        break;
+      }
+      const T* __restrict__ cur = buf[k & 1];
+      T* __restrict__ nxt = buf[(k + 1) & 1];
+      const T dk = cur[k];
+      const bool drop = !(dk > tol);
+      if (drop && k >= ndrop && !(zdrop && dk == (T)0)) {  // uniform: every thread read dk
+        fc = k;
+        stop = true;
+        break;
+      }
+      if (tid == 0) dd[k] = drop ? (T)0 : dk;
+      const T invd = drop ? (T)0 : (T)1 / dk;
+      // the multipliers l_i = W_ik / d_k of the owned rows, from the lane holding column k
+      T l[RS];
+#pragma unroll
+      for (int r = r0; r < RS; ++r)
+        l[r] = __shfl_sync(0xffffffffu, M[r][q], (lane & 16) | kw) * invd;
+#pragma unroll
+      for (int r = r0; r < RS; ++r) {
+        const int i = g + 32 * r;
+        if (i > k && i < ka) {
+#pragma unroll
+          for (int c = 0; c < CS; ++c) {
+            const int j = cl + 16 * c;
+            if (j <= i) {
+              if (drop) {
+                if (j == k) M[r][c] = (T)0;
+              } else {
+                M[r][c] = j == k ? -l[r] : fmaf(-l[r], cur[j], M[r][c]);
+              }
+            }
+          }
+        }
+      }
+      // the next step's buffer: column k + 1 (rows >= k + 1) and row k + 1 of L^-1 (c <= k)
+      const int k1 = k + 1;
+      if (k1 < ka) {
+        if (cl == (k1 & 15)) {
+          if (kw < 15) {
+#pragma unroll
+            for (int r = r0; r < RS; ++r) {
+              const int i = g + 32 * r;
+              if (i >= k1 && i < ka) nxt[i] = M[r][q];
+            }
+          } else if (q + 1 < CS) {
+#pragma unroll
+            for (int r = r0; r < RS; ++r) {
+              const int i = g + 32 * r;
+              if (i >= k1 && i < ka) nxt[i] = M[r][q + 1 < CS ? q + 1 : q];
+            }
+          }
+        }
+        if (g == (k1 & 31)) {
+#pragma unroll
+          for (int r = 0; r < RS; ++r)
+            if (g + 32 * r == k1) {
+#pragma unroll
+              for (int c = 0; c < CS; ++c) {
+                const int j = cl + 16 * c;
+                if (j < k1) nxt[j] = M[r][c];
+              }
+            }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) sfc = fc;
+  __syncthreads();
+  fc = sfc;
+  if (ndropped && tid == 0) {
+    const int lim = fc >= 0 ? fc : ka;
+    int cnt = 0;
+    for (int k = 0; k < lim; ++k) cnt += dd[k] == (T)0;
+    if (cnt) atomicAdd(ndropped, cnt);
+  }
+  int kk = ka;  // size of the leading block whose transform is returned
+  if (fc >= 0) {
+    if (pflag && keep > 0 && fc >= keep) {
+      kk = keep;
+      if (tid == 0) *pflag = 0;
+    } else {
+      if (tid == 0) {
+        atomicOr(status, ST_CHOL_FAIL);
+        if (fail_col) *fail_col = fc;
+      }
+      return;
+    }
+  }
+  // Tm[r][c] = s_r (L^-1)_cr d_c^-1/2 for r <= c < kk, else 0; the owner of M[i][j] (row i,
+  // column j, j <= i) writes Tm[j][i]
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      const int i = g + 32 * r, j = cl + 16 * c;
+      if (i < ka && j < ka) {
+        T v = 0;
+        if (j <= i && i < kk) {
+          const T di = dd[i];
+          const T rd = di > (T)0 ? rsqrtf(di) : (T)0;
+          v = s[j] * (i == j ? (T)1 : M[r][c]) * rd;
+        }
+        Tm[(long long)j * ka + i] = v;
+      }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -1648,10 +1819,36 @@ cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int
                         int ndrop, int* ndropped, double rfloor, double pfloor,
                         int nthreads);
 
+
+template <int RS>
+cudaError_t chol_inv_rt(cudaStream_t st, int ka, const double* G, int ldg, float* Tm,
+                        int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
+                        int ndrop, int* ndropped, double rfloor, double pfloor) {
+  ProfScope ps(st, "chol_inv");
+  k_chol_inv_rt<RS><<<1, RT_NT, 0, st>>>(ka, G, ldg, Tm, d_status, fail_col, pivot_tol, keep,
+                                         pflag, ndrop, ndropped, rfloor, pfloor);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ldg, T* Tm,
                      int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
                      int ndrop, int* ndropped, double rfloor, double pfloor) {
+  if constexpr (sizeof(T) == 4) {
+    if (ka >= 1 && ka <= 64)
+      return chol_inv_rt<2>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
+                            ndropped, rfloor, pfloor);
+    if (ka <= 96)
+      return chol_inv_rt<3>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
+                            ndropped, rfloor, pfloor);
+    if (ka <= 128)
+      return chol_inv_rt<4>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
+                            ndropped, rfloor, pfloor);
+    if (ka <= 160)
+      return chol_inv_rt<5>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
+                            ndropped, rfloor, pfloor);
+  }
   return chol_inv_nt<T>(st, al, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
                         ndropped, rfloor, pfloor, 512);
 }
@@ -1799,3 +1996,10 @@ template cudaError_t rr_eig<double>(cudaStream_t, Alloc&, int, int, const double
                                     double*, double*, int*, int*, int, int*);
 
 }  // namespace sc
+
+#ifdef SC_RR_PHASES
+// Debug builds only: the clock64() marks of the last Rayleigh-Ritz launch (phase starts).
+extern "C" int sc_debug_rr_phases(long long* out) {
+  return cudaMemcpyFromSymbol(out, sc::g_rr_phase, sizeof(long long) * 8) == cudaSuccess ? 0 : -6;
+}
+#endif
