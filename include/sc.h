@@ -94,6 +94,23 @@ uint64_t sc_ctx_kernel_launches(const sc_ctx* ctx);
 int sc_profile_begin(sc_ctx* ctx, const char* kernels);
 int sc_profile_end(sc_ctx* ctx, char* report, size_t len);
 
+/* ---- fault injection for tests ---------------------------------------------------------
+ * Failure handling is exercised without faulting the GPU: a test arms one injected failure
+ * on a context and the later calls on that context see it, until it is disarmed
+ * (SC_INJECT_NONE).  The paper has no counterpart; these hooks exist for tests.
+ *  SC_INJECT_WAIT_TIMEOUT: every tensor-core Gram launch (SC_PREC_MIXED, MIXED_DD) adds, after
+ *    its copies and MMAs have completed, a bounded wait on an mbarrier phase that nothing
+ *    completes, giving up after `arg` (>= 1) polls.  The kernel records the time-out in the
+ *    context's status word and returns normally, so the call fails with SC_ETIMEOUT and the
+ *    context stays usable.
+ *  SC_INJECT_P_BREAKDOWN: LOBPCG pass number `arg` (0-based, counted from the first pass that
+ *    has a direction block P, i.e. arg >= 1) reports P as broken down, as the Cholesky-QR of
+ *    [R P] does when P has sunk into span{X, R}; that pass's Rayleigh-Ritz step runs on
+ *    [X R] only (counted in sc_eig_info.fallbacks).
+ * Errors: SC_EINVAL (unknown kind, a wait limit < 1). */
+enum { SC_INJECT_NONE = 0, SC_INJECT_WAIT_TIMEOUT = 1, SC_INJECT_P_BREAKDOWN = 2 };
+int sc_debug_inject(sc_ctx* ctx, int kind, long long arg);
+
 /* ---- Laplacian (Sec. II.A; Sec. III stores the directed adjacency sparse) --------------
  * sc_build_laplacian: directed edge list (src[e] -> dst[e], e < m, 0 <= src, dst < n) to
  * the symmetrized CSR of W and the degrees D of L = D - W.  Self-loops are dropped (they

@@ -132,7 +132,8 @@ cudaError_t gram(cudaStream_t st, Alloc& al, long long n, const Cat3<T>& A, cons
 // segA/segB: (start, count) pairs listing the columns that appear in the compact output C.
 cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, long long lda,
                     int a, const int* segA, int nsegA, const float* B, long long ldb, int b,
-                    const int* segB, int nsegB, double* C, int ldc, bool sym, int* d_status);
+                    const int* segB, int nsegB, double* C, int ldc, bool sym, int* d_status,
+                    long long probe_spins = 0);
 
 // Tall GEMM: out (n x b, ldo) = beta * Cin + A (n x a) W (a x b, row-major ldw, type T).
 template <typename T>

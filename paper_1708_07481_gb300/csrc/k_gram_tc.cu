@@ -14,7 +14,14 @@
 //   that frees the operand buffer.  The epilogue reads TMEM with tcgen05.ld and writes the
 //   tile's FP64 partial; a second kernel sums the partials over chunks in fixed order.
 // Every wait is bounded: on a timeout the CTA records ST_TIMEOUT, waits (bounded) for its
-// own outstanding copies and MMAs, frees its tensor memory and returns.
+// own outstanding copies and MMAs, frees its tensor memory and returns.  If that draining wait
+// gives up as well, the CTA still frees its tensor memory and returns, with an MMA or a copy
+// possibly still running; the launch has then already failed with ST_TIMEOUT, and the
+// context's status word reports it.
+// Test hook (probe_spins > 0): after every copy and MMA of the CTA has completed, thread 0
+// waits on an mbarrier phase that nothing completes, for at most probe_spins polls; the wait
+// gives up and records ST_TIMEOUT with nothing in flight, which exercises the time-out
+// reporting without a fault.
 #include <algorithm>
 #include <cstring>
 
@@ -76,7 +83,7 @@ __device__ inline void convert_stage(const float* stage, uint8_t* big, uint8_t* 
 __global__ void __launch_bounds__(NTH, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               long long n, int nbt, int sym, int nch, int ntiles, long long rows_per_chunk,
-              int a, int b, double* __restrict__ part, int* status) {
+              int a, int b, double* __restrict__ part, int* status, long long probe_spins) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled operands
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -87,7 +94,8 @@ __global__ void __launch_bounds__(NTH, 1)
   uint64_t* bars = (uint64_t*)(stB + NSTG * (STAGE_BYTES / 4));
   uint64_t* full = bars;            // [NSTG] TMA landed
   uint64_t* mdone = bars + NSTG;    // [2] MMAs of an operand buffer finished
-  uint32_t* tmem_slot = (uint32_t*)(bars + NSTG + 2);
+  uint64_t* probe = bars + NSTG + 2; // test hook: a phase nothing completes
+  uint32_t* tmem_slot = (uint32_t*)(bars + NSTG + 3);
   __shared__ int abort_flag;
 
   const int tile = blockIdx.x / nch, chunk = blockIdx.x % nch;
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(NTH, 1)
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int q = 0; q < NSTG + 2; ++q) mbar_init(&bars[q], 1);
+    for (int q = 0; q < NSTG + 3; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
@@ -234,6 +242,10 @@ __global__ void __launch_bounds__(NTH, 1)
   } else if (!last_ok && threadIdx.x == 0) {
     atomicOr(status, ST_TIMEOUT);
   }
+  if (probe_spins > 0 && threadIdx.x == 0 && last_ok) {
+    // every copy and MMA of this CTA has completed (waited above): nothing is in flight
+    if (!mbar_wait(probe, 0u, probe_spins)) atomicOr(status, ST_TIMEOUT);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -312,7 +324,8 @@ int gram_tc_smem_bytes() { return SMEM_BYTES; }
 // B = columns [0, b) of another; the segment maps drop padding columns from the output.
 cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, long long lda,
                     int a, const int* segA, int nsegA, const float* B, long long ldb, int b,
-                    const int* segB, int nsegB, double* C, int ldc, bool sym, int* d_status) {
+                    const int* segB, int nsegB, double* C, int ldc, bool sym, int* d_status,
+                    long long probe_spins) {
   if (a == 0 || b == 0) return cudaSuccess;
   SegMap ma{}, mb{};
   ma.nseg = nsegA;
@@ -350,7 +363,7 @@ cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, lon
       ProfScope ps(st, "gram_tc");
       k_gram_tc<<<(unsigned)(nt * nch), NTH, SMEM_BYTES, st>>>(mapA, mapB, n, nb, sym ? 1 : 0,
                                                                (int)nch, nt, rpc, a, b, part,
-                                                               d_status);
+                                                               d_status, probe_spins);
       note_launch();
       k_gram_tc_reduce<<<(unsigned)(nt * TN), TM * RH, 0, st>>>(part, (int)nch, nt, nb, a, b, ma, mb,
                                                             C, ldc, sym ? 1 : 0);

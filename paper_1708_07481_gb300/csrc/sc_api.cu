@@ -86,6 +86,10 @@ struct sc_ctx {
   std::string err;
   int* d_status = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // test hook (sc_debug_inject): the armed failure and its argument
+  int inject_kind = 0;
+  long long inject_arg = 0;
+  long long probe_spins() const { return inject_kind == SC_INJECT_WAIT_TIMEOUT ? inject_arg : 0; }
 };
 
 struct sc_graph {
@@ -230,6 +234,17 @@ size_t sc_ctx_bytes_peak(sc_ctx* c) {
   return p;
 }
 uint64_t sc_ctx_kernel_launches(const sc_ctx*) { return launches_total(); }
+
+int sc_debug_inject(sc_ctx* c, int kind, long long arg) {
+  if (!c) return SC_EINVAL;
+  if (kind != SC_INJECT_NONE && kind != SC_INJECT_WAIT_TIMEOUT && kind != SC_INJECT_P_BREAKDOWN)
+    return fail(c, SC_EINVAL, "sc_debug_inject: unknown kind");
+  if (kind == SC_INJECT_WAIT_TIMEOUT && arg < 1)
+    return fail(c, SC_EINVAL, "sc_debug_inject: the wait limit must be >= 1");
+  c->inject_kind = kind;
+  c->inject_arg = arg;
+  return SC_OK;
+}
 
 int sc_profile_begin(sc_ctx* c, const char* kernels) {
   if (!c || !kernels) return SC_EINVAL;
@@ -622,7 +637,7 @@ struct LobRun : RunBase {
           spb = std::max(spb, vb[q].start + vb[q].count);
         }
         return gram_tc(st, al, n, (const float*)A, lda, spa, pa, (int)va.size(), (const float*)B,
-                       ldb, spb, pb, (int)vb.size(), C, ldc, sym, dstatus);
+                       ldb, spb, pb, (int)vb.size(), C, ldc, sym, dstatus, c->probe_spins());
       }
     }
     Cat3<T> ca{}, cb{};
@@ -917,6 +932,10 @@ struct LobRun : RunBase {
       CK(spmm_lap<T>(st, g->csr, Rslot, ld3, LRslot, ld3, ka), "spmm");
       if (haveP) CK(spmm_lap<T>(st, g->csr, Pslot, ld3, LPslot, ld3, ka), "spmm");
     }
+    // test hook: this pass's direction block is reported as broken down, as the Cholesky-QR
+    // does when P has sunk into span{X, R} (the Rayleigh-Ritz step then runs without P)
+    if (haveP && c->inject_kind == SC_INJECT_P_BREAKDOWN && done_passes == c->inject_arg)
+      CK(cudaMemsetAsync(dP, 0, sizeof(int), st), "inject");
     // (4) Rayleigh-Ritz on S = [X R_a P_a]
     const bool useP = haveP;
     const int m = K + ka + (useP ? ka : 0);
@@ -1459,7 +1478,7 @@ static int gram_t(sc_ctx* c, int prec, int64_t n, int a, int b, const T* A, int6
     if (prec == SC_PREC_MIXED) {
       int sa[2] = {0, a}, sb[2] = {0, b};
       CK(gram_tc(c->stream, al, n, (const float*)dA, ap, a, sa, 1, (const float*)dB, bp, b, sb, 1,
-                 dC, b, false, c->d_status), "gram_tc");
+                 dC, b, false, c->d_status, c->probe_spins()), "gram_tc");
     } else {
       CK(gram<T>(c->stream, al, n, cat<T>(dA, ap, a), cat<T>(dB, bp, b), dC, b, false, 0), "gram");
     }

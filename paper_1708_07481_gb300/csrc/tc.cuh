@@ -27,10 +27,11 @@ __device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; returns false on timeout.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for phase `parity` of an mbarrier (at most `limit` polls); returns false on
+// timeout.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = SPIN_LIMIT) {
   uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < SPIN_LIMIT; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"

@@ -84,6 +84,7 @@ def lib():
         "sc_ctx_bytes_in_use": ([vp], C.c_size_t),
         "sc_ctx_bytes_peak": ([vp], C.c_size_t),
         "sc_ctx_kernel_launches": ([vp], u64),
+        "sc_debug_inject": ([vp, C.c_int, C.c_longlong], C.c_int),
         "sc_profile_begin": ([vp, C.c_char_p], C.c_int),
         "sc_profile_end": ([vp, C.c_char_p, C.c_size_t], C.c_int),
         "sc_build_laplacian": ([vp, i32, i64, vp, vp, vp, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
@@ -209,6 +210,14 @@ class Graph:
 
 def sc_ctx_create(device=0, stream=None, budget=0) -> Ctx:
     return Ctx(device, stream, budget)
+
+
+SC_INJECT_NONE, SC_INJECT_WAIT_TIMEOUT, SC_INJECT_P_BREAKDOWN = 0, 1, 2
+
+
+def sc_debug_inject(ctx: Ctx, kind, arg=0):
+    """Arm (or with SC_INJECT_NONE disarm) an injected failure on the context (tests only)."""
+    ctx.check(lib().sc_debug_inject(ctx.h, int(kind), int(arg)))
 
 
 def sc_profile_begin(ctx: Ctx, kernels: str = "*"):
