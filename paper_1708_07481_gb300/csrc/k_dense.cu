@@ -799,9 +799,37 @@ __global__ void __launch_bounds__(RR_NT)
 }
 
 
+// The K smallest eigenvalues of the tridiagonal (d, e2 = e^2) inside [glo, ghi] by
+// (LG + 1)-point multisection on Sturm counts, LG lanes per eigenvalue, to the tolerance
+// max(2 eps max(|a|, |b|), abstol) + 4 pivmin.
+template <typename T, int NT, int LG>
+__device__ void rr_multisect(int m, int K, const T* __restrict__ d, const T* __restrict__ e2,
+                             T glo, T ghi, T abstol, T pivmin, T* __restrict__ lam) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int grp = tid / LG, sl = tid % LG;
+  const unsigned gmask = (LG == 32 ? 0xffffffffu : ((1u << LG) - 1u)) << (lane & (32 - LG));
+  for (int j = grp; j < K; j += NT / LG) {
+    T a = glo, b = ghi;
+    for (int it = 0; it < 64; ++it) {
+      T tol = max((T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)), abstol) + (T)4 * pivmin;
+      if (b - a <= tol) break;
+      T h = (b - a) / (T)(LG + 1);
+      int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
+      unsigned bal = __ballot_sync(gmask, c > j) >> (lane & (32 - LG));
+      int first = bal ? (__ffs(bal) - 1) : LG;
+      T na = first == 0 ? a : a + h * (T)first;
+      T nb = first == LG ? b : a + h * (T)(first + 1);
+      if (!(nb > na)) break;
+      a = na;
+      b = nb;
+    }
+    if (sl == 0) lam[j] = (T)0.5 * (a + b);
+  }
+}
+
 // ---- phases 2 and 3 of the register-slot Rayleigh-Ritz kernels (shared) ------------------
 // Phase 2: Gershgorin bounds of the tridiagonal T = (d, e); the K smallest eigenvalues of T by
-// 17-point multisection on Sturm counts, 16 lanes per eigenvalue, into lam[K].  Outputs the
+// multisection on Sturm counts (rr_multisect), into lam[K].  Outputs the
 // norm bound tnorm and the pivot floor pivmin that phase 3 uses.  NT threads take part; red
 // holds 3 NW per-warp slots followed by the scalar slots RS ...
 template <typename T, int NT>
@@ -813,7 +841,7 @@ __device__ void rr_phase_eigvals(int m, int K, const T* __restrict__ d, const T*
   constexpr int RS = 3 * NW;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   (void)FULL;
-  // ---- 2. Gershgorin bounds; 17-point multisection, 16 lanes per eigenvalue
+  // ---- 2. Gershgorin bounds; multisection
   {
     T lo_p = (T)3e38, hi_p = (T)-3e38, emax = 0;
     for (int i = tid; i < m; i += NT) {
@@ -854,27 +882,12 @@ __device__ void rr_phase_eigvals(int m, int K, const T* __restrict__ d, const T*
   const T glo = red[RS] - (T)2 * Lim<T>::eps() * tnorm - pivmin;
   const T ghi = red[RS + 1] + (T)2 * Lim<T>::eps() * tnorm + pivmin;
   const T abstol = Lim<T>::eps() * tnorm;
-  {
-    const int grp = tid >> 4, sl = tid & 15;
-    const unsigned gmask = 0xFFFFu << (lane & 16);
-    for (int j = grp; j < K; j += NT >> 4) {
-      T a = glo, b = ghi;
-      for (int it = 0; it < 48; ++it) {
-        T tol = max((T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)), abstol) + (T)4 * pivmin;
-        if (b - a <= tol) break;
-        T h = (b - a) / (T)17;
-        int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
-        unsigned bal = __ballot_sync(gmask, c > j) >> (lane & 16);
-        int first = bal ? (__ffs(bal) - 1) : 16;
-        T na = first == 0 ? a : a + h * (T)first;
-        T nb = first == 16 ? b : a + h * (T)(first + 1);
-        if (!(nb > na)) break;
-        a = na;
-        b = nb;
-      }
-      if (sl == 0) lam[j] = (T)0.5 * (a + b);
-    }
-  }
+  // 16 lanes per eigenvalue when the block has a group for each; otherwise 8, so that all K
+  // eigenvalues are found in one round
+  if (K <= NT / 16)
+    rr_multisect<T, NT, 16>(m, K, d, e2, glo, ghi, abstol, pivmin, lam);
+  else
+    rr_multisect<T, NT, 8>(m, K, d, e2, glo, ghi, abstol, pivmin, lam);
   __syncthreads();
 }
 
@@ -1369,12 +1382,13 @@ __device__ __forceinline__ float halfwarp_sum(float v) {
 constexpr int RT_NW = 16;
 constexpr int RT_NT = RT_NW * 32;
 
-__host__ __device__ inline int rt_ldv(int m) { return m | 1; }
+// Row stride of the reflector store: the padded width 32 RS, plus one.
+__host__ __device__ inline int rt_ldv(int rs) { return 32 * rs + 1; }
 
-// Shared-memory floats of k_rr_eig_rt for an m x m problem with K wanted pairs.
-__host__ __device__ inline size_t rt_smem_floats(int m, int K) {
-  return (size_t)6 * m + 7 * (size_t)K + 3 * RT_NW + 8 + 64 + (size_t)m * rt_ldv(m) +
-         4 * (size_t)m * K + (size_t)K * K;
+// Shared-memory floats of k_rr_eig_rt<RS> for an m x m problem with K wanted pairs.
+__host__ __device__ inline size_t rt_smem_floats(int m, int K, int rs) {
+  return (size_t)5 * m + 32 * (size_t)rs + 7 * (size_t)K + 3 * RT_NW + 8 + 64 +
+         (size_t)m * rt_ldv(rs) + 4 * (size_t)m * K + (size_t)K * K;
 }
 
 template <int RS>
@@ -1392,8 +1406,8 @@ __global__ void __launch_bounds__(RT_NT, 1)
   T* beta = e + m;        // m
   T* e2 = beta + m;       // m
   T* ivs = e2 + m;        // m: 1 / v0 of each reflector
-  T* pvec = ivs + m;      // m: p of the current step
-  T* lam = pvec + m;      // K
+  T* pvec = ivs + m;      // 32 RS: p of the current step (padded rows included)
+  T* lam = pvec + 32 * RS;  // K
   T* shift = lam + K;     // K
   T* dd = shift + K;      // K
   T* cbuf = dd + K;       // 2 K
@@ -1402,7 +1416,7 @@ __global__ void __launch_bounds__(RT_NT, 1)
   T* red = coef + K;      // 3 NW + 8 (the shared phases' slots)
   T* rs2 = red + 3 * RT_NW + 8;  // 32 half-warp sums of x^2
   T* rpv = rs2 + 32;             // 32 half-warp sums of p_i v_i
-  const int ldv = rt_ldv(m);
+  const int ldv = rt_ldv(RS);
   T* Vs = rpv + 32;              // m x ldv: row k = x of reflector k
   T* Z = Vs + (size_t)m * ldv;   // m x K
   T* U = Z + (size_t)m * K;      // 3 m K
@@ -1447,6 +1461,12 @@ __global__ void __launch_bounds__(RT_NT, 1)
   RR_MARK(0);
 
   // ---- 1. tridiagonalization
+  // Row k of Vs receives x_i (i > k) in step k and is zero elsewhere (zero-filled here, and
+  // padded to 32 RS columns), so that v = x / v0 needs no masks: its entries at i <= k and at
+  // i >= m come out zero.  Entries of A outside the trailing block (rows or columns <= k) and
+  // the upper / padded slots receive updates that are never read again.
+  for (int idx = tid; idx < m * ldv; idx += RT_NT) Vs[idx] = (T)0;
+  __syncthreads();
   bool stop = false;
 #pragma unroll
   for (int q = 0; q < CS; ++q) {
@@ -1467,10 +1487,8 @@ __global__ void __launch_bounds__(RT_NT, 1)
         for (int r = r0; r < RS; ++r) {
           const int i = g + 32 * r;
           const T x = A[r][q];
-          if (i > k && i < m) {
-            xs[i] = x;
-            if (i > k1) s2 = fmaf(x, x, s2);
-          }
+          if (i > k) xs[i] = x;
+          s2 = fmaf(i > k1 ? x : (T)0, x, s2);
         }
         rs2[g] = s2;
         if (g == (k & 31)) d[k] = A[r0][q];
@@ -1487,8 +1505,8 @@ __global__ void __launch_bounds__(RT_NT, 1)
         // v = x / v0 stays <= 1 however small sigma is; beta = 2 / (1 + sigma / v0^2)
         const T mu = sqrtf(x0 * x0 + sg);
         const T v0 = x0 + copysignf(mu, x0);
-        iv0 = (T)1 / v0;
-        bet = (T)2 / ((T)1 + sg * iv0 * iv0);
+        iv0 = __frcp_rn(v0);
+        bet = (T)2 * __frcp_rn((T)1 + sg * iv0 * iv0);
         ek = -copysignf(mu, x0);
       }
       if (tid == 0) {
@@ -1499,13 +1517,13 @@ __global__ void __launch_bounds__(RT_NT, 1)
       T vc[CS], vr[RS], pr[RS];
 #pragma unroll
       for (int c = q; c < CS; ++c) {
-        const int j = cl + 16 * c;
-        vc[c] = j == k1 ? (T)1 : ((j > k1 && j < m) ? xs[j] * iv0 : (T)0);
+        vc[c] = xs[cl + 16 * c] * iv0;
+        if (c <= q + 1 && cl + 16 * c == k1) vc[c] = (T)1;  // only slots q, q + 1 can hold k + 1
       }
 #pragma unroll
       for (int r = r0; r < RS; ++r) {
-        const int i = g + 32 * r;
-        vr[r] = i == k1 ? (T)1 : ((i > k1 && i < m) ? xs[i] * iv0 : (T)0);
+        vr[r] = xs[g + 32 * r] * iv0;
+        if (r <= r0 + 1 && g + 32 * r == k1) vr[r] = (T)1;
       }
       // (c)
       T pvp = 0;
@@ -1514,17 +1532,13 @@ __global__ void __launch_bounds__(RT_NT, 1)
         T sacc = 0;
 #pragma unroll
         for (int c = q; c < CS; ++c) sacc = fmaf(A[r][c], vc[c], sacc);
-        sacc = halfwarp_sum<16>(sacc);
-        pr[r] = (g + 32 * r > k) ? bet * sacc : (T)0;
+        pr[r] = bet * halfwarp_sum<16>(sacc);
         pvp = fmaf(pr[r], vr[r], pvp);
       }
       if (cl == 0) {
         rpv[g] = pvp;
 #pragma unroll
-        for (int r = r0; r < RS; ++r) {
-          const int i = g + 32 * r;
-          if (i < m) pvec[i] = pr[r];
-        }
+        for (int r = r0; r < RS; ++r) pvec[g + 32 * r] = pr[r];
       }
       __syncthreads();
       // (d)
@@ -1532,15 +1546,14 @@ __global__ void __launch_bounds__(RT_NT, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(FULL, pv, o);
       const T kc = bet * (T)0.5 * pv;
+      T wr[RS];
+#pragma unroll
+      for (int r = r0; r < RS; ++r) wr[r] = fmaf(-kc, vr[r], pr[r]);
 #pragma unroll
       for (int c = q; c < CS; ++c) {
-        const int j = cl + 16 * c;
-        const T wj = (j > k && j < m) ? pvec[j] - kc * vc[c] : (T)0;
+        const T wj = fmaf(-kc, vc[c], pvec[cl + 16 * c]);
 #pragma unroll
-        for (int r = r0; r < RS; ++r) {
-          const T wi = pr[r] - kc * vr[r];
-          A[r][c] = fmaf(-vr[r], wj, fmaf(-wi, vc[c], A[r][c]));
-        }
+        for (int r = r0; r < RS; ++r) A[r][c] = fmaf(-vr[r], wj, fmaf(-wr[r], vc[c], A[r][c]));
       }
     }
   }
@@ -1573,7 +1586,7 @@ __global__ void __launch_bounds__(RT_NT, 1)
 
   // ---- 4. back-transformation Y = H_0 ... H_{m-3} Z, CPW columns per warp in registers
   {
-    constexpr int CPW = 4;
+    constexpr int CPW = 3;
     for (int j0 = CPW * warp; j0 < K; j0 += CPW * RT_NW) {
       T z[CPW][RS];
 #pragma unroll
@@ -1590,7 +1603,7 @@ __global__ void __launch_bounds__(RT_NT, 1)
 #pragma unroll
         for (int u = 0; u < RS; ++u) {
           const int i = lane + 32 * u;
-          cv[u] = i == kr + 1 ? (T)1 : ((i > kr + 1 && i < m) ? xk[i] * iv : (T)0);
+          cv[u] = i == kr + 1 ? (T)1 : xk[i] * iv;  // zero at i <= kr and i >= m
         }
       };
       T cv[RS], nv[RS];
@@ -1681,19 +1694,20 @@ __global__ void __launch_bounds__(RT_NT, 1)
       }
       M[r][c] = v;
     }
-  // the first step's buffer: column 0
+  // the first step's buffer: column 0 (entries past ka stay zero)
+  for (int i = tid; i < 2 * 32 * RS; i += RT_NT) (&buf[0][0])[i] = (T)0;
+  __syncthreads();
   if (cl == 0) {
 #pragma unroll
-    for (int r = 0; r < RS; ++r) {
-      const int i = g + 32 * r;
-      if (i < ka) buf[0][i] = M[r][0];
-    }
+    for (int r = 0; r < RS; ++r) buf[0][g + 32 * r] = M[r][0];
   }
   __syncthreads();
   const T tol = (T)pivot_tol;
   const bool zdrop = ndrop > 0;
   int fc = -1;
   bool stop = false;
+  // Each step updates every owned entry with one FMA: rows <= k get the multiplier 0, and the
+  // entries above the diagonal (and the padded ones) take updates that are never read.
 #pragma unroll
   for (int q = 0; q < CS; ++q) {
     if (stop) break;
@@ -1714,58 +1728,44 @@ __global__ void __launch_bounds__(RT_NT, 1)
         break;
       }
       if (tid == 0) dd[k] = drop ? (T)0 : dk;
-      const T invd = drop ? (T)0 : (T)1 / dk;
-      // the multipliers l_i = W_ik / d_k of the owned rows, from the lane holding column k
+      const T invd = drop ? (T)0 : __frcp_rn(dk);
+      // the multipliers l_i = W_ik / d_k of the owned rows i > k, from the lane holding column k
       T l[RS];
 #pragma unroll
-      for (int r = r0; r < RS; ++r)
-        l[r] = __shfl_sync(0xffffffffu, M[r][q], (lane & 16) | kw) * invd;
-#pragma unroll
       for (int r = r0; r < RS; ++r) {
-        const int i = g + 32 * r;
-        if (i > k && i < ka) {
+        const T wik = __shfl_sync(0xffffffffu, M[r][q], (lane & 16) | kw);
+        l[r] = g + 32 * r > k ? wik * invd : (T)0;
+      }
 #pragma unroll
-          for (int c = 0; c < CS; ++c) {
-            const int j = cl + 16 * c;
-            if (j <= i) {
-              if (drop) {
-                if (j == k) M[r][c] = (T)0;
-              } else {
-                M[r][c] = j == k ? -l[r] : fmaf(-l[r], cur[j], M[r][c]);
-              }
-            }
-          }
-        }
+      for (int c = 0; c < CS; ++c) {
+        const T y = cur[cl + 16 * c];
+#pragma unroll
+        for (int r = r0; r < RS; ++r) M[r][c] = fmaf(-l[r], y, M[r][c]);
+      }
+      // column k of L^-1: -l_i (a dropped column: 0)
+      if (cl == kw) {
+#pragma unroll
+        for (int r = r0; r < RS; ++r)
+          if (g + 32 * r > k) M[r][q] = -l[r];
       }
       // the next step's buffer: column k + 1 (rows >= k + 1) and row k + 1 of L^-1 (c <= k)
       const int k1 = k + 1;
-      if (k1 < ka) {
-        if (cl == (k1 & 15)) {
-          if (kw < 15) {
+      if (cl == (k1 & 15)) {
 #pragma unroll
-            for (int r = r0; r < RS; ++r) {
-              const int i = g + 32 * r;
-              if (i >= k1 && i < ka) nxt[i] = M[r][q];
-            }
-          } else if (q + 1 < CS) {
+        for (int r = r0; r < RS; ++r) {
+          const int i = g + 32 * r;
+          if (i >= k1) nxt[i] = kw < 15 ? M[r][q] : M[r][q + 1 < CS ? q + 1 : q];
+        }
+      }
+      if (g == (k1 & 31)) {
+        const int rk = k1 >> 5;  // the slot of row k + 1
 #pragma unroll
-            for (int r = r0; r < RS; ++r) {
-              const int i = g + 32 * r;
-              if (i >= k1 && i < ka) nxt[i] = M[r][q + 1 < CS ? q + 1 : q];
-            }
+        for (int r = r0; r < RS; ++r)
+          if (r == rk) {
+#pragma unroll
+            for (int c = 0; c < CS; ++c)
+              if (cl + 16 * c < k1) nxt[cl + 16 * c] = M[r][c];
           }
-        }
-        if (g == (k1 & 31)) {
-#pragma unroll
-          for (int r = 0; r < RS; ++r)
-            if (g + 32 * r == k1) {
-#pragma unroll
-              for (int c = 0; c < CS; ++c) {
-                const int j = cl + 16 * c;
-                if (j < k1) nxt[j] = M[r][c];
-              }
-            }
-        }
       }
       __syncthreads();
     }
@@ -1920,7 +1920,7 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
 template <int RS>
 cudaError_t rr_eig_rt(cudaStream_t st, int m, int K, const double* G, int ldg, double* theta,
                       float* Y, int* d_status, int* pflag, int mP, int* nfallback) {
-  const size_t sm = sizeof(float) * rt_smem_floats(m, K);
+  const size_t sm = sizeof(float) * rt_smem_floats(m, K, RS);
   if (m > 32 * RS || sm > 225 * 1024) return cudaErrorNotSupported;
   auto kern = k_rr_eig_rt<RS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
