@@ -188,6 +188,116 @@ __device__ int blk_ldl_inv(int n, T* M, int ldm, T* dd, T* cb, T tol, int ndrop 
   return -1;
 }
 
+
+// Register form of blk_ldl_inv run by the first NW warps of the block (named barrier 1): the
+// same elimination, pivots and drops (L^-1 left in the strictly lower part of M, the pivots in
+// dd, the first failing column returned, else -1), with the lower triangle of the n x n
+// matrix held in registers: half-warp g (0 .. 2 NW - 1) owns rows g + 2 NW r (r < RS), lane
+// cl = lane % 16 owns columns cl + 16 c (c < CS); n <= min(2 NW RS, 16 CS).  Few warps with many
+// entries each keep the per-column overhead (pivot, reciprocal, buffer hand-over) small next
+// to the one FMA per owned entry.  Step k reads a shared buffer (2 x 16 CS floats, double-
+// buffered by the parity of k) that holds row k of L^-1 in its entries c < k and the current
+// pivot column in its entries i >= k; the owners of column k + 1 and row k + 1 write the next
+// one right after their update, so one barrier per column suffices.  Entries above the
+// diagonal and past n take updates that are never read.  Only threads < 32 NW may call it.
+template <int NW, int RS, int CS>
+__device__ int ldl_inv_reg(int n, float* M, int ldm, float* dd, float* buf, float tol,
+                           int ndrop, bool zdrop) {
+  using T = float;
+  constexpr int NHW = 2 * NW;
+  constexpr int NTH = 32 * NW;
+  constexpr int BL = 16 * CS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = 2 * warp + (lane >> 4), cl = lane & 15;
+  auto sync = [] { asm volatile("bar.sync 1, %0;" ::"r"(NTH) : "memory"); };
+  T R[RS][CS];
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      const int i = g + NHW * r, j = cl + 16 * c;
+      R[r][c] = (i < n && j <= i) ? M[(long long)i * ldm + j] : (T)0;
+    }
+  for (int i = tid; i < 2 * BL; i += NTH) buf[i] = (T)0;
+  sync();
+  if (cl == 0) {
+#pragma unroll
+    for (int r = 0; r < RS; ++r)
+      if (g + NHW * r < BL) buf[g + NHW * r] = R[r][0];
+  }
+  sync();
+  int fc = -1;
+  bool stop = false;
+#pragma unroll
+  for (int q = 0; q < CS; ++q) {
+    if (stop) break;
+    const int r0 = (16 * q) / NHW;  // slots below hold rows < 16 q only
+    for (int kw = 0; kw < 16; ++kw) {
+      const int k = 16 * q + kw;
+      if (k >= n) {
+        stop = true;
+        break;
+      }
+      const T* __restrict__ cur = buf + (k & 1) * BL;
+      T* __restrict__ nxt = buf + ((k + 1) & 1) * BL;
+      const T dk = cur[k];
+      const bool drop = !(dk > tol);
+      if (drop && k >= ndrop && !(zdrop && dk == (T)0)) {  // uniform: every thread read dk
+        fc = k;
+        stop = true;
+        break;
+      }
+      if (tid == 0) dd[k] = drop ? (T)0 : dk;
+      const T invd = drop ? (T)0 : __frcp_rn(dk);
+      T l[RS];
+#pragma unroll
+      for (int r = r0; r < RS; ++r) {
+        const T wik = __shfl_sync(0xffffffffu, R[r][q], (lane & 16) | kw);
+        l[r] = g + NHW * r > k ? wik * invd : (T)0;
+      }
+#pragma unroll
+      for (int c = 0; c < CS; ++c) {
+        const T y = cur[cl + 16 * c];
+#pragma unroll
+        for (int r = r0; r < RS; ++r) R[r][c] = fmaf(-l[r], y, R[r][c]);
+      }
+      if (cl == kw) {
+#pragma unroll
+        for (int r = r0; r < RS; ++r)
+          if (g + NHW * r > k) R[r][q] = -l[r];
+      }
+      const int k1 = k + 1;
+      if (cl == (k1 & 15)) {
+#pragma unroll
+        for (int r = r0; r < RS; ++r) {
+          const int i = g + NHW * r;
+          if (i >= k1 && i < BL) nxt[i] = kw < 15 ? R[r][q] : R[r][q + 1 < CS ? q + 1 : q];
+        }
+      }
+      if (g == k1 % NHW) {
+        const int rk = k1 / NHW;
+#pragma unroll
+        for (int r = r0; r < RS; ++r)
+          if (r == rk) {
+#pragma unroll
+            for (int c = 0; c < CS; ++c)
+              if (cl + 16 * c < k1) nxt[cl + 16 * c] = R[r][c];
+          }
+      }
+      sync();
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RS; ++r)
+#pragma unroll
+    for (int c = 0; c < CS; ++c) {
+      const int i = g + NHW * r, j = cl + 16 * c;
+      if (i < n && j <= i) M[(long long)i * ldm + j] = R[r][c];
+    }
+  sync();
+  return fc;
+}
+
 // Cholesky-QR transform in the arithmetic of T: from the FP64 Gram G (accumulated in FP64
 // across CTAs), scale s = diag(G)^-1/2 in FP64, factor s G s = L D L' in T (with L^-1 formed
 // alongside), and write Tm = diag(s) L^-T D^-1/2 (ka x ka upper triangular) so that V Tm has
@@ -992,7 +1102,24 @@ __device__ void rr_phase_eigvecs(int m, int K, const T* __restrict__ d, const T*
         if (b <= a) Gs[a * K + b] *= wv[a] * wv[b];
       }
       __syncthreads();
-      const int fc = blk_ldl_inv<T>(K, Gs, K, dd, cbuf, (T)(sizeof(T) == 4 ? 1e-6 : 1e-14));
+      int fc;
+      if constexpr (sizeof(T) == 4) {
+        // the K x K factorization by four warps in registers (the others wait)
+        __shared__ int s_fc;
+        __shared__ float s_ldlbuf[2 * 64];
+        if (K <= 64) {
+          if (warp < 4) {
+            const int f = ldl_inv_reg<4, 8, 4>(K, Gs, K, dd, s_ldlbuf, 1e-6f, 0, false);
+            if (tid == 0) s_fc = f;
+          }
+          __syncthreads();
+          fc = s_fc;
+        } else {
+          fc = blk_ldl_inv<T>(K, Gs, K, dd, cbuf, (T)1e-6);
+        }
+      } else {
+        fc = blk_ldl_inv<T>(K, Gs, K, dd, cbuf, (T)1e-14);
+      }
       __syncthreads();
       RR_INV(2, tinv);
       if (fc >= 0) {
@@ -1654,125 +1781,41 @@ __global__ void __launch_bounds__(RT_NT, 1)
 }
 
 
-// Cholesky-QR transform with the matrix in registers, FP32, ka <= 32 RS, 16 warps: the same
-// arithmetic as k_chol_inv (scaled FP64 Gram, in-place LDL' with L^-1 formed alongside,
-// column drops, floors, the direction-block fallback), laid out like k_rr_eig_rt: half-warp
-// g owns rows g + 32 r, lane cl owns columns cl + 16 c.  Step k reads one shared buffer
-// (double-buffered by the parity of k) that holds row k of L^-1 in its entries c < k and the
-// current pivot column in its entries i >= k; the owners of column k + 1 and row k + 1 write
-// the next step's buffer right after their own update, so one barrier per column suffices.
-template <int RS>
-__global__ void __launch_bounds__(RT_NT, 1)
+// Cholesky-QR transform in FP32 with the factorization in registers (ldl_inv_reg, four warps,
+// ka <= min(8 RS, 16 CS)): the same arithmetic as k_chol_inv (scaled FP64 Gram, in-place LDL'
+// with L^-1 formed alongside, column drops, floors, the direction-block fallback).
+constexpr int CR_NW = 4;
+template <int RS, int CS>
+__global__ void __launch_bounds__(CR_NW * 32, 1)
     k_chol_inv_rt(int ka, const double* __restrict__ G, int ldg, float* __restrict__ Tm,
                   int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
                   int* ndropped, double rfloor, double pfloor) {
   using T = float;
-  constexpr int CS = 2 * RS;
-  __shared__ T s[32 * RS];
-  __shared__ T dd[32 * RS];
-  __shared__ T buf[2][32 * RS];
+  constexpr int NTH = CR_NW * 32;
+  extern __shared__ __align__(16) unsigned char craw[];
+  T* s = (T*)craw;                 // ka scale factors
+  T* dd = s + ka;                  // ka pivots
+  T* buf = dd + ka;                // 2 x 16 CS
+  T* W = buf + 2 * 16 * CS;        // ka x ka
   __shared__ int sfc;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = 2 * warp + (lane >> 4), cl = lane & 15;
-  for (int i = tid; i < ka; i += RT_NT) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < ka; i += NTH) {
     const double dgi = G[(long long)i * ldg + i];
     const double fl = i < keep ? rfloor * rfloor : pfloor * pfloor;
     s[i] = dgi > fl ? (T)rsqrt(dgi) : (T)0;
   }
-  if (tid == 0) sfc = -1;
   __syncthreads();
-  T M[RS][CS];
-#pragma unroll
-  for (int r = 0; r < RS; ++r)
-#pragma unroll
-    for (int c = 0; c < CS; ++c) {
-      const int i = g + 32 * r, j = cl + 16 * c;
-      T v = 0;
-      if (i < ka && j <= i) {
-        const double gg = 0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]);
-        v = (T)gg * s[i] * s[j];
-      }
-      M[r][c] = v;
-    }
-  // the first step's buffer: column 0 (entries past ka stay zero)
-  for (int i = tid; i < 2 * 32 * RS; i += RT_NT) (&buf[0][0])[i] = (T)0;
-  __syncthreads();
-  if (cl == 0) {
-#pragma unroll
-    for (int r = 0; r < RS; ++r) buf[0][g + 32 * r] = M[r][0];
+  for (int idx = tid; idx < ka * ka; idx += NTH) {
+    const int i = idx / ka, j = idx % ka;
+    if (j > i) continue;
+    const double gg = 0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]);
+    W[i * ka + j] = (T)gg * s[i] * s[j];
   }
   __syncthreads();
-  const T tol = (T)pivot_tol;
-  const bool zdrop = ndrop > 0;
-  int fc = -1;
-  bool stop = false;
-  // Each step updates every owned entry with one FMA: rows <= k get the multiplier 0, and the
-  // entries above the diagonal (and the padded ones) take updates that are never read.
-#pragma unroll
-  for (int q = 0; q < CS; ++q) {
-    if (stop) break;
-    const int r0 = q / 2;
-    for (int kw = 0; kw < 16; ++kw) {
-      const int k = 16 * q + kw;
-      if (k >= ka) {
-        stop = true;
-        break;
-      }
-      const T* __restrict__ cur = buf[k & 1];
-      T* __restrict__ nxt = buf[(k + 1) & 1];
-      const T dk = cur[k];
-      const bool drop = !(dk > tol);
-      if (drop && k >= ndrop && !(zdrop && dk == (T)0)) {  // uniform: every thread read dk
-        fc = k;
-        stop = true;
-        break;
-      }
-      if (tid == 0) dd[k] = drop ? (T)0 : dk;
-      const T invd = drop ? (T)0 : __frcp_rn(dk);
-      // the multipliers l_i = W_ik / d_k of the owned rows i > k, from the lane holding column k
-      T l[RS];
-#pragma unroll
-      for (int r = r0; r < RS; ++r) {
-        const T wik = __shfl_sync(0xffffffffu, M[r][q], (lane & 16) | kw);
-        l[r] = g + 32 * r > k ? wik * invd : (T)0;
-      }
-#pragma unroll
-      for (int c = 0; c < CS; ++c) {
-        const T y = cur[cl + 16 * c];
-#pragma unroll
-        for (int r = r0; r < RS; ++r) M[r][c] = fmaf(-l[r], y, M[r][c]);
-      }
-      // column k of L^-1: -l_i (a dropped column: 0)
-      if (cl == kw) {
-#pragma unroll
-        for (int r = r0; r < RS; ++r)
-          if (g + 32 * r > k) M[r][q] = -l[r];
-      }
-      // the next step's buffer: column k + 1 (rows >= k + 1) and row k + 1 of L^-1 (c <= k)
-      const int k1 = k + 1;
-      if (cl == (k1 & 15)) {
-#pragma unroll
-        for (int r = r0; r < RS; ++r) {
-          const int i = g + 32 * r;
-          if (i >= k1) nxt[i] = kw < 15 ? M[r][q] : M[r][q + 1 < CS ? q + 1 : q];
-        }
-      }
-      if (g == (k1 & 31)) {
-        const int rk = k1 >> 5;  // the slot of row k + 1
-#pragma unroll
-        for (int r = r0; r < RS; ++r)
-          if (r == rk) {
-#pragma unroll
-            for (int c = 0; c < CS; ++c)
-              if (cl + 16 * c < k1) nxt[cl + 16 * c] = M[r][c];
-          }
-      }
-      __syncthreads();
-    }
-  }
-  if (tid == 0) sfc = fc;
+  const int f = ldl_inv_reg<CR_NW, RS, CS>(ka, W, ka, dd, buf, (T)pivot_tol, ndrop, ndrop > 0);
+  if (tid == 0) sfc = f;
   __syncthreads();
-  fc = sfc;
+  const int fc = sfc;
   if (ndropped && tid == 0) {
     const int lim = fc >= 0 ? fc : ka;
     int cnt = 0;
@@ -1792,23 +1835,15 @@ __global__ void __launch_bounds__(RT_NT, 1)
       return;
     }
   }
-  // Tm[r][c] = s_r (L^-1)_cr d_c^-1/2 for r <= c < kk, else 0; the owner of M[i][j] (row i,
-  // column j, j <= i) writes Tm[j][i]
-#pragma unroll
-  for (int r = 0; r < RS; ++r)
-#pragma unroll
-    for (int c = 0; c < CS; ++c) {
-      const int i = g + 32 * r, j = cl + 16 * c;
-      if (i < ka && j < ka) {
-        T v = 0;
-        if (j <= i && i < kk) {
-          const T di = dd[i];
-          const T rd = di > (T)0 ? rsqrtf(di) : (T)0;
-          v = s[j] * (i == j ? (T)1 : M[r][c]) * rd;
-        }
-        Tm[(long long)j * ka + i] = v;
-      }
-    }
+  for (int i = tid; i < kk; i += NTH) buf[i] = dd[i] > (T)0 ? rsqrtf(dd[i]) : (T)0;
+  __syncthreads();
+  // Tm[r][c] = s_r (L^-1)_cr d_c^-1/2 for r <= c < kk, else 0
+  for (int idx = tid; idx < ka * ka; idx += NTH) {
+    const int r = idx / ka, c = idx % ka;
+    T v = 0;
+    if (r <= c && c < kk) v = s[r] * (r == c ? (T)1 : W[c * ka + r]) * buf[c];
+    Tm[(long long)r * ka + c] = v;
+  }
 }
 
 }  // namespace
@@ -1820,13 +1855,17 @@ cudaError_t chol_inv_nt(cudaStream_t st, Alloc& al, int ka, const double* G, int
                         int nthreads);
 
 
-template <int RS>
+template <int RS, int CS>
 cudaError_t chol_inv_rt(cudaStream_t st, int ka, const double* G, int ldg, float* Tm,
                         int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
                         int ndrop, int* ndropped, double rfloor, double pfloor) {
+  const size_t sm = sizeof(float) * ((size_t)2 * ka + 32 * CS + (size_t)ka * ka);
+  auto kern = k_chol_inv_rt<RS, CS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
   ProfScope ps(st, "chol_inv");
-  k_chol_inv_rt<RS><<<1, RT_NT, 0, st>>>(ka, G, ldg, Tm, d_status, fail_col, pivot_tol, keep,
-                                         pflag, ndrop, ndropped, rfloor, pfloor);
+  kern<<<1, CR_NW * 32, sm, st>>>(ka, G, ldg, Tm, d_status, fail_col, pivot_tol, keep, pflag,
+                                  ndrop, ndropped, rfloor, pfloor);
   note_launch();
   return cudaGetLastError();
 }
@@ -1837,17 +1876,14 @@ cudaError_t chol_inv(cudaStream_t st, Alloc& al, int ka, const double* G, int ld
                      int ndrop, int* ndropped, double rfloor, double pfloor) {
   if constexpr (sizeof(T) == 4) {
     if (ka >= 1 && ka <= 64)
-      return chol_inv_rt<2>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
-                            ndropped, rfloor, pfloor);
+      return chol_inv_rt<8, 4>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag,
+                               ndrop, ndropped, rfloor, pfloor);
     if (ka <= 96)
-      return chol_inv_rt<3>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
-                            ndropped, rfloor, pfloor);
+      return chol_inv_rt<12, 6>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag,
+                                ndrop, ndropped, rfloor, pfloor);
     if (ka <= 128)
-      return chol_inv_rt<4>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
-                            ndropped, rfloor, pfloor);
-    if (ka <= 160)
-      return chol_inv_rt<5>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
-                            ndropped, rfloor, pfloor);
+      return chol_inv_rt<16, 8>(st, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag,
+                                ndrop, ndropped, rfloor, pfloor);
   }
   return chol_inv_nt<T>(st, al, ka, G, ldg, Tm, d_status, pivot_tol, fail_col, keep, pflag, ndrop,
                         ndropped, rfloor, pfloor, 512);
