@@ -330,6 +330,19 @@ void sc_server_destroy(sc_server* s);
 int sc_gram(sc_ctx* ctx, int prec, int64_t n, int a, int b, const void* A, int64_t lda,
             const void* B, int64_t ldb, double* C, int on_device);
 
+/* sc_tall_update: out = beta Cin + A W, the tall-skinny update of a LOBPCG pass (the new
+ * X = [X R P] Y and its L-image, P = [R P] Y_RP; Knyazev 2001, Sec. II.B), for an n x a block A
+ * (row-major, leading dimension lda), an a x b matrix W (row-major, dense), an optional n x b
+ * Cin (NULL = no accumulate input; leading dimension ldc) and the n x b result out (leading
+ * dimension ldo).  prec: SC_PREC_MIXED = tcgen05 tensor cores, 3-term split TF32 products with
+ * FP32 accumulation (when the shape fits; otherwise CUDA cores); SC_PREC_FP32 / MIXED_DD = FP32
+ * CUDA cores; SC_PREC_FP64 = double arrays and arithmetic.  Arrays are device or host per
+ * on_device; the call returns after the result is written.
+ * Errors: SC_EINVAL (sizes, null pointers), SC_ENOMEM, SC_ECUDA, SC_ETIMEOUT. */
+int sc_tall_update(sc_ctx* ctx, int prec, int64_t n, int a, int b, const void* A, int64_t lda,
+                   const void* W, const void* Cin, int64_t ldc, double beta, void* out,
+                   int64_t ldo, int on_device);
+
 /* sc_rr_solve: Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of
  * the symmetric m x m matrix G (host, FP64, row-major; symmetrized on entry).  theta[K]
  * ascending (host FP64), Y[m*K] (host FP64, row-major, orthonormal columns).

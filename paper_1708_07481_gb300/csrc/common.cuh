@@ -136,10 +136,12 @@ cudaError_t gram_tc(cudaStream_t st, Alloc& al, long long n, const float* A, lon
                     long long probe_spins = 0);
 
 // Tall GEMM: out (n x b, ldo) = beta * Cin + A (n x a) W (a x b, row-major ldw, type T).
+// use_tc (FP32 only): run on tcgen05 tensor cores as 3-term split TF32 products when the shape
+// fits (k_tall_tc.cu), otherwise on CUDA cores.
 template <typename T>
 cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W, int ldw,
                       int b, T* out, long long ldo, const T* Cin, long long ldc, T beta,
-                      int* d_status = nullptr);
+                      int* d_status = nullptr, bool use_tc = false);
 // One output segment of a tall update: columns go to out (stride ldo), plus beta * Cin,
 // computed with the W block (stride ldw) whose rows start at row wskip of the concatenated A
 // (the rows before it are zero for this segment).
@@ -157,7 +159,11 @@ struct TallSeg {
 // [out_0 | out_1] = beta [Cin_0 | Cin_1] + A [W_0 | W_1] in one pass over A
 template <typename T>
 cudaError_t tall_gemm2(cudaStream_t st, long long n, const Cat3<T>& A, const TallSeg<T>& s0,
-                       const TallSeg<T>& s1, T beta, int* d_status = nullptr);
+                       const TallSeg<T>& s1, T beta, int* d_status = nullptr,
+                       bool use_tc = false);
+cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
+                         const TallSeg<float>& s0, const TallSeg<float>& s1, float beta,
+                         int* d_status);
 
 
 // Residual: R = LX - X diag(theta); rho2[j] = sum_i R_ij^2 (FP64).  With deg non-null the

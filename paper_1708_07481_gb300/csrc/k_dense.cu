@@ -2035,7 +2035,12 @@ template cudaError_t rr_eig<double>(cudaStream_t, Alloc&, int, int, const double
 
 #ifdef SC_RR_PHASES
 // Debug builds only: the clock64() marks of the last Rayleigh-Ritz launch (phase starts).
+// out[0..7]: phase marks; out[8..11]: accumulated eigenvector sub-phase clocks (LU solves,
+// Gram, factorization, transform) since the previous call, which clears them.
 extern "C" int sc_debug_rr_phases(long long* out) {
-  return cudaMemcpyFromSymbol(out, sc::g_rr_phase, sizeof(long long) * 8) == cudaSuccess ? 0 : -6;
+  if (cudaMemcpyFromSymbol(out, sc::g_rr_phase, sizeof(long long) * 8) != cudaSuccess) return -6;
+  if (cudaMemcpyFromSymbol(out + 8, sc::g_rr_inv, sizeof(long long) * 4) != cudaSuccess) return -6;
+  long long z[4] = {0, 0, 0, 0};
+  return cudaMemcpyToSymbol(sc::g_rr_inv, z, sizeof(z)) == cudaSuccess ? 0 : -6;
 }
 #endif

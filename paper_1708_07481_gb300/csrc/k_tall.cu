@@ -554,11 +554,14 @@ inline unsigned cap_grid(long long g, long long cap) {
 
 template <typename T>
 cudaError_t tall_gemm2(cudaStream_t st, long long n, const Cat3<T>& A, const TallSeg<T>& s0,
-                       const TallSeg<T>& s1, T beta, int* d_status) {
-  (void)d_status;
+                       const TallSeg<T>& s1, T beta, int* d_status, bool use_tc) {
   const int b = s0.b + s1.b;
   if (n == 0 || b == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
+    if (use_tc) {
+      const cudaError_t e = tall_gemm_tc(st, n, A, s0, s1, beta, d_status);
+      if (e != cudaErrorNotSupported) return e;
+    }
     // cp.async kernels: A segments 16-byte aligned.  Each segment is read up to its column
     // count rounded up to 4 (inside its row); the extra columns are zero-filled in shared
     // memory and meet zero rows of W.
@@ -679,10 +682,10 @@ cudaError_t tall_gemm2(cudaStream_t st, long long n, const Cat3<T>& A, const Tal
 template <typename T>
 cudaError_t tall_gemm(cudaStream_t st, long long n, const Cat3<T>& A, const T* W, int ldw,
                       int b, T* out, long long ldo, const T* Cin, long long ldc, T beta,
-                      int* d_status) {
+                      int* d_status, bool use_tc) {
   TallSeg<T> s0{out, ldo, Cin, ldc, W, ldw, 0, b};
   TallSeg<T> s1{};
-  return tall_gemm2<T>(st, n, A, s0, s1, beta, d_status);
+  return tall_gemm2<T>(st, n, A, s0, s1, beta, d_status, use_tc);
 }
 
 template <typename T>
@@ -779,9 +782,9 @@ template cudaError_t convert_mat<double, float>(cudaStream_t, long long, int, co
   template cudaError_t cast_mat<T>(cudaStream_t, int, int, const double*, int, T*, int,      \
                                    double);                                                  \
   template cudaError_t tall_gemm<T>(cudaStream_t, long long, const Cat3<T>&, const T*, int,  \
-                                    int, T*, long long, const T*, long long, T, int*);       \
+                                    int, T*, long long, const T*, long long, T, int*, bool); \
   template cudaError_t tall_gemm2<T>(cudaStream_t, long long, const Cat3<T>&,                \
-                                     const TallSeg<T>&, const TallSeg<T>&, T, int*);         \
+                                     const TallSeg<T>&, const TallSeg<T>&, T, int*, bool);   \
   template cudaError_t residual<T>(cudaStream_t, Alloc&, long long, int, const T*, const T*, \
                                    long long, const double*, T*, double*, const T*);         \
   template cudaError_t gather_cols<T>(cudaStream_t, long long, const T*, long long, T*,      \

@@ -1,0 +1,369 @@
+// Tall-skinny LOBPCG updates on tcgen05 tensor cores (Sec. IV: the O(n l) multi-vector
+// work): out (n x b) = beta Cin + [A_0 A_1 A_2] W for FP32 blocks, as the update
+// [X R P] Y, the projections R - X F and the Cholesky-QR transforms V Tm of one pass.
+//
+// 3-term split TF32 as in the Gram kernel: x = x_big + x_small, x_big = tf32(x),
+// x_small = tf32(x - x_big); A W ~ Ab Wb + Ab Ws + As Wb, FP32 accumulation in tensor memory.
+//
+// Operands (both K-major, 128-byte swizzle):
+//   A side (M = 128 rows of the tall block, K = 32 columns per chunk): a TMA tiled load of the
+//   FP32 rows with SWIZZLE_128B lands exactly in the K-major SW128 layout the MMA reads, so the
+//   split is an in-place sweep over the staged tile (big overwrites the FP32 values, small
+//   goes to a second buffer at the same offsets);
+//   B side (N = output columns, rounded up to 16, K = the same chunks): W^T split once per CTA
+//   into shared memory and kept for all the CTA's row tiles.
+// Each A segment is cut into chunks of 32 columns (the last one zero-filled by the TMA past
+// the segment's width, and the matching rows of W^T are zero).  A persistent CTA walks row
+// tiles of 128 with NSTG staged chunks in flight; one thread issues the TMA copies and the
+// MMAs (4 K-steps x 3 products per chunk), commits per stage (to refill it) and per tile (for
+// the epilogue); four warps read the accumulator with tcgen05.ld (warp w: rows 32 w .. +32)
+// and write beta Cin + acc.  Every wait is bounded; on a time-out the CTA records ST_TIMEOUT,
+// waits (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
+#include <algorithm>
+#include <cstring>
+
+#include "tc.cuh"
+
+namespace sc {
+namespace {
+
+constexpr int TT_M = 128;       // rows per tile (MMA M)
+constexpr int TT_K = 32;        // columns per chunk (one 128-byte swizzle row of FP32)
+constexpr int TT_NSTG = 3;      // staged chunks in flight
+constexpr int TT_NTH = 128;     // four warps: one accumulator lane quarter each
+constexpr int TT_STAGE = TT_M * TT_K * 4;  // 16 KB
+constexpr int TT_MAXW = 120 * 1024;        // W^T big + small resident in shared memory
+constexpr int TT_SMEM = 1024 + TT_NSTG * 2 * TT_STAGE + TT_MAXW + 256;
+
+struct TcTall {
+  int nseg;
+  int nch[3];     // chunks of each A segment
+  int cseg[3];    // columns of each A segment
+  int wrow[3];    // first logical row of W for each segment
+  int nchunks;    // total chunks
+  int nn;         // MMA N: output columns rounded up to 16
+  long long n;
+  int ntiles;
+  // outputs: columns [0, b0) -> segment 0, [b0, b) -> segment 1
+  float* out[2];
+  long long ldo[2];
+  const float* cin[2];
+  long long ldc[2];
+  const float* w[2];
+  int ldw[2];
+  int wskip[2];
+  int vec[2];
+  int b0, b;
+  float beta;
+};
+
+__device__ __forceinline__ float tt_w(const TcTall& p, int lr, int col) {
+  if (col >= p.b) return 0.f;
+  const bool s1 = col >= p.b0;
+  const int skip = s1 ? p.wskip[1] : p.wskip[0];
+  if (lr < skip) return 0.f;
+  const float* w = s1 ? p.w[1] : p.w[0];
+  const int ldw = s1 ? p.ldw[1] : p.ldw[0];
+  return w[(long long)(lr - skip) * ldw + (s1 ? col - p.b0 : col)];
+}
+
+__device__ __forceinline__ void tma_load_2d_tt(void* dst, const CUtensorMap* map, int x, int y,
+                                               uint64_t* bar) {
+  tma_load_2d(dst, map, x, y, bar);
+}
+
+__global__ void __launch_bounds__(TT_NTH, 1)
+    k_tall_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+              const __grid_constant__ CUtensorMap map2, const __grid_constant__ TcTall p,
+              int* status) {
+  extern __shared__ __align__(1024) uint8_t tt_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)tt_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* stg = base;                                   // [NSTG] FP32 -> big, 16 KB each
+  uint8_t* sml = stg + TT_NSTG * TT_STAGE;               // [NSTG] small, 16 KB each
+  uint8_t* wbig = sml + TT_NSTG * TT_STAGE;              // [nchunks] nn x 128 B
+  const int wchunk = p.nn * 128;
+  uint8_t* wsml = wbig + p.nchunks * wchunk;
+  uint64_t* bars = (uint64_t*)(wsml + p.nchunks * wchunk);
+  uint64_t* full = bars;                // [NSTG] TMA landed
+  uint64_t* mdone = bars + TT_NSTG;     // [NSTG] MMAs reading the stage finished
+  uint64_t* accd = bars + 2 * TT_NSTG;  // accumulator of the tile complete
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TT_NSTG + 1);
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const CUtensorMap* maps[3] = {&map0, &map1, &map2};
+  int tcols = 32;
+  while (tcols < p.nn) tcols <<= 1;
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int q = 0; q < 2 * TT_NSTG + 1; ++q) mbar_init(&bars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int q = 0; q < p.nseg; ++q)
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)maps[q]) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // W^T, split into big / small TF32, K-major SW128: chunk c, operand row r (output column),
+  // k in [0, 32)
+  for (int idx = tid; idx < p.nchunks * p.nn * TT_K; idx += TT_NTH) {
+    const int kk = idx % TT_K, r = (idx / TT_K) % p.nn, ch = idx / (TT_K * p.nn);
+    int q = 0, cc = ch;
+    while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
+    const int lc = cc * TT_K + kk;
+    const float wv = lc < p.cseg[q] ? tt_w(p, p.wrow[q] + lc, r) : 0.f;
+    const uint32_t bgv = to_tf32(wv);
+    const uint32_t smv = to_tf32(wv - __uint_as_float(bgv));
+    const uint32_t off = (uint32_t)ch * wchunk + sw128_off(r, kk);
+    *reinterpret_cast<uint32_t*>(wbig + off) = bgv;
+    *reinterpret_cast<uint32_t*>(wsml + off) = smv;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.nn >> 3) << 17) |
+                         ((uint32_t)(TT_M >> 4) << 24);
+
+  // the CTA's sequence of (tile, chunk) loads: index i -> tile blockIdx.x + (i / nchunks) grid,
+  // chunk i % nchunks
+  const int my_tiles = blockIdx.x < p.ntiles ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total = (long long)my_tiles * p.nchunks;
+  auto issue = [&](long long i) {  // thread 0
+    const int s = (int)(i % TT_NSTG);
+    const int tile = blockIdx.x + (int)(i / p.nchunks) * gridDim.x;
+    int q = 0, cc = (int)(i % p.nchunks);
+    while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
+    mbar_expect_tx(&full[s], TT_STAGE);
+    tma_load_2d_tt(stg + s * TT_STAGE, maps[q], cc * TT_K, tile * TT_M, &full[s]);
+  };
+  long long issued = 0, mma_commits[TT_NSTG] = {0, 0, 0}, acc_commits = 0;
+  if (tid == 0)
+    for (; issued < total && issued < TT_NSTG; ++issued) issue(issued);
+
+  for (long long i = 0; i < total; ++i) {
+    const int s = (int)(i % TT_NSTG);
+    const int ch = (int)(i % p.nchunks);
+    const int tile = blockIdx.x + (int)(i / p.nchunks) * gridDim.x;
+    bool ok = mbar_wait(&full[s], (uint32_t)((i / TT_NSTG) & 1));
+    if (!ok) atomicExch(&abort_flag, 1);
+    __syncthreads();
+    if (abort_flag) break;
+    // split the staged FP32 tile in place: big over the FP32 values, small beside it
+    {
+      uint4* sb = reinterpret_cast<uint4*>(stg + s * TT_STAGE);
+      uint4* ss = reinterpret_cast<uint4*>(sml + s * TT_STAGE);
+#pragma unroll 4
+      for (int v = tid; v < TT_STAGE / 16; v += TT_NTH) {
+        const uint4 x = sb[v];
+        uint4 bg, sm;
+        bg.x = to_tf32(__uint_as_float(x.x));
+        bg.y = to_tf32(__uint_as_float(x.y));
+        bg.z = to_tf32(__uint_as_float(x.z));
+        bg.w = to_tf32(__uint_as_float(x.w));
+        sm.x = to_tf32(__uint_as_float(x.x) - __uint_as_float(bg.x));
+        sm.y = to_tf32(__uint_as_float(x.y) - __uint_as_float(bg.y));
+        sm.z = to_tf32(__uint_as_float(x.z) - __uint_as_float(bg.z));
+        sm.w = to_tf32(__uint_as_float(x.w) - __uint_as_float(bg.w));
+        sb[v] = bg;
+        ss[v] = sm;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ab = smem_u32(stg + s * TT_STAGE), as_ = smem_u32(sml + s * TT_STAGE);
+      const uint32_t wb = smem_u32(wbig + ch * wchunk), ws = smem_u32(wsml + ch * wchunk);
+#pragma unroll
+      for (int ks = 0; ks < TT_K / 8; ++ks) {
+        const uint32_t ko = ks * 32;
+        const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+        mma_tf32(tmem, sw128_desc(as_ + ko), sw128_desc(wb + ko), idesc, acc0);
+        mma_tf32(tmem, sw128_desc(ab + ko), sw128_desc(ws + ko), idesc, 1u);
+        mma_tf32(tmem, sw128_desc(ab + ko), sw128_desc(wb + ko), idesc, 1u);
+      }
+      mma_commit(&mdone[s]);
+      mma_commits[s] += 1;
+      if (ch == p.nchunks - 1) {
+        mma_commit(accd);
+        acc_commits += 1;
+      }
+      // refill this stage once its MMAs are done
+      if (issued < total) {
+        const bool okm = mbar_wait(&mdone[s], (uint32_t)((mma_commits[s] - 1) & 1));
+        if (!okm) {
+          atomicExch(&abort_flag, 1);
+        } else {
+          issue(issued);
+          ++issued;
+        }
+      }
+    }
+    if (ch == p.nchunks - 1) {
+      // epilogue of the tile: all threads wait for the accumulator
+      __shared__ int acc_ok;
+      if (tid == 0) acc_ok = mbar_wait(accd, (uint32_t)((acc_commits - 1) & 1)) ? 1 : 0;
+      __syncthreads();
+      if (!acc_ok) {
+        if (tid == 0) atomicExch(&abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const long long row = (long long)tile * TT_M + 32 * warp + lane;
+      for (int c0 = 0; c0 < p.b; c0 += 32) {  // uniform
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+              "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < p.n) {
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            const int col = c0 + 4 * j4;
+            if (col >= p.b) break;
+            const bool s1 = col >= p.b0;
+            const int cs = s1 ? col - p.b0 : col;
+            const int bs = s1 ? p.b - p.b0 : p.b0;
+            float* out = p.out[s1];
+            const long long ldo = p.ldo[s1];
+            const float* cin = p.cin[s1];
+            const long long ldc = p.ldc[s1];
+            float r4[4] = {__uint_as_float(v[4 * j4]), __uint_as_float(v[4 * j4 + 1]),
+                           __uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3])};
+            if (p.vec[s1] && cs + 3 < bs) {
+              if (cin) {
+                const float4 cv = *reinterpret_cast<const float4*>(cin + row * ldc + cs);
+                r4[0] = fmaf(p.beta, cv.x, r4[0]);
+                r4[1] = fmaf(p.beta, cv.y, r4[1]);
+                r4[2] = fmaf(p.beta, cv.z, r4[2]);
+                r4[3] = fmaf(p.beta, cv.w, r4[3]);
+              }
+              *reinterpret_cast<float4*>(out + row * ldo + cs) =
+                  make_float4(r4[0], r4[1], r4[2], r4[3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int cj = col + j;
+                if (cj >= p.b) break;
+                const bool t1 = cj >= p.b0;
+                const int ct = t1 ? cj - p.b0 : cj;
+                const float* cn = p.cin[t1];
+                float x = r4[j];
+                if (cn) x = fmaf(p.beta, cn[row * p.ldc[t1] + ct], x);
+                p.out[t1][row * p.ldo[t1] + ct] = x;
+              }
+            }
+          }
+        }
+      }
+      // the accumulator is read: the next tile's first MMA may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  // drain: after a time-out, wait (bounded) for this CTA's MMAs and copies in flight
+  if (tid == 0) {
+    bool ok = !abort_flag;
+    for (int q = 0; q < TT_NSTG; ++q)
+      if (mma_commits[q] > 0) ok = mbar_wait(&mdone[q], (uint32_t)((mma_commits[q] - 1) & 1)) && ok;
+    if (acc_commits > 0) ok = mbar_wait(accd, (uint32_t)((acc_commits - 1) & 1)) && ok;
+    if (!ok) atomicExch(&abort_flag, 1);
+    if (abort_flag) {
+      // the loads issued for indices the loop did not consume
+      for (int q = 0; q < TT_NSTG; ++q) {
+        // index of the latest load into stage q, if any was issued
+        long long last = -1;
+        for (long long j = issued - 1; j >= 0 && j >= issued - TT_NSTG; --j)
+          if (j % TT_NSTG == q) last = j;
+        if (last >= 0) mbar_wait(&full[q], (uint32_t)((last / TT_NSTG) & 1));
+      }
+      atomicOr(status, ST_TIMEOUT);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tcols)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+// out = beta Cin + A W on tensor cores when the shape fits (A segments 16-byte aligned with
+// strides a multiple of 4 floats, W^T resident in shared memory, N <= 256); otherwise
+// cudaErrorNotSupported and the caller uses the CUDA-core kernels.
+cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
+                         const TallSeg<float>& s0, const TallSeg<float>& s1, float beta,
+                         int* d_status) {
+  const int b = s0.b + s1.b;
+  if (n <= 0 || b <= 0) return cudaErrorNotSupported;
+  TcTall p{};
+  p.nseg = A.nblk;
+  p.n = n;
+  int ch = 0, wr = 0;
+  for (int q = 0; q < A.nblk; ++q) {
+    if (((uintptr_t)A.p[q] & 15) || (A.ld[q] & 3) || A.c[q] <= 0) return cudaErrorNotSupported;
+    p.cseg[q] = A.c[q];
+    p.nch[q] = (A.c[q] + TT_K - 1) / TT_K;
+    p.wrow[q] = wr;
+    ch += p.nch[q];
+    wr += A.c[q];
+  }
+  p.nchunks = ch;
+  p.nn = (b + 15) & ~15;
+  if (p.nn > 256 || (size_t)2 * ch * p.nn * 128 > (size_t)TT_MAXW) return cudaErrorNotSupported;
+  const TallSeg<float>* sg[2] = {&s0, &s1};
+  for (int q = 0; q < 2; ++q) {
+    const TallSeg<float>& g = *sg[q];
+    p.out[q] = g.out;
+    p.ldo[q] = g.ldo;
+    p.cin[q] = g.Cin;
+    p.ldc[q] = g.ldc;
+    p.w[q] = g.W;
+    p.ldw[q] = g.ldw;
+    p.wskip[q] = g.wskip;
+    p.vec[q] = g.b > 0 && ((uintptr_t)g.out & 15) == 0 && (g.ldo & 3) == 0 &&
+               (!g.Cin || (((uintptr_t)g.Cin & 15) == 0 && (g.ldc & 3) == 0)) &&
+               (q == 0 || (s0.b & 3) == 0);
+  }
+  if (s1.b > 0 && (s0.b & 3)) p.vec[1] = 0;
+  p.b0 = s0.b;
+  p.b = b;
+  p.beta = beta;
+  p.ntiles = (int)((n + TT_M - 1) / TT_M);
+  CUtensorMap m[3];
+  for (int q = 0; q < 3; ++q) {
+    const int qq = q < A.nblk ? q : 0;
+    if (!make_map_fp32(&m[q], A.p[qq], n, A.c[qq], A.ld[qq], TT_K, TT_M,
+                       CU_TENSOR_MAP_SWIZZLE_128B))
+      return cudaErrorNotSupported;
+  }
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_tall_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM);
+  });
+  const int grid = std::min(p.ntiles, 152);
+  ProfScope ps(st, "tall_gemm");
+  k_tall_tc<<<grid, TT_NTH, TT_SMEM, st>>>(m[0], m[1], m[2], p, d_status);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace sc

@@ -681,7 +681,8 @@ struct LobRun : RunBase {
     cudaError_t e = gram_seg(Yc, ldyc, {{0, kc}}, V, ldv, {{0, cols}}, Gy, cols, false);
     if (e == cudaSuccess) e = cast_mat<T>(st, kc, cols, Gy, cols, Ty, cols, -1.0);
     if (e == cudaSuccess)
-      e = tall_gemm<T>(st, n, cat<T>(Yc, ldyc, kc), Ty, cols, cols, V, ldv, V, ldv, (T)1, dstatus);
+      e = tall_gemm<T>(st, n, cat<T>(Yc, ldyc, kc), Ty, cols, cols, V, ldv, V, ldv, (T)1, dstatus,
+                       use_tc != 0);
     return e;
   }
 
@@ -695,7 +696,7 @@ struct LobRun : RunBase {
     if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
     *failed = (hs & (ST_CHOL_FAIL | ST_NONFINITE)) != 0;
     if (*failed) return SC_OK;
-    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0, dstatus), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
     return SC_OK;
   }
 
@@ -812,8 +813,8 @@ struct LobRun : RunBase {
     // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
     CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, true), "gram");
     CK(rr(K, G), "rr");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
     std::swap(S, S2);
     std::swap(LS, LS2);
     CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2, pdeg), "residual");
@@ -893,7 +894,7 @@ struct LobRun : RunBase {
     {
       TallSeg<T> sr{WR, ldw, WR, ldw, Tm, w, 0, ka};
       TallSeg<T> sp{WP, ldw, WP, ldw, Tm + ka, w, 0, haveP ? ka : 0};
-      CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus), "tall");
+      CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus, use_tc != 0), "tall");
     }
     // (2) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too), into
     //     the R and P slots.  A breakdown inside the P columns is handled on the device: the
@@ -913,13 +914,13 @@ struct LobRun : RunBase {
       else
         CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
       CK(chol(wq, G, TmA, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
-      CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus), "tall");
+      CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
       CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
       CK(chol(wq, G, TmB, dfail, ka, pf, ka, nullptr), "chol");
       // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
-      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
       if (haveP)
-        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus), "tall");
+        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
     }
     // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken
     //     on the orthonormalized block so that its images are products with L rather than
@@ -950,10 +951,10 @@ struct LobRun : RunBase {
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
     Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);
     fork();  // the L-images on the second stream
-    CK(tall_gemm<T>(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus), "tall");
-    CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1, dstatus), "tall");
-    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1, dstatus), "tall");
+    CK(tall_gemm<T>(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1, dstatus, use_tc != 0), "tall");
     join();
     std::swap(S, S2);
     std::swap(LS, LS2);
@@ -965,8 +966,8 @@ struct LobRun : RunBase {
     if ((done_passes + 1) % kReorth == 0) {
       CK(gram_seg(S, ld3, {{0, K}}, S, ld3, {{0, K}}, G, K, true), "gram");
       CK(chol(K, G, Tm), "chol");
-      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus), "tall");
-      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
       CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, T1, sizeof(T) * kp, sizeof(T) * K, n,
                            cudaMemcpyDeviceToDevice, st), "reorth");
       CK(cudaMemcpy2DAsync(LS, sizeof(T) * ld3, W1, sizeof(T) * kp, sizeof(T) * K, n,
@@ -1506,6 +1507,67 @@ int sc_gram(sc_ctx* c, int prec, int64_t n, int a, int b, const void* A, int64_t
   if (prec == SC_PREC_FP64)
     return gram_t<double>(c, prec, n, a, b, (const double*)A, lda, (const double*)B, ldb, C, on_device);
   return gram_t<float>(c, prec, n, a, b, (const float*)A, lda, (const float*)B, ldb, C, on_device);
+}
+
+template <typename T>
+static int update_t(sc_ctx* c, int prec, int64_t n, int a, int b, const T* A, int64_t lda,
+                    const T* W, const T* Cin, int64_t ldc, double beta, T* out, int64_t ldo,
+                    int on_device) {
+  Alloc al = alloc_of(c);
+  const int V = 16 / sizeof(T);
+  const int ap = (a + V - 1) / V * V, bp = (b + V - 1) / V * V;
+  T* dA = al.get<T>((size_t)n * ap + 1);
+  T* dW = al.get<T>((size_t)a * b + 1);
+  T* dC = Cin ? al.get<T>((size_t)n * bp + 1) : nullptr;
+  T* dO = al.get<T>((size_t)n * bp + 1);
+  int rc = SC_OK;
+  if (!dA || !dW || !dO || (Cin && !dC)) {
+    rc = fail(c, SC_ENOMEM, "sc_tall_update: out of device memory or HBM budget");
+  } else {
+    cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+      e = cudaMemcpy2DAsync(dA, sizeof(T) * ap, A, sizeof(T) * lda, sizeof(T) * a, n, kin, c->stream);
+      if (e == cudaSuccess && Cin)
+        e = cudaMemcpy2DAsync(dC, sizeof(T) * bp, Cin, sizeof(T) * ldc, sizeof(T) * b, n, kin, c->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dW, W, sizeof(T) * (size_t)a * b, kin, c->stream);
+    if (e == cudaSuccess)
+      e = tall_gemm<T>(c->stream, n, cat<T>(dA, ap, a), dW, b, b, dO, bp, dC, bp, (T)beta,
+                       c->d_status, prec == SC_PREC_MIXED);
+    if (e == cudaSuccess && n > 0)
+      e = cudaMemcpy2DAsync(out, sizeof(T) * ldo, dO, sizeof(T) * bp, sizeof(T) * b, n, kout, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "sc_tall_update");
+  }
+  al.put(dA);
+  al.put(dW);
+  al.put(dC);
+  al.put(dO);
+  cudaStreamSynchronize(c->stream);
+  if (rc != SC_OK) return rc;
+  int hs = 0;
+  rc = read_status(c, &hs);
+  if (rc != SC_OK) return rc;
+  if (hs & 32) return fail(c, SC_ETIMEOUT, "sc_tall_update: a bounded device wait gave up");
+  return SC_OK;
+}
+
+int sc_tall_update(sc_ctx* c, int prec, int64_t n, int a, int b, const void* A, int64_t lda,
+                   const void* W, const void* Cin, int64_t ldc, double beta, void* out,
+                   int64_t ldo, int on_device) {
+  if (!c) return SC_EINVAL;
+  if (n < 0 || a < 1 || b < 1 || !A || !W || !out || lda < a || ldo < b || (Cin && ldc < b) ||
+      prec < SC_PREC_MIXED || prec > SC_PREC_MIXED_DD)
+    return fail(c, SC_EINVAL, "sc_tall_update: invalid argument");
+  cudaSetDevice(c->device);
+  if (prec == SC_PREC_FP64)
+    return update_t<double>(c, prec, n, a, b, (const double*)A, lda, (const double*)W,
+                            (const double*)Cin, ldc, beta, (double*)out, ldo, on_device);
+  return update_t<float>(c, prec, n, a, b, (const float*)A, lda, (const float*)W,
+                         (const float*)Cin, ldc, beta, (float*)out, ldo, on_device);
 }
 
 template <typename T>

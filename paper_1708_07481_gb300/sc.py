@@ -104,6 +104,8 @@ def lib():
         "sc_stream_update": ([vp, vp, i32, i64, vp, vp, vp, C.c_int], C.c_int),
         "sc_gram": ([vp, C.c_int, i64, C.c_int, C.c_int, vp, i64, vp, i64, vp, C.c_int], C.c_int),
         "sc_rr_solve": ([vp, C.c_int, C.c_int, C.c_int, vp, vp, vp], C.c_int),
+        "sc_tall_update": ([vp, C.c_int, i64, C.c_int, C.c_int, vp, i64, vp, vp, i64, dbl, vp, i64,
+                            C.c_int], C.c_int),
         "sc_lobpcg_batch": ([vp, C.c_int, vp, vp, vp, vp], C.c_int),
         "sc_lobpcg_blocks": ([vp, vp, C.c_int, C.c_int, C.POINTER(LobpcgOpts), vp, vp,
                               C.POINTER(EigInfo)], C.c_int),
@@ -389,6 +391,19 @@ def sc_gram(ctx: Ctx, A, B, prec=SC_PREC_FP32):
     pa, dev = _ptr(A)
     ctx.check(lib().sc_gram(ctx.h, prec, n, a, b, pa, a, _ptr(B)[0], b, _ptr(Cm)[0], dev))
     return Cm
+
+
+def sc_tall_update(ctx: Ctx, A, W, Cin=None, beta=1.0, prec=SC_PREC_MIXED):
+    """out = beta Cin + A W (host numpy arrays; float64 with SC_PREC_FP64, else float32)."""
+    dt = np.float64 if prec == SC_PREC_FP64 else np.float32
+    A, W = _np(A, dt), _np(W, dt)
+    n, a = int(A.shape[0]), int(A.shape[1])
+    b = int(W.shape[1])
+    Cin = None if Cin is None else _np(Cin, dt)
+    out = np.empty((n, b), dt)
+    ctx.check(lib().sc_tall_update(ctx.h, prec, n, a, b, _ptr(A)[0], a, _ptr(W)[0], _ptr(Cin)[0],
+                                   b, float(beta), _ptr(out)[0], b, 0))
+    return out
 
 
 def sc_rr_solve(ctx: Ctx, G, K, prec=SC_PREC_FP32):

@@ -158,6 +158,37 @@ def test_gram_tc_ragged_and_structured(sc, ctx):
         assert np.all(np.abs(Cm - ref) <= bound), (n, a, b)
 
 
+# ------------------------------------------------------------------ a7: tall update
+
+
+@pytest.mark.parametrize("n,a,b", [(1, 3, 5), (33, 5, 7), (777, 44, 44), (50001, 132, 44),
+                                   (4099, 88, 96), (3000, 40, 300), (2000, 500, 40)])
+@pytest.mark.parametrize("prec", ["mixed", "fp32", "fp64"])
+def test_tall_update(sc, ctx, n, a, b, prec):
+    """out = beta Cin + A W element by element against the FP64 product of the same (rounded)
+    inputs: tcgen05 3xTF32 (mixed; shapes past its shared-memory limit fall back to CUDA
+    cores), FP32 CUDA cores, FP64."""
+    rng = np.random.default_rng(n + a + b)
+    A = rng.standard_normal((n, a))
+    W = rng.standard_normal((a, b))
+    Cin = rng.standard_normal((n, b))
+    if prec == "fp64":
+        out = sc.sc_tall_update(ctx, A, W, Cin, -0.5, sc.SC_PREC_FP64)
+        ref = -0.5 * Cin + A @ W
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-13 * (np.abs(A) @ np.abs(W)).max())
+        return
+    A32, W32, C32 = A.astype(np.float32), W.astype(np.float32), Cin.astype(np.float32)
+    p = sc.SC_PREC_MIXED if prec == "mixed" else sc.SC_PREC_FP32
+    out = sc.sc_tall_update(ctx, A32, W32, C32, -0.5, p)
+    Ad, Wd, Cd = (x.astype(np.float64) for x in (A32, W32, C32))
+    ref = -0.5 * Cd + Ad @ Wd
+    scale = np.abs(Ad) @ np.abs(Wd) + 0.5 * np.abs(Cd)
+    assert np.all(np.abs(out - ref) <= 4e-6 * scale + 1e-30), (n, a, b, prec)
+    # no accumulate input
+    out0 = sc.sc_tall_update(ctx, A32, W32, None, 0.0, p)
+    assert np.all(np.abs(out0 - Ad @ Wd) <= 4e-6 * (np.abs(Ad) @ np.abs(Wd)) + 1e-30)
+
+
 # ------------------------------------------------------------------ a6: Rayleigh-Ritz solve
 
 
