@@ -16,8 +16,8 @@
 // the segment's width, and the matching rows of W^T are zero).  A persistent CTA walks row
 // tiles of 128 with NSTG staged chunks in flight; one thread issues the TMA copies and the
 // MMAs (4 K-steps x 3 products per chunk), commits per stage (to refill it) and per tile (for
-// the epilogue); four warps read the accumulator with tcgen05.ld (warp w: rows 32 w .. +32)
-// and write beta Cin + acc.  Every wait is bounded; on a time-out the CTA records ST_TIMEOUT,
+// the epilogue); eight warps read the accumulator with tcgen05.ld (warp w: rows
+// 32 (w % 4) .. +32, columns 32 (w / 4) + 64 j .. +32) and write beta Cin + acc.  Every wait is bounded; on a time-out the CTA records ST_TIMEOUT,
 // waits (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstring>
@@ -30,7 +30,7 @@ namespace {
 constexpr int TT_M = 128;       // rows per tile (MMA M)
 constexpr int TT_K = 32;        // columns per chunk (one 128-byte swizzle row of FP32)
 constexpr int TT_NSTG = 3;      // staged chunks in flight
-constexpr int TT_NTH = 128;     // four warps: one accumulator lane quarter each
+constexpr int TT_NTH = 256;     // eight warps: warps w, w + 4 share lane quarter w % 4
 constexpr int TT_STAGE = TT_M * TT_K * 4;  // 16 KB
 constexpr int TT_MAXW = 120 * 1024;        // W^T big + small resident in shared memory
 constexpr int TT_SMEM = 1024 + TT_NSTG * 2 * TT_STAGE + TT_MAXW + 256;
@@ -195,9 +195,11 @@ __global__ void __launch_bounds__(TT_NTH, 1)
         mma_commit(accd);
         acc_commits += 1;
       }
-      // refill this stage once its MMAs are done
-      if (issued < total) {
-        const bool okm = mbar_wait(&mdone[s], (uint32_t)((mma_commits[s] - 1) & 1));
+      // refill the previous chunk's stage (its MMAs were issued one chunk ago and have had
+      // this chunk's wait and split to finish): load i + NSTG - 1 goes where load i - 1 was
+      if (i >= 1 && issued < total) {
+        const int sp = (int)((i - 1) % TT_NSTG);
+        const bool okm = mbar_wait(&mdone[sp], (uint32_t)((mma_commits[sp] - 1) & 1));
         if (!okm) {
           atomicExch(&abort_flag, 1);
         } else {
@@ -216,10 +218,10 @@ __global__ void __launch_bounds__(TT_NTH, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const long long row = (long long)tile * TT_M + 32 * warp + lane;
-      for (int c0 = 0; c0 < p.b; c0 += 32) {  // uniform
+      const long long row = (long long)tile * TT_M + 32 * (warp & 3) + lane;
+      for (int c0 = 32 * (warp >> 2); c0 < p.b; c0 += 64) {  // uniform in the warp
         uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
