@@ -27,10 +27,14 @@ __device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier (at most `limit` polls); returns false on
-// timeout.
+// Bounded wait for phase `parity` of an mbarrier: at most `limit` polls and at most
+// WAIT_CLOCKS SM clocks (about two seconds); returns false on timeout.  try_wait suspends the
+// thread in hardware between polls, so no software back-off is added (a sleep after each
+// failed poll delayed every wake-up).
+constexpr long long WAIT_CLOCKS = 4LL << 30;
 __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = SPIN_LIMIT) {
   uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
   for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
@@ -40,7 +44,7 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (it > 64) __nanosleep(64);
+    if ((it & 255) == 255 && clock64() - t0 > WAIT_CLOCKS) return false;
   }
   return false;
 }
