@@ -519,6 +519,9 @@ struct LobRun : RunBase {
   RunAlloc ra;
   Alloc al;
   int use_tc;
+  // tall updates on tensor cores: off, the CUDA-core kernels are faster at these shapes so far
+  // (the tensor-core form serves sc_tall_update)
+  bool tall_tc = false;
   bool dense64 = false;      // small dense solves in FP64, results cast to T
   double *Gd = nullptr, *Yd = nullptr;  // FP64 results of those solves
   double pivot_tol;
@@ -682,7 +685,7 @@ struct LobRun : RunBase {
     if (e == cudaSuccess) e = cast_mat<T>(st, kc, cols, Gy, cols, Ty, cols, -1.0);
     if (e == cudaSuccess)
       e = tall_gemm<T>(st, n, cat<T>(Yc, ldyc, kc), Ty, cols, cols, V, ldv, V, ldv, (T)1, dstatus,
-                       use_tc != 0);
+                       tall_tc);
     return e;
   }
 
@@ -696,7 +699,7 @@ struct LobRun : RunBase {
     if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
     *failed = (hs & (ST_CHOL_FAIL | ST_NONFINITE)) != 0;
     if (*failed) return SC_OK;
-    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
     return SC_OK;
   }
 
@@ -813,8 +816,8 @@ struct LobRun : RunBase {
     // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
     CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, true), "gram");
     CK(rr(K, G), "rr");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
     std::swap(S, S2);
     std::swap(LS, LS2);
     CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2, pdeg), "residual");
@@ -894,7 +897,7 @@ struct LobRun : RunBase {
     {
       TallSeg<T> sr{WR, ldw, WR, ldw, Tm, w, 0, ka};
       TallSeg<T> sp{WP, ldw, WP, ldw, Tm + ka, w, 0, haveP ? ka : 0};
-      CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus, use_tc != 0), "tall");
+      CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus, tall_tc), "tall");
     }
     // (2) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too), into
     //     the R and P slots.  A breakdown inside the P columns is handled on the device: the
@@ -914,13 +917,13 @@ struct LobRun : RunBase {
       else
         CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
       CK(chol(wq, G, TmA, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
-      CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+      CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
       CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
       CK(chol(wq, G, TmB, dfail, ka, pf, ka, nullptr), "chol");
       // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
-      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
       if (haveP)
-        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
     }
     // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken
     //     on the orthonormalized block so that its images are products with L rather than
@@ -951,10 +954,10 @@ struct LobRun : RunBase {
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
     Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);
     fork();  // the L-images on the second stream
-    CK(tall_gemm<T>(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
-    CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1, dstatus, use_tc != 0), "tall");
-    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1, dstatus, use_tc != 0), "tall");
+    CK(tall_gemm<T>(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+    CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1, dstatus, tall_tc), "tall");
+    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1, dstatus, tall_tc), "tall");
     join();
     std::swap(S, S2);
     std::swap(LS, LS2);
@@ -966,8 +969,8 @@ struct LobRun : RunBase {
     if ((done_passes + 1) % kReorth == 0) {
       CK(gram_seg(S, ld3, {{0, K}}, S, ld3, {{0, K}}, G, K, true), "gram");
       CK(chol(K, G, Tm), "chol");
-      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
-      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus, use_tc != 0), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
       CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, T1, sizeof(T) * kp, sizeof(T) * K, n,
                            cudaMemcpyDeviceToDevice, st), "reorth");
       CK(cudaMemcpy2DAsync(LS, sizeof(T) * ld3, W1, sizeof(T) * kp, sizeof(T) * K, n,
