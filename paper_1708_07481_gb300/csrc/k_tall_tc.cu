@@ -5,20 +5,22 @@
 // 3-term split TF32 as in the Gram kernel: x = x_big + x_small, x_big = tf32(x),
 // x_small = tf32(x - x_big); A W ~ Ab Wb + Ab Ws + As Wb, FP32 accumulation in tensor memory.
 //
-// Operands (both K-major, 128-byte swizzle):
-//   A side (M = 128 rows of the tall block, K = 32 columns per chunk): a TMA tiled load of the
-//   FP32 rows with SWIZZLE_128B lands exactly in the K-major SW128 layout the MMA reads, so the
-//   split is an in-place sweep over the staged tile (big overwrites the FP32 values, small
-//   goes to a second buffer at the same offsets);
-//   B side (N = output columns, rounded up to 16, K = the same chunks): W^T split once per CTA
-//   into shared memory and kept for all the CTA's row tiles.
+// Operands (both K-major, 128-byte swizzle), in chunks of 32 columns of A (= 32 rows of W):
+//   A side (M = 128 rows of the tall block): a TMA tiled load of the FP32 rows with
+//   SWIZZLE_128B lands exactly in the K-major SW128 layout the MMA reads, so the split is an
+//   in-place sweep over the staged tile (big overwrites the FP32 values, small goes to a second
+//   buffer at the same offsets);
+//   B side (N = output columns rounded up to 16): W^T is split once per call by a small kernel
+//   into an image of per-chunk big / small SW128 tiles in global memory, and each chunk's tile
+//   comes with the A chunk as one bulk copy completing on the same mbarrier.
 // Each A segment is cut into chunks of 32 columns (the last one zero-filled by the TMA past
-// the segment's width, and the matching rows of W^T are zero).  A persistent CTA walks row
-// tiles of 128 with NSTG staged chunks in flight; one thread issues the TMA copies and the
-// MMAs (4 K-steps x 3 products per chunk), commits per stage (to refill it) and per tile (for
-// the epilogue); eight warps read the accumulator with tcgen05.ld (warp w: rows
-// 32 (w % 4) .. +32, columns 32 (w / 4) + 64 j .. +32) and write beta Cin + acc.  Every wait is bounded; on a time-out the CTA records ST_TIMEOUT,
-// waits (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
+// the segment's width; the matching rows of W^T are zero).  A persistent CTA walks row tiles
+// of 128 with up to four staged chunks in flight (as many as fit beside each other); one thread
+// issues the copies and the MMAs (4 K-steps x 3 products per chunk), commits per stage and per
+// tile, and refills the previous chunk's stage; eight warps read the accumulator with
+// tcgen05.ld (warp w: rows 32 (w % 4) .. +32, columns 32 (w / 4) + 64 j .. +32) and write
+// beta Cin + acc.  Every wait is bounded; on a time-out the CTA records ST_TIMEOUT, waits
+// (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstring>
 
@@ -27,13 +29,13 @@
 namespace sc {
 namespace {
 
-constexpr int TT_M = 128;       // rows per tile (MMA M)
-constexpr int TT_K = 32;        // columns per chunk (one 128-byte swizzle row of FP32)
-constexpr int TT_NSTG = 3;      // staged chunks in flight
-constexpr int TT_NTH = 256;     // eight warps: warps w, w + 4 share lane quarter w % 4
-constexpr int TT_STAGE = TT_M * TT_K * 4;  // 16 KB
-constexpr int TT_MAXW = 120 * 1024;        // W^T big + small resident in shared memory
-constexpr int TT_SMEM = 1024 + TT_NSTG * 2 * TT_STAGE + TT_MAXW + 256;
+constexpr int TT_M = 128;     // rows per tile (MMA M)
+constexpr int TT_K = 32;      // columns per chunk (one 128-byte swizzle row of FP32)
+constexpr int TT_MAXSTG = 4;  // staged chunks in flight, at most
+constexpr int TT_NTH = 256;   // eight warps: warps w, w + 4 share lane quarter w % 4
+constexpr int TT_ATILE = TT_M * TT_K * 4;             // 16 KB: one FP32 (then big) A chunk
+constexpr int TT_SMEM = 225 * 1024;                   // dynamic shared memory of a CTA
+constexpr int TT_SMEM_USE = TT_SMEM - 1024 - 256;     // stages (after alignment and barriers)
 
 struct TcTall {
   int nseg;
@@ -42,8 +44,11 @@ struct TcTall {
   int wrow[3];    // first logical row of W for each segment
   int nchunks;    // total chunks
   int nn;         // MMA N: output columns rounded up to 16
+  int nstg;       // stages
+  int stage;      // bytes per stage: A big + A small + W^T chunk (big + small)
   long long n;
   int ntiles;
+  const uint8_t* wimg;  // W^T image: per chunk nn x 128 B big, then nn x 128 B small
   // outputs: columns [0, b0) -> segment 0, [b0, b) -> segment 1
   float* out[2];
   long long ldo[2];
@@ -67,9 +72,35 @@ __device__ __forceinline__ float tt_w(const TcTall& p, int lr, int col) {
   return w[(long long)(lr - skip) * ldw + (s1 ? col - p.b0 : col)];
 }
 
-__device__ __forceinline__ void tma_load_2d_tt(void* dst, const CUtensorMap* map, int x, int y,
-                                               uint64_t* bar) {
-  tma_load_2d(dst, map, x, y, bar);
+// The W^T image: for chunk ch (segment q, local chunk cc), operand row r (output column) and
+// k < 32, logical row lr = wrow[q] + 32 cc + k of W; entries past the segment's width are 0.
+__global__ void k_tall_wsplit(const __grid_constant__ TcTall p, uint8_t* __restrict__ img) {
+  const long long tot = (long long)p.nchunks * p.nn * TT_K;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int kk = (int)(idx % TT_K), r = (int)((idx / TT_K) % p.nn);
+    const int ch = (int)(idx / ((long long)TT_K * p.nn));
+    int q = 0, cc = ch;
+    while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
+    const int lc = cc * TT_K + kk;
+    const float wv = lc < p.cseg[q] ? tt_w(p, p.wrow[q] + lc, r) : 0.f;
+    const uint32_t bgv = to_tf32(wv);
+    const uint32_t smv = to_tf32(wv - __uint_as_float(bgv));
+    uint8_t* base = img + (size_t)ch * 2 * p.nn * 128;
+    const uint32_t off = sw128_off(r, kk);
+    *reinterpret_cast<uint32_t*>(base + off) = bgv;
+    *reinterpret_cast<uint32_t*>(base + (size_t)p.nn * 128 + off) = smv;
+  }
+}
+
+// Bulk copy of `bytes` contiguous bytes (16-byte aligned, a multiple of 16) into shared
+// memory, completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __global__ void __launch_bounds__(TT_NTH, 1)
@@ -78,25 +109,24 @@ __global__ void __launch_bounds__(TT_NTH, 1)
               int* status) {
   extern __shared__ __align__(1024) uint8_t tt_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)tt_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* stg = base;                                   // [NSTG] FP32 -> big, 16 KB each
-  uint8_t* sml = stg + TT_NSTG * TT_STAGE;               // [NSTG] small, 16 KB each
-  uint8_t* wbig = sml + TT_NSTG * TT_STAGE;              // [nchunks] nn x 128 B
-  const int wchunk = p.nn * 128;
-  uint8_t* wsml = wbig + p.nchunks * wchunk;
-  uint64_t* bars = (uint64_t*)(wsml + p.nchunks * wchunk);
-  uint64_t* full = bars;                // [NSTG] TMA landed
-  uint64_t* mdone = bars + TT_NSTG;     // [NSTG] MMAs reading the stage finished
-  uint64_t* accd = bars + 2 * TT_NSTG;  // accumulator of the tile complete
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TT_NSTG + 1);
-  __shared__ int abort_flag;
+  const int nstg = p.nstg, sb = p.stage, wbytes = p.nn * 128;
+  uint64_t* bars = (uint64_t*)(base + (size_t)nstg * sb);
+  uint64_t* full = bars;                   // [nstg] A chunk and W^T chunk landed
+  uint64_t* mdone = bars + TT_MAXSTG;      // [nstg] MMAs reading the stage finished
+  uint64_t* accd = bars + 2 * TT_MAXSTG;   // accumulator of the tile complete
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TT_MAXSTG + 1);
+  __shared__ int abort_flag, acc_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const CUtensorMap* maps[3] = {&map0, &map1, &map2};
   int tcols = 32;
   while (tcols < p.nn) tcols <<= 1;
+  auto a_big = [&](int s) { return base + (size_t)s * sb; };
+  auto a_sml = [&](int s) { return base + (size_t)s * sb + TT_ATILE; };
+  auto w_big = [&](int s) { return base + (size_t)s * sb + 2 * TT_ATILE; };
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int q = 0; q < 2 * TT_NSTG + 1; ++q) mbar_init(&bars[q], 1);
+    for (int q = 0; q < 2 * TT_MAXSTG + 1; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     for (int q = 0; q < p.nseg; ++q)
@@ -109,21 +139,6 @@ __global__ void __launch_bounds__(TT_NTH, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // W^T, split into big / small TF32, K-major SW128: chunk c, operand row r (output column),
-  // k in [0, 32)
-  for (int idx = tid; idx < p.nchunks * p.nn * TT_K; idx += TT_NTH) {
-    const int kk = idx % TT_K, r = (idx / TT_K) % p.nn, ch = idx / (TT_K * p.nn);
-    int q = 0, cc = ch;
-    while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
-    const int lc = cc * TT_K + kk;
-    const float wv = lc < p.cseg[q] ? tt_w(p, p.wrow[q] + lc, r) : 0.f;
-    const uint32_t bgv = to_tf32(wv);
-    const uint32_t smv = to_tf32(wv - __uint_as_float(bgv));
-    const uint32_t off = (uint32_t)ch * wchunk + sw128_off(r, kk);
-    *reinterpret_cast<uint32_t*>(wbig + off) = bgv;
-    *reinterpret_cast<uint32_t*>(wsml + off) = smv;
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -131,37 +146,38 @@ __global__ void __launch_bounds__(TT_NTH, 1)
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.nn >> 3) << 17) |
                          ((uint32_t)(TT_M >> 4) << 24);
 
-  // the CTA's sequence of (tile, chunk) loads: index i -> tile blockIdx.x + (i / nchunks) grid,
-  // chunk i % nchunks
+  // the CTA's sequence of loads: index i -> tile blockIdx.x + (i / nchunks) gridDim.x, chunk
+  // i % nchunks, stage i % nstg
   const int my_tiles = blockIdx.x < p.ntiles ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long total = (long long)my_tiles * p.nchunks;
   auto issue = [&](long long i) {  // thread 0
-    const int s = (int)(i % TT_NSTG);
+    const int s = (int)(i % nstg);
     const int tile = blockIdx.x + (int)(i / p.nchunks) * gridDim.x;
-    int q = 0, cc = (int)(i % p.nchunks);
+    const int ch = (int)(i % p.nchunks);
+    int q = 0, cc = ch;
     while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
-    mbar_expect_tx(&full[s], TT_STAGE);
-    tma_load_2d_tt(stg + s * TT_STAGE, maps[q], cc * TT_K, tile * TT_M, &full[s]);
+    mbar_expect_tx(&full[s], TT_ATILE + 2 * wbytes);
+    tma_load_2d(a_big(s), maps[q], cc * TT_K, tile * TT_M, &full[s]);
+    bulk_load(w_big(s), p.wimg + (size_t)ch * 2 * wbytes, 2 * wbytes, &full[s]);
   };
-  long long issued = 0, mma_commits[TT_NSTG] = {0, 0, 0}, acc_commits = 0;
+  long long issued = 0, mma_commits[TT_MAXSTG] = {0, 0, 0, 0}, acc_commits = 0;
   if (tid == 0)
-    for (; issued < total && issued < TT_NSTG; ++issued) issue(issued);
+    for (; issued < total && issued < nstg; ++issued) issue(issued);
 
   for (long long i = 0; i < total; ++i) {
-    const int s = (int)(i % TT_NSTG);
+    const int s = (int)(i % nstg);
     const int ch = (int)(i % p.nchunks);
     const int tile = blockIdx.x + (int)(i / p.nchunks) * gridDim.x;
-    bool ok = mbar_wait(&full[s], (uint32_t)((i / TT_NSTG) & 1));
-    if (!ok) atomicExch(&abort_flag, 1);
+    if (!mbar_wait(&full[s], (uint32_t)((i / nstg) & 1))) atomicExch(&abort_flag, 1);
     __syncthreads();
     if (abort_flag) break;
-    // split the staged FP32 tile in place: big over the FP32 values, small beside it
+    // split the staged FP32 A chunk in place: big over the FP32 values, small beside it
     {
-      uint4* sb = reinterpret_cast<uint4*>(stg + s * TT_STAGE);
-      uint4* ss = reinterpret_cast<uint4*>(sml + s * TT_STAGE);
-#pragma unroll 4
-      for (int v = tid; v < TT_STAGE / 16; v += TT_NTH) {
-        const uint4 x = sb[v];
+      uint4* sbg = reinterpret_cast<uint4*>(a_big(s));
+      uint4* ssm = reinterpret_cast<uint4*>(a_sml(s));
+#pragma unroll
+      for (int v = tid; v < TT_ATILE / 16; v += TT_NTH) {
+        const uint4 x = sbg[v];
         uint4 bg, sm;
         bg.x = to_tf32(__uint_as_float(x.x));
         bg.y = to_tf32(__uint_as_float(x.y));
@@ -171,16 +187,16 @@ __global__ void __launch_bounds__(TT_NTH, 1)
         sm.y = to_tf32(__uint_as_float(x.y) - __uint_as_float(bg.y));
         sm.z = to_tf32(__uint_as_float(x.z) - __uint_as_float(bg.z));
         sm.w = to_tf32(__uint_as_float(x.w) - __uint_as_float(bg.w));
-        sb[v] = bg;
-        ss[v] = sm;
+        sbg[v] = bg;
+        ssm[v] = sm;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ab = smem_u32(stg + s * TT_STAGE), as_ = smem_u32(sml + s * TT_STAGE);
-      const uint32_t wb = smem_u32(wbig + ch * wchunk), ws = smem_u32(wsml + ch * wchunk);
+      const uint32_t ab = smem_u32(a_big(s)), as_ = smem_u32(a_sml(s));
+      const uint32_t wb = smem_u32(w_big(s)), ws = wb + wbytes;
 #pragma unroll
       for (int ks = 0; ks < TT_K / 8; ++ks) {
         const uint32_t ko = ks * 32;
@@ -195,12 +211,11 @@ __global__ void __launch_bounds__(TT_NTH, 1)
         mma_commit(accd);
         acc_commits += 1;
       }
-      // refill the previous chunk's stage (its MMAs were issued one chunk ago and have had
-      // this chunk's wait and split to finish): load i + NSTG - 1 goes where load i - 1 was
+      // refill the previous chunk's stage (its MMAs were issued one chunk ago): load
+      // i + nstg - 1 goes where load i - 1 was
       if (i >= 1 && issued < total) {
-        const int sp = (int)((i - 1) % TT_NSTG);
-        const bool okm = mbar_wait(&mdone[sp], (uint32_t)((mma_commits[sp] - 1) & 1));
-        if (!okm) {
+        const int sp = (int)((i - 1) % nstg);
+        if (!mbar_wait(&mdone[sp], (uint32_t)((mma_commits[sp] - 1) & 1))) {
           atomicExch(&abort_flag, 1);
         } else {
           issue(issued);
@@ -210,7 +225,6 @@ __global__ void __launch_bounds__(TT_NTH, 1)
     }
     if (ch == p.nchunks - 1) {
       // epilogue of the tile: all threads wait for the accumulator
-      __shared__ int acc_ok;
       if (tid == 0) acc_ok = mbar_wait(accd, (uint32_t)((acc_commits - 1) & 1)) ? 1 : 0;
       __syncthreads();
       if (!acc_ok) {
@@ -238,31 +252,28 @@ __global__ void __launch_bounds__(TT_NTH, 1)
           for (int j4 = 0; j4 < 8; ++j4) {
             const int col = c0 + 4 * j4;
             if (col >= p.b) break;
-            const bool s1 = col >= p.b0;
+            const int s1 = col >= p.b0 ? 1 : 0;
             const int cs = s1 ? col - p.b0 : col;
             const int bs = s1 ? p.b - p.b0 : p.b0;
-            float* out = p.out[s1];
-            const long long ldo = p.ldo[s1];
-            const float* cin = p.cin[s1];
-            const long long ldc = p.ldc[s1];
             float r4[4] = {__uint_as_float(v[4 * j4]), __uint_as_float(v[4 * j4 + 1]),
                            __uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3])};
             if (p.vec[s1] && cs + 3 < bs) {
+              const float* cin = p.cin[s1];
               if (cin) {
-                const float4 cv = *reinterpret_cast<const float4*>(cin + row * ldc + cs);
+                const float4 cv = *reinterpret_cast<const float4*>(cin + row * p.ldc[s1] + cs);
                 r4[0] = fmaf(p.beta, cv.x, r4[0]);
                 r4[1] = fmaf(p.beta, cv.y, r4[1]);
                 r4[2] = fmaf(p.beta, cv.z, r4[2]);
                 r4[3] = fmaf(p.beta, cv.w, r4[3]);
               }
-              *reinterpret_cast<float4*>(out + row * ldo + cs) =
+              *reinterpret_cast<float4*>(p.out[s1] + row * p.ldo[s1] + cs) =
                   make_float4(r4[0], r4[1], r4[2], r4[3]);
             } else {
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
                 const int cj = col + j;
                 if (cj >= p.b) break;
-                const bool t1 = cj >= p.b0;
+                const int t1 = cj >= p.b0 ? 1 : 0;
                 const int ct = t1 ? cj - p.b0 : cj;
                 const float* cn = p.cin[t1];
                 float x = r4[j];
@@ -278,22 +289,17 @@ __global__ void __launch_bounds__(TT_NTH, 1)
       __syncthreads();
     }
   }
-  // drain: after a time-out, wait (bounded) for this CTA's MMAs and copies in flight
+  // drain: wait (bounded) for this CTA's MMAs, and after a time-out for its copies in flight
   if (tid == 0) {
     bool ok = !abort_flag;
-    for (int q = 0; q < TT_NSTG; ++q)
+    for (int q = 0; q < nstg; ++q)
       if (mma_commits[q] > 0) ok = mbar_wait(&mdone[q], (uint32_t)((mma_commits[q] - 1) & 1)) && ok;
     if (acc_commits > 0) ok = mbar_wait(accd, (uint32_t)((acc_commits - 1) & 1)) && ok;
-    if (!ok) atomicExch(&abort_flag, 1);
-    if (abort_flag) {
-      // the loads issued for indices the loop did not consume
-      for (int q = 0; q < TT_NSTG; ++q) {
-        // index of the latest load into stage q, if any was issued
-        long long last = -1;
-        for (long long j = issued - 1; j >= 0 && j >= issued - TT_NSTG; --j)
-          if (j % TT_NSTG == q) last = j;
-        if (last >= 0) mbar_wait(&full[q], (uint32_t)((last / TT_NSTG) & 1));
-      }
+    if (!ok) {
+      // the latest load into each stage (a load into a stage is issued only after the one
+      // before it was consumed, so waiting for the latest covers them all)
+      for (long long j = std::max(0LL, issued - nstg); j < issued; ++j)
+        mbar_wait(&full[j % nstg], (uint32_t)((j / nstg) & 1));
       atomicOr(status, ST_TIMEOUT);
     }
   }
@@ -309,8 +315,9 @@ __global__ void __launch_bounds__(TT_NTH, 1)
 }  // namespace
 
 // out = beta Cin + A W on tensor cores when the shape fits (A segments 16-byte aligned with
-// strides a multiple of 4 floats, W^T resident in shared memory, N <= 256); otherwise
-// cudaErrorNotSupported and the caller uses the CUDA-core kernels.
+// strides a multiple of 4 floats, N <= 256 output columns); otherwise cudaErrorNotSupported and
+// the caller uses the CUDA-core kernels.  The W^T image (2 x chunks x N x 128 bytes, at most
+// 1 MB) is a stream-ordered allocation of the call, freed behind the launch.
 cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
                          const TallSeg<float>& s0, const TallSeg<float>& s1, float beta,
                          int* d_status) {
@@ -330,7 +337,10 @@ cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
   }
   p.nchunks = ch;
   p.nn = (b + 15) & ~15;
-  if (p.nn > 256 || (size_t)2 * ch * p.nn * 128 > (size_t)TT_MAXW) return cudaErrorNotSupported;
+  if (p.nn > 256) return cudaErrorNotSupported;
+  p.stage = 2 * TT_ATILE + 2 * p.nn * 128;
+  p.nstg = std::min(TT_MAXSTG, TT_SMEM_USE / p.stage);
+  if (p.nstg < 2) return cudaErrorNotSupported;
   const TallSeg<float>* sg[2] = {&s0, &s1};
   for (int q = 0; q < 2; ++q) {
     const TallSeg<float>& g = *sg[q];
@@ -345,7 +355,6 @@ cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
                (!g.Cin || (((uintptr_t)g.Cin & 15) == 0 && (g.ldc & 3) == 0)) &&
                (q == 0 || (s0.b & 3) == 0);
   }
-  if (s1.b > 0 && (s0.b & 3)) p.vec[1] = 0;
   p.b0 = s0.b;
   p.b = b;
   p.beta = beta;
@@ -357,15 +366,27 @@ cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
                        CU_TENSOR_MAP_SWIZZLE_128B))
       return cudaErrorNotSupported;
   }
+  const size_t img_bytes = (size_t)2 * ch * p.nn * 128;
+  uint8_t* img = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&img, img_bytes, st);
+  if (e != cudaSuccess) return e;
+  p.wimg = img;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_tall_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM);
   });
-  const int grid = std::min(p.ntiles, 152);
-  ProfScope ps(st, "tall_gemm");
-  k_tall_tc<<<grid, TT_NTH, TT_SMEM, st>>>(m[0], m[1], m[2], p, d_status);
-  note_launch();
-  return cudaGetLastError();
+  {
+    ProfScope ps(st, "tall_gemm");
+    const long long tot = (long long)ch * p.nn * TT_K;
+    k_tall_wsplit<<<(unsigned)std::min<long long>((tot + 255) / 256, 1024), 256, 0, st>>>(p, img);
+    note_launch();
+    const int grid = std::min(p.ntiles, 152);
+    k_tall_tc<<<grid, TT_NTH, TT_SMEM, st>>>(m[0], m[1], m[2], p, d_status);
+    note_launch();
+  }
+  e = cudaGetLastError();
+  cudaFreeAsync(img, st);
+  return e;
 }
 
 }  // namespace sc

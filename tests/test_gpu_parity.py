@@ -162,12 +162,14 @@ def test_gram_tc_ragged_and_structured(sc, ctx):
 
 
 @pytest.mark.parametrize("n,a,b", [(1, 3, 5), (33, 5, 7), (777, 44, 44), (50001, 132, 44),
-                                   (4099, 88, 96), (3000, 40, 300), (2000, 500, 40)])
+                                   (4099, 88, 96), (3000, 40, 300), (2000, 500, 40),
+                                   (100003, 480, 160), (20001, 320, 256)])
 @pytest.mark.parametrize("prec", ["mixed", "fp32", "fp64"])
 def test_tall_update(sc, ctx, n, a, b, prec):
     """out = beta Cin + A W element by element against the FP64 product of the same (rounded)
-    inputs: tcgen05 3xTF32 (mixed; shapes past its shared-memory limit fall back to CUDA
-    cores), FP32 CUDA cores, FP64."""
+    inputs: tcgen05 3xTF32 (mixed; more than 256 output columns fall back to CUDA cores), FP32
+    CUDA cores, FP64.  The shapes include the n = 2M workload's widest update (3K = 480 columns
+    into K = 160) at a smaller n, and 256 output columns (two staged chunks)."""
     rng = np.random.default_rng(n + a + b)
     A = rng.standard_normal((n, a))
     W = rng.standard_normal((a, b))
