@@ -318,9 +318,41 @@ __global__ void __launch_bounds__(TT_NTH, 1)
 // strides a multiple of 4 floats, N <= 256 output columns); otherwise cudaErrorNotSupported and
 // the caller uses the CUDA-core kernels.  The W^T image (2 x chunks x N x 128 bytes, at most
 // 1 MB) is a stream-ordered allocation of the call, freed behind the launch.
+static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<float>& A,
+                                    const TallSeg<float>& s0, const TallSeg<float>& s1,
+                                    float beta, int* d_status);
+
+// Outputs wider than one MMA (N > 256) run as column pieces of at most 256 (multiples of 16),
+// each its own pass over A.
 cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
                          const TallSeg<float>& s0, const TallSeg<float>& s1, float beta,
                          int* d_status) {
+  const int b = s0.b + s1.b;
+  if (n <= 0 || b <= 0) return cudaErrorNotSupported;
+  if (((b + 15) & ~15) <= 256) return tall_gemm_tc_one(st, n, A, s0, s1, beta, d_status);
+  const TallSeg<float>* sg[2] = {&s0, &s1};
+  for (int q = 0; q < 2; ++q) {
+    const TallSeg<float>& g = *sg[q];
+    if (g.b == 0) continue;
+    const int pieces = (g.b + 255) / 256;
+    const int width = ((g.b + pieces - 1) / pieces + 15) & ~15;
+    for (int c0 = 0; c0 < g.b; c0 += width) {
+      TallSeg<float> part = g;
+      part.b = std::min(width, g.b - c0);
+      part.out = g.out + c0;
+      part.Cin = g.Cin ? g.Cin + c0 : nullptr;
+      part.W = g.W + c0;
+      const TallSeg<float> none{};
+      const cudaError_t e = tall_gemm_tc_one(st, n, A, part, none, beta, d_status);
+      if (e != cudaSuccess) return e;  // (a piece that is not supported aborts the call)
+    }
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<float>& A,
+                                    const TallSeg<float>& s0, const TallSeg<float>& s1,
+                                    float beta, int* d_status) {
   const int b = s0.b + s1.b;
   if (n <= 0 || b <= 0) return cudaErrorNotSupported;
   TcTall p{};
