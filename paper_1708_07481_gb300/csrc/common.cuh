@@ -1,5 +1,7 @@
 // Shared declarations of the GB300 spectral-clustering library (sm_103a).
 #pragma once
+#include <functional>
+#include <string>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -116,10 +118,22 @@ cudaError_t build_csr(cudaStream_t st, Alloc& al, int n, long long m, const int*
 cudaError_t merge_csr(cudaStream_t st, Alloc& al, const CsrDev& a, const CsrDev& b,
                       int algebraic, int* d_status, CsrDev* out, int* host_status);
 
-// SpMM: Y = D V - W V (n x k block, row stride ldv/ldy, ld multiple of 16 bytes).
+// SpMM: Y = D V - W V (n x k block, row stride ldv/ldy, ld multiple of 16 bytes).  shape: a
+// kernel shape index from spmm_shapes (lanes per row x chunks per lane), -1 = the default.
 template <typename T>
 cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv, T* Y,
-                     long long ldy, int k);
+                     long long ldy, int k, int shape = -1);
+// Kernel shapes valid for nvec 16-byte column chunks (at most 13); out[0] is the default.
+int spmm_shapes(int nvec, int* out);
+
+// Project autotuner (tune.cu): the fastest variant per key, measured on first use (each
+// variant issued by run(v) on stream st), cached for the process and persisted to
+// SC_AUTOTUNE_FILE; SC_TUNE_<KERNEL> forces a variant, SC_AUTOTUNE=0 returns `fallback` for
+// keys not yet chosen.
+int tune_pick(const std::string& key, const char* kernel, cudaStream_t st, int nvar,
+              int fallback, const std::function<cudaError_t(int)>& run);
+int tune_lookup(const std::string& key);
+int tune_table_size();
 
 // Gram: C (a x b, FP64 row-major, ldc) = A' B over n rows.  `sym` = A and B are the same
 // matrix: only the upper tile triangle is computed and mirrored.  Workspace from `al`.

@@ -136,16 +136,66 @@ cudaError_t launch(cudaStream_t st, const CsrDev& g, const T* deg, const T* V, l
 
 }  // namespace
 
+// Kernel shapes the autotuner chooses among: (lanes per row, 16-byte chunks per lane).
+struct SpmmShape {
+  int tl, nc;
+};
+constexpr SpmmShape kSpmmShapes[] = {{4, 1},  {8, 1},  {16, 1}, {32, 1}, {8, 2},
+                                     {16, 2}, {32, 2}, {8, 3},  {16, 3}, {32, 3},
+                                     {8, 4},  {16, 4}, {32, 4}};
+constexpr int kNumSpmmShapes = sizeof(kSpmmShapes) / sizeof(kSpmmShapes[0]);
+
+template <typename T>
+cudaError_t launch_shape(int v, cudaStream_t st, const CsrDev& g, const T* deg, const T* V,
+                         long long ldv, T* Y, long long ldy, int nvec) {
+  switch (v) {
+    case 0: return launch<T, 4, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 1: return launch<T, 8, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 2: return launch<T, 16, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 3: return launch<T, 32, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 4: return launch<T, 8, 2>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 5: return launch<T, 16, 2>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 6: return launch<T, 32, 2>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 7: return launch<T, 8, 3>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 8: return launch<T, 16, 3>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 9: return launch<T, 32, 3>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 10: return launch<T, 8, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
+    case 11: return launch<T, 16, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
+    default: return launch<T, 32, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
+  }
+}
+
+// The kernel shapes that fit nvec 16-byte column chunks with no wholly idle chunk per lane;
+// out[0] is the built-in default (the smallest team that covers the row with one chunk, then
+// 32 lanes with as many chunks as needed).
+int spmm_shapes(int nvec, int* out) {
+  int cnt = 0, def = -1;
+  if (nvec <= 4) def = 0;
+  else if (nvec <= 8) def = 1;
+  else if (nvec <= 16) def = 2;
+  else if (nvec <= 32) def = 3;
+  else if (nvec <= 64) def = 6;
+  else if (nvec <= 96) def = 9;
+  else def = 12;
+  out[cnt++] = def;
+  for (int v = 0; v < kNumSpmmShapes; ++v) {
+    const SpmmShape sh = kSpmmShapes[v];
+    if (v == def || sh.tl * sh.nc < nvec || sh.tl * (sh.nc - 1) >= nvec) continue;
+    out[cnt++] = v;
+  }
+  return cnt;
+}
+
 template <typename T>
 cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv, T* Y,
-                     long long ldy, int k) {
+                     long long ldy, int k, int shape) {
   constexpr int W = Vec<T>::W;
   if (ldv % W || ldy % W) return cudaErrorInvalidValue;
   int nvec = (k + W - 1) / W;
   if (nvec > 32 * MAXC) {  // wider blocks: column chunks of the widest kernel shape
     const int kc = 32 * MAXC * W;
     for (int c0 = 0; c0 < k; c0 += kc) {
-      cudaError_t e = spmm_lap<T>(st, g, V + c0, ldv, Y + c0, ldy, std::min(kc, k - c0));
+      cudaError_t e = spmm_lap<T>(st, g, V + c0, ldv, Y + c0, ldy, std::min(kc, k - c0), -1);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -154,18 +204,18 @@ cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv
   if constexpr (sizeof(T) == 4) deg = (const T*)g.degf;
   else deg = (const T*)g.degd;
   if (g.n == 0) return cudaSuccess;
-  if (nvec <= 4) return launch<T, 4, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 8) return launch<T, 8, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 16) return launch<T, 16, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 32) return launch<T, 32, 1>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 64) return launch<T, 32, 2>(st, g, deg, V, ldv, Y, ldy, nvec);
-  if (nvec <= 96) return launch<T, 32, 3>(st, g, deg, V, ldv, Y, ldy, nvec);
-  return launch<T, 32, 4>(st, g, deg, V, ldv, Y, ldy, nvec);
+  if (shape < 0 || shape >= kNumSpmmShapes ||
+      kSpmmShapes[shape].tl * kSpmmShapes[shape].nc < nvec) {
+    int list[kNumSpmmShapes];
+    spmm_shapes(nvec, list);
+    shape = list[0];
+  }
+  return launch_shape<T>(shape, st, g, deg, V, ldv, Y, ldy, nvec);
 }
 
 template cudaError_t spmm_lap<float>(cudaStream_t, const CsrDev&, const float*, long long,
-                                     float*, long long, int);
+                                     float*, long long, int, int);
 template cudaError_t spmm_lap<double>(cudaStream_t, const CsrDev&, const double*, long long,
-                                      double*, long long, int);
+                                      double*, long long, int, int);
 
 }  // namespace sc

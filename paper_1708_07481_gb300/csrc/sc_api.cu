@@ -519,10 +519,6 @@ struct LobRun : RunBase {
   RunAlloc ra;
   Alloc al;
   int use_tc;
-  // tall updates on tensor cores for large blocks: measured on GB300, the tcgen05 form is 2.3x
-  // (K = 160, 160 columns) to 3.6x (480 columns) faster at n = 2M, while at n = 50,000 the
-  // CUDA-core kernels, whose blocks sit in L2, are faster
-  bool tall_tc = false;
   bool dense64 = false;      // small dense solves in FP64, results cast to T
   double *Gd = nullptr, *Yd = nullptr;  // FP64 results of those solves
   double pivot_tol;
@@ -569,7 +565,6 @@ struct LobRun : RunBase {
     al = Alloc{run_alloc, run_free, &ra};
     use_tc = (sizeof(T) == 4 && (o.prec == SC_PREC_MIXED || o.prec == SC_PREC_MIXED_DD)) ? 1 : 0;
     dense64 = sizeof(T) == 4 && o.prec == SC_PREC_MIXED_DD;
-    tall_tc = use_tc && n >= 250000;
     pivot_tol = sizeof(T) == 4 ? 1e-8 : 1e-10;
     dir_floor = 64.0 * (sizeof(T) == 4 ? 0x1p-24 : 0x1p-53);
     res_floor = dir_floor * 2.0 * g->csr.deg_max;
@@ -686,9 +681,72 @@ struct LobRun : RunBase {
     cudaError_t e = gram_seg(Yc, ldyc, {{0, kc}}, V, ldv, {{0, cols}}, Gy, cols, false);
     if (e == cudaSuccess) e = cast_mat<T>(st, kc, cols, Gy, cols, Ty, cols, -1.0);
     if (e == cudaSuccess)
-      e = tall_gemm<T>(st, n, cat<T>(Yc, ldyc, kc), Ty, cols, cols, V, ldv, V, ldv, (T)1, dstatus,
-                       tall_tc);
+      e = tall(st, n, cat<T>(Yc, ldyc, kc), Ty, cols, cols, V, ldv, V, ldv, (T)1);
     return e;
+  }
+
+  // ---- autotuned kernel choices (tune.cu) --------------------------------------------------
+  static int log2ceil(long long x) {
+    int l = 0;
+    while ((1LL << l) < x) ++l;
+    return l;
+  }
+  T* tune_scratch = nullptr;  // n x (2 kp + 8): outputs of the update variants being timed
+  // The tall update on CUDA cores (variant 0) or tensor cores (variant 1, FP32 mixed only),
+  // whichever the autotuner measured faster for this (n bucket, columns, segments); without a
+  // measurement, tensor cores from n = 250,000 on.
+  int tall_variant(cudaStream_t s, const Cat3<T>& A, const TallSeg<T>& s0, const TallSeg<T>& s1,
+                   T beta) {
+    if constexpr (sizeof(T) != 4) {
+      return 0;
+    } else {
+      if (!use_tc) return 0;
+      const int fallback = n >= 250000 ? 1 : 0;
+      char key[128];
+      snprintf(key, sizeof(key), "tall/f32/n2=%d/a=%d/b=%d/seg=%d", log2ceil(n), A.cols(),
+               s0.b + s1.b, A.nblk);
+      return tune_pick(key, "tall", s, 2, fallback, [&](int v) -> cudaError_t {
+        if (!tune_scratch) {
+          tune_scratch = get<T>((size_t)n * (2 * kp + 8));
+          if (!tune_scratch) return cudaErrorMemoryAllocation;
+          // allocated in the order of the run's stream; the second stream may use it next
+          cudaStreamSynchronize(st);
+        }
+        const long long b0 = (s0.b + 3) & ~3, lds = b0 + ((s1.b + 3) & ~3);
+        TallSeg<T> a0 = s0, a1 = s1;
+        a0.out = tune_scratch;
+        a0.ldo = lds;
+        a1.out = tune_scratch + b0;
+        a1.ldo = lds;
+        return tall_gemm2<T>(s, n, A, a0, a1, beta, dstatus, v == 1);
+      });
+    }
+  }
+  cudaError_t tall2(cudaStream_t s, long long nn, const Cat3<T>& A, const TallSeg<T>& s0,
+                    const TallSeg<T>& s1, T beta) {
+    return tall_gemm2<T>(s, nn, A, s0, s1, beta, dstatus, tall_variant(s, A, s0, s1, beta) == 1);
+  }
+  cudaError_t tall(cudaStream_t s, long long nn, const Cat3<T>& A, const T* W, int ldw, int b,
+                   T* out, long long ldo, const T* Cin, long long ldc, T beta) {
+    TallSeg<T> s0{out, ldo, Cin, ldc, W, ldw, 0, b};
+    TallSeg<T> s1{};
+    return tall2(s, nn, A, s0, s1, beta);
+  }
+  // SpMM with the kernel shape (lanes per row x chunks per lane) the autotuner measured fastest
+  // for this (n bucket, average degree bucket, columns).
+  cudaError_t spmm(const T* V, long long ldv, T* Yo, long long ldy, int k) {
+    const int Wd = 16 / sizeof(T);
+    const int nvec = (k + Wd - 1) / Wd;
+    int list[16];
+    const int cnt = nvec <= 128 ? spmm_shapes(nvec, list) : 0;
+    if (cnt <= 1) return spmm_lap<T>(st, g->csr, V, ldv, Yo, ldy, k, -1);
+    char key[128];
+    snprintf(key, sizeof(key), "spmm/%s/n2=%d/deg2=%d/k=%d", sizeof(T) == 4 ? "f32" : "f64",
+             log2ceil(n), log2ceil(std::max<long long>(1, g->csr.nnz / std::max(1, n))), k);
+    const int v = tune_pick(key, "spmm", st, cnt, 0, [&](int i) {
+      return spmm_lap<T>(st, g->csr, V, ldv, Yo, ldy, k, list[i]);
+    });
+    return spmm_lap<T>(st, g->csr, V, ldv, Yo, ldy, k, list[v]);
   }
 
   // Cholesky-QR of V (n x kc, stride ldv) into out (stride ldo); failure -> *failed.
@@ -701,7 +759,7 @@ struct LobRun : RunBase {
     if (hs & 32) return fail(c, SC_ETIMEOUT, "a bounded device wait gave up");
     *failed = (hs & (ST_CHOL_FAIL | ST_NONFINITE)) != 0;
     if (*failed) return SC_OK;
-    CK(tall_gemm<T>(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+    CK(tall(st, n, cat<T>(V, ldv, kc), Tm, kc, kc, out, ldo, nullptr, 0, (T)0), "tall");
     return SC_OK;
   }
 
@@ -814,12 +872,12 @@ struct LobRun : RunBase {
     if (!bad) rc = cholqr_step(T1, kp, K, S, ld3, &bad);
     if (rc != SC_OK) return rc;
     if (bad) return fail(c, SC_EBREAKDOWN, "start block is rank deficient");
-    CK(spmm_lap<T>(st, g->csr, S, ld3, LS, ld3, K), "spmm");
+    CK(spmm(S, ld3, LS, ld3, K), "spmm");
     // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
     CK(gram_seg(S, ld3, {{0, K}}, LS, ld3, {{0, K}}, G, K, true), "gram");
     CK(rr(K, G), "rr");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+    CK(tall(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall(st, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, nullptr, 0, (T)0), "tall");
     std::swap(S, S2);
     std::swap(LS, LS2);
     CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2, pdeg), "residual");
@@ -899,7 +957,7 @@ struct LobRun : RunBase {
     {
       TallSeg<T> sr{WR, ldw, WR, ldw, Tm, w, 0, ka};
       TallSeg<T> sp{WP, ldw, WP, ldw, Tm + ka, w, 0, haveP ? ka : 0};
-      CK(tall_gemm2<T>(st, n, cat<T>(S, ld3, K), sr, sp, (T)1, dstatus, tall_tc), "tall");
+      CK(tall2(st, n, cat<T>(S, ld3, K), sr, sp, (T)1), "tall");
     }
     // (2) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too), into
     //     the R and P slots.  A breakdown inside the P columns is handled on the device: the
@@ -919,13 +977,13 @@ struct LobRun : RunBase {
       else
         CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
       CK(chol(wq, G, TmA, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
-      CK(tall_gemm<T>(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+      CK(tall(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
       CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
       CK(chol(wq, G, TmB, dfail, ka, pf, ka, nullptr), "chol");
       // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
-      CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+      CK(tall(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0), "tall");
       if (haveP)
-        CK(tall_gemm<T>(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+        CK(tall(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0), "tall");
     }
     // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken
     //     on the orthonormalized block so that its images are products with L rather than
@@ -933,10 +991,10 @@ struct LobRun : RunBase {
     //     the factors grow ill-conditioned near convergence).  With every column active the
     //     R and P slots are adjacent (R slot padding is zero) and one SpMM covers both.
     if (haveP && all) {
-      CK(spmm_lap<T>(st, g->csr, Rslot, ld3, LRslot, ld3, kp + ka), "spmm");
+      CK(spmm(Rslot, ld3, LRslot, ld3, kp + ka), "spmm");
     } else {
-      CK(spmm_lap<T>(st, g->csr, Rslot, ld3, LRslot, ld3, ka), "spmm");
-      if (haveP) CK(spmm_lap<T>(st, g->csr, Pslot, ld3, LPslot, ld3, ka), "spmm");
+      CK(spmm(Rslot, ld3, LRslot, ld3, ka), "spmm");
+      if (haveP) CK(spmm(Pslot, ld3, LPslot, ld3, ka), "spmm");
     }
     // test hook: this pass's direction block is reported as broken down, as the Cholesky-QR
     // does when P has sunk into span{X, R} (the Rayleigh-Ritz step then runs without P)
@@ -956,10 +1014,10 @@ struct LobRun : RunBase {
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
     Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);
     fork();  // the L-images on the second stream
-    CK(tall_gemm<T>(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
-    CK(tall_gemm<T>(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1, dstatus, tall_tc), "tall");
-    CK(tall_gemm<T>(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
-    CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1, dstatus, tall_tc), "tall");
+    CK(tall(st2, n, LRP, Yrp, K, K, LS2 + 2 * kp, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall(st2, n, cat<T>(LS, ld3, K), Y, K, K, LS2, ld3, LS2 + 2 * kp, ld3, (T)1), "tall");
+    CK(tall(st, n, RP, Yrp, K, K, S2 + 2 * kp, ld3, nullptr, 0, (T)0), "tall");
+    CK(tall(st, n, cat<T>(S, ld3, K), Y, K, K, S2, ld3, S2 + 2 * kp, ld3, (T)1), "tall");
     join();
     std::swap(S, S2);
     std::swap(LS, LS2);
@@ -971,8 +1029,8 @@ struct LobRun : RunBase {
     if ((done_passes + 1) % kReorth == 0) {
       CK(gram_seg(S, ld3, {{0, K}}, S, ld3, {{0, K}}, G, K, true), "gram");
       CK(chol(K, G, Tm), "chol");
-      CK(tall_gemm<T>(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
-      CK(tall_gemm<T>(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0, dstatus, tall_tc), "tall");
+      CK(tall(st, n, cat<T>(S, ld3, K), Tm, K, K, T1, kp, nullptr, 0, (T)0), "tall");
+      CK(tall(st, n, cat<T>(LS, ld3, K), Tm, K, K, W1, kp, nullptr, 0, (T)0), "tall");
       CK(cudaMemcpy2DAsync(S, sizeof(T) * ld3, T1, sizeof(T) * kp, sizeof(T) * K, n,
                            cudaMemcpyDeviceToDevice, st), "reorth");
       CK(cudaMemcpy2DAsync(LS, sizeof(T) * ld3, W1, sizeof(T) * kp, sizeof(T) * K, n,
