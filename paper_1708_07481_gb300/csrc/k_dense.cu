@@ -1132,47 +1132,38 @@ __device__ void rr_phase_eigvecs(int m, int K, const T* __restrict__ d, const T*
         for (int a = 0; a < K; ++a) mind = min(mind, dd[a]);
         red[RS + 3] = mind;
       }
-      // the transform M = diag(wv) L^-T D^-1/2 into the upper triangle of Gs (the lower one
-      // holds L^-1): M[a][b] = wv_a (L^-1)_ba d_b^-1/2 for a < b, M[b][b] = wv_b d_b^-1/2
+      // L^-1 transposed into the (unused) upper triangle: Gs[a][b] = (L^-1)_ba for a < b,
+      // so lanes that own consecutive output columns b read consecutive addresses
       for (int p = tid; p < K * K; p += NT) {
         const int a = p / K, b = p % K;
-        if (b > a) Gs[a * K + b] = wv[a] * Gs[b * K + a] * cbuf[b];
-        else if (b == a) Gs[a * K + a] = wv[a] * cbuf[a];
+        if (b > a) Gs[a * K + b] = Gs[b * K + a];
       }
       __syncthreads();
-      // Z <- Z M: TPR threads per row (a power of two, in one warp) split the output columns
-      // b = t + TPR j (j < 16); each keeps its outputs in registers until every thread of the
-      // row has read the row
-      {
-        const int TPR = K <= 16 ? 1 : K <= 32 ? 2 : K <= 64 ? 4 : K <= 128 ? 8 : 16;
-        const int t = tid % TPR;
-        for (int base = 0; base < m; base += NT / TPR) {  // uniform
-          const int r = base + tid / TPR;
-          T out[16];
+      // Z <- Z diag(wv) L^-T D^-1/2: out_b = d_b^-1/2 sum_{a <= b} z_a wv_a (L^-1)_ba; a warp
+      // per row, lanes own output columns (kept in registers until the row has been read)
+      for (int r = warp; r < m; r += NW) {
+        T* zr = Z + r * K;
+        T out[16];
+        const int nq = (K + 31) >> 5;  // uniform
 #pragma unroll
-          for (int j = 0; j < 16; ++j) out[j] = 0;
-          if (r < m) {
-            const T* zr = Z + r * K;
-            for (int a = 0; a < K; ++a) {
-              const T za = zr[a];
-              const T* Ma = Gs + a * K;
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int b = t + TPR * j;
-                if (b < K && b >= a) out[j] = fma(za, Ma[b], out[j]);
-              }
-            }
+        for (int q = 0; q < 16; ++q) {
+          if (q >= nq) break;
+          const int b = lane + 32 * q;
+          T acc = 0;
+          if (b < K) {
+            for (int a = 0; a < b; ++a) acc = fma(zr[a] * wv[a], Gs[a * K + b], acc);
+            acc = (acc + zr[b] * wv[b]) * cbuf[b];
           }
-          __syncwarp();
-          if (r < m) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int b = t + TPR * j;
-              if (b < K) Z[r * K + b] = out[j];
-            }
-          }
-          __syncwarp();
+          out[q] = acc;
         }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (q >= nq) break;
+          const int b = lane + 32 * q;
+          if (b < K) zr[b] = out[q];
+        }
+        __syncwarp();
       }
       __syncthreads();
       RR_INV(3, tinv);
