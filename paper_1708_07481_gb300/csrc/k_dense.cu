@@ -1551,7 +1551,24 @@ __global__ void __launch_bounds__(RT_NT, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = 2 * warp + (lane >> 4), cl = lane & 15;
 
-  // ---- load (symmetrized), Gershgorin bound, lift the diagonal of dropped columns
+  // ---- load (symmetrized), Gershgorin bound, lift the diagonal of dropped columns.  G is
+  // staged in the (not yet used) reflector / eigenvector region with coalesced row reads when
+  // it fits there, so that the symmetrization's transposed reads hit shared memory
+  const double* Gsrc = G;
+  long long lds = ldg;
+  {
+    double* Gst = (double*)(((uintptr_t)Vs + 7) & ~(uintptr_t)7);
+    const size_t room = (size_t)m * ldv + 4 * (size_t)m * K + (size_t)K * K - 2;
+    if ((size_t)2 * m * m <= room) {
+      for (int idx = tid; idx < m * m; idx += RT_NT) {
+        const int i = idx / m, j = idx % m;
+        Gst[idx] = G[(long long)i * ldg + j];
+      }
+      __syncthreads();
+      Gsrc = Gst;
+      lds = m;
+    }
+  }
   T A[RS][CS];
   T gmax = 0;
 #pragma unroll
@@ -1562,7 +1579,7 @@ __global__ void __launch_bounds__(RT_NT, 1)
     for (int c = 0; c < CS; ++c) {
       const int j = cl + 16 * c;
       T a = 0;
-      if (i < m && j < m) a = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+      if (i < m && j < m) a = (T)(0.5 * (Gsrc[(long long)i * lds + j] + Gsrc[(long long)j * lds + i]));
       A[r][c] = a;
       rs += fabsf(a);
     }
@@ -1797,10 +1814,17 @@ __global__ void __launch_bounds__(CR_NW * 32, 1)
   T* dd = s + ka;                  // ka pivots
   T* buf = dd + ka;                // 2 x 16 CS
   T* W = buf + 2 * 16 * CS;        // ka x ka
+  double* Gs = (double*)(((uintptr_t)(W + (size_t)ka * ka) + 15) & ~(uintptr_t)15);  // ka x ka
   __shared__ int sfc;
   const int tid = threadIdx.x;
+  // the FP64 Gram staged with coalesced row reads (the symmetrization reads its transpose)
+  for (int idx = tid; idx < ka * ka; idx += NTH) {
+    const int i = idx / ka, j = idx % ka;
+    Gs[idx] = G[(long long)i * ldg + j];
+  }
+  __syncthreads();
   for (int i = tid; i < ka; i += NTH) {
-    const double dgi = G[(long long)i * ldg + i];
+    const double dgi = Gs[i * ka + i];
     const double fl = i < keep ? rfloor * rfloor : pfloor * pfloor;
     s[i] = dgi > fl ? (T)rsqrt(dgi) : (T)0;
   }
@@ -1808,7 +1832,7 @@ __global__ void __launch_bounds__(CR_NW * 32, 1)
   for (int idx = tid; idx < ka * ka; idx += NTH) {
     const int i = idx / ka, j = idx % ka;
     if (j > i) continue;
-    const double gg = 0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]);
+    const double gg = 0.5 * (Gs[i * ka + j] + Gs[j * ka + i]);
     W[i * ka + j] = (T)gg * s[i] * s[j];
   }
   __syncthreads();
@@ -1859,7 +1883,8 @@ template <int RS, int CS>
 cudaError_t chol_inv_rt(cudaStream_t st, int ka, const double* G, int ldg, float* Tm,
                         int* d_status, double pivot_tol, int* fail_col, int keep, int* pflag,
                         int ndrop, int* ndropped, double rfloor, double pfloor) {
-  const size_t sm = sizeof(float) * ((size_t)2 * ka + 32 * CS + (size_t)ka * ka);
+  const size_t sm = sizeof(float) * ((size_t)2 * ka + 32 * CS + (size_t)ka * ka) + 16 +
+                    sizeof(double) * (size_t)ka * ka;
   auto kern = k_chol_inv_rt<RS, CS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
