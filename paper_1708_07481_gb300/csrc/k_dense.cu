@@ -1248,7 +1248,10 @@ template <typename T, int NS, int NW, bool SM>
 __global__ void __launch_bounds__(NW * 32)
     k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
                  double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
-                 int* status, int* pflag, int mP, int* nfallback) {
+                 int* status, int* pflag, int mP, int* nfallback, const T* dext = nullptr,
+                 const T* eext = nullptr, const T* bext = nullptr, int ldext = 0) {
+  // dext != nullptr: the tridiagonal form (d, e, beta) and the reflector rows of Ag (row stride
+  // ldext) were computed by the cluster kernel (k_tridiag_cl); the load and phase 1 are skipped
   constexpr int NT = NW * 32;
   constexpr unsigned FULL = 0xffffffffu;
   const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
@@ -1267,14 +1270,15 @@ __global__ void __launch_bounds__(NW * 32)
   T* red = coef + K;    // 3 NW per-warp parts, then scalar slots RS ..
   T* nxt = red + 3 * NW + 8;
   T* A = SM ? nxt : Ag;                             // m x m (row stride m)
-  const int lda = rr_lda(m, rr_tpr(m, NT));  // row stride of the matrix
+  const bool ext = dext != nullptr;
+  const int lda = ext ? ldext : rr_lda(m, rr_tpr(m, NT));  // row stride of the matrix
   T* Z = SM ? A + (size_t)m * lda : Zg;             // m x K
   T* U = SM ? Z + (size_t)m * K : Ug;               // 3 m K
   T* Gs = SM ? U + (size_t)3 * m * K : Gsg;         // K x K
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // red[3 NW + 0..4]: lo, hi, max e^2, min pivot, MGS scale (the shared phases use them)
 
-  {
+  if (!ext) {
     T gmax = 0;  // Gershgorin bound of A: the largest row sum of |a_ij|
     for (int i = warp; i < m; i += NW) {
       T rs = 0;
@@ -1292,6 +1296,13 @@ __global__ void __launch_bounds__(NW * 32)
   }
   RR_MARK(0);
 
+  if (ext) {
+    for (int i = tid; i < m; i += NT) {
+      d[i] = dext[i];
+      e[i] = eext[i];
+      beta[i] = bext[i];
+    }
+  } else {
   // ---- 1. tridiagonalization (Golub & Van Loan Alg. 8.3.1), two barriers per step
   // tpr threads per row: thread t < ntri owns row i = t / tpr and, of the columns j that step
   // k touches, those with j = k + 1 + q (mod tpr), q = t % tpr.  Step k:
@@ -1409,6 +1420,7 @@ __global__ void __launch_bounds__(NW * 32)
         e[m - 1] = 0;
       }
     }
+  }
   }
   __syncthreads();
   RR_MARK(1);
@@ -1963,14 +1975,30 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
   if constexpr (can_sm) {
     if (insm) kern = k_rr_eig_reg<T, NS, NW, true>;
   }
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // FP32 with the matrix in global memory: the tridiagonalization runs on a cluster of CTAs
+  // holding the matrix in registers (k_tridiag_cl), the other phases here
+  T* tri = nullptr;
+  cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (!insm && m > 160) {
+      tri = al.get<T>((size_t)3 * m);
+      if (!tri) e = cudaErrorMemoryAllocation;
+      if (e == cudaSuccess)
+        e = tridiag_cluster(st, m, K, G, ldg, (float*)Ag, m, (float*)tri, (float*)tri + m,
+                            (float*)tri + 2 * m, pflag, mP);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess) {
     ProfScope ps(st, "rr_eig");
     kern<<<1, NW * 32, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, d_status, pflag, mP,
-                                 nfallback);
+                                 nfallback, tri, tri ? tri + m : nullptr,
+                                 tri ? tri + 2 * m : nullptr, tri ? m : 0);
     note_launch();
     e = cudaGetLastError();
   }
+  al.put(tri);
   al.put(Ag);
   return e;
 }
