@@ -1,0 +1,50 @@
+"""Small, self-contained cases for kernel profiling (ncu -k / -c on one kernel).
+
+    python -m paper_1708_07481_gb300.profile_cases rr    # 3 Rayleigh-Ritz solves, m = 132, K = 44
+    python -m paper_1708_07481_gb300.profile_cases lob   # 3 LOBPCG passes, DC-SBM n = 50,000, K = 44
+    python -m paper_1708_07481_gb300.profile_cases big   # 2 LOBPCG passes, DC-SBM n = 300,000, K = 160
+
+`rr` feeds the dense Rayleigh-Ritz solve a 132 x 132 FP64 Gram with K = 44 small and 88 large
+eigenvalues (the spectrum shape of the [X R P] projection at n = 50,000, K = 44).  `lob`
+exercises the Cholesky-QR factors of 44 and 88 columns.  `big` runs the SpMM, the tensor-core
+Gram and the tensor-core tall update on blocks (300,000 x 480 FP32 = 576 MB) larger than L2,
+while holding only a few GB of device memory.  Every case goes through the C ABI and prints
+"ok <case>" when it ends.
+"""
+import sys
+
+import numpy as np
+
+from . import sc
+from . import workload as W
+
+
+def main(argv=None):
+    mode = (argv or sys.argv[1:] or ["rr"])[0]
+    ctx = sc.sc_ctx_create(0)
+    if mode == "rr":
+        rng = np.random.default_rng(0)
+        m, K = 132, 44
+        ev = np.concatenate([np.sort(rng.uniform(0, 12, K)),
+                             np.sort(rng.uniform(10, 200, m - K))])
+        Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        G = (Q * ev) @ Q.T
+        for _ in range(3):
+            sc.sc_rr_solve(ctx, G, K, sc.SC_PREC_FP32)
+    elif mode == "lob":
+        g = W.dcsbm(50000, 44, seed=0)
+        Gr = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
+        sc.sc_lobpcg(ctx, Gr, 44, iters=3, seed=0, cold=1, want_X=False)
+    elif mode == "big":
+        import torch
+        g = W.dcsbm(300000, 160, seed=0)
+        Gr = sc.sc_build_laplacian(ctx, g.n, torch.from_numpy(g.src).cuda(),
+                                   torch.from_numpy(g.dst).cuda())
+        sc.sc_lobpcg(ctx, Gr, 160, iters=2, seed=0, cold=1, want_X=False)
+    else:
+        raise SystemExit(f"unknown case {mode!r}: rr, lob or big")
+    print("ok", mode)
+
+
+if __name__ == "__main__":
+    main()
