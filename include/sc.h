@@ -84,8 +84,15 @@ size_t sc_ctx_bytes_in_use(const sc_ctx* ctx);
 /* High-water mark of the device bytes the context held since the previous call (or since
  * creation); the mark is reset to the current use.  Not thread-safe (like the context). */
 size_t sc_ctx_bytes_peak(sc_ctx* ctx);
-/* Number of kernels the library has launched so far in this process (launch accounting). */
+/* Number of kernels the library has launched so far in this process (launch accounting;
+ * kernels replayed from a CUDA graph count once per replay). */
 uint64_t sc_ctx_kernel_launches(const sc_ctx* ctx);
+/* Number of LOBPCG passes replayed from CUDA graphs so far in this process.  A solve with a
+ * fixed pass count (tol_abs = tol_lock = 0) records its pass once per buffer parity, after one
+ * eager pass with the direction block, and replays it: the same kernels on the same buffers,
+ * so results are bitwise those of eager passes.  The environment variable SC_CUDA_GRAPHS=0
+ * (read when a solve starts) keeps every pass eager. */
+uint64_t sc_ctx_graph_replays(const sc_ctx* ctx);
 /* Kernel timing: between sc_profile_begin and sc_profile_end, every launch of a kernel
  * named in `kernels` (comma-separated names such as "spmm,gram,rr_eig", or "*" for all) is
  * bracketed by CUDA events on the stream it is launched on.  sc_profile_end synchronizes the

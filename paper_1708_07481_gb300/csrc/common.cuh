@@ -2,6 +2,7 @@
 #pragma once
 #include <functional>
 #include <string>
+#include <vector>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,12 +68,14 @@ inline Cat3<T> cat(const T* p0, long long ld0, int c0, const T* p1, long long ld
 
 // Launch accounting: every kernel launch of the library goes through note_launch().
 void note_launch();
+void note_launches(uint64_t k);  // k launches replayed from a CUDA graph
 uint64_t launches_total();
 
 // Per-kernel timing with CUDA events on the launching stream.  A ProfScope placed around a
 // launch records an event pair when profiling is on for that kernel name.
 void prof_begin(cudaStream_t st, const char* name);
 void prof_end(cudaStream_t st, const char* name);
+bool prof_active();  // an event-pair profile is being taken (no graph replay meanwhile)
 struct ProfScope {
   cudaStream_t st;
   const char* name;
@@ -250,5 +253,56 @@ cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const floa
 cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
                   long long lde, const int* seeds_dev, int iters, int* labels_dev,
                   double* cent_dev, int* iters_run, double* inertia);
+
+// ---- lockstep batches (sc_lobpcg_batch): one launch per kernel shape for all runs ---------
+// A descriptor holds one run's arguments of the single-run call; a batched launch runs one CTA
+// (one cluster for the cluster tridiagonalization, a share of the rows for the SpMM) per
+// descriptor with the single-run kernel's arithmetic, so every run's results are bitwise its
+// single-run results.  Descriptor tables live in device memory, written once per batch.
+struct CholDesc {
+  int ka, ldg, keep, ndrop;
+  const double* G;
+  float* Tm;
+  float* Wg;  // ka x ka scratch when the factorization does not fit in shared memory
+  int *status, *fail_col, *pflag, *ndropped;
+  double pivot_tol, rfloor, pfloor;
+};
+struct RrDesc {
+  int m, K, ldg, mP;
+  const double* G;
+  double* theta;
+  float* Y;
+  int *status, *pflag, *nfallback;
+  float* Ag;   // global-memory working set (rr_batch_scratch floats) or null
+  float* tri;  // 3 m floats (d, e, beta of the cluster tridiagonalization) or null
+};
+struct SpmmDesc {
+  long long row0;  // first row of this graph in the batch's concatenated row range
+  int n, nvec;     // rows; 16-byte column chunks per row
+  const int *rp, *ci;
+  const float *val, *deg, *V;
+  float* Y;
+  long long ldv, ldy;
+};
+// A run of consecutive descriptors launched together: kind (the kernel shape), its first
+// descriptor and count, the template parameter and the dynamic shared memory it needs.
+struct BatchGroup {
+  int kind, first, count, param;
+  size_t smem;
+};
+// Orders the descriptors by kernel shape and returns the groups; entries whose shape has no
+// batched form are left out of every group (their indices in *single) and run one by one.
+void chol_batch_plan(std::vector<CholDesc>& d, std::vector<BatchGroup>& groups,
+                     std::vector<int>& single);
+cudaError_t chol_batch_launch(cudaStream_t st, const CholDesc* dtab,
+                              const std::vector<BatchGroup>& groups);
+size_t chol_batch_scratch(int ka);  // floats of Wg needed (0: shared memory suffices)
+void rr_batch_plan(std::vector<RrDesc>& d, std::vector<BatchGroup>& groups, std::vector<int>& single);
+cudaError_t rr_batch_launch(cudaStream_t st, const RrDesc* dtab, const std::vector<BatchGroup>& groups);
+size_t rr_batch_scratch(int m, int K);  // floats of Ag (0: none); tri needs 3 m when m > 160
+bool rr_batch_cluster(int m);           // the group tridiagonalizes on a cluster of CTAs
+cudaError_t tridiag_cluster_batch(cudaStream_t st, int count, const RrDesc* dtab, int mmax);
+cudaError_t spmm_batch_launch(cudaStream_t st, const SpmmDesc* dtab, int count, long long rows,
+                              int nvec_max);
 
 }  // namespace sc

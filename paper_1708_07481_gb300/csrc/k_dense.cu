@@ -310,10 +310,11 @@ __device__ int ldl_inv_reg(int n, float* M, int ldm, float* dd, float* buf, floa
 // and *pflag cleared.
 // SM = the matrix lives in shared memory.
 template <typename T, bool SM>
-__global__ void __launch_bounds__(1024)
-    k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
-               int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
-               int* ndropped, double rfloor, double pfloor) {
+__device__ __forceinline__ void k_chol_inv_body(int ka, const double* __restrict__ G, int ldg,
+                                                T* __restrict__ Tm, T* Wg, int* status,
+                                                int* fail_col, double pivot_tol, int keep,
+                                                int* pflag, int ndrop, int* ndropped,
+                                                double rfloor, double pfloor) {
   extern __shared__ __align__(16) unsigned char craw[];
   T* s = (T*)craw;    // ka scale factors
   T* dd = s + ka;     // ka pivots
@@ -363,6 +364,22 @@ __global__ void __launch_bounds__(1024)
     if (r <= c && c < kk) v = s[r] * (r == c ? (T)1 : W[c * ka + r]) * cb[c];
     Tm[(long long)r * ka + c] = v;
   }
+}
+
+template <typename T, bool SM>
+__global__ void __launch_bounds__(1024)
+    k_chol_inv(int ka, const double* __restrict__ G, int ldg, T* __restrict__ Tm, T* Wg,
+               int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
+               int* ndropped, double rfloor, double pfloor) {
+  k_chol_inv_body<T, SM>(ka, G, ldg, Tm, Wg, status, fail_col, pivot_tol, keep, pflag, ndrop,
+                         ndropped, rfloor, pfloor);
+}
+// One CTA per descriptor of a lockstep batch (FP32).
+template <bool SM>
+__global__ void __launch_bounds__(1024) k_chol_inv_b(const CholDesc* __restrict__ tab) {
+  const CholDesc a = tab[blockIdx.x];
+  k_chol_inv_body<float, SM>(a.ka, a.G, a.ldg, a.Tm, a.Wg, a.status, a.fail_col, a.pivot_tol,
+                             a.keep, a.pflag, a.ndrop, a.ndropped, a.rfloor, a.pfloor);
 }
 
 template <typename T>
@@ -1245,11 +1262,12 @@ __device__ __forceinline__ void rr_named_sync(int n) {
 }
 
 template <typename T, int NS, int NW, bool SM>
-__global__ void __launch_bounds__(NW * 32)
-    k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
-                 double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
-                 int* status, int* pflag, int mP, int* nfallback, const T* dext = nullptr,
-                 const T* eext = nullptr, const T* bext = nullptr, int ldext = 0) {
+__device__ __forceinline__ void k_rr_eig_reg_body(int m_full, int K, const double* __restrict__ G,
+                                                  int ldg, double* __restrict__ theta,
+                                                  T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
+                                                  int* status, int* pflag, int mP,
+                                                  int* nfallback, const T* dext,
+                                                  const T* eext, const T* bext, int ldext) {
   // dext != nullptr: the tridiagonal form (d, e, beta) and the reflector rows of Ag (row stride
   // ldext) were computed by the cluster kernel (k_tridiag_cl); the load and phase 1 are skipped
   constexpr int NT = NW * 32;
@@ -1490,6 +1508,30 @@ __global__ void __launch_bounds__(NW * 32)
 }
 
 
+template <typename T, int NS, int NW, bool SM>
+__global__ void __launch_bounds__(NW * 32)
+    k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
+                 double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
+                 int* status, int* pflag, int mP, int* nfallback, const T* dext = nullptr,
+                 const T* eext = nullptr, const T* bext = nullptr, int ldext = 0) {
+  k_rr_eig_reg_body<T, NS, NW, SM>(m_full, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, status, pflag,
+                                   mP, nfallback, dext, eext, bext, ldext);
+}
+// One CTA per descriptor of a lockstep batch (FP32).  With the matrix in global memory the
+// working set is Ag (m (m + 16) floats, then Z, U, Gs); with tri set, the tridiagonal form and
+// the reflector rows (stride m) come from the cluster kernel.
+template <int NS, int NW, bool SM>
+__global__ void __launch_bounds__(NW * 32) k_rr_eig_reg_b(const RrDesc* __restrict__ tab) {
+  const RrDesc a = tab[blockIdx.x];
+  float* Zg = SM ? nullptr : a.Ag + (size_t)a.m * (a.m + 16);
+  float* Ug = SM ? nullptr : Zg + (size_t)a.m * a.K;
+  float* Gsg = SM ? nullptr : Ug + (size_t)3 * a.m * a.K;
+  k_rr_eig_reg_body<float, NS, NW, SM>(a.m, a.K, a.G, a.ldg, a.theta, a.Y, a.Ag, Zg, Ug, Gsg,
+                                       a.status, a.pflag, a.mP, a.nfallback, a.tri,
+                                       a.tri ? a.tri + a.m : nullptr,
+                                       a.tri ? a.tri + 2 * a.m : nullptr, a.tri ? a.m : 0);
+}
+
 // ---------------------------------------------------------------------------------------
 // Rayleigh-Ritz with the matrix held in registers, m <= 32 RS, FP32, 16 warps.  Half-warp
 // g = 2 warp + lane / 16 (0..31) owns rows g + 32 r (r < RS); lane cl = lane % 16 of it owns
@@ -1531,10 +1573,10 @@ __host__ __device__ inline size_t rt_smem_floats(int m, int K, int rs) {
 }
 
 template <int RS>
-__global__ void __launch_bounds__(RT_NT, 1)
-    k_rr_eig_rt(int m_full, int K, const double* __restrict__ G, int ldg,
-                double* __restrict__ theta, float* __restrict__ Y, int* status, int* pflag,
-                int mP, int* nfallback) {
+__device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double* __restrict__ G,
+                                                 int ldg, double* __restrict__ theta,
+                                                 float* __restrict__ Y, int* status, int* pflag,
+                                                 int mP, int* nfallback) {
   using T = float;
   constexpr int CS = 2 * RS;
   constexpr unsigned FULL = 0xffffffffu;
@@ -1810,15 +1852,30 @@ __global__ void __launch_bounds__(RT_NT, 1)
 }
 
 
+template <int RS>
+__global__ void __launch_bounds__(RT_NT, 1)
+    k_rr_eig_rt(int m_full, int K, const double* __restrict__ G, int ldg,
+                double* __restrict__ theta, float* __restrict__ Y, int* status, int* pflag,
+                int mP, int* nfallback) {
+  k_rr_eig_rt_body<RS>(m_full, K, G, ldg, theta, Y, status, pflag, mP, nfallback);
+}
+// One CTA per descriptor of a lockstep batch.
+template <int RS>
+__global__ void __launch_bounds__(RT_NT, 1) k_rr_eig_rt_b(const RrDesc* __restrict__ tab) {
+  const RrDesc a = tab[blockIdx.x];
+  k_rr_eig_rt_body<RS>(a.m, a.K, a.G, a.ldg, a.theta, a.Y, a.status, a.pflag, a.mP, a.nfallback);
+}
+
 // Cholesky-QR transform in FP32 with the factorization in registers (ldl_inv_reg, four warps,
 // ka <= min(8 RS, 16 CS)): the same arithmetic as k_chol_inv (scaled FP64 Gram, in-place LDL'
 // with L^-1 formed alongside, column drops, floors, the direction-block fallback).
 constexpr int CR_NW = 4;
 template <int RS, int CS>
-__global__ void __launch_bounds__(CR_NW * 32, 1)
-    k_chol_inv_rt(int ka, const double* __restrict__ G, int ldg, float* __restrict__ Tm,
-                  int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
-                  int* ndropped, double rfloor, double pfloor) {
+__device__ __forceinline__ void k_chol_inv_rt_body(int ka, const double* __restrict__ G, int ldg,
+                                                   float* __restrict__ Tm, int* status,
+                                                   int* fail_col, double pivot_tol, int keep,
+                                                   int* pflag, int ndrop, int* ndropped,
+                                                   double rfloor, double pfloor) {
   using T = float;
   constexpr int NTH = CR_NW * 32;
   extern __shared__ __align__(16) unsigned char craw[];
@@ -1880,6 +1937,22 @@ __global__ void __launch_bounds__(CR_NW * 32, 1)
     if (r <= c && c < kk) v = s[r] * (r == c ? (T)1 : W[c * ka + r]) * buf[c];
     Tm[(long long)r * ka + c] = v;
   }
+}
+
+template <int RS, int CS>
+__global__ void __launch_bounds__(CR_NW * 32, 1)
+    k_chol_inv_rt(int ka, const double* __restrict__ G, int ldg, float* __restrict__ Tm,
+                  int* status, int* fail_col, double pivot_tol, int keep, int* pflag, int ndrop,
+                  int* ndropped, double rfloor, double pfloor) {
+  k_chol_inv_rt_body<RS, CS>(ka, G, ldg, Tm, status, fail_col, pivot_tol, keep, pflag, ndrop,
+                             ndropped, rfloor, pfloor);
+}
+// One CTA per descriptor of a lockstep batch.
+template <int RS, int CS>
+__global__ void __launch_bounds__(CR_NW * 32, 1) k_chol_inv_rt_b(const CholDesc* __restrict__ tab) {
+  const CholDesc a = tab[blockIdx.x];
+  k_chol_inv_rt_body<RS, CS>(a.ka, a.G, a.ldg, a.Tm, a.status, a.fail_col, a.pivot_tol, a.keep,
+                             a.pflag, a.ndrop, a.ndropped, a.rfloor, a.pfloor);
 }
 
 }  // namespace
@@ -2073,6 +2146,167 @@ cudaError_t rr_eig(cudaStream_t st, Alloc& al, int m, int K, const double* G, in
   al.put(lu);
   al.put(Gs);
   return e;
+}
+
+// ---- lockstep batches ------------------------------------------------------------------
+// Groups of the batched Cholesky-QR transforms (FP32): kind 0 = the four-warp register form
+// (ka <= 128; param = the register shape of the group's largest ka), kind 1 = the shared-memory
+// form, kind 2 = the global-memory form (Wg per descriptor).  The register shapes differ only in
+// unused slots, so a factorization gives the same bits in any of them.
+static int chol_rt_shape(int ka) { return ka <= 64 ? 0 : ka <= 96 ? 1 : 2; }
+static size_t chol_rt_smem(int ka, int shape) {
+  const int CS = shape == 0 ? 4 : shape == 1 ? 6 : 8;
+  return sizeof(float) * ((size_t)2 * ka + 32 * CS + (size_t)ka * ka) + 16 +
+         sizeof(double) * (size_t)ka * ka;
+}
+static size_t chol_nt_base(int ka) { return sizeof(float) * 4 * (size_t)ka; }
+static bool chol_nt_insm(int ka) {
+  return chol_nt_base(ka) + sizeof(float) * (size_t)ka * ka <= 200 * 1024;
+}
+size_t chol_batch_scratch(int ka) { return (ka > 128 && !chol_nt_insm(ka)) ? (size_t)ka * ka : 0; }
+
+void chol_batch_plan(std::vector<CholDesc>& d, std::vector<BatchGroup>& groups,
+                     std::vector<int>& single) {
+  auto kind = [](const CholDesc& a) { return a.ka <= 128 ? 0 : chol_nt_insm(a.ka) ? 1 : 2; };
+  std::stable_sort(d.begin(), d.end(),
+                   [&](const CholDesc& x, const CholDesc& y) { return kind(x) < kind(y); });
+  groups.clear();
+  single.clear();
+  for (int i = 0; i < (int)d.size();) {
+    const int k = kind(d[i]);
+    int j = i, kamax = 0;
+    while (j < (int)d.size() && kind(d[j]) == k) kamax = std::max(kamax, d[j++].ka);
+    BatchGroup gr{k, i, j - i, 0, 0};
+    if (k == 0) {
+      gr.param = chol_rt_shape(kamax);
+      for (int q = i; q < j; ++q) gr.smem = std::max(gr.smem, chol_rt_smem(d[q].ka, gr.param));
+    } else {
+      gr.smem = chol_nt_base(kamax) + (k == 1 ? sizeof(float) * (size_t)kamax * kamax : 0);
+    }
+    groups.push_back(gr);
+    i = j;
+  }
+}
+
+cudaError_t chol_batch_launch(cudaStream_t st, const CholDesc* dtab,
+                              const std::vector<BatchGroup>& groups) {
+  for (const BatchGroup& g : groups) {
+    if (g.count <= 0) continue;
+    const CholDesc* t = dtab + g.first;
+    cudaError_t e = cudaSuccess;
+    ProfScope ps(st, "chol_inv");
+    if (g.kind == 0) {
+      auto kern = g.param == 0 ? k_chol_inv_rt_b<8, 4>
+                  : g.param == 1 ? k_chol_inv_rt_b<12, 6> : k_chol_inv_rt_b<16, 8>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+      if (e == cudaSuccess) kern<<<g.count, CR_NW * 32, g.smem, st>>>(t);
+    } else {
+      auto kern = g.kind == 1 ? k_chol_inv_b<true> : k_chol_inv_b<false>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+      if (e == cudaSuccess) kern<<<g.count, 512, g.smem, st>>>(t);
+    }
+    note_launch();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Groups of the batched Rayleigh-Ritz solves (FP32): kind 0 = the register-resident kernel
+// (param = RS of the group's largest m), kind 1 / 2 = the register-slot kernel of 1,024 threads
+// with its working set in shared / global memory (m <= 160), kind 3 = the cluster
+// tridiagonalization and the register-slot kernel in its external-input mode (160 < m <= 480).
+// Larger m run one by one.  Wider register shapes only add zero slots: the same bits.
+static int rr_rt_rs(int m) { return m <= 64 ? 2 : m <= 96 ? 3 : m <= 128 ? 4 : 5; }
+static size_t rr_rt_bytes(int m, int K, int rs) { return sizeof(float) * rt_smem_floats(m, K, rs); }
+static size_t rr_reg5_base(int m, int K) { return sizeof(float) * ((size_t)6 * m + 7 * (size_t)K + 3 * 32 + 8); }
+static size_t rr_reg_big(int m, int K) {
+  return sizeof(float) * ((size_t)m * (m + 16) + 4 * (size_t)m * K + (size_t)K * K);
+}
+static int rr_kind(int m, int K) {
+  if (m <= 160 && rr_rt_bytes(m, K, rr_rt_rs(m)) <= 225 * 1024) return 0;
+  if (m <= 160) return rr_reg5_base(m, K) + rr_reg_big(m, K) <= 220 * 1024 ? 1 : 2;
+  if (m <= 480) return 3;
+  return 4;
+}
+bool rr_batch_cluster(int m) { return m > 160 && m <= 480; }
+size_t rr_batch_scratch(int m, int K) {
+  const int k = rr_kind(m, K);
+  return (k == 2 || k == 3) ? rr_reg_big(m, K) / sizeof(float) : 0;
+}
+
+void rr_batch_plan(std::vector<RrDesc>& d, std::vector<BatchGroup>& groups,
+                   std::vector<int>& single) {
+  std::vector<RrDesc> in = d;
+  d.clear();
+  groups.clear();
+  single.clear();
+  for (int k = 0; k < 4; ++k) {
+    const int first = (int)d.size();
+    int mmax = 0;
+    for (const RrDesc& a : in)
+      if (rr_kind(a.m, a.K) == k) mmax = std::max(mmax, a.m);
+    BatchGroup gr{k, first, 0, 0, 0};
+    if (k == 0) gr.param = rr_rt_rs(mmax);
+    for (const RrDesc& a : in) {
+      if (rr_kind(a.m, a.K) != k) continue;
+      size_t need = 0;
+      if (k == 0) need = rr_rt_bytes(a.m, a.K, gr.param);
+      else if (k == 1) need = rr_reg5_base(a.m, a.K) + rr_reg_big(a.m, a.K);
+      else if (k == 2) need = rr_reg5_base(a.m, a.K);
+      else need = sizeof(float) * ((size_t)6 * a.m + 7 * (size_t)a.K + 3 * 16 + 8);
+      if (k == 0 && need > 225 * 1024) continue;  // does not fit the group's register shape
+      gr.smem = std::max(gr.smem, need);
+      d.push_back(a);
+    }
+    gr.count = (int)d.size() - first;
+    if (gr.count > 0) {
+      if (k == 3) gr.param = mmax;
+      groups.push_back(gr);
+    }
+  }
+  // the rest (m > 480, or a kernel shape the group's cannot hold) one by one, after the groups
+  for (const RrDesc& a : in) {
+    bool placed = false;
+    for (const RrDesc& b : d) placed = placed || (b.theta == a.theta);
+    if (!placed) {
+      single.push_back((int)d.size());
+      d.push_back(a);
+    }
+  }
+}
+
+cudaError_t rr_batch_launch(cudaStream_t st, const RrDesc* dtab,
+                            const std::vector<BatchGroup>& groups) {
+  for (const BatchGroup& g : groups) {
+    if (g.count <= 0) continue;
+    const RrDesc* t = dtab + g.first;
+    cudaError_t e = cudaSuccess;
+    if (g.kind == 3) {
+      e = tridiag_cluster_batch(st, g.count, t, g.param);
+      if (e != cudaSuccess) return e;
+    }
+    ProfScope ps(st, "rr_eig");
+    if (g.kind == 0) {
+      auto kern = g.param == 2 ? k_rr_eig_rt_b<2>
+                  : g.param == 3 ? k_rr_eig_rt_b<3>
+                  : g.param == 4 ? k_rr_eig_rt_b<4> : k_rr_eig_rt_b<5>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+      if (e == cudaSuccess) kern<<<g.count, RT_NT, g.smem, st>>>(t);
+    } else if (g.kind == 1 || g.kind == 2) {
+      auto kern = g.kind == 1 ? k_rr_eig_reg_b<5, 32, true> : k_rr_eig_reg_b<5, 32, false>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+      if (e == cudaSuccess) kern<<<g.count, 32 * 32, g.smem, st>>>(t);
+    } else {
+      auto kern = k_rr_eig_reg_b<15, 16, false>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+      if (e == cudaSuccess) kern<<<g.count, 16 * 32, g.smem, st>>>(t);
+    }
+    note_launch();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template cudaError_t chol_inv<float>(cudaStream_t, Alloc&, int, const double*, int, float*,

@@ -47,74 +47,106 @@ constexpr int MAXC = 4;  // chunks per lane: TL=32 x 4 chunks x 4 floats = 512 c
 
 // NC = 16-byte chunks per lane (compile time).  Neighbours are processed four at a time with
 // all of their row loads issued before the first accumulation, so each lane keeps 4 * NC
-// gathers in flight instead of one.
+// gathers in flight instead of one.  The neighbours of a row are summed in CSR order whatever
+// TL and NC are, so every kernel shape gives the same bits.
+template <typename T, int TL, int NC>
+__device__ __forceinline__ void spmm_row(long long row, int lane, unsigned gmask,
+                                         const int* __restrict__ rp, const int* __restrict__ ci,
+                                         const float* __restrict__ val, const T* __restrict__ deg,
+                                         const T* __restrict__ V, long long ldv,
+                                         T* __restrict__ Y, long long ldy, int nvec) {
+  using V4 = typename Vec<T>::type;
+  bool act[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) act[c] = lane + c * TL < nvec;
+  V4 acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = Vec<T>::zero();
+  const int s = rp[row], e = rp[row + 1];
+  for (int base = s; base < e; base += TL) {
+    const int my = base + lane < e ? ci[base + lane] : 0;
+    const float mw = (val && base + lane < e) ? val[base + lane] : 1.0f;
+    const int cnt = min(TL, e - base);
+    int t = 0;
+    for (; t + 4 <= cnt; t += 4) {
+      int j[4];
+      T w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        j[u] = __shfl_sync(gmask, my, t + u, TL);
+        w[u] = (T)__shfl_sync(gmask, mw, t + u, TL);
+      }
+      V4 x[4][NC];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const V4* vr = reinterpret_cast<const V4*>(V + (long long)j[u] * ldv);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) x[u][c] = act[c] ? __ldg(vr + lane + c * TL) : Vec<T>::zero();
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          if (val) Vec<T>::fma(acc[c], w[u], x[u][c]);
+          else Vec<T>::add(acc[c], x[u][c]);
+        }
+    }
+    for (; t < cnt; ++t) {
+      const int jj = __shfl_sync(gmask, my, t, TL);
+      const T ww = (T)__shfl_sync(gmask, mw, t, TL);
+      const V4* vr = reinterpret_cast<const V4*>(V + (long long)jj * ldv);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (act[c]) {
+          V4 x = __ldg(vr + lane + c * TL);
+          if (val) Vec<T>::fma(acc[c], ww, x);
+          else Vec<T>::add(acc[c], x);
+        }
+      }
+    }
+  }
+  const T d = deg[row];
+  const V4* vi = reinterpret_cast<const V4*>(V + row * ldv);
+  V4* yo = reinterpret_cast<V4*>(Y + row * ldy);
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (act[c]) yo[lane + c * TL] = Vec<T>::lap(d, vi[lane + c * TL], acc[c]);
+}
+
+template <int TL>
+__device__ __forceinline__ unsigned team_mask() {
+  return (TL == 32) ? 0xffffffffu : (((1u << TL) - 1u) << ((threadIdx.x & 31) / TL * TL));
+}
+
 template <typename T, int TL, int NC>
 __global__ void __launch_bounds__(256)
     k_spmm(int n, const int* __restrict__ rp, const int* __restrict__ ci,
            const float* __restrict__ val, const T* __restrict__ deg, const T* __restrict__ V,
            long long ldv, T* __restrict__ Y, long long ldy, int nvec) {
-  using V4 = typename Vec<T>::type;
   const int lane = threadIdx.x % TL;
-  const unsigned gmask = (TL == 32) ? 0xffffffffu
-                                    : (((1u << TL) - 1u) << ((threadIdx.x & 31) / TL * TL));
+  const unsigned gmask = team_mask<TL>();
   long long team = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / TL;
   long long nteams = ((long long)gridDim.x * blockDim.x) / TL;
-  bool act[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) act[c] = lane + c * TL < nvec;
-  for (long long row = team; row < n; row += nteams) {
-    V4 acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = Vec<T>::zero();
-    const int s = rp[row], e = rp[row + 1];
-    for (int base = s; base < e; base += TL) {
-      const int my = base + lane < e ? ci[base + lane] : 0;
-      const float mw = (val && base + lane < e) ? val[base + lane] : 1.0f;
-      const int cnt = min(TL, e - base);
-      int t = 0;
-      for (; t + 4 <= cnt; t += 4) {
-        int j[4];
-        T w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          j[u] = __shfl_sync(gmask, my, t + u, TL);
-          w[u] = (T)__shfl_sync(gmask, mw, t + u, TL);
-        }
-        V4 x[4][NC];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const V4* vr = reinterpret_cast<const V4*>(V + (long long)j[u] * ldv);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) x[u][c] = act[c] ? __ldg(vr + lane + c * TL) : Vec<T>::zero();
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            if (val) Vec<T>::fma(acc[c], w[u], x[u][c]);
-            else Vec<T>::add(acc[c], x[u][c]);
-          }
-      }
-      for (; t < cnt; ++t) {
-        const int jj = __shfl_sync(gmask, my, t, TL);
-        const T ww = (T)__shfl_sync(gmask, mw, t, TL);
-        const V4* vr = reinterpret_cast<const V4*>(V + (long long)jj * ldv);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          if (act[c]) {
-            V4 x = __ldg(vr + lane + c * TL);
-            if (val) Vec<T>::fma(acc[c], ww, x);
-            else Vec<T>::add(acc[c], x);
-          }
-        }
-      }
-    }
-    const T d = deg[row];
-    const V4* vi = reinterpret_cast<const V4*>(V + row * ldv);
-    V4* yo = reinterpret_cast<V4*>(Y + row * ldy);
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (act[c]) yo[lane + c * TL] = Vec<T>::lap(d, vi[lane + c * TL], acc[c]);
+  for (long long row = team; row < n; row += nteams)
+    spmm_row<T, TL, NC>(row, lane, gmask, rp, ci, val, deg, V, ldv, Y, ldy, nvec);
+}
+
+// Lockstep batch (FP32): the rows of every graph of the descriptor table form one range that
+// the teams stride through; a team's rows only grow, so it finds each row's graph by moving
+// forward through the table (descriptors in row0 order).
+template <int TL, int NC>
+__global__ void __launch_bounds__(256)
+    k_spmm_b(const SpmmDesc* __restrict__ tab, int count, long long rows) {
+  const int lane = threadIdx.x % TL;
+  const unsigned gmask = team_mask<TL>();
+  long long team = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / TL;
+  long long nteams = ((long long)gridDim.x * blockDim.x) / TL;
+  int q = 0;
+  for (long long grow = team; grow < rows; grow += nteams) {
+    while (q + 1 < count && tab[q + 1].row0 <= grow) ++q;
+    const SpmmDesc& a = tab[q];
+    spmm_row<float, TL, NC>(grow - a.row0, lane, gmask, a.rp, a.ci, a.val, a.deg, a.V, a.ldv,
+                            a.Y, a.ldy, a.nvec);
   }
 }
 
@@ -211,6 +243,33 @@ cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv
     shape = list[0];
   }
   return launch_shape<T>(shape, st, g, deg, V, ldv, Y, ldy, nvec);
+}
+
+template <int TL, int NC>
+static cudaError_t launch_b(cudaStream_t st, const SpmmDesc* dtab, int count, long long rows) {
+  long long blocks = (rows * TL + 255) / 256;
+  const long long cap = 152LL * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  ProfScope ps(st, "spmm");
+  k_spmm_b<TL, NC><<<(unsigned)blocks, 256, 0, st>>>(dtab, count, rows);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// One launch for the SpMM of every graph of a lockstep batch, with the default kernel shape
+// of the widest block (nvec_max <= 128 chunks).
+cudaError_t spmm_batch_launch(cudaStream_t st, const SpmmDesc* dtab, int count, long long rows,
+                              int nvec_max) {
+  if (count <= 0 || rows <= 0) return cudaSuccess;
+  if (nvec_max > 32 * MAXC) return cudaErrorInvalidValue;
+  if (nvec_max <= 4) return launch_b<4, 1>(st, dtab, count, rows);
+  if (nvec_max <= 8) return launch_b<8, 1>(st, dtab, count, rows);
+  if (nvec_max <= 16) return launch_b<16, 1>(st, dtab, count, rows);
+  if (nvec_max <= 32) return launch_b<32, 1>(st, dtab, count, rows);
+  if (nvec_max <= 64) return launch_b<32, 2>(st, dtab, count, rows);
+  if (nvec_max <= 96) return launch_b<32, 3>(st, dtab, count, rows);
+  return launch_b<32, 4>(st, dtab, count, rows);
 }
 
 template cudaError_t spmm_lap<float>(cudaStream_t, const CsrDev&, const float*, long long,

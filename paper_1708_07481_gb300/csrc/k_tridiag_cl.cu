@@ -65,10 +65,12 @@ __global__ void k_sym_f32(int m, const double* __restrict__ G, int ldg, float* _
   }
 }
 
-__global__ void __launch_bounds__(TC_NW * 32, 1)
-    k_tridiag_cl(int m_full, int K, const double* __restrict__ G, int ldg, float* __restrict__ Ag,
-                 int lda, float* __restrict__ d_out, float* __restrict__ e_out,
-                 float* __restrict__ b_out, const int* pflag, int mP) {
+__device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const double* __restrict__ G,
+                                                  int ldg, float* __restrict__ Ag, int lda,
+                                                  float* __restrict__ d_out,
+                                                  float* __restrict__ e_out,
+                                                  float* __restrict__ b_out, const int* pflag,
+                                                  int mP) {
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ float xs[TC_MMAX];      // x of the current step (every row)
   __shared__ float pvec[TC_MMAX];    // p of the current step (every row)
@@ -249,6 +251,33 @@ __global__ void __launch_bounds__(TC_NW * 32, 1)
   cluster_sync();  // no CTA leaves while another may still touch its shared memory
 }
 
+__global__ void __launch_bounds__(TC_NW * 32, 1)
+    k_tridiag_cl(int m_full, int K, const double* __restrict__ G, int ldg, float* __restrict__ Ag,
+                 int lda, float* __restrict__ d_out, float* __restrict__ e_out,
+                 float* __restrict__ b_out, const int* pflag, int mP) {
+  k_tridiag_cl_body(m_full, K, G, ldg, Ag, lda, d_out, e_out, b_out, pflag, mP);
+}
+
+// Lockstep batch: cluster c of the grid (TC_CL CTAs) tridiagonalizes descriptor c's matrix;
+// the reflector rows go to its Ag (stride m), d, e, beta to its tri.
+__global__ void __launch_bounds__(TC_NW * 32, 1) k_tridiag_cl_b(const RrDesc* __restrict__ tab) {
+  const RrDesc a = tab[blockIdx.x / TC_CL];
+  k_tridiag_cl_body(a.m, a.K, a.G, a.ldg, a.Ag, a.m, a.tri, a.tri + a.m, a.tri + 2 * a.m,
+                    a.pflag, a.mP);
+}
+
+// Lockstep batch: blockIdx.y = descriptor; its symmetrized FP32 matrix into Ag (stride m).
+__global__ void k_sym_f32_b(const RrDesc* __restrict__ tab) {
+  const RrDesc a = tab[blockIdx.y];
+  const int m = a.m;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)m * m;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / m), j = (int)(idx % m);
+    a.Ag[(long long)i * m + j] =
+        (float)(0.5 * (a.G[(long long)i * a.ldg + j] + a.G[(long long)j * a.ldg + i]));
+  }
+}
+
 }  // namespace
 
 // Tridiagonalization of the symmetric m x m FP64 matrix G (m <= 512, symmetrized on the fly) on
@@ -276,6 +305,34 @@ cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int 
   cudaError_t e0 = cudaGetLastError();
   if (e0 != cudaSuccess) return e0;
   e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl, m, K, G, ldg, Ag, lda, d, e, beta, pflag, mP);
+  note_launch();
+  return e0;
+}
+
+// The same for every descriptor of a lockstep batch (m <= mmax <= 512 each): one launch of
+// the symmetrization, one of count clusters.
+cudaError_t tridiag_cluster_batch(cudaStream_t st, int count, const RrDesc* dtab, int mmax) {
+  if (count <= 0) return cudaSuccess;
+  if (mmax < 1 || mmax > TC_MMAX) return cudaErrorInvalidValue;
+  ProfScope ps(st, "rr_eig");
+  const unsigned bx = (unsigned)std::min<long long>(((long long)mmax * mmax + 255) / 256, 256);
+  k_sym_f32_b<<<dim3(bx, (unsigned)count), 256, 0, st>>>(dtab);
+  note_launch();
+  cudaError_t e0 = cudaGetLastError();
+  if (e0 != cudaSuccess) return e0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(TC_CL * (unsigned)count, 1, 1);
+  cfg.blockDim = dim3(TC_NW * 32, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = TC_CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl_b, dtab);
   note_launch();
   return e0;
 }

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -25,7 +26,14 @@
 // ---------------------------------------------------------------------------------------
 namespace sc {
 static std::atomic<uint64_t> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local uint64_t t_launches = 0;  // this thread's launches (graph capture counts)
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void note_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+// launches noted while a pass was only being recorded into a graph are taken back
+static void unnote_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // Event-pair profiler (process-wide): the kernels named in the filter ("*" = all) get an
@@ -53,6 +61,10 @@ static bool prof_match(const char* name) {
   if (g_prof.filter == "*") return true;
   std::string f = "," + g_prof.filter + ",";
   return f.find("," + std::string(name) + ",") != std::string::npos;
+}
+bool prof_active() {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  return g_prof.on;
 }
 void prof_begin(cudaStream_t st, const char* name) {
   std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -234,6 +246,8 @@ size_t sc_ctx_bytes_peak(sc_ctx* c) {
   return p;
 }
 uint64_t sc_ctx_kernel_launches(const sc_ctx*) { return launches_total(); }
+static std::atomic<uint64_t> g_graph_replays{0};
+uint64_t sc_ctx_graph_replays(const sc_ctx*) { return g_graph_replays.load(); }
 
 int sc_debug_inject(sc_ctx* c, int kind, long long arg) {
   if (!c) return SC_EINVAL;
@@ -458,15 +472,35 @@ namespace {
 
 // Stream-bound allocator of one LOBPCG run: stream-ordered allocations on the run's stream,
 // counted against the context budget.
+// A run's allocator: stream-ordered allocations on the run's stream.  With `cache` set, a
+// freed block is kept for the next request of the same size instead of being returned to the
+// pool, so that after one pass of each shape the passes allocate nothing (the condition for
+// capturing them into a CUDA graph).  Every user of a cached block is ordered on the run's
+// stream, which makes the reuse safe.  While `capturing`, a request the cache cannot serve
+// fails (and sets `miss`) instead of allocating inside the capture.
 struct RunAlloc {
   sc_ctx* c;
   cudaStream_t st;
+  bool cache = false, capturing = false, miss = false;
+  std::multimap<size_t, void*> kept;
 };
 void* run_alloc(void* self, size_t bytes) {
   RunAlloc* r = (RunAlloc*)self;
   sc_ctx* c = r->c;
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~(size_t)255;
+  if (r->cache) {
+    auto it = r->kept.find(bytes);
+    if (it != r->kept.end()) {
+      void* p = it->second;
+      r->kept.erase(it);
+      return p;
+    }
+    if (r->capturing) {
+      r->miss = true;
+      return nullptr;
+    }
+  }
   if (c->budget && c->in_use + bytes > c->budget) return nullptr;
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, r->st) != cudaSuccess) {
@@ -482,11 +516,22 @@ void run_free(void* self, void* p) {
   RunAlloc* r = (RunAlloc*)self;
   if (!p) return;
   auto it = r->c->sizes.find(p);
+  if (r->cache && it != r->c->sizes.end()) {
+    r->kept.emplace(it->second, p);
+    return;
+  }
   if (it != r->c->sizes.end()) {
     r->c->in_use -= it->second;
     r->c->sizes.erase(it);
   }
   cudaFreeAsync(p, r->st);
+}
+
+// Returns the cached blocks to the pool (the run's stream orders the frees after their uses).
+void run_release(RunAlloc* r) {
+  r->cache = false;
+  for (auto& kv : r->kept) run_free(r, kv.second);
+  r->kept.clear();
 }
 
 struct Seg {
@@ -555,6 +600,12 @@ struct LobRun : RunBase {
   int it = 0, done_passes = 0, converged = 0;
   bool haveP = false, over = false;
   std::vector<double> hrho, hth;
+  // CUDA graphs of the pass (fixed-pass solves): one executable graph per buffer parity
+  bool graphs = false;
+  T* Sa = nullptr;  // the X/R/P block at the first pass: parity 0
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  uint64_t glaunch[2] = {0, 0};
+  int eager_p = 0;  // passes with P run eagerly
 
   LobRun(sc_ctx* c_, sc_graph* g_, int K_, const sc_lobpcg_opts* o_, cudaStream_t st_)
       : c(c_), g(g_), n(g_->csr.n), K(K_), o(*o_), st(st_) {
@@ -576,10 +627,16 @@ struct LobRun : RunBase {
     }
     hrho.assign(K, 0.0);
     hth.assign(K, 0.0);
+    const char* ge = std::getenv("SC_CUDA_GRAPHS");
+    graphs = !(ge && std::strcmp(ge, "0") == 0) && o.tol_abs <= 0 && o.tol_lock <= 0;
+    ra.cache = graphs;
   }
   ~LobRun() override {
     if (st2) cudaStreamSynchronize(st2);
+    for (cudaGraphExec_t& x : gexec)
+      if (x) cudaGraphExecDestroy(x);
     for (void* p : bufs) al.put(p);
+    run_release(&ra);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (evf) cudaEventDestroy(evf);
@@ -883,16 +940,118 @@ struct LobRun : RunBase {
     CK(residual<T>(st, al, n, K, S, LS, ld3, theta, S + kp, rho2, pdeg), "residual");
     it = 0;
     over = o.iters <= 0;
+    Sa = S;
     return SC_OK;
+  }
+
+  // Fixed-pass solves (no host decision between passes) replay the pass from a CUDA graph: the
+  // pass is the same launch sequence every time except that S / S2 and LS / LS2 swap roles, so
+  // one executable graph per buffer parity is recorded and relaunched.  Recording starts after
+  // one pass with P has run eagerly, by when the autotuner has measured every shape and the
+  // run's allocator holds a scratch block of every size, so a recorded pass allocates nothing.
+  // The passes that re-orthonormalize X, and passes while a profile or a test hook is armed,
+  // run eagerly; a recording that fails turns graphs off for the run (the pass then runs
+  // eagerly, with the same kernels).
+  int pass() override {
+    if (over) return SC_OK;
+    if (graph_eligible()) {
+      const int par = S == Sa ? 0 : 1;
+      if (!gexec[par] && eager_p >= 1) record(par);
+      if (gexec[par]) {
+        CK(cudaGraphLaunch(gexec[par], st), "graph");
+        note_launches(glaunch[par]);
+        g_graph_replays.fetch_add(1, std::memory_order_relaxed);
+        std::swap(S, S2);
+        std::swap(LS, LS2);
+        ++done_passes;
+        if (++it >= o.iters) over = true;
+        return SC_OK;
+      }
+    }
+    const bool withP = haveP;
+    const int rc = pass_body();
+    if (rc == SC_OK && withP) ++eager_p;
+    return rc;
+  }
+  bool graph_eligible() const {
+    return graphs && haveP && (done_passes + 1) % kReorth != 0 && c->inject_kind == 0 &&
+           !prof_active();
+  }
+  void record(int par) {
+    T *s0 = S, *s1 = S2, *l0s = LS, *l1s = LS2;
+    const bool hp = haveP, ov = over;
+    const int dp = done_passes, it0 = it;
+    const uint64_t k0 = t_launches;
+    cudaGraph_t gr = nullptr;
+    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      ra.capturing = true;
+      ra.miss = false;
+      const int rc = pass_body();
+      ra.capturing = false;
+      const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+      ok = rc == SC_OK && ec == cudaSuccess && gr != nullptr && !ra.miss;
+    }
+    const uint64_t k = t_launches - k0;
+    unnote_launches(k);
+    // the pass was recorded, not run: its host-side state changes are undone
+    S = s0;
+    S2 = s1;
+    LS = l0s;
+    LS2 = l1s;
+    haveP = hp;
+    over = ov;
+    done_passes = dp;
+    it = it0;
+    if (ok) {
+      cudaGraphExec_t ex = nullptr;
+      ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+      if (ok) {
+        gexec[par] = ex;
+        glaunch[par] = k;
+      }
+    }
+    if (gr) cudaGraphDestroy(gr);
+    if (!ok) {
+      graphs = false;
+      cudaGetLastError();
+      c->err.clear();
+    }
   }
 
   // One LOBPCG pass (Sec. II.B), issued on the run's stream.  The host reads the residual
   // norms between passes only when it has to decide something (a stopping tolerance or soft
   // locking); otherwise passes are issued back to back without synchronization.
-  int pass() override {
-    if (over) return SC_OK;
+  // The pass in stages around its small dense solves and its SpMM, so that a lockstep batch
+  // can issue each of those for all of its runs in one launch (sc_lobpcg_batch); a single run
+  // calls the stages and the solves in order (pass_body).  ps_* hold the pass's active set.
+  std::vector<int> ps_act;
+  int ps_ka = 0, ps_w = 0, ps_offP = 0;
+  bool ps_all = true;
+  T *ps_WR = nullptr, *ps_WP = nullptr;
+  long long ps_ldw = 0;
+
+  int pass_body() {
+    bool go = false;
+    int rc = pass_select(&go);
+    if (rc != SC_OK || !go) return rc;
+    if ((rc = stage_project()) != SC_OK) return rc;
+    CK(chol_a(), "chol");
+    if ((rc = stage_second_gram()) != SC_OK) return rc;
+    CK(chol_b(), "chol");
+    if ((rc = stage_images_pre()) != SC_OK) return rc;
+    if ((rc = stage_spmm()) != SC_OK) return rc;
+    if ((rc = stage_rr_gram()) != SC_OK) return rc;
+    CK(rr_pass(), "rr");
+    return stage_update();
+  }
+
+  // Active set: every column, unless a tolerance asks the host to look at the residuals.
+  int pass_select(bool* go) {
+    *go = false;
     const bool watch = o.tol_abs > 0 || o.tol_lock > 0;
-    std::vector<int> act;
+    std::vector<int>& act = ps_act;
+    act.clear();
     if (watch) {
       int hs = 0;
       CK(cudaMemcpyAsync(hrho.data(), rho2, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "rho");
@@ -923,32 +1082,40 @@ struct LobRun : RunBase {
       for (int j = 0; j < K; ++j) act[j] = j;
     }
     const int ka = (int)act.size();
-    const bool all = ka == K;
+    ps_ka = ka;
+    ps_all = ka == K;
     T* Rslot = S + kp;
-    T* LRslot = LS + kp;
     T* Pslot = S + 2 * kp;
-    T* LPslot = LS + 2 * kp;
     // Working copies of the active R and P columns: the S slots themselves when every column
     // is active; otherwise gathered into W1 = [R_a | P_a] (n x 2kp).
-    T* WR = Rslot;
-    T* WP = Pslot;
-    long long ldw = ld3;
-    const int offP = kp;
-    if (!all) {
+    ps_WR = Rslot;
+    ps_WP = Pslot;
+    ps_ldw = ld3;
+    ps_offP = kp;
+    if (!ps_all) {
       CK(cudaMemcpyAsync(dcols, act.data(), sizeof(int) * ka, cudaMemcpyHostToDevice, st), "cols");
       CK(gather_cols<T>(st, n, Rslot, ld3, W1, 2 * kp, dcols, ka), "gather");
-      WR = W1;
-      WP = W1 + kp;
-      ldw = 2 * kp;
-      if (haveP) CK(gather_cols<T>(st, n, Pslot, ld3, WP, ldw, dcols, ka), "gather");
+      ps_WR = W1;
+      ps_WP = W1 + kp;
+      ps_ldw = 2 * kp;
+      if (haveP) CK(gather_cols<T>(st, n, Pslot, ld3, ps_WP, ps_ldw, dcols, ka), "gather");
       // the gathered column list must stay valid until the copy ran
       CK(cudaStreamSynchronize(st), "cols");
     }
-    const int w = haveP ? 2 * ka : ka;
-    // (0) hard locking: the residual block leaves the span of the constraint block (P and X
-    //     stay in its complement as combinations of blocks that are)
+    ps_w = haveP ? 2 * ka : ka;
+    *go = true;
+    return SC_OK;
+  }
+
+  // (0) hard locking: the residual block leaves the span of the constraint block (P and X stay
+  //     in its complement as combinations of blocks that are)
+  // (1) project [R_a P_a] against X: F = X'[R_a P_a]; [R_a P_a] -= X F in one pass over X
+  // (2) first half of the Cholesky-QR of [R_a P_a]: its Gram, into G
+  int stage_project() {
+    const int ka = ps_ka, w = ps_w, offP = ps_offP;
+    T *WR = ps_WR, *WP = ps_WP;
+    const long long ldw = ps_ldw;
     if (kc > 0) CK(project_off(WR, ldw, ka), "constraint");
-    // (1) project [R_a P_a] against X: F = X'[R_a P_a]; [R_a P_a] -= X F in one pass over X
     if (haveP)
       CK(gram_seg(S, ld3, {{0, K}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, false), "gram");
     else
@@ -959,57 +1126,86 @@ struct LobRun : RunBase {
       TallSeg<T> sp{WP, ldw, WP, ldw, Tm + ka, w, 0, haveP ? ka : 0};
       CK(tall2(st, n, cat<T>(S, ld3, K), sr, sp, (T)1), "tall");
     }
-    // (2) Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too), into
-    //     the R and P slots.  A breakdown inside the P columns is handled on the device: the
-    //     kernel keeps the R transform, zeroes P's, and clears *dP, which the Rayleigh-Ritz
-    //     step reads to solve without P.  A residual column whose pivot falls below the
-    //     tolerance (it lies in the span of X and the R columns before it, to working
-    //     accuracy: converged columns' residuals sink to rounding noise) is dropped from this
-    //     pass's basis, and so are residual and direction columns whose norms are at rounding
-    //     level (res_floor, dir_floor); their zero columns are kept out of the Rayleigh-Ritz
-    //     solve.
-    {
-      const int wq = w;
-      int* pf = haveP ? dP : nullptr;
-      Cat3<T> Vw = haveP ? cat<T>(WR, ldw, ka, WP, ldw, ka) : cat<T>(WR, ldw, ka);
-      if (haveP)
-        CK(gram_seg(WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, wq, true), "gram");
-      else
-        CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, wq, true), "gram");
-      CK(chol(wq, G, TmA, dfail, ka, pf, ka, ddrop, res_floor, dir_floor), "chol");
-      CK(tall(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
-      CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
-      CK(chol(wq, G, TmB, dfail, ka, pf, ka, nullptr), "chol");
-      // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
-      CK(tall(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, Rslot, ld3, nullptr, 0, (T)0), "tall");
-      if (haveP)
-        CK(tall(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, Pslot, ld3, nullptr, 0, (T)0), "tall");
-    }
-    // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken
-    //     on the orthonormalized block so that its images are products with L rather than
-    //     images carried through the Cholesky factors (in FP32 those lose accuracy as fast as
-    //     the factors grow ill-conditioned near convergence).  With every column active the
-    //     R and P slots are adjacent (R slot padding is zero) and one SpMM covers both.
-    if (haveP && all) {
-      CK(spmm(Rslot, ld3, LRslot, ld3, kp + ka), "spmm");
+    // Cholesky-QR twice of [R_a P_a] (R first, so P is orthogonalized against R too), into the
+    // R and P slots.  A breakdown inside the P columns is handled on the device: the kernel
+    // keeps the R transform, zeroes P's, and clears *dP, which the Rayleigh-Ritz step reads to
+    // solve without P.  A residual column whose pivot falls below the tolerance (it lies in the
+    // span of X and the R columns before it, to working accuracy: converged columns' residuals
+    // sink to rounding noise) is dropped from this pass's basis, and so are residual and
+    // direction columns whose norms are at rounding level (res_floor, dir_floor); their zero
+    // columns are kept out of the Rayleigh-Ritz solve.
+    if (haveP)
+      CK(gram_seg(WR, ldw, {{0, ka}, {offP, ka}}, WR, ldw, {{0, ka}, {offP, ka}}, G, w, true), "gram");
+    else
+      CK(gram_seg(WR, ldw, {{0, ka}}, WR, ldw, {{0, ka}}, G, w, true), "gram");
+    return SC_OK;
+  }
+  cudaError_t chol_a() {
+    return chol(ps_w, G, TmA, dfail, ps_ka, haveP ? dP : nullptr, ps_ka, ddrop, res_floor,
+                dir_floor);
+  }
+  int stage_second_gram() {
+    const int wq = ps_w;
+    Cat3<T> Vw = haveP ? cat<T>(ps_WR, ps_ldw, ps_ka, ps_WP, ps_ldw, ps_ka)
+                       : cat<T>(ps_WR, ps_ldw, ps_ka);
+    CK(tall(st, n, Vw, TmA, wq, wq, Q1, 2 * kp, nullptr, 0, (T)0), "tall");
+    CK(gram_seg(Q1, 2 * kp, {{0, wq}}, Q1, 2 * kp, {{0, wq}}, G, wq, true), "gram");
+    return SC_OK;
+  }
+  cudaError_t chol_b() {
+    return chol(ps_w, G, TmB, dfail, ps_ka, haveP ? dP : nullptr, ps_ka, nullptr);
+  }
+  int stage_images_pre() {
+    const int wq = ps_w, ka = ps_ka;
+    // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
+    CK(tall(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, S + kp, ld3, nullptr, 0, (T)0), "tall");
+    if (haveP)
+      CK(tall(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, S + 2 * kp, ld3, nullptr, 0, (T)0),
+         "tall");
+    return SC_OK;
+  }
+  // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken on
+  //     the orthonormalized block so that its images are products with L rather than images
+  //     carried through the Cholesky factors (in FP32 those lose accuracy as fast as the
+  //     factors grow ill-conditioned near convergence).  With every column active the R and P
+  //     slots are adjacent (R slot padding is zero) and one SpMM covers both.
+  bool spmm_single() const { return haveP && ps_all; }
+  int stage_spmm() {
+    const int ka = ps_ka;
+    if (spmm_single()) {
+      CK(spmm(S + kp, ld3, LS + kp, ld3, kp + ka), "spmm");
     } else {
-      CK(spmm(Rslot, ld3, LRslot, ld3, ka), "spmm");
-      if (haveP) CK(spmm(Pslot, ld3, LPslot, ld3, ka), "spmm");
+      CK(spmm(S + kp, ld3, LS + kp, ld3, ka), "spmm");
+      if (haveP) CK(spmm(S + 2 * kp, ld3, LS + 2 * kp, ld3, ka), "spmm");
     }
+    return SC_OK;
+  }
+  int stage_rr_gram() {
+    const int ka = ps_ka;
     // test hook: this pass's direction block is reported as broken down, as the Cholesky-QR
     // does when P has sunk into span{X, R} (the Rayleigh-Ritz step then runs without P)
     if (haveP && c->inject_kind == SC_INJECT_P_BREAKDOWN && done_passes == c->inject_arg)
       CK(cudaMemsetAsync(dP, 0, sizeof(int), st), "inject");
-    // (4) Rayleigh-Ritz on S = [X R_a P_a]
-    const bool useP = haveP;
-    const int m = K + ka + (useP ? ka : 0);
-    // S'LS is symmetric in exact arithmetic: the upper tiles are computed and mirrored
-    if (useP)
+    // (4) Rayleigh-Ritz on S = [X R_a P_a]; S'LS is symmetric in exact arithmetic: the upper
+    //     tiles are computed and mirrored
+    const int m = rr_m();
+    if (haveP)
       CK(gram_seg(S, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, LS, ld3, {{0, K}, {kp, ka}, {2 * kp, ka}}, G, m, true), "gram");
     else
       CK(gram_seg(S, ld3, {{0, K}, {kp, ka}}, LS, ld3, {{0, K}, {kp, ka}}, G, m, true), "gram");
-    CK(rr(m, G, useP ? dP : nullptr, ka, dfb), "rr");
-    // (5) update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike); R = LX - X theta
+    return SC_OK;
+  }
+  int rr_m() const { return K + ps_ka + (haveP ? ps_ka : 0); }
+  cudaError_t rr_pass() { return rr(rr_m(), G, haveP ? dP : nullptr, ps_ka, dfb); }
+  // (5) update into S2 / LS2: P = [R_a P_a] Y_RP, X = X Y_X + P (L-images alike);
+  //     R = LX - X theta
+  int stage_update() {
+    const int ka = ps_ka;
+    const bool useP = haveP;
+    T* Rslot = S + kp;
+    T* LRslot = LS + kp;
+    T* Pslot = S + 2 * kp;
+    T* LPslot = LS + 2 * kp;
     const T* Yrp = Y + (size_t)K * K;
     Cat3<T> RP = useP ? cat<T>(Rslot, ld3, ka, Pslot, ld3, ka) : cat<T>(Rslot, ld3, ka);
     Cat3<T> LRP = useP ? cat<T>(LRslot, ld3, ka, LPslot, ld3, ka) : cat<T>(LRslot, ld3, ka);

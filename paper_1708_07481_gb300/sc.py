@@ -84,6 +84,7 @@ def lib():
         "sc_ctx_bytes_in_use": ([vp], C.c_size_t),
         "sc_ctx_bytes_peak": ([vp], C.c_size_t),
         "sc_ctx_kernel_launches": ([vp], u64),
+        "sc_ctx_graph_replays": ([vp], u64),
         "sc_debug_inject": ([vp, C.c_int, C.c_longlong], C.c_int),
         "sc_profile_begin": ([vp, C.c_char_p], C.c_int),
         "sc_profile_end": ([vp, C.c_char_p, C.c_size_t], C.c_int),
@@ -191,6 +192,10 @@ class Ctx:
     @property
     def launches(self):
         return lib().sc_ctx_kernel_launches(self.h)
+
+    @property
+    def graph_replays(self):
+        return lib().sc_ctx_graph_replays(self.h)
 
 
 class Graph:
