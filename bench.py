@@ -117,7 +117,7 @@ def whole_job_rate(units_per_step, steps, world, seconds):
 # DRAM bytes (read + write) per launch from one ncu --set full capture of each kernel at this
 # workload's sizes (Rayleigh-Ritz m = 132, K = 44; Cholesky-QR of 88 columns; n = 50,000); to
 # be cleared whenever the kernel changes after the capture.
-NCU_TRAFFIC = {"rr_eig": 278784, "spmm": 32049920, "tall_gemm": 14492160, "chol_inv": 121856,
+NCU_TRAFFIC = {"rr_eig": 279808, "spmm": 32049920, "tall_gemm": 14492160, "chol_inv": 123392,
                "gram": 23246592}
 
 

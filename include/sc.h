@@ -93,6 +93,14 @@ uint64_t sc_ctx_kernel_launches(const sc_ctx* ctx);
  * so results are bitwise those of eager passes.  The environment variable SC_CUDA_GRAPHS=0
  * (read when a solve starts) keeps every pass eager. */
 uint64_t sc_ctx_graph_replays(const sc_ctx* ctx);
+/* Number of lockstep batch passes issued so far in this process (sc_lobpcg_batch).  A batch
+ * whose runs are all SC_PREC_MIXED with the same fixed pass count (no tolerance, no constraint
+ * block) runs its first pass run by run and the rest in lockstep: per pass, the two
+ * Cholesky-QR transforms, the SpMM and the Rayleigh-Ritz solve of every run go out as one
+ * launch per kernel shape, from descriptor tables written once per batch; from the second
+ * lockstep pass on the whole batch pass is replayed from a CUDA graph.  Results are bitwise
+ * those of single solves.  SC_BATCH_LOCKSTEP=0 (read per call) issues runs in turn instead. */
+uint64_t sc_ctx_batch_lockstep_passes(const sc_ctx* ctx);
 /* Kernel timing: between sc_profile_begin and sc_profile_end, every launch of a kernel
  * named in `kernels` (comma-separated names such as "spmm,gram,rr_eig", or "*" for all) is
  * bracketed by CUDA events on the stream it is launched on.  sc_profile_end synchronizes the

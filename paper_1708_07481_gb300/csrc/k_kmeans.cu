@@ -14,6 +14,7 @@
 //   update: per-CTA FP64 sums accumulated in row order (one thread per column), the last
 //           CTA adds the CTA partials in fixed order and divides; empty clusters keep their
 //           centroid.  Deterministic for a given n.
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -77,15 +78,12 @@ __global__ void k_pp_first(int n, const double* u, int* seeds, int* chosen) {
   }
 }
 
-__global__ void __launch_bounds__(PB)
-    k_pp_update(int n, int d, const float* __restrict__ E, long long lde, const int* seeds, int t,
-                double* D2, double* bsum) {
-  extern __shared__ double cs[];  // d + 33
-  double* sh = cs + d;
-  const int s = seeds[t];
-  for (int c = threadIdx.x; c < d; c += blockDim.x) cs[c] = (double)E[(long long)s * lde + c];
-  __syncthreads();
-  long long i = (long long)blockIdx.x * PB + threadIdx.x;
+// Block b of the D2 update: D2_i <- min(D2_i, ||E_i - c||^2) for the PB rows of block b, c in
+// cs (FP64), and the block's sum into bsum[b].
+__device__ __forceinline__ void pp_update_block(int b, int n, int d, const float* __restrict__ E,
+                                                long long lde, int t, const double* cs,
+                                                double* sh, double* D2, double* bsum) {
+  long long i = (long long)b * PB + threadIdx.x;
   double v = 0.0;
   if (i < n) {
     const float* e = E + i * lde;
@@ -97,19 +95,32 @@ __global__ void __launch_bounds__(PB)
     v = (t == 0) ? acc : fmin(D2[i], acc);
     D2[i] = v;
   }
-  double b = block_sum_d(v, sh);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = b;
+  double bs = block_sum_d(v, sh);
+  if (threadIdx.x == 0) bsum[b] = bs;
 }
 
 __global__ void __launch_bounds__(PB)
-    k_pp_pick(int n, int nb, const double* __restrict__ D2, const double* __restrict__ bsum,
-              const double* u, int t, int* seeds, int* chosen) {
+    k_pp_update(int n, int d, const float* __restrict__ E, long long lde, const int* seeds, int t,
+                double* D2, double* bsum) {
+  extern __shared__ double cs[];  // d + 33
+  double* sh = cs + d;
+  const int s = seeds[t];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) cs[c] = (double)E[(long long)s * lde + c];
+  __syncthreads();
+  pp_update_block(blockIdx.x, n, d, E, lde, t, cs, sh, D2, bsum);
+}
+
+// The pick of round t by one CTA of PB threads.  D2 and the block sums are read through L2
+// (__ldcg): in the persistent seeding they were written by other CTAs of the same launch.
+__device__ __forceinline__ void pp_pick_body(int n, int nb, const double* __restrict__ D2,
+                                             const double* __restrict__ bsum, const double* u,
+                                             int t, int* seeds, int* chosen) {
   __shared__ double sh[40];
   __shared__ int sel;
   __shared__ double base_sh;
   // total over block sums in fixed order (thread-strided partial sums, then the tree)
   double p = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) p += bsum[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) p += __ldcg(bsum + b);
   double total = block_sum_d(p, sh);
   if (threadIdx.x == 0) sel = -1;
   __syncthreads();
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(PB)
     int bstar = -1;
     for (int b0 = 0; b0 < nb && bstar < 0; b0 += PB) {
       int b = b0 + threadIdx.x;
-      double v = b < nb ? bsum[b] : 0.0;
+      double v = b < nb ? __ldcg(bsum + b) : 0.0;
       double inc = block_incl_scan_d(v, sh) + carry;
       double exc = inc - v;
       if (b < nb && exc <= target && target < inc) {
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(PB)
       __syncthreads();
       double base = base_sh;
       long long i = (long long)bstar * PB + threadIdx.x;
-      double v = i < n ? D2[i] : 0.0;
+      double v = i < n ? __ldcg(D2 + i) : 0.0;
       double inc = block_incl_scan_d(v, sh) + base;
       if (i < n && inc > target && inc - v <= target) sel = (int)i;
       __syncthreads();
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(PB)
       int pick = bstar;
       if (pick < 0) {  // rounding put the target past the end: last row with D2 > 0
         for (long long i = n - 1; i >= 0; --i)
-          if (D2[i] > 0.0) {
+          if (__ldcg(D2 + i) > 0.0) {
             pick = (int)i;
             break;
           }
@@ -171,6 +182,76 @@ __global__ void __launch_bounds__(PB)
       seeds[t] = pick;
       chosen[pick] = 1;
     }
+  }
+}
+
+__global__ void __launch_bounds__(PB)
+    k_pp_pick(int n, int nb, const double* __restrict__ D2, const double* __restrict__ bsum,
+              const double* u, int t, int* seeds, int* chosen) {
+  pp_pick_body(n, nb, D2, bsum, u, t, seeds, chosen);
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): an arrival counter bar[0]
+// and a generation word bar[1] in global memory.  The wait is bounded (about two seconds of SM
+// clocks); a CTA that gives up sets *flag, and every CTA that sees the flag returns false.
+constexpr long long GB_WAIT_CLOCKS = 4LL << 30;
+__device__ bool grid_barrier(unsigned* bar, int* flag) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = atomicAdd(bar + 1, 0u);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (atomicAdd(bar + 1, 0u) == gen) {
+        if (clock64() - t0 > GB_WAIT_CLOCKS) {
+          ok = 0;
+          atomicOr(flag, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (atomicAdd(flag, 0) != 0) ok = 0;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// k-means++ seeding in one cooperative launch: the first seed, then rounds t = 0 .. k - 2 of
+// (D2 update with seed t by every CTA over blocks b = blockIdx.x, blockIdx.x + gridDim.x, ...;
+// pick of seed t + 1 by CTA 0), with a grid barrier after each phase.  The blocks, their sums
+// and the pick are those of k_pp_update / k_pp_pick, so the seeds are the same.
+__global__ void __launch_bounds__(PB)
+    k_pp_all(int n, int d, int k, const float* __restrict__ E, long long lde, const double* u,
+             int* seeds, int* chosen, double* D2, double* bsum, unsigned* bar, int* flag) {
+  extern __shared__ double cs[];  // d + 40
+  double* sh = cs + d;
+  const int nb = (n + PB - 1) / PB;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long i = (long long)floor(u[0] * (double)n);
+    if (i > n - 1) i = n - 1;
+    if (i < 0) i = 0;
+    seeds[0] = (int)i;
+    chosen[i] = 1;
+  }
+  if (!grid_barrier(bar, flag)) return;
+  for (int t = 0; t + 1 < k; ++t) {
+    const int sd = __ldcg(seeds + t);
+    for (int c = threadIdx.x; c < d; c += PB) cs[c] = (double)E[(long long)sd * lde + c];
+    __syncthreads();
+    for (int b = blockIdx.x; b < nb; b += gridDim.x)
+      pp_update_block(b, n, d, E, lde, t, cs, sh, D2, bsum);
+    if (!grid_barrier(bar, flag)) return;
+    if (blockIdx.x == 0) pp_pick_body(n, nb, D2, bsum, u, t + 1, seeds, chosen);
+    if (!grid_barrier(bar, flag)) return;
   }
 }
 
@@ -451,16 +532,39 @@ cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const floa
   double* D2 = al.get<double>(n);
   double* bsum = al.get<double>(nb);
   int* chosen = al.get<int>(n);
+  int* bar = al.get<int>(4);  // grid barrier: arrivals, generation, time-out flag
   cudaError_t e = cudaSuccess;
-  if (!u || !D2 || !bsum || !chosen) {
+  if (!u || !D2 || !bsum || !chosen || !bar) {
     e = cudaErrorMemoryAllocation;
   } else {
     cudaMemcpyAsync(u, u_host, sizeof(double) * k, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(chosen, 0, sizeof(int) * n, st);
-    k_pp_first<<<1, 32, 0, st>>>(n, u, seeds, chosen);
-    note_launch();
     size_t sm = sizeof(double) * (d + 40);
-    for (int t = 0; t < k; ++t) {
+    // one cooperative launch for every round when the device runs one (all CTAs resident)
+    bool persistent = false;
+    if (bar) {
+      cudaMemsetAsync(bar, 0, sizeof(int) * 4, st);
+      int dev = 0, nsm = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pp_all, PB, sm) == cudaSuccess &&
+          per > 0 && nsm > 0) {
+        int grid = std::min(nb, per * nsm);
+        unsigned* barp = (unsigned*)bar;
+        int* flag = bar + 2;
+        void* args[] = {&n, &d, &k, (void*)&E, &lde, &u, &seeds, &chosen, &D2, &bsum, &barp, &flag};
+        ProfScope ps(st, "kmeanspp_update");
+        persistent = cudaLaunchCooperativeKernel((const void*)k_pp_all, dim3(grid), dim3(PB), args,
+                                                 sm, st) == cudaSuccess;
+        note_launch();
+        if (!persistent) cudaGetLastError();
+      }
+    }
+    if (!persistent) {
+      k_pp_first<<<1, 32, 0, st>>>(n, u, seeds, chosen);
+      note_launch();
+    }
+    for (int t = 0; t < k && !persistent; ++t) {
       if (t > 0) {
         k_pp_pick<<<1, PB, 0, st>>>(n, nb, D2, bsum, u, t, seeds, chosen);
         note_launch();
@@ -474,7 +578,13 @@ cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const floa
     e = cudaGetLastError();
     // u_host may be a stack array of the caller: make sure the copy finished
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && persistent) {
+      int hf = 0;
+      e = cudaMemcpy(&hf, bar + 2, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && hf) e = cudaErrorTimeout;  // a grid barrier gave up
+    }
   }
+  al.put(bar);
   al.put(u);
   al.put(D2);
   al.put(bsum);

@@ -1446,8 +1446,268 @@ int sc_lobpcg64(sc_ctx* c, sc_graph* g, int K, const sc_lobpcg_opts* o, const do
   return rc;
 }
 
-// Batched solves: the runs are issued pass by pass in turn, each on its own stream, so their
-// kernels -- in particular the one-CTA small dense solves -- overlap on the device.
+namespace {
+
+// Lockstep batch: FP32 mixed-precision runs with the same fixed pass count advance together,
+// and each pass's two Cholesky-QR transforms, its SpMM and its Rayleigh-Ritz solve go out for
+// all runs at once -- one launch per kernel shape (descriptor tables written once, grouped by
+// shape) on the batch stream, which joins the runs' streams before and after.  The Gram,
+// update and residual kernels stay per run, on the runs' streams, where they overlap.  From
+// the second lockstep pass on, the whole batch pass is recorded into one CUDA graph per buffer
+// parity and relaunched.  Each run's results are bitwise its single-run results.
+struct Lockstep {
+  sc_ctx* c;
+  std::vector<LobRun<float>*> r;
+  cudaStream_t bs = nullptr;
+  cudaEvent_t evb = nullptr;
+  std::vector<cudaEvent_t> evr;
+  void* dmem = nullptr;
+  CholDesc* dchol[2] = {nullptr, nullptr};
+  RrDesc* drr = nullptr;
+  SpmmDesc* dspmm[2] = {nullptr, nullptr};
+  std::vector<BatchGroup> gchol[2], grr;
+  std::vector<LobRun<float>*> rr_one;  // solved one by one (no batched kernel shape)
+  long long rows = 0;
+  int nvec_max = 0, lock_passes = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  uint64_t glaunch[2] = {0, 0};
+  bool graphs = true;
+
+  ~Lockstep() {
+    for (cudaGraphExec_t& x : gexec)
+      if (x) cudaGraphExecDestroy(x);
+    if (bs) cudaStreamSynchronize(bs);
+    if (dmem) ctx_free(c, dmem);
+    for (cudaEvent_t e : evr) cudaEventDestroy(e);
+    if (evb) cudaEventDestroy(evb);
+    if (bs) cudaStreamDestroy(bs);
+  }
+  static bool eligible(const std::vector<RunBase*>& runs) {
+    const char* v = std::getenv("SC_BATCH_LOCKSTEP");
+    if (v && std::strcmp(v, "0") == 0) return false;
+    if (runs.empty()) return false;
+    int iters = -1;
+    for (RunBase* b : runs) {
+      auto* q = dynamic_cast<LobRun<float>*>(b);
+      if (!q || q->dense64 || !q->use_tc || q->o.tol_abs > 0 || q->o.tol_lock > 0 || q->kc > 0)
+        return false;
+      if (iters >= 0 && q->o.iters != iters) return false;
+      iters = q->o.iters;
+      if ((q->kp + q->K + 3) / 4 > 128) return false;  // the SpMM's widest kernel shape
+    }
+    return true;
+  }
+  // batch stream after every run's work so far / every run after the batch stream
+  void to_batch() {
+    for (size_t q = 0; q < r.size(); ++q) {
+      cudaEventRecord(evr[q], r[q]->st);
+      cudaStreamWaitEvent(bs, evr[q], 0);
+    }
+  }
+  void from_batch() {
+    cudaEventRecord(evb, bs);
+    for (auto* q : r) cudaStreamWaitEvent(q->st, evb, 0);
+  }
+  // Descriptor tables, after the first pass (every run has P from then on).
+  int build() {
+    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(c, SC_ECUDA, "stream creation failed");
+    cudaEventCreateWithFlags(&evb, cudaEventDisableTiming);
+    evr.resize(r.size());
+    for (auto& e : evr) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    const char* ge = std::getenv("SC_CUDA_GRAPHS");
+    graphs = !(ge && std::strcmp(ge, "0") == 0);
+    std::vector<CholDesc> ca, cb;
+    std::vector<RrDesc> rd;
+    std::vector<SpmmDesc> sp[2];
+    for (auto* q : r) {
+      const int K = q->K, w = 2 * K, m = 3 * K;
+      float* Wg = nullptr;
+      if (size_t f = chol_batch_scratch(w)) {
+        Wg = q->template get<float>(f);
+        if (!Wg) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: scratch");
+      }
+      CholDesc a{w, w, K, K, q->G, q->TmA, Wg, q->dstatus, q->dfail, q->dP, q->ddrop,
+                 q->pivot_tol, q->res_floor, q->dir_floor};
+      CholDesc b{w, w, K, K, q->G, q->TmB, Wg, q->dstatus, q->dfail, q->dP, nullptr,
+                 q->pivot_tol, 0.0, 0.0};
+      ca.push_back(a);
+      cb.push_back(b);
+      float* Ag = nullptr;
+      float* tri = nullptr;
+      if (size_t f = rr_batch_scratch(m, K)) {
+        Ag = q->template get<float>(f);
+        if (!Ag) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: scratch");
+      }
+      if (rr_batch_cluster(m)) {
+        tri = q->template get<float>((size_t)3 * m);
+        if (!tri) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: scratch");
+      }
+      rd.push_back(RrDesc{m, K, m, K, q->G, q->theta, q->Y, q->dstatus, q->dP, q->dfb, Ag, tri});
+      const int nv = (q->kp + K + 3) / 4;
+      nvec_max = std::max(nvec_max, nv);
+      // parity 0 = the pass starts with S at its setup buffer (Sa); the first pass has swapped
+      const int cur = q->S == q->Sa ? 0 : 1;
+      for (int par = 0; par < 2; ++par) {
+        float* Sx = par == cur ? q->S : q->S2;
+        float* LSx = par == cur ? q->LS : q->LS2;
+        const CsrDev& g = q->g->csr;
+        sp[par].push_back(SpmmDesc{rows, g.n, nv, g.row_ptr, g.col_idx, g.val, g.degf,
+                                   Sx + q->kp, LSx + q->kp, q->ld3, q->ld3});
+      }
+      rows += q->n;
+    }
+    std::vector<int> one;
+    chol_batch_plan(ca, gchol[0], one);
+    chol_batch_plan(cb, gchol[1], one);
+    rr_batch_plan(rd, grr, one);
+    for (int i : one)
+      for (auto* q : r)
+        if (q->theta == rd[i].theta) rr_one.push_back(q);
+    const size_t nb = r.size();
+    const size_t bytes = 2 * nb * sizeof(CholDesc) + nb * sizeof(RrDesc) + 2 * nb * sizeof(SpmmDesc) + 64;
+    dmem = ctx_alloc(c, bytes);
+    if (!dmem) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: descriptor tables");
+    char* p = (char*)dmem;
+    dchol[0] = (CholDesc*)p;
+    dchol[1] = dchol[0] + nb;
+    drr = (RrDesc*)(dchol[1] + nb);
+    dspmm[0] = (SpmmDesc*)(drr + nb);
+    dspmm[1] = dspmm[0] + nb;
+    // the runs' setup and first pass were issued on their streams (and the table memory on the
+    // context's): the tables go in after them
+    for (auto* q : r) CK(cudaStreamSynchronize(q->st), "batch");
+    CK(cudaStreamSynchronize(c->stream), "batch");
+    CK(cudaMemcpy(dchol[0], ca.data(), nb * sizeof(CholDesc), cudaMemcpyHostToDevice), "batch");
+    CK(cudaMemcpy(dchol[1], cb.data(), nb * sizeof(CholDesc), cudaMemcpyHostToDevice), "batch");
+    CK(cudaMemcpy(drr, rd.data(), nb * sizeof(RrDesc), cudaMemcpyHostToDevice), "batch");
+    CK(cudaMemcpy(dspmm[0], sp[0].data(), nb * sizeof(SpmmDesc), cudaMemcpyHostToDevice), "batch");
+    CK(cudaMemcpy(dspmm[1], sp[1].data(), nb * sizeof(SpmmDesc), cudaMemcpyHostToDevice), "batch");
+    return SC_OK;
+  }
+  // One lockstep pass, issued (or recorded) on the runs' streams and the batch stream.
+  int issue(int par) {
+    int rc = SC_OK;
+    for (auto* q : r) {
+      bool go = false;
+      if ((rc = q->pass_select(&go)) != SC_OK) return rc;
+      if (!go) return fail(c, SC_EINVAL, "sc_lobpcg_batch: lockstep pass without work");
+      if ((rc = q->stage_project()) != SC_OK) return rc;
+    }
+    to_batch();
+    CK(chol_batch_launch(bs, dchol[0], gchol[0]), "chol");
+    from_batch();
+    for (auto* q : r)
+      if ((rc = q->stage_second_gram()) != SC_OK) return rc;
+    to_batch();
+    CK(chol_batch_launch(bs, dchol[1], gchol[1]), "chol");
+    from_batch();
+    for (auto* q : r)
+      if ((rc = q->stage_images_pre()) != SC_OK) return rc;
+    to_batch();
+    CK(spmm_batch_launch(bs, dspmm[par], (int)r.size(), rows, nvec_max), "spmm");
+    from_batch();
+    for (auto* q : r)
+      if ((rc = q->stage_rr_gram()) != SC_OK) return rc;
+    for (auto* q : rr_one) CK(q->rr_pass(), "rr");
+    to_batch();
+    CK(rr_batch_launch(bs, drr, grr), "rr");
+    from_batch();
+    for (auto* q : r)
+      if ((rc = q->stage_update()) != SC_OK) return rc;
+    return SC_OK;
+  }
+  void record(int par) {
+    struct Saved {
+      float *S, *S2, *LS, *LS2;
+      bool haveP, over;
+      int done, it;
+    };
+    std::vector<Saved> sv;
+    for (auto* q : r) sv.push_back(Saved{q->S, q->S2, q->LS, q->LS2, q->haveP, q->over,
+                                         q->done_passes, q->it});
+    const uint64_t k0 = t_launches;
+    cudaGraph_t gr = nullptr;
+    bool ok = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      from_batch();  // the runs' streams join the recording
+      for (auto* q : r) {
+        q->ra.capturing = true;
+        q->ra.miss = false;
+      }
+      const int rc = issue(par);
+      to_batch();  // and leave it
+      bool miss = false;
+      for (auto* q : r) {
+        q->ra.capturing = false;
+        miss = miss || q->ra.miss;
+      }
+      const cudaError_t ec = cudaStreamEndCapture(bs, &gr);
+      ok = rc == SC_OK && ec == cudaSuccess && gr != nullptr && !miss;
+    }
+    const uint64_t k = t_launches - k0;
+    unnote_launches(k);
+    for (size_t i = 0; i < r.size(); ++i) {
+      auto* q = r[i];
+      q->S = sv[i].S;
+      q->S2 = sv[i].S2;
+      q->LS = sv[i].LS;
+      q->LS2 = sv[i].LS2;
+      q->haveP = sv[i].haveP;
+      q->over = sv[i].over;
+      q->done_passes = sv[i].done;
+      q->it = sv[i].it;
+    }
+    if (ok) {
+      cudaGraphExec_t ex = nullptr;
+      ok = cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+      if (ok) {
+        gexec[par] = ex;
+        glaunch[par] = k;
+      }
+    }
+    if (gr) cudaGraphDestroy(gr);
+    if (!ok) {
+      graphs = false;
+      cudaGetLastError();
+      c->err.clear();
+    }
+  }
+  int pass() {
+    auto* q0 = r[0];
+    const int par = q0->S == q0->Sa ? 0 : 1;
+    const bool replayable = graphs && lock_passes >= 1 && (q0->done_passes + 1) % q0->kReorth != 0 &&
+                            c->inject_kind == 0 && !prof_active();
+    if (replayable && !gexec[par]) record(par);
+    if (replayable && gexec[par]) {
+      to_batch();
+      CK(cudaGraphLaunch(gexec[par], bs), "graph");
+      from_batch();
+      note_launches(glaunch[par]);
+      g_graph_replays.fetch_add(1, std::memory_order_relaxed);
+      for (auto* q : r) {
+        std::swap(q->S, q->S2);
+        std::swap(q->LS, q->LS2);
+        ++q->done_passes;
+        if (++q->it >= q->o.iters) q->over = true;
+      }
+      ++lock_passes;
+      return SC_OK;
+    }
+    const int rc = issue(par);
+    if (rc == SC_OK) ++lock_passes;
+    return rc;
+  }
+};
+
+}  // namespace
+
+static std::atomic<uint64_t> g_lockstep_passes{0};
+uint64_t sc_ctx_batch_lockstep_passes(const sc_ctx*) { return g_lockstep_passes.load(); }
+
+// Batched solves: each run on its own stream.  FP32 mixed-precision runs with one fixed pass
+// count go in lockstep (Lockstep above); otherwise the runs are issued pass by pass in turn,
+// and their kernels -- in particular the one-CTA small dense solves -- overlap on the device.
 int sc_lobpcg_batch(sc_ctx* c, int count, sc_graph* const* graphs, const int* K,
                     const sc_lobpcg_opts* opts, sc_eig_info* infos) {
   if (!c) return SC_EINVAL;
@@ -1469,6 +1729,21 @@ int sc_lobpcg_batch(sc_ctx* c, int count, sc_graph* const* graphs, const int* K,
     }
     runs[q] = make_run(c, graphs[q], K[q], &opts[q], streams[q]);
     rc = runs[q]->setup(nullptr, 0);
+  }
+  // the first pass (no direction block yet) run by run; then lockstep when the runs allow it
+  for (int q = 0; q < count && rc == SC_OK; ++q)
+    if (!runs[q]->finished()) rc = runs[q]->pass();
+  bool lock = rc == SC_OK && Lockstep::eligible(runs) && !runs[0]->finished();
+  Lockstep ls;
+  ls.c = c;
+  if (lock) {
+    for (RunBase* b : runs) ls.r.push_back(dynamic_cast<LobRun<float>*>(b));
+    rc = ls.build();
+    while (rc == SC_OK && !runs[0]->finished()) {
+      rc = ls.pass();
+      g_lockstep_passes.fetch_add(1, std::memory_order_relaxed);
+    }
+    if (ls.bs) cudaStreamSynchronize(ls.bs);
   }
   bool any = true;
   while (rc == SC_OK && any) {

@@ -85,6 +85,7 @@ def lib():
         "sc_ctx_bytes_peak": ([vp], C.c_size_t),
         "sc_ctx_kernel_launches": ([vp], u64),
         "sc_ctx_graph_replays": ([vp], u64),
+        "sc_ctx_batch_lockstep_passes": ([vp], u64),
         "sc_debug_inject": ([vp, C.c_int, C.c_longlong], C.c_int),
         "sc_profile_begin": ([vp, C.c_char_p], C.c_int),
         "sc_profile_end": ([vp, C.c_char_p, C.c_size_t], C.c_int),
@@ -196,6 +197,10 @@ class Ctx:
     @property
     def graph_replays(self):
         return lib().sc_ctx_graph_replays(self.h)
+
+    @property
+    def lockstep_passes(self):
+        return lib().sc_ctx_batch_lockstep_passes(self.h)
 
 
 class Graph:

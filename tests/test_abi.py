@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol(built):
 def test_binding_names_match_header():
     for s in sc.declared_symbols():
         if s in ("sc_ctx_destroy", "sc_last_error", "sc_ctx_bytes_in_use", "sc_ctx_bytes_peak",
-                 "sc_ctx_kernel_launches", "sc_ctx_graph_replays",
+                 "sc_ctx_kernel_launches", "sc_ctx_graph_replays", "sc_ctx_batch_lockstep_passes",
                  "sc_graph_destroy", "sc_server_submit", "sc_server_poll", "sc_server_wait",
                  "sc_server_stats", "sc_server_destroy"):
             continue  # methods of Ctx / Graph / Server

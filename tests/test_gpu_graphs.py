@@ -70,7 +70,10 @@ def test_graph_replay_in_a_batch_is_bitwise_the_eager_batch(sc, ctx, monkeypatch
         Ks.append(K)
     out = []
     sc.sc_lobpcg_batch(ctx, graphs, Ks, iters=12, prec=sc.SC_PREC_MIXED, seeds=[1, 2, 3])
-    for flag in (False, True):
+    # runs issued in turn, eager / each run replaying its own pass graphs; then the lockstep
+    # batch, which replays one graph of the whole batch pass
+    for lockstep, flag in ((False, False), (False, True), (True, True)):
+        monkeypatch.setenv("SC_BATCH_LOCKSTEP", "1" if lockstep else "0")
         if flag:
             monkeypatch.delenv("SC_CUDA_GRAPHS", raising=False)
         else:
@@ -79,10 +82,10 @@ def test_graph_replay_in_a_batch_is_bitwise_the_eager_batch(sc, ctx, monkeypatch
         infos = sc.sc_lobpcg_batch(ctx, graphs, Ks, iters=12, prec=sc.SC_PREC_MIXED,
                                    seeds=[1, 2, 3])
         out.append((infos, ctx.graph_replays - r0))
-    assert out[0][1] == 0 and out[1][1] == 3 * 10
-    for ia, ib in zip(out[0][0], out[1][0]):
-        assert np.array_equal(ia["lam"], ib["lam"])
-        assert np.array_equal(ia["resid"], ib["resid"])
-        assert ia["kernels"] == ib["kernels"]
+    assert [o[1] for o in out] == [0, 3 * 10, 10]
+    for other in out[1:]:
+        for ia, ib in zip(out[0][0], other[0]):
+            assert np.array_equal(ia["lam"], ib["lam"])
+            assert np.array_equal(ia["resid"], ib["resid"])
     for G in graphs:
         G.close()
