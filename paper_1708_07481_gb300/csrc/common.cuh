@@ -137,6 +137,8 @@ int spmm_shapes(int nvec, int* out);
 // variant issued by run(v) on stream st), cached for the process and persisted to
 // SC_AUTOTUNE_FILE; SC_TUNE_<KERNEL> forces a variant, SC_AUTOTUNE=0 returns `fallback` for
 // keys not yet chosen.
+// SC_TUNE_<KERNEL>=<variant> (kernel name upper-cased), or -1 when unset.
+int tune_override(const char* kernel);
 int tune_pick(const std::string& key, const char* kernel, cudaStream_t st, int nvar,
               int fallback, const std::function<cudaError_t(int)>& run);
 int tune_lookup(const std::string& key);
@@ -253,6 +255,14 @@ cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const floa
 cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* E,
                   long long lde, const int* seeds_dev, int iters, int* labels_dev,
                   double* cent_dev, int* iters_run, double* inertia);
+
+// k-means assignment on tensor cores (3-term split TF32 distances ||c||^2 - 2 e.c, near ties
+// re-decided with FP64 distances): labels of the n x d rows E against the k x d centroids,
+// k <= 256; *changes += rows whose label changed (all rows when first).  Returns
+// cudaErrorNotSupported when the shape does not fit (the caller uses the CUDA-core kernel).
+cudaError_t assign_tc(cudaStream_t st, long long n, int d, int k, const float* E, long long lde,
+                      const float* C32, const float* cn, const double* C64, int* labels,
+                      int* changes, int first, float tie, const int* ctl, int* d_status);
 
 // ---- lockstep batches (sc_lobpcg_batch): one launch per kernel shape for all runs ---------
 // A descriptor holds one run's arguments of the single-run call; a batched launch runs one CTA

@@ -606,9 +606,14 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
   double* part = al.get<double>((size_t)nct * k * d);
   int* pcnt = al.get<int>((size_t)nct * k);
   double* ipart = al.get<double>(152);
+  int* tstat = al.get<int>(1);  // time-outs of the tensor-core assignment's bounded waits
+  // The assignment runs on tensor cores (assign_tc) for large n k d, or when SC_TUNE_ASSIGN=1;
+  // SC_TUNE_ASSIGN=0 keeps the CUDA-core kernel.  Both give the labels of FP64 arithmetic.
+  const int forced = tune_override("assign");
+  bool use_tc = forced >= 0 ? forced == 1 : (long long)n * k * d >= (1LL << 28);
   cudaError_t e = cudaSuccess;
   int done = 0;
-  if (!C32 || !cn || !changes || !part || !pcnt || !ipart) {
+  if (!C32 || !cn || !changes || !part || !pcnt || !ipart || !tstat) {
     e = cudaErrorMemoryAllocation;
     goto out;
   }
@@ -641,13 +646,31 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
     cudaMemsetAsync(changes, 0, sizeof(int) * ((size_t)iters + 2), st);
     // Rounds are issued without waiting: a round that changes no label sets the stop flag on
     // the device and every later kernel returns at once; the host looks every 4 rounds.
+    cudaMemsetAsync(tstat, 0, sizeof(int), st);
     for (int it = 0; it < iters; ++it) {
-      {
+      // FP32 distances of unit rows to centroids of norm <= 1 carry at most ~2.5e-7 d of
+      // rounding each; margins below twice that (plus slack) are re-decided in FP64.  The
+      // tensor cores' 3-term split TF32 products and their FP32 accumulation are held to four
+      // times that margin.
+      const double tie = 2e-5 + 5e-7 * d;
+      bool on_tc = false;
+      if (use_tc) {
+        const cudaError_t et = assign_tc(st, n, d, k, E, lde, C32, cn, C64, labels,
+                                         changes + it, it == 0, (float)(4.0 * tie), ctl, tstat);
+        if (et == cudaSuccess) {
+          on_tc = true;
+        } else if (et == cudaErrorNotSupported) {
+          use_tc = false;
+          cudaGetLastError();
+        } else {
+          e = et;
+          goto out;
+        }
+      }
+      if (!on_tc) {
         ProfScope ps(st, "kmeans_assign");
-        // FP32 distances of unit rows to centroids of norm <= 1 carry at most ~2.5e-7 d of
-        // rounding each; margins below twice that (plus slack) are re-decided in FP64
         afn<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes + it,
-                                         it == 0, 2e-5 + 5e-7 * d, ctl);
+                                         it == 0, tie, ctl);
         note_launch();
       }
       // a launch that did not start leaves the labels unwritten: stop here
@@ -677,6 +700,9 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
     for (int q = 0; q < 152; ++q) s += hp[q];
     if (inertia) *inertia = s;
     if (iters_run) *iters_run = done;
+    int ht = 0;
+    if ((e = cudaMemcpy(&ht, tstat, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) goto out;
+    if (ht) e = cudaErrorTimeout;  // a bounded wait of the tensor-core assignment gave up
   }
 out:
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -686,6 +712,7 @@ out:
   al.put(part);
   al.put(pcnt);
   al.put(ipart);
+  al.put(tstat);
   return e;
 }
 

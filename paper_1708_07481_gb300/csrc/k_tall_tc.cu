@@ -35,7 +35,9 @@ constexpr int TT_MAXSTG = 4;  // staged chunks in flight, at most
 constexpr int TT_NTH = 256;   // eight warps: warps w, w + 4 share lane quarter w % 4
 constexpr int TT_ATILE = TT_M * TT_K * 4;             // 16 KB: one FP32 (then big) A chunk
 constexpr int TT_SMEM = 225 * 1024;                   // dynamic shared memory of a CTA
-constexpr int TT_SMEM_USE = TT_SMEM - 1024 - 256;     // stages (after alignment and barriers)
+constexpr int TT_AM_BYTES = TT_M * 12;                // assignment mode: the upper warps' part
+constexpr int TT_SMEM_USE = TT_SMEM - 1024 - 256 - TT_AM_BYTES;  // stages (after alignment,
+                                                                  // barriers, assignment part)
 
 struct TcTall {
   int nseg;
@@ -60,6 +62,19 @@ struct TcTall {
   int vec[2];
   int b0, b;
   float beta;
+  // W given transposed (W[lr][col] = w[col * ldw + lr]), as the centroid matrix in k-means
+  int wt;
+  // k-means assignment mode (amode): the accumulator holds e_i . c_j for the k = b centroids;
+  // the epilogue turns it into labels instead of writing it (see k_tall_tc)
+  int amode, first, d;
+  float tie;
+  const float* cn;      // ||c_j||^2 (FP32)
+  const double* C64;    // FP64 centroids, k x d
+  const float* E;       // the rows, n x d (stride lde)
+  long long lde;
+  int* labels;
+  int* changes;
+  const int* ctl;       // ctl[0] != 0: converged in an earlier round (nothing to do)
 };
 
 __device__ __forceinline__ float tt_w(const TcTall& p, int lr, int col) {
@@ -69,12 +84,14 @@ __device__ __forceinline__ float tt_w(const TcTall& p, int lr, int col) {
   if (lr < skip) return 0.f;
   const float* w = s1 ? p.w[1] : p.w[0];
   const int ldw = s1 ? p.ldw[1] : p.ldw[0];
-  return w[(long long)(lr - skip) * ldw + (s1 ? col - p.b0 : col)];
+  const int c = s1 ? col - p.b0 : col;
+  return p.wt ? w[(long long)c * ldw + (lr - skip)] : w[(long long)(lr - skip) * ldw + c];
 }
 
 // The W^T image: for chunk ch (segment q, local chunk cc), operand row r (output column) and
 // k < 32, logical row lr = wrow[q] + 32 cc + k of W; entries past the segment's width are 0.
 __global__ void k_tall_wsplit(const __grid_constant__ TcTall p, uint8_t* __restrict__ img) {
+  if (p.amode && p.ctl && *p.ctl) return;  // uniform: written by an earlier kernel
   const long long tot = (long long)p.nchunks * p.nn * TT_K;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -103,18 +120,108 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+// Assignment epilogue of a tile (every thread of the CTA calls it).  Thread (warp w, lane l)
+// owns row 32 (w % 4) + l and the accumulator columns 32 (w / 4) + 64 j: for each it forms the
+// FP32 distance ||c_j||^2 - 2 e.c_j and keeps the best (lowest index among equal values) and
+// the second best; the upper four warps hand theirs to the lower four through shared memory,
+// which merge them.  A row whose margin (second - best) is below p.tie is re-decided with
+// exact FP64 distances ||e - c_j||^2 over every centroid (ties -> lowest index); the margin
+// bounds twice the error of the 3-term split TF32 distances, so the labels are those of FP64
+// arithmetic.
+__device__ __forceinline__ void assign_epilogue(const TcTall& p, uint32_t tmem, int warp, int lane,
+                                                long long row, float* sb, float* ss, int* sj,
+                                                int* nchg) {
+  float best = 3.4e38f, second = 3.4e38f;
+  int bj = 0;
+  for (int c0 = 32 * (warp >> 2); c0 < p.b; c0 += 64) {  // uniform in the warp
+    uint32_t v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int col = c0 + j;
+      if (col < p.b) {
+        const float dist = fmaf(-2.f, __uint_as_float(v[j]), p.cn[col]);
+        if (dist < best) {
+          second = best;
+          best = dist;
+          bj = col;
+        } else if (dist < second) {
+          second = dist;
+        }
+      }
+    }
+  }
+  const int r = 32 * (warp & 3) + lane;
+  if (warp >= 4) {
+    sb[r] = best;
+    ss[r] = second;
+    sj[r] = bj;
+  }
+  __syncthreads();
+  if (warp < 4 && row < p.n) {
+    // merge with the upper warp's columns (which all come after this warp's in each pair of
+    // 32-column groups, so equal values resolve by index)
+    const float b2 = sb[r], s2 = ss[r];
+    const int j2 = sj[r];
+    if (b2 < best || (b2 == best && j2 < bj)) {
+      second = fminf(s2, best);
+      best = b2;
+      bj = j2;
+    } else {
+      second = fminf(second, b2);
+    }
+    if (p.b > 1 && second - best < p.tie) {
+      const float* e = p.E + row * p.lde;
+      double bd = 1e300;
+      int bb = 0;
+      for (int j = 0; j < p.b; ++j) {
+        const double* c = p.C64 + (long long)j * p.d;
+        double acc = 0.0;
+        for (int q = 0; q < p.d; ++q) {
+          const double df = (double)e[q] - c[q];
+          acc = fma(df, df, acc);
+        }
+        if (acc < bd) {
+          bd = acc;
+          bb = j;
+        }
+      }
+      bj = bb;
+    }
+    const int old = p.labels[row];
+    if (p.first || old != bj) atomicAdd(nchg, 1);
+    p.labels[row] = bj;
+  }
+}
+
 __global__ void __launch_bounds__(TT_NTH, 1)
     k_tall_tc(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
               const __grid_constant__ CUtensorMap map2, const __grid_constant__ TcTall p,
               int* status) {
+  if (p.amode && p.ctl && *p.ctl) return;  // uniform: written by an earlier kernel
   extern __shared__ __align__(1024) uint8_t tt_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)tt_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ int am_chg;
   const int nstg = p.nstg, sb = p.stage, wbytes = p.nn * 128;
   uint64_t* bars = (uint64_t*)(base + (size_t)nstg * sb);
   uint64_t* full = bars;                   // [nstg] A chunk and W^T chunk landed
   uint64_t* mdone = bars + TT_MAXSTG;      // [nstg] MMAs reading the stage finished
   uint64_t* accd = bars + 2 * TT_MAXSTG;   // accumulator of the tile complete
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * TT_MAXSTG + 1);
+  float* am_best = (float*)((uint8_t*)bars + 256);  // assignment mode: the upper warps' part
+  float* am_second = am_best + TT_M;
+  int* am_bj = (int*)(am_second + TT_M);
   __shared__ int abort_flag, acc_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const CUtensorMap* maps[3] = {&map0, &map1, &map2};
@@ -126,6 +233,7 @@ __global__ void __launch_bounds__(TT_NTH, 1)
 
   if (tid == 0) {
     abort_flag = 0;
+    am_chg = 0;
     for (int q = 0; q < 2 * TT_MAXSTG + 1; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -233,6 +341,12 @@ __global__ void __launch_bounds__(TT_NTH, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long row = (long long)tile * TT_M + 32 * (warp & 3) + lane;
+      if (p.amode) {
+        assign_epilogue(p, tmem, warp, lane, row, am_best, am_second, am_bj, &am_chg);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        continue;
+      }
       for (int c0 = 32 * (warp >> 2); c0 < p.b; c0 += 64) {  // uniform in the warp
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
@@ -305,6 +419,7 @@ __global__ void __launch_bounds__(TT_NTH, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (p.amode && tid == 0 && am_chg) atomicAdd(p.changes, am_chg);
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tcols)
@@ -320,7 +435,7 @@ __global__ void __launch_bounds__(TT_NTH, 1)
 // 1 MB) is a stream-ordered allocation of the call, freed behind the launch.
 static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<float>& A,
                                     const TallSeg<float>& s0, const TallSeg<float>& s1,
-                                    float beta, int* d_status);
+                                    float beta, int* d_status, const TcTall* am = nullptr);
 
 // Outputs wider than one MMA (N > 256) run as column pieces of at most 256 (multiples of 16),
 // each its own pass over A.
@@ -352,10 +467,24 @@ cudaError_t tall_gemm_tc(cudaStream_t st, long long n, const Cat3<float>& A,
 
 static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<float>& A,
                                     const TallSeg<float>& s0, const TallSeg<float>& s1,
-                                    float beta, int* d_status) {
+                                    float beta, int* d_status, const TcTall* am) {
   const int b = s0.b + s1.b;
   if (n <= 0 || b <= 0) return cudaErrorNotSupported;
   TcTall p{};
+  if (am) {  // the k-means assignment mode (assign_tc)
+    p.wt = am->wt;
+    p.amode = am->amode;
+    p.first = am->first;
+    p.d = am->d;
+    p.tie = am->tie;
+    p.cn = am->cn;
+    p.C64 = am->C64;
+    p.E = am->E;
+    p.lde = am->lde;
+    p.labels = am->labels;
+    p.changes = am->changes;
+    p.ctl = am->ctl;
+  }
   p.nseg = A.nblk;
   p.n = n;
   int ch = 0, wr = 0;
@@ -408,7 +537,7 @@ static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<flo
     cudaFuncSetAttribute(k_tall_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM);
   });
   {
-    ProfScope ps(st, "tall_gemm");
+    ProfScope ps(st, am ? "kmeans_assign" : "tall_gemm");
     const long long tot = (long long)ch * p.nn * TT_K;
     k_tall_wsplit<<<(unsigned)std::min<long long>((tot + 255) / 256, 1024), 256, 0, st>>>(p, img);
     note_launch();
@@ -419,6 +548,32 @@ static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<flo
   e = cudaGetLastError();
   cudaFreeAsync(img, st);
   return e;
+}
+
+// k-means assignment on tensor cores: the update kernel with A = E (n x d rows) and W = C^T (the
+// k x d FP32 centroids read transposed), its epilogue turning e_i . c_j into labels (k <= 256;
+// near ties re-decided in FP64).  cudaErrorNotSupported when the shape does not fit the tensor
+// map rules (E 16-byte aligned, lde a multiple of 4); the caller then uses the CUDA-core kernel.
+cudaError_t assign_tc(cudaStream_t st, long long n, int d, int k, const float* E, long long lde,
+                      const float* C32, const float* cn, const double* C64, int* labels,
+                      int* changes, int first, float tie, const int* ctl, int* d_status) {
+  if (n <= 0 || d < 1 || k < 1 || k > 256) return cudaErrorNotSupported;
+  TcTall am{};
+  am.wt = 1;
+  am.amode = 1;
+  am.first = first;
+  am.d = d;
+  am.tie = tie;
+  am.cn = cn;
+  am.C64 = C64;
+  am.E = E;
+  am.lde = lde;
+  am.labels = labels;
+  am.changes = changes;
+  am.ctl = ctl;
+  const TallSeg<float> s0{nullptr, 0, nullptr, 0, C32, d, 0, k};
+  const TallSeg<float> s1{};
+  return tall_gemm_tc_one(st, n, cat<float>(E, lde, d), s0, s1, 0.f, d_status, &am);
 }
 
 }  // namespace sc

@@ -2192,6 +2192,7 @@ struct SrvSlot {
   sc_graph* g = nullptr;
   RunBase* run = nullptr;
   cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after the last pass was issued
   size_t est = 0;
 };
 
@@ -2248,6 +2249,8 @@ static void srv_complete(sc_server* s, SrvSlot& sl, int status) {
   res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - sl.req.t0).count();
   delete sl.run;
   sl.run = nullptr;
+  if (sl.done) cudaEventDestroy(sl.done);
+  sl.done = nullptr;
   if (sl.st) cudaStreamDestroy(sl.st);
   sl.st = nullptr;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -2345,24 +2348,56 @@ static void srv_loop(sc_server* s) {
       }
       s->active.push_back(std::move(sl));
     }
-    // one pass for every active solve, then retire the finished ones
+    // Issue work: a fixed-pass solve (no stopping tolerance: the host decides nothing between
+    // passes) has all of its passes queued on its stream at once, so the device always holds
+    // work of every admitted request; a solve with a tolerance advances one pass per round.
+    // An event after the last pass marks the solve's device work.
     for (auto& sl : s->active) {
-      if (!sl.run->finished()) {
-        int rc = sl.run->pass();
-        if (rc != SC_OK) {
-          delete sl.run;
-          sl.run = nullptr;
-          srv_complete(s, sl, rc);
-        }
+      if (!sl.run || sl.done) continue;
+      const bool fixed = sl.req.r.tol_abs <= 0;
+      int rc = SC_OK;
+      do {
+        rc = sl.run->pass();
+      } while (rc == SC_OK && fixed && !sl.run->finished());
+      if (rc == SC_OK && sl.run->finished()) {
+        if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(sl.done, sl.st) != cudaSuccess)
+          rc = fail(s->c, SC_ECUDA, "event");
+      }
+      if (rc != SC_OK) {
+        delete sl.run;
+        sl.run = nullptr;
+        srv_complete(s, sl, rc);
       }
     }
+    // retire the solves whose device work is done (outputs, embedding and k-means), in
+    // admission order; the others keep running on the device meanwhile
     std::vector<SrvSlot> keep;
+    bool progressed = !admit.empty();
     for (auto& sl : s->active) {
-      if (!sl.run) continue;  // failed and completed above
-      if (sl.run->finished()) srv_complete(s, sl, SC_OK);
-      else keep.push_back(std::move(sl));
+      if (!sl.run) {  // failed and completed above
+        progressed = true;
+        continue;
+      }
+      const cudaError_t q = sl.done ? cudaEventQuery(sl.done) : cudaErrorNotReady;
+      if (q == cudaSuccess) {
+        srv_complete(s, sl, SC_OK);
+        progressed = true;
+      } else if (q != cudaErrorNotReady) {
+        cudaGetLastError();
+        srv_complete(s, sl, SC_ECUDA);
+        progressed = true;
+      } else {
+        keep.push_back(std::move(sl));
+      }
     }
     s->active.swap(keep);
+    if (!progressed && !s->active.empty()) {
+      // nothing finished and nothing admitted: wait briefly for an arrival or the device
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait_for(lk, std::chrono::microseconds(200),
+                          [&] { return s->stop || !s->queue.empty(); });
+    }
   }
 }
 

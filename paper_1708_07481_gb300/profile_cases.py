@@ -3,6 +3,7 @@
     python -m paper_1708_07481_gb300.profile_cases rr    # 3 Rayleigh-Ritz solves, m = 132, K = 44
     python -m paper_1708_07481_gb300.profile_cases lob   # 3 LOBPCG passes, DC-SBM n = 50,000, K = 44
     python -m paper_1708_07481_gb300.profile_cases big   # 2 LOBPCG passes, DC-SBM n = 300,000, K = 160
+    python -m paper_1708_07481_gb300.profile_cases kmeans  # k-means, 50,000 unit rows, d = k = 44
 
 `rr` feeds the dense Rayleigh-Ritz solve a 132 x 132 FP64 Gram with K = 44 small and 88 large
 eigenvalues (the spectrum shape of the [X R P] projection at n = 50,000, K = 44).  `lob`
@@ -41,8 +42,17 @@ def main(argv=None):
         Gr = sc.sc_build_laplacian(ctx, g.n, torch.from_numpy(g.src).cuda(),
                                    torch.from_numpy(g.dst).cuda())
         sc.sc_lobpcg(ctx, Gr, 160, iters=2, seed=0, cold=1, want_X=False)
+    elif mode == "kmeans":
+        # unit rows around 44 centres (the embedding's shape at the bench workload); the
+        # assignment path follows SC_TUNE_ASSIGN (1: tensor cores, 0: CUDA cores)
+        rng = np.random.default_rng(0)
+        C = rng.standard_normal((44, 44))
+        E = C[rng.integers(0, 44, 50000)] + 0.05 * rng.standard_normal((50000, 44))
+        E = (E / np.linalg.norm(E, axis=1, keepdims=True)).astype(np.float32)
+        for _ in range(2):
+            sc.sc_kmeans(ctx, E, 44, iters=50, seed=5)
     else:
-        raise SystemExit(f"unknown case {mode!r}: rr, lob or big")
+        raise SystemExit(f"unknown case {mode!r}: rr, lob, big or kmeans")
     print("ok", mode)
 
 

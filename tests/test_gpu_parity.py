@@ -463,11 +463,24 @@ def _clustered(n, d, k, seed, spread=0.05):
     return O.embed_rows(E).astype(np.float32), lab
 
 
+@pytest.mark.parametrize("assign", ["simt", "tc"])
 @pytest.mark.parametrize("n,d,k", [(1000, 11, 11), (50000, 44, 44), (3001, 5, 1), (3000, 100, 70), (3000, 156, 150), (2000, 200, 40)])
-def test_kmeans_seeds_and_labels_bit_exact(sc, ctx, n, d, k):
+def test_kmeans_seeds_and_labels_bit_exact(sc, ctx, n, d, k, assign, monkeypatch):
+    # assign = tc: the Lloyd assignment on tensor cores (3-term split TF32 distances, FP64
+    # re-decision of near ties) wherever the shape allows it (rows 16-byte aligned: d % 4 == 0)
+    monkeypatch.setenv("SC_TUNE_ASSIGN", "1" if assign == "tc" else "0")
     E, _ = _clustered(n, d, max(k, 2), n)
     u = W.kmeans_uniforms(5, k)
+    l0 = ctx.launches
     labels, cent, seeds, inertia, ran = sc.sc_kmeans(ctx, E, k, iters=50, seed=5)
+    if assign == "tc" and d % 4 == 0 and k > 1:
+        # the tensor-core path ran: per round it launches the split of C' and its kernel where
+        # the CUDA-core path launches one kernel
+        launches_tc = ctx.launches - l0
+        monkeypatch.setenv("SC_TUNE_ASSIGN", "0")
+        l0 = ctx.launches
+        sc.sc_kmeans(ctx, E, k, iters=50, seed=5)
+        assert launches_tc > ctx.launches - l0
     Ed = E.astype(np.float64)
     rl, rC, ridx, rin = O.kmeans(Ed, k, u, 50)
     assert np.array_equal(seeds, ridx)
