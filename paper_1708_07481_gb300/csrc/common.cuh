@@ -256,8 +256,10 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
                   long long lde, const int* seeds_dev, int iters, int* labels_dev,
                   double* cent_dev, int* iters_run, double* inertia);
 
-// k-means assignment on tensor cores (3-term split TF32 distances ||c||^2 - 2 e.c, near ties
-// re-decided with FP64 distances): labels of the n x d rows E against the k x d centroids,
+// k-means assignment on tensor cores (3-term split TF32 distances ||c||^2 - 2 e.c; a row whose
+// margin is below 4 tie is re-decided with FP64 distances to the centroids within 4 tie of its
+// best, tie being the CUDA-core kernel's margin): labels of the n x d rows E against the k x d
+// centroids,
 // k <= 256; *changes += rows whose label changed (all rows when first).  Returns
 // cudaErrorNotSupported when the shape does not fit (the caller uses the CUDA-core kernel).
 cudaError_t assign_tc(cudaStream_t st, long long n, int d, int k, const float* E, long long lde,

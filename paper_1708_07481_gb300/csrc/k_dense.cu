@@ -21,6 +21,27 @@
 namespace sc {
 namespace {
 
+// Copies the rows x cols FP64 matrix G (row stride ldg) into shared memory Gs (stride cols)
+// with nth threads: each thread's loads of a batch of 8 are issued before any of them is stored,
+// so eight reads per thread are in flight instead of one.
+__device__ __forceinline__ void stage_f64(const double* __restrict__ G, long long ldg, int rows,
+                                          int cols, double* Gs, int tid, int nth) {
+  const int tot = rows * cols;
+  for (int base = tid; base < tot; base += 8 * nth) {
+    double t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * nth;
+      t[u] = idx < tot ? G[(long long)(idx / cols) * ldg + idx % cols] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * nth;
+      if (idx < tot) Gs[idx] = t[u];
+    }
+  }
+}
+
 template <typename T> struct Lim;
 template <> struct Lim<float> {
   __device__ static float eps() { return FLT_EPSILON; }
@@ -255,11 +276,17 @@ __device__ int ldl_inv_reg(int n, float* M, int ldm, float* dd, float* buf, floa
         const T wik = __shfl_sync(0xffffffffu, R[r][q], (lane & 16) | kw);
         l[r] = g + NHW * r > k ? wik * invd : (T)0;
       }
+      // R -= l y' on the owned entries, two columns per packed FMA (each half rounds as fmaf)
+      static_assert(CS % 2 == 0, "column slots come in pairs");
 #pragma unroll
-      for (int c = 0; c < CS; ++c) {
-        const T y = cur[cl + 16 * c];
+      for (int c = 0; c < CS; c += 2) {
+        const float2 y2 = make_float2(cur[cl + 16 * c], cur[cl + 16 * (c + 1)]);
 #pragma unroll
-        for (int r = r0; r < RS; ++r) R[r][c] = fmaf(-l[r], y, R[r][c]);
+        for (int r = r0; r < RS; ++r) {
+          const float2 a = __ffma2_rn(make_float2(-l[r], -l[r]), y2, make_float2(R[r][c], R[r][c + 1]));
+          R[r][c] = a.x;
+          R[r][c + 1] = a.y;
+        }
       }
       if (cl == kw) {
 #pragma unroll
@@ -475,7 +502,10 @@ __device__ long long g_rr_inv[4];
 
 constexpr int RR_NT = 1024;
 #ifndef RR_SWEEPS
-#define RR_SWEEPS 2  // inverse-iteration sweeps of the register-slot Rayleigh-Ritz
+#define RR_SWEEPS 2  // inverse-iteration sweeps of the Rayleigh-Ritz eigenvector phase (FP64)
+#endif
+#ifndef RR_SWEEPS_F32
+#define RR_SWEEPS_F32 2  // the same in FP32
 #endif
 
 // Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of the symmetric
@@ -1048,7 +1078,8 @@ __device__ void rr_phase_eigvecs(int m, int K, const T* __restrict__ d, const T*
   const T small_piv = Lim<T>::eps() * tnorm + pivmin;
 #define UF(i, a) U[((i) * 3 + (a)) * K + j]
   long long tinv = clock64();
-  for (int sweep = 0; sweep < RR_SWEEPS; ++sweep) {
+  constexpr int kSweeps = sizeof(T) == 4 ? RR_SWEEPS_F32 : RR_SWEEPS;
+  for (int sweep = 0; sweep < kSweeps; ++sweep) {
     for (int j = tid; j < K; j += NT) {
       // LU with partial pivoting of T - s I, the right-hand side eliminated alongside
       const T sj = shift[j];
@@ -1614,10 +1645,7 @@ __device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double
     double* Gst = (double*)(((uintptr_t)Vs + 7) & ~(uintptr_t)7);
     const size_t room = (size_t)m * ldv + 4 * (size_t)m * K + (size_t)K * K - 2;
     if ((size_t)2 * m * m <= room) {
-      for (int idx = tid; idx < m * m; idx += RT_NT) {
-        const int i = idx / m, j = idx % m;
-        Gst[idx] = G[(long long)i * ldg + j];
-      }
+      stage_f64(G, ldg, m, m, Gst, tid, RT_NT);
       __syncthreads();
       Gsrc = Gst;
       lds = m;
@@ -1714,9 +1742,9 @@ __device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double
       }
       T vc[CS], vr[RS], pr[RS];
 #pragma unroll
-      for (int c = q; c < CS; ++c) {
-        vc[c] = xs[cl + 16 * c] * iv0;
-        if (c <= q + 1 && cl + 16 * c == k1) vc[c] = (T)1;  // only slots q, q + 1 can hold k + 1
+      for (int c = q & ~1; c < CS; ++c) {
+        vc[c] = xs[cl + 16 * c] * iv0;  // slot q - 1 (q odd): columns <= k, zero in row k
+        if (c >= q && c <= q + 1 && cl + 16 * c == k1) vc[c] = (T)1;  // only slots q, q + 1
       }
 #pragma unroll
       for (int r = r0; r < RS; ++r) {
@@ -1725,12 +1753,15 @@ __device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double
       }
       // (c)
       T pvp = 0;
+      // (the column pairs start at an even slot: slot q - 1, when q is odd, holds columns <= k,
+      // whose v entries are zero)
 #pragma unroll
       for (int r = r0; r < RS; ++r) {
-        T sacc = 0;
+        float2 sacc2 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = q; c < CS; ++c) sacc = fmaf(A[r][c], vc[c], sacc);
-        pr[r] = bet * halfwarp_sum<16>(sacc);
+        for (int c = q & ~1; c < CS; c += 2)
+          sacc2 = __ffma2_rn(make_float2(A[r][c], A[r][c + 1]), make_float2(vc[c], vc[c + 1]), sacc2);
+        pr[r] = bet * halfwarp_sum<16>(sacc2.x + sacc2.y);
         pvp = fmaf(pr[r], vr[r], pvp);
       }
       if (cl == 0) {
@@ -1747,11 +1778,21 @@ __device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double
       T wr[RS];
 #pragma unroll
       for (int r = r0; r < RS; ++r) wr[r] = fmaf(-kc, vr[r], pr[r]);
+      // rank-2 update, two columns per packed FMA (each half rounds as fmaf; the pair that
+      // starts at slot q - 1 updates dead entries)
 #pragma unroll
-      for (int c = q; c < CS; ++c) {
-        const T wj = fmaf(-kc, vc[c], pvec[cl + 16 * c]);
+      for (int c = q & ~1; c < CS; c += 2) {
+        const float2 vc2 = make_float2(vc[c], vc[c + 1]);
+        const float2 wj2 = __ffma2_rn(make_float2(-kc, -kc), vc2,
+                                      make_float2(pvec[cl + 16 * c], pvec[cl + 16 * (c + 1)]));
 #pragma unroll
-        for (int r = r0; r < RS; ++r) A[r][c] = fmaf(-vr[r], wj, fmaf(-wr[r], vc[c], A[r][c]));
+        for (int r = r0; r < RS; ++r) {
+          const float2 a = __ffma2_rn(make_float2(-vr[r], -vr[r]), wj2,
+                                      __ffma2_rn(make_float2(-wr[r], -wr[r]), vc2,
+                                                 make_float2(A[r][c], A[r][c + 1])));
+          A[r][c] = a.x;
+          A[r][c + 1] = a.y;
+        }
       }
     }
   }
@@ -1814,10 +1855,12 @@ __device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double
           T sa[CPW];
 #pragma unroll
           for (int t = 0; t < CPW; ++t) {
-            T acc = 0;
+            float2 acc2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < RS; ++u) acc = fmaf(cv[u], z[t][u], acc);
-            sa[t] = acc;
+            for (int u = 0; u + 1 < RS; u += 2)
+              acc2 = __ffma2_rn(make_float2(cv[u], cv[u + 1]), make_float2(z[t][u], z[t][u + 1]), acc2);
+            if (RS % 2) acc2.x = fmaf(cv[RS - 1], z[t][RS - 1], acc2.x);
+            sa[t] = acc2.x + acc2.y;
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1)
@@ -1827,7 +1870,13 @@ __device__ __forceinline__ void k_rr_eig_rt_body(int m_full, int K, const double
           for (int t = 0; t < CPW; ++t) {
             const T f = bet * sa[t];
 #pragma unroll
-            for (int u = 0; u < RS; ++u) z[t][u] = fmaf(-f, cv[u], z[t][u]);
+            for (int u = 0; u + 1 < RS; u += 2) {
+              const float2 zz = __ffma2_rn(make_float2(-f, -f), make_float2(cv[u], cv[u + 1]),
+                                           make_float2(z[t][u], z[t][u + 1]));
+              z[t][u] = zz.x;
+              z[t][u + 1] = zz.y;
+            }
+            if (RS % 2) z[t][RS - 1] = fmaf(-f, cv[RS - 1], z[t][RS - 1]);
           }
         }
 #pragma unroll
@@ -1887,10 +1936,7 @@ __device__ __forceinline__ void k_chol_inv_rt_body(int ka, const double* __restr
   __shared__ int sfc;
   const int tid = threadIdx.x;
   // the FP64 Gram staged with coalesced row reads (the symmetrization reads its transpose)
-  for (int idx = tid; idx < ka * ka; idx += NTH) {
-    const int i = idx / ka, j = idx % ka;
-    Gs[idx] = G[(long long)i * ldg + j];
-  }
+  stage_f64(G, ldg, ka, ka, Gs, tid, NTH);
   __syncthreads();
   for (int i = tid; i < ka; i += NTH) {
     const double dgi = Gs[i * ka + i];

@@ -656,7 +656,7 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
       bool on_tc = false;
       if (use_tc) {
         const cudaError_t et = assign_tc(st, n, d, k, E, lde, C32, cn, C64, labels,
-                                         changes + it, it == 0, (float)(4.0 * tie), ctl, tstat);
+                                         changes + it, it == 0, (float)tie, ctl, tstat);
         if (et == cudaSuccess) {
           on_tc = true;
         } else if (et == cudaErrorNotSupported) {

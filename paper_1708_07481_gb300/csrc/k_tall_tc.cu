@@ -67,7 +67,7 @@ struct TcTall {
   // k-means assignment mode (amode): the accumulator holds e_i . c_j for the k = b centroids;
   // the epilogue turns it into labels instead of writing it (see k_tall_tc)
   int amode, first, d;
-  float tie;
+  float tie;  // margin of the tensor-core distances (at least twice their error)
   const float* cn;      // ||c_j||^2 (FP32)
   const double* C64;    // FP64 centroids, k x d
   const float* E;       // the rows, n x d (stride lde)
@@ -120,14 +120,31 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+// Reads 32 accumulator columns c0 .. c0 + 31 of the warp's lane quarter (row 32 (w % 4) + l).
+__device__ __forceinline__ void tt_ld32(uint32_t tmem, int warp, int c0, uint32_t (&v)[32]) {
+  const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Assignment epilogue of a tile (every thread of the CTA calls it).  Thread (warp w, lane l)
 // owns row 32 (w % 4) + l and the accumulator columns 32 (w / 4) + 64 j: for each it forms the
 // FP32 distance ||c_j||^2 - 2 e.c_j and keeps the best (lowest index among equal values) and
 // the second best; the upper four warps hand theirs to the lower four through shared memory,
 // which merge them.  A row whose margin (second - best) is below p.tie is re-decided with
-// exact FP64 distances ||e - c_j||^2 over every centroid (ties -> lowest index); the margin
-// bounds twice the error of the 3-term split TF32 distances, so the labels are those of FP64
-// arithmetic.
+// exact FP64 distances ||e - c_j||^2 for the centroids whose tensor-core distance lies within
+// p.tie of the best (ties -> lowest index): p.tie is at least twice the error of the 3-term
+// split TF32 distances, so the exact nearest centroid is among them and the labels are those
+// of FP64 arithmetic.  The candidates are read back from tensor memory by both warps of the
+// row; their FP64 minima are merged like the FP32 ones.
 __device__ __forceinline__ void assign_epilogue(const TcTall& p, uint32_t tmem, int warp, int lane,
                                                 long long row, float* sb, float* ss, int* sj,
                                                 int* nchg) {
@@ -135,18 +152,7 @@ __device__ __forceinline__ void assign_epilogue(const TcTall& p, uint32_t tmem, 
   int bj = 0;
   for (int c0 = 32 * (warp >> 2); c0 < p.b; c0 += 64) {  // uniform in the warp
     uint32_t v[32];
-    const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tt_ld32(tmem, warp, c0, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int col = c0 + j;
@@ -169,9 +175,9 @@ __device__ __forceinline__ void assign_epilogue(const TcTall& p, uint32_t tmem, 
     sj[r] = bj;
   }
   __syncthreads();
-  if (warp < 4 && row < p.n) {
-    // merge with the upper warp's columns (which all come after this warp's in each pair of
-    // 32-column groups, so equal values resolve by index)
+  bool tie = false;
+  if (warp < 4) {
+    // merge with the upper warp's columns
     const float b2 = sb[r], s2 = ss[r];
     const int j2 = sj[r];
     if (b2 < best || (b2 == best && j2 < bj)) {
@@ -181,21 +187,61 @@ __device__ __forceinline__ void assign_epilogue(const TcTall& p, uint32_t tmem, 
     } else {
       second = fminf(second, b2);
     }
-    if (p.b > 1 && second - best < p.tie) {
-      const float* e = p.E + row * p.lde;
-      double bd = 1e300;
-      int bb = 0;
-      for (int j = 0; j < p.b; ++j) {
-        const double* c = p.C64 + (long long)j * p.d;
-        double acc = 0.0;
-        for (int q = 0; q < p.d; ++q) {
-          const double df = (double)e[q] - c[q];
-          acc = fma(df, df, acc);
+    tie = row < p.n && p.b > 1 && second - best < p.tie;
+  }
+  __syncthreads();
+  if (warp < 4) {
+    sb[r] = best;          // the row's best, for the candidates of both warps
+    sj[r] = tie ? 1 : 0;
+  }
+  __syncthreads();
+  if (warp >= 4) {
+    best = sb[r];
+    tie = sj[r] != 0;
+  }
+  // FP64 distances of the candidates (warps with a near-tie row only)
+  double bd = 1e300;
+  int bb = 0x7fffffff;
+  if (__any_sync(0xffffffffu, tie)) {
+    const float* e = p.E + (tie ? row : 0) * p.lde;
+    for (int c0 = 32 * (warp >> 2); c0 < p.b; c0 += 64) {
+      uint32_t v[32];
+      tt_ld32(tmem, warp, c0, v);
+      if (tie) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = c0 + j;
+          if (col >= p.b) break;
+          const float dist = fmaf(-2.f, __uint_as_float(v[j]), p.cn[col]);
+          if (dist - best >= p.tie) continue;
+          const double* c = p.C64 + (long long)col * p.d;
+          double acc = 0.0;
+          for (int q = 0; q < p.d; ++q) {
+            const double df = (double)e[q] - c[q];
+            acc = fma(df, df, acc);
+          }
+          if (acc < bd) {  // columns ascend within a warp: the first minimum is the lowest
+            bd = acc;
+            bb = col;
+          }
         }
-        if (acc < bd) {
-          bd = acc;
-          bb = j;
-        }
+      }
+    }
+  }
+  __syncthreads();  // every read of sb / ss / sj is done: the area takes the FP64 minima
+  double* sd = reinterpret_cast<double*>(sb);  // 128 doubles over sb and ss
+  if (warp >= 4) {
+    sd[r] = bd;
+    sj[r] = bb;
+  }
+  __syncthreads();
+  if (warp < 4 && row < p.n) {
+    if (tie) {
+      const double bd2 = sd[r];
+      const int bb2 = sj[r];
+      if (bd2 < bd || (bd2 == bd && bb2 < bb)) {
+        bd = bd2;
+        bb = bb2;
       }
       bj = bb;
     }
@@ -563,7 +609,7 @@ cudaError_t assign_tc(cudaStream_t st, long long n, int d, int k, const float* E
   am.amode = 1;
   am.first = first;
   am.d = d;
-  am.tie = tie;
+  am.tie = 4.f * tie;
   am.cn = cn;
   am.C64 = C64;
   am.E = E;
