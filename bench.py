@@ -450,6 +450,22 @@ def cfg_large(sc, W, ctx, n=2_000_000, K=160, fp64_cap=60):
                         "kernel_ms": {k: v[1] for k, v in prof.items()},
                         "kernel_launches": {k: v[0] for k, v in prof.items()},
                         "note": "kernel_ms from CUDA events around every launch (profiled run)"}
+        if "spmm" in prof:
+            # SpMM roofline: the start-up launch takes the K columns of X, every pass one launch
+            # of the 2K columns of [R P]; per launch each stored nonzero gathers one row of the
+            # block (FP32), plus the CSR, the degrees and the rows' own block and image rows
+            nl, ms = prof["spmm"]
+            nnz = out["nnz"]
+            kp = (K + 3) // 4 * 4
+            cols = [K] + [kp + K] * max(nl - 1, 0)
+            alg = sum(4 * nnz * c + 4 * (n + 1) + 4 * nnz + 4 * n + 8 * n * c for c in cols)
+            peak = peaks().get("hbm_gbs", 6800.0)
+            gbs = alg / (ms / 1e3) / 1e9
+            out["mixed"]["spmm_roofline"] = {
+                "launches": nl, "ms": ms, "algorithmic_gb": alg / 1e9, "achieved_gbs": gbs,
+                "peak_gbs": peak, "frac": gbs / peak,
+                "note": "algorithmic bytes count every neighbour-row gather once (no cache reuse); "
+                        "above 1.0 would mean L2 serves gathers"}
     except sc.ScError as e:
         out["mixed"] = {"error": str(e)}
     out["hbm_peak_gb"] = ctx.bytes_peak() / 1e9
