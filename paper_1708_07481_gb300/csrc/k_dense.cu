@@ -507,6 +507,9 @@ constexpr int RR_NT = 1024;
 #ifndef RR_SWEEPS_F32
 #define RR_SWEEPS_F32 2  // the same in FP32
 #endif
+#ifndef RR_EARLY_PASSES
+#define RR_EARLY_PASSES 2  // Cholesky-QR passes at most after a sweep other than the last
+#endif
 
 // Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of the symmetric
 // m x m matrix G (FP64 in, arithmetic in T), one CTA of 1024 threads.
@@ -1125,7 +1128,8 @@ __device__ void rr_phase_eigvecs(int m, int K, const T* __restrict__ d, const T*
     __syncthreads();
     RR_INV(0, tinv);
     bool ok = true;
-    for (int pass = 0; pass < 2 && ok; ++pass) {
+    const int max_pass = sweep + 1 < kSweeps ? RR_EARLY_PASSES : 2;
+    for (int pass = 0; pass < max_pass && ok; ++pass) {
       // Gram Z'Z (lower triangle), one thread per entry, four accumulators
       for (int p = tid; p < K * K; p += NT) {
         const int a = p / K, b = p % K;

@@ -1157,11 +1157,16 @@ struct LobRun : RunBase {
   }
   int stage_images_pre() {
     const int wq = ps_w, ka = ps_ka;
-    // R = Q1_R T_RR uses only the R columns of Q1 (TmB is upper triangular)
-    CK(tall(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, S + kp, ld3, nullptr, 0, (T)0), "tall");
-    if (haveP)
-      CK(tall(st, n, cat<T>(Q1, 2 * kp, wq), TmB + ka, wq, ka, S + 2 * kp, ld3, nullptr, 0, (T)0),
-         "tall");
+    if (haveP) {
+      // [R P] = Q1 TmB in one pass over Q1: two output segments (TmB is upper triangular, so
+      // the R columns take zeros from Q1's P columns)
+      TallSeg<T> sr{S + kp, ld3, nullptr, 0, TmB, wq, 0, ka};
+      TallSeg<T> sp{S + 2 * kp, ld3, nullptr, 0, TmB + ka, wq, 0, ka};
+      CK(tall2(st, n, cat<T>(Q1, 2 * kp, wq), sr, sp, (T)0), "tall");
+    } else {
+      // R = Q1_R T_RR uses only the R columns of Q1
+      CK(tall(st, n, cat<T>(Q1, 2 * kp, ka), TmB, wq, ka, S + kp, ld3, nullptr, 0, (T)0), "tall");
+    }
     return SC_OK;
   }
   // (3) [LR_a LP_a] = L [R_a P_a]: the one multiplication by L of the pass (Sec. III), taken on
