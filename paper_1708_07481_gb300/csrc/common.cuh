@@ -126,10 +126,13 @@ cudaError_t merge_csr(cudaStream_t st, Alloc& al, const CsrDev& a, const CsrDev&
 template <typename T>
 cudaError_t spmm_lap(cudaStream_t st, const CsrDev& g, const T* V, long long ldv, T* Y,
                      long long ldy, int k, int shape = -1);
-// Householder tridiagonalization of an m x m FP64 matrix (m <= 512) on a cluster of 8 CTAs
-// (k_tridiag_cl.cu): d, e, beta and the scaled reflector rows (row stride lda) of Ag.
+// Householder tridiagonalization of an m x m FP64 matrix on a cluster of 8 CTAs
+// (k_tridiag_cl.cu), in FP32 (m <= 512) or FP64 (m <= 256): d, e, beta and the scaled reflector
+// rows (row stride lda) of Ag.
 cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int ldg, float* Ag,
                             int lda, float* d, float* e, float* beta, const int* pflag, int mP);
+cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int ldg, double* Ag,
+                            int lda, double* d, double* e, double* beta, const int* pflag, int mP);
 // Kernel shapes valid for nvec 16-byte column chunks (at most 13); out[0] is the default.
 int spmm_shapes(int nvec, int* out);
 

@@ -507,9 +507,6 @@ constexpr int RR_NT = 1024;
 #ifndef RR_SWEEPS_F32
 #define RR_SWEEPS_F32 2  // the same in FP32
 #endif
-#ifndef RR_EARLY_PASSES
-#define RR_EARLY_PASSES 2  // Cholesky-QR passes at most after a sweep other than the last
-#endif
 
 // Rayleigh-Ritz in an orthonormal trial basis: the K smallest eigenpairs of the symmetric
 // m x m matrix G (FP64 in, arithmetic in T), one CTA of 1024 threads.
@@ -995,7 +992,7 @@ __device__ void rr_multisect(int m, int K, const T* __restrict__ d, const T* __r
 template <typename T, int NT>
 __device__ void rr_phase_eigvals(int m, int K, const T* __restrict__ d, const T* __restrict__ e,
                                  T* __restrict__ e2, T* red, T* __restrict__ lam, int* status,
-                                 T& tnorm, T& pivmin) {
+                                 T& tnorm, T& pivmin, const T* __restrict__ lam_ext = nullptr) {
   constexpr int NW = NT / 32;
   constexpr unsigned FULL = 0xffffffffu;
   constexpr int RS = 3 * NW;
@@ -1042,6 +1039,11 @@ __device__ void rr_phase_eigvals(int m, int K, const T* __restrict__ d, const T*
   const T glo = red[RS] - (T)2 * Lim<T>::eps() * tnorm - pivmin;
   const T ghi = red[RS + 1] + (T)2 * Lim<T>::eps() * tnorm + pivmin;
   const T abstol = Lim<T>::eps() * tnorm;
+  if (lam_ext) {  // the eigenvalues were found by k_rr_eigvals_cta: the bounds only
+    for (int j = tid; j < K; j += NT) lam[j] = lam_ext[j];
+    __syncthreads();
+    return;
+  }
   // 16 lanes per eigenvalue when the block has a group for each; otherwise 8, so that all K
   // eigenvalues are found in one round
   if (K <= NT / 16)
@@ -1128,8 +1130,7 @@ __device__ void rr_phase_eigvecs(int m, int K, const T* __restrict__ d, const T*
     __syncthreads();
     RR_INV(0, tinv);
     bool ok = true;
-    const int max_pass = sweep + 1 < kSweeps ? RR_EARLY_PASSES : 2;
-    for (int pass = 0; pass < max_pass && ok; ++pass) {
+    for (int pass = 0; pass < 2 && ok; ++pass) {
       // Gram Z'Z (lower triangle), one thread per entry, four accumulators
       for (int p = tid; p < K * K; p += NT) {
         const int a = p / K, b = p % K;
@@ -1302,7 +1303,8 @@ __device__ __forceinline__ void k_rr_eig_reg_body(int m_full, int K, const doubl
                                                   T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
                                                   int* status, int* pflag, int mP,
                                                   int* nfallback, const T* dext,
-                                                  const T* eext, const T* bext, int ldext) {
+                                                  const T* eext, const T* bext, int ldext,
+                                                  const T* lamext, int* mext) {
   // dext != nullptr: the tridiagonal form (d, e, beta) and the reflector rows of Ag (row stride
   // ldext) were computed by the cluster kernel (k_tridiag_cl); the load and phase 1 are skipped
   constexpr int NT = NW * 32;
@@ -1479,7 +1481,7 @@ __device__ __forceinline__ void k_rr_eig_reg_body(int m_full, int K, const doubl
   RR_MARK(1);
 
   T tnorm, pivmin;
-  rr_phase_eigvals<T, NT>(m, K, d, e, e2, red, lam, status, tnorm, pivmin);
+  rr_phase_eigvals<T, NT>(m, K, d, e, e2, red, lam, status, tnorm, pivmin, lamext);
   RR_MARK(2);
 
   rr_phase_eigvecs<T, NT>(m, K, d, e, lam, shift, Z, U, Gs, dd, cbuf, wv, coef, red, tnorm,
@@ -1487,7 +1489,8 @@ __device__ __forceinline__ void k_rr_eig_reg_body(int m_full, int K, const doubl
   RR_MARK(4);
 
   // ---- 4. back-transformation Y = H_0 ... H_{m-3} Z, two columns per warp in registers
-  for (int j0 = 2 * warp; j0 < K; j0 += 2 * NW) {
+  // (with mext set it is left to k_rr_back, which spreads the columns over SMs)
+  for (int j0 = 2 * warp; !mext && j0 < K; j0 += 2 * NW) {
     const int j1 = j0 + 1;
     const bool two = j1 < K;  // uniform in the warp
     T za[NS], zb[NS];
@@ -1535,7 +1538,9 @@ __device__ __forceinline__ void k_rr_eig_reg_body(int m_full, int K, const doubl
   }
   RR_MARK(5);
   for (int j = tid; j < K; j += NT) theta[j] = (double)lam[j];
-  if (pflag && tid == 0) {
+  if (mext) {
+    if (tid == 0) *mext = m;  // k_rr_back reads the solved size and re-arms *pflag
+  } else if (pflag && tid == 0) {
     if (*pflag == 0 && nfallback) *nfallback += 1;
     *pflag = 1;  // re-armed for the next pass
   }
@@ -1548,9 +1553,10 @@ __global__ void __launch_bounds__(NW * 32)
     k_rr_eig_reg(int m_full, int K, const double* __restrict__ G, int ldg,
                  double* __restrict__ theta, T* __restrict__ Y, T* Ag, T* Zg, T* Ug, T* Gsg,
                  int* status, int* pflag, int mP, int* nfallback, const T* dext = nullptr,
-                 const T* eext = nullptr, const T* bext = nullptr, int ldext = 0) {
+                 const T* eext = nullptr, const T* bext = nullptr, int ldext = 0,
+                 const T* lamext = nullptr, int* mext = nullptr) {
   k_rr_eig_reg_body<T, NS, NW, SM>(m_full, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, status, pflag,
-                                   mP, nfallback, dext, eext, bext, ldext);
+                                   mP, nfallback, dext, eext, bext, ldext, lamext, mext);
 }
 // One CTA per descriptor of a lockstep batch (FP32).  With the matrix in global memory the
 // working set is Ag (m (m + 16) floats, then Z, U, Gs); with tri set, the tridiagonal form and
@@ -1564,7 +1570,117 @@ __global__ void __launch_bounds__(NW * 32) k_rr_eig_reg_b(const RrDesc* __restri
   k_rr_eig_reg_body<float, NS, NW, SM>(a.m, a.K, a.G, a.ldg, a.theta, a.Y, a.Ag, Zg, Ug, Gsg,
                                        a.status, a.pflag, a.mP, a.nfallback, a.tri,
                                        a.tri ? a.tri + a.m : nullptr,
-                                       a.tri ? a.tri + 2 * a.m : nullptr, a.tri ? a.m : 0);
+                                       a.tri ? a.tri + 2 * a.m : nullptr, a.tri ? a.m : 0,
+                                       nullptr, nullptr);
+}
+
+// ---- the FP64 Rayleigh-Ritz spread over SMs ---------------------------------------------
+// GB300 runs FP64 at 2 FMA per clock per SM, so a one-CTA FP64 solve is bound by one SM's FP64
+// pipe.  For 64 < m <= 256 the phases go to many SMs: the cluster tridiagonalization
+// (k_tridiag_cl<double>), the eigenvalues here (one CTA per eigenvalue), the eigenvectors in
+// k_rr_eig_reg (one CTA: dependent LU chains), and the back-transformation in k_rr_back (one
+// CTA per column).
+constexpr int EV_MMAX = 256;
+
+// Eigenvalue blockIdx.x of the tridiagonal T = (d, e) (m rows: m_full, less mP when *pflag is
+// 0) by 9-point multisection on Sturm counts with 8 lanes -- the arithmetic of rr_multisect --
+// after the Gershgorin bounds of rr_phase_eigvals, recomputed by every CTA.
+template <typename T>
+__global__ void __launch_bounds__(32)
+    k_rr_eigvals_cta(int m_full, int K, int mP, const int* pflag, const T* __restrict__ d,
+                     const T* __restrict__ e, T* __restrict__ lam, int* status) {
+  constexpr int LG = 8;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ T e2[EV_MMAX];
+  const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
+  const int lane = threadIdx.x, j = blockIdx.x;
+  T lo = (T)3e38, hi = (T)-3e38, emax = 0;
+  for (int i = lane; i < m; i += 32) {
+    T r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0);
+    lo = min(lo, d[i] - r);
+    hi = max(hi, d[i] + r);
+    emax = max(emax, e[i] * e[i]);
+    e2[i] = e[i] * e[i];
+    if (j == 0 && (!isfinite(d[i]) || !isfinite(e[i]))) atomicOr(status, ST_NONFINITE);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+    hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    emax = max(emax, __shfl_xor_sync(FULL, emax, o));
+  }
+  __syncwarp();
+  const T tnorm = max(fabs(lo), fabs(hi));
+  const T pivmin = Lim<T>::tiny() * max((T)1, emax);
+  const T glo = lo - (T)2 * Lim<T>::eps() * tnorm - pivmin;
+  const T ghi = hi + (T)2 * Lim<T>::eps() * tnorm + pivmin;
+  const T abstol = Lim<T>::eps() * tnorm;
+  if (lane >= LG) return;
+  const int sl = lane;
+  const unsigned gmask = (1u << LG) - 1u;
+  T a = glo, b = ghi;
+  for (int it = 0; it < 64; ++it) {
+    T tol = max((T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)), abstol) + (T)4 * pivmin;
+    if (b - a <= tol) break;
+    T h = (b - a) / (T)(LG + 1);
+    int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
+    unsigned bal = __ballot_sync(gmask, c > j);
+    int first = bal ? (__ffs(bal) - 1) : LG;
+    T na = first == 0 ? a : a + h * (T)first;
+    T nb = first == LG ? b : a + h * (T)(first + 1);
+    if (!(nb > na)) break;
+    a = na;
+    b = nb;
+  }
+  if (sl == 0) lam[j] = (T)0.5 * (a + b);
+}
+
+// Back-transformation Y = H_0 ... H_{m-3} Z of one column per CTA (one warp): the arithmetic
+// of k_rr_eig_reg's phase 4 for that column.  The reflectors are the rows of Ag (stride lda),
+// m the solved size k_rr_eig_reg left in *mext; CTA 0 then re-arms *pflag (nothing else reads
+// it before the next pass).
+template <typename T, int NS>
+__global__ void __launch_bounds__(32)
+    k_rr_back(int m_full, int K, const int* __restrict__ mext, const T* __restrict__ Ag, int lda,
+              const T* __restrict__ beta, const T* __restrict__ Z, T* __restrict__ Y, int* pflag,
+              int* nfallback) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int j = blockIdx.x, lane = threadIdx.x;
+  const int m = *mext;
+  T za[NS];
+#pragma unroll
+  for (int u = 0; u < NS; ++u) {
+    const int i = lane + 32 * u;
+    za[u] = i < m ? Z[(long long)i * K + j] : (T)0;
+  }
+  for (int kr = m - 3; kr >= 0; --kr) {
+    const T bet = beta[kr];
+    if (bet == (T)0) continue;
+    const int k1 = kr + 1;
+    const T* vk = Ag + (long long)kr * lda;
+    T cv[NS];
+    T sa = 0;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+      const int i = lane + 32 * u;
+      cv[u] = (i == k1) ? (T)1 : ((i > k1 && i < m) ? vk[i] : (T)0);
+      sa = fma(cv[u], za[u], sa);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(FULL, sa, o);
+    sa *= bet;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) za[u] = fma(-sa, cv[u], za[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < NS; ++u) {
+    const int i = lane + 32 * u;
+    if (i < m_full) Y[(long long)i * K + j] = i < m ? za[u] : (T)0;
+  }
+  if (j == 0 && lane == 0 && pflag) {
+    if (*pflag == 0 && nfallback) *nfallback += 1;
+    *pflag = 1;  // re-armed for the next pass
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2098,6 +2214,36 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
   if constexpr (can_sm) {
     if (insm) kern = k_rr_eig_reg<T, NS, NW, true>;
   }
+  // FP64, 64 < m <= 256: the phases spread over SMs (tridiagonalization on a cluster, one CTA
+  // per eigenvalue, the eigenvectors here, one CTA per back-transformed column)
+  if constexpr (sizeof(T) == 8) {
+    if (!insm && m > 64 && m <= EV_MMAX) {
+      T* tri = al.get<T>((size_t)3 * m + K);  // d, e, beta, eigenvalues
+      int* mx = al.get<int>(1);
+      cudaError_t e = (tri && mx) ? cudaSuccess : cudaErrorMemoryAllocation;
+      if (e == cudaSuccess)
+        e = tridiag_cluster(st, m, K, G, ldg, Ag, m, tri, tri + m, tri + 2 * m, pflag, mP);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e == cudaSuccess) {
+        ProfScope ps(st, "rr_eig");
+        k_rr_eigvals_cta<T><<<K, 32, 0, st>>>(m, K, mP, pflag, tri, tri + m, tri + 3 * m,
+                                               d_status);
+        note_launch();
+        kern<<<1, NW * 32, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, d_status, pflag, mP,
+                                     nfallback, tri, tri + m, tri + 2 * m, m, tri + 3 * m, mx);
+        note_launch();
+        k_rr_back<T, EV_MMAX / 32><<<K, 32, 0, st>>>(m, K, mx, Ag, m, tri + 2 * m, Zg, Y, pflag,
+                                                     nfallback);
+        note_launch();
+        e = cudaGetLastError();
+      }
+      al.put(mx);
+      al.put(tri);
+      al.put(Ag);
+      return e;
+    }
+  }
   // FP32 with the matrix in global memory: the tridiagonalization runs on a cluster of CTAs
   // holding the matrix in registers (k_tridiag_cl), the other phases here
   T* tri = nullptr;
@@ -2117,7 +2263,7 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
     ProfScope ps(st, "rr_eig");
     kern<<<1, NW * 32, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, d_status, pflag, mP,
                                  nfallback, tri, tri ? tri + m : nullptr,
-                                 tri ? tri + 2 * m : nullptr, tri ? m : 0);
+                                 tri ? tri + 2 * m : nullptr, tri ? m : 0, nullptr, nullptr);
     note_launch();
     e = cudaGetLastError();
   }

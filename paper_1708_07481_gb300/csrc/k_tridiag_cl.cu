@@ -41,13 +41,21 @@ __device__ __forceinline__ void st_remote(float* p, int t, float v) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(t));
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
 }
+__device__ __forceinline__ void st_remote(double* p, int t, double v) {
+  uint32_t a = (uint32_t)__cvta_generic_to_shared(p), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(t));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 // Cluster-wide barrier; its release / acquire orders the distributed shared memory stores.
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" :::
                    "memory");
 }
 
-__device__ __forceinline__ float hw_sum(float v) {
+template <typename T>
+__device__ __forceinline__ T hw_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -56,28 +64,29 @@ __device__ __forceinline__ float hw_sum(float v) {
 // Ag[i][j] = 0.5 (G_ij + G_ji) in FP32 (i, j < m): the cluster kernel's input, read back row
 // by row with coalesced loads.  The same buffer then receives the reflector rows; the cluster
 // barrier after the load separates the two uses.
-__global__ void k_sym_f32(int m, const double* __restrict__ G, int ldg, float* __restrict__ Ag,
-                          int lda) {
+template <typename T>
+__global__ void k_sym(int m, const double* __restrict__ G, int ldg, T* __restrict__ Ag, int lda) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)m * m;
        idx += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(idx / m), j = (int)(idx % m);
-    Ag[(long long)i * lda + j] = (float)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
+    Ag[(long long)i * lda + j] = (T)(0.5 * (G[(long long)i * ldg + j] + G[(long long)j * ldg + i]));
   }
 }
 
+template <typename T, int RS, int CS>
 __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const double* __restrict__ G,
-                                                  int ldg, float* __restrict__ Ag, int lda,
-                                                  float* __restrict__ d_out,
-                                                  float* __restrict__ e_out,
-                                                  float* __restrict__ b_out, const int* pflag,
+                                                  int ldg, T* __restrict__ Ag, int lda,
+                                                  T* __restrict__ d_out, T* __restrict__ e_out,
+                                                  T* __restrict__ b_out, const int* pflag,
                                                   int mP) {
+  constexpr int MMAX = TC_NH * RS;
   constexpr unsigned FULL = 0xffffffffu;
-  __shared__ float xs[TC_MMAX];      // x of the current step (every row)
-  __shared__ float pvec[TC_MMAX];    // p of the current step (every row)
-  __shared__ float rs2all[TC_NH];    // per-warp partial sums of x_i^2
-  __shared__ float rpvall[TC_NH];    // per-warp partial sums of p_i v_i
-  __shared__ float gmx[TC_CL];       // per-CTA Gershgorin partial maxima
-  __shared__ float wmax[TC_NW];
+  __shared__ T xs[MMAX];      // x of the current step (every row)
+  __shared__ T pvec[MMAX];    // p of the current step (every row)
+  __shared__ T rs2all[TC_NH];    // per-warp partial sums of x_i^2
+  __shared__ T rpvall[TC_NH];    // per-warp partial sums of p_i v_i
+  __shared__ T gmx[TC_CL];       // per-CTA Gershgorin partial maxima
+  __shared__ T wmax[TC_NW];
   unsigned rank_u;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank_u));
   const int rank = (int)rank_u;
@@ -86,40 +95,40 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
   const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
 
   // ---- load (symmetrized), Gershgorin bound over the cluster, lift dropped columns
-  float A[TC_RS][TC_CS];
-  float gm = 0.f;
+  T A[RS][CS];
+  T gm = (T)0;
 #pragma unroll
-  for (int r = 0; r < TC_RS; ++r) {
+  for (int r = 0; r < RS; ++r) {
     const int i = h + TC_NH * r;
-    float rs = 0.f;
+    T rs = (T)0;
 #pragma unroll
-    for (int c = 0; c < TC_CS; ++c) {
+    for (int c = 0; c < CS; ++c) {
       const int j = cl + 32 * c;
-      float a = 0.f;
+      T a = (T)0;
       if (i < m && j < m) a = Ag[(long long)i * lda + j];  // symmetrized FP32 copy of G
       A[r][c] = a;
-      rs += fabsf(a);
+      rs += fabs(a);
     }
-    gm = fmaxf(gm, hw_sum(rs));
+    gm = fmax(gm, hw_sum(rs));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(FULL, gm, o));
+  for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(FULL, gm, o));
   if (lane == 0) wmax[warp] = gm;
   __syncthreads();
   if (tid == 0) {
-    float mx = 0.f;
-    for (int w = 0; w < TC_NW; ++w) mx = fmaxf(mx, wmax[w]);
+    T mx = (T)0;
+    for (int w = 0; w < TC_NW; ++w) mx = fmax(mx, wmax[w]);
     for (int t = 0; t < TC_CL; ++t) st_remote(&gmx[rank], t, mx);
   }
   cluster_sync();
   {
-    float big = 0.f;
-    for (int t = 0; t < TC_CL; ++t) big = fmaxf(big, gmx[t]);
-    big = big * 1.25f + 1.f;
+    T big = (T)0;
+    for (int t = 0; t < TC_CL; ++t) big = fmax(big, gmx[t]);
+    big = big * (T)1.25 + (T)1;
 #pragma unroll
-    for (int r = 0; r < TC_RS; ++r)
+    for (int r = 0; r < RS; ++r)
 #pragma unroll
-      for (int c = 0; c < TC_CS; ++c) {
+      for (int c = 0; c < CS; ++c) {
         const int i = h + TC_NH * r, j = cl + 32 * c;
         if (i == j && i >= K && i < m && G[(long long)i * ldg + i] == 0.0) A[r][c] = big;
       }
@@ -128,7 +137,7 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
   // ---- the Householder steps
   bool stop = false;
 #pragma unroll
-  for (int q = 0; q < TC_CS; ++q) {
+  for (int q = 0; q < CS; ++q) {
     if (stop) break;
     const int r0 = q >> 2;  // row slot r holds rows 128 r .. 128 r + 127, dead once k >= 128 r + 127
     for (int kw = 0; kw < 32; ++kw) {
@@ -140,33 +149,33 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
       const int k1 = k + 1;
       // (a)
       if (cl == kw) {
-        float s2 = 0.f;
+        T s2 = (T)0;
 #pragma unroll
-        for (int r = 0; r < TC_RS; ++r) {
+        for (int r = 0; r < RS; ++r) {
           const int i = h + TC_NH * r;
-          const float x = A[r][q];
-          const float val = i > k ? x : 0.f;
+          const T x = A[r][q];
+          const T val = i > k ? x : (T)0;
           for (int t = 0; t < TC_CL; ++t) st_remote(&xs[i], t, val);
-          s2 = fmaf(i > k1 ? x : 0.f, x, s2);
+          s2 = fma(i > k1 ? x : (T)0, x, s2);
         }
         for (int t = 0; t < TC_CL; ++t) st_remote(&rs2all[h], t, s2);
         if (h == (k & (TC_NH - 1))) d_out[k] = A[q >> 2][q];
       }
       cluster_sync();
       // (b)
-      float sg = 0.f;
+      T sg = (T)0;
 #pragma unroll
       for (int j = 0; j < TC_NH / 32; ++j) sg += rs2all[lane + 32 * j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(FULL, sg, o);
-      const float x0 = xs[k1];
-      float bet = 0.f, iv0 = 0.f, ek = x0;
-      if (sg != 0.f) {
-        const float mu = sqrtf(x0 * x0 + sg);
-        const float v0 = x0 + copysignf(mu, x0);
-        iv0 = __frcp_rn(v0);
-        bet = 2.f * __frcp_rn(1.f + sg * iv0 * iv0);
-        ek = -copysignf(mu, x0);
+      const T x0 = xs[k1];
+      T bet = (T)0, iv0 = (T)0, ek = x0;
+      if (sg != (T)0) {
+        const T mu = sqrt(x0 * x0 + sg);
+        const T v0 = x0 + copysign(mu, x0);
+        iv0 = rcp_rn(v0);
+        bet = (T)2 * rcp_rn((T)1 + sg * iv0 * iv0);
+        ek = -copysign(mu, x0);
       }
       if (rank == 0 && tid == 0) {
         e_out[k] = ek;
@@ -174,70 +183,70 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
       }
       // v on the owned columns is re-read from xs where it is needed (registers hold A)
       auto vcol = [&](int c) {
-        const float v = xs[cl + 32 * c] * iv0;
-        return (c <= q + 1 && cl + 32 * c == k1) ? 1.f : v;
+        const T v = xs[cl + 32 * c] * iv0;
+        return (c <= q + 1 && cl + 32 * c == k1) ? (T)1 : v;
       };
-      float vr[TC_RS], pr[TC_RS];
+      T vr[RS], pr[RS];
 #pragma unroll
-      for (int r = 0; r < TC_RS; ++r) {
+      for (int r = 0; r < RS; ++r) {
         const int i = h + TC_NH * r;
-        vr[r] = i == k1 ? 1.f : xs[i] * iv0;
+        vr[r] = i == k1 ? (T)1 : xs[i] * iv0;
       }
       // (c)
-      float sacc[TC_RS];
+      T sacc[RS];
 #pragma unroll
-      for (int r = 0; r < TC_RS; ++r) sacc[r] = 0.f;
+      for (int r = 0; r < RS; ++r) sacc[r] = (T)0;
 #pragma unroll
-      for (int c = q; c < TC_CS; ++c) {
-        const float vc = vcol(c);
+      for (int c = q; c < CS; ++c) {
+        const T vc = vcol(c);
 #pragma unroll
-        for (int r = r0; r < TC_RS; ++r) sacc[r] = fmaf(A[r][c], vc, sacc[r]);
+        for (int r = r0; r < RS; ++r) sacc[r] = fma(A[r][c], vc, sacc[r]);
       }
-      float pvp = 0.f;
+      T pvp = (T)0;
 #pragma unroll
-      for (int r = r0; r < TC_RS; ++r) {
+      for (int r = r0; r < RS; ++r) {
         pr[r] = bet * hw_sum(sacc[r]);
-        pvp = fmaf(pr[r], vr[r], pvp);
+        pvp = fma(pr[r], vr[r], pvp);
       }
       if (cl == 0) {
 #pragma unroll
-        for (int r = r0; r < TC_RS; ++r)
+        for (int r = r0; r < RS; ++r)
           for (int t = 0; t < TC_CL; ++t) st_remote(&pvec[h + TC_NH * r], t, pr[r]);
         for (int t = 0; t < TC_CL; ++t) st_remote(&rpvall[h], t, pvp);
       }
       if (cl == kw) {
         // the scaled reflector: row k of Ag holds v_i for i > k + 1 (v_{k+1} = 1 is implied)
 #pragma unroll
-        for (int r = r0; r < TC_RS; ++r) {
+        for (int r = r0; r < RS; ++r) {
           const int i = h + TC_NH * r;
           if (i > k1 && i < m) Ag[(long long)k * lda + i] = A[r][q] * iv0;
         }
       }
       cluster_sync();
       // (d)
-      float pv = 0.f;
+      T pv = (T)0;
 #pragma unroll
       for (int j = 0; j < TC_NH / 32; ++j) pv += rpvall[lane + 32 * j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(FULL, pv, o);
-      const float kc = bet * 0.5f * pv;
-      float wr[TC_RS];
+      const T kc = bet * (T)0.5 * pv;
+      T wr[RS];
 #pragma unroll
-      for (int r = r0; r < TC_RS; ++r) wr[r] = fmaf(-kc, vr[r], pr[r]);
+      for (int r = r0; r < RS; ++r) wr[r] = fma(-kc, vr[r], pr[r]);
 #pragma unroll
-      for (int c = q; c < TC_CS; ++c) {
-        const float vc = vcol(c);
-        const float wj = fmaf(-kc, vc, pvec[cl + 32 * c]);
+      for (int c = q; c < CS; ++c) {
+        const T vc = vcol(c);
+        const T wj = fma(-kc, vc, pvec[cl + 32 * c]);
 #pragma unroll
-        for (int r = r0; r < TC_RS; ++r) A[r][c] = fmaf(-vr[r], wj, fmaf(-wr[r], vc, A[r][c]));
+        for (int r = r0; r < RS; ++r) A[r][c] = fma(-vr[r], wj, fma(-wr[r], vc, A[r][c]));
       }
     }
   }
   // the trailing 2 x 2 block of T (or the 1 x 1 matrix), from the owners of its entries
 #pragma unroll
-  for (int r = 0; r < TC_RS; ++r)
+  for (int r = 0; r < RS; ++r)
 #pragma unroll
-    for (int c = 0; c < TC_CS; ++c) {
+    for (int c = 0; c < CS; ++c) {
       const int i = h + TC_NH * r, j = cl + 32 * c;
       if (m >= 2) {
         if (i == m - 2 && j == m - 2) d_out[m - 2] = A[r][c];
@@ -247,23 +256,26 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
         d_out[0] = A[r][c];
       }
     }
-  if (rank == 0 && tid == 0 && m >= 1) e_out[m - 1] = 0.f;
+  if (rank == 0 && tid == 0 && m >= 1) e_out[m - 1] = (T)0;
   cluster_sync();  // no CTA leaves while another may still touch its shared memory
 }
 
+// FP32 for m <= 512 (4 row slots, 16 column slots); FP64 for m <= 256 (2 and 8: the FP64
+// entries take two registers each).
+template <typename T, int RS, int CS>
 __global__ void __launch_bounds__(TC_NW * 32, 1)
-    k_tridiag_cl(int m_full, int K, const double* __restrict__ G, int ldg, float* __restrict__ Ag,
-                 int lda, float* __restrict__ d_out, float* __restrict__ e_out,
-                 float* __restrict__ b_out, const int* pflag, int mP) {
-  k_tridiag_cl_body(m_full, K, G, ldg, Ag, lda, d_out, e_out, b_out, pflag, mP);
+    k_tridiag_cl(int m_full, int K, const double* __restrict__ G, int ldg, T* __restrict__ Ag,
+                 int lda, T* __restrict__ d_out, T* __restrict__ e_out, T* __restrict__ b_out,
+                 const int* pflag, int mP) {
+  k_tridiag_cl_body<T, RS, CS>(m_full, K, G, ldg, Ag, lda, d_out, e_out, b_out, pflag, mP);
 }
 
 // Lockstep batch: cluster c of the grid (TC_CL CTAs) tridiagonalizes descriptor c's matrix;
 // the reflector rows go to its Ag (stride m), d, e, beta to its tri.
 __global__ void __launch_bounds__(TC_NW * 32, 1) k_tridiag_cl_b(const RrDesc* __restrict__ tab) {
   const RrDesc a = tab[blockIdx.x / TC_CL];
-  k_tridiag_cl_body(a.m, a.K, a.G, a.ldg, a.Ag, a.m, a.tri, a.tri + a.m, a.tri + 2 * a.m,
-                    a.pflag, a.mP);
+  k_tridiag_cl_body<float, TC_RS, TC_CS>(a.m, a.K, a.G, a.ldg, a.Ag, a.m, a.tri, a.tri + a.m,
+                                         a.tri + 2 * a.m, a.pflag, a.mP);
 }
 
 // Lockstep batch: blockIdx.y = descriptor; its symmetrized FP32 matrix into Ag (stride m).
@@ -280,12 +292,16 @@ __global__ void k_sym_f32_b(const RrDesc* __restrict__ tab) {
 
 }  // namespace
 
-// Tridiagonalization of the symmetric m x m FP64 matrix G (m <= 512, symmetrized on the fly) on
-// one cluster of 8 CTAs: d, e (m floats each), beta (m) and the scaled reflectors in rows
-// 0 .. m - 3 of Ag (row stride lda), as the single-CTA Rayleigh-Ritz kernel expects them.
-cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int ldg, float* Ag,
-                            int lda, float* d, float* e, float* beta, const int* pflag, int mP) {
-  if (m < 1 || m > TC_MMAX) return cudaErrorInvalidValue;
+// Tridiagonalization of the symmetric m x m FP64 matrix G (symmetrized on the fly) on one
+// cluster of 8 CTAs, in the arithmetic of T (FP32: m <= 512; FP64: m <= 256): d, e (m each),
+// beta (m) and the scaled reflectors in rows 0 .. m - 3 of Ag (row stride lda), as the
+// register-slot Rayleigh-Ritz kernel takes them in its external-input mode.
+template <typename T>
+static cudaError_t tridiag_cluster_t(cudaStream_t st, int m, int K, const double* G, int ldg,
+                                     T* Ag, int lda, T* d, T* e, T* beta, const int* pflag,
+                                     int mP) {
+  constexpr bool f32 = sizeof(T) == 4;
+  if (m < 1 || m > (f32 ? TC_NH * TC_RS : TC_NH * 2)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(TC_CL, 1, 1);
   cfg.blockDim = dim3(TC_NW * 32, 1, 1);
@@ -299,14 +315,28 @@ cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   ProfScope ps(st, "rr_eig");
-  k_sym_f32<<<(unsigned)std::min<long long>(((long long)m * m + 255) / 256, 1024), 256, 0, st>>>(
+  k_sym<T><<<(unsigned)std::min<long long>(((long long)m * m + 255) / 256, 1024), 256, 0, st>>>(
       m, G, ldg, Ag, lda);
   note_launch();
   cudaError_t e0 = cudaGetLastError();
   if (e0 != cudaSuccess) return e0;
-  e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl, m, K, G, ldg, Ag, lda, d, e, beta, pflag, mP);
+  if constexpr (f32)
+    e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl<float, TC_RS, TC_CS>, m, K, G, ldg, Ag, lda, d, e,
+                            beta, pflag, mP);
+  else
+    e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl<double, 2, 8>, m, K, G, ldg, Ag, lda, d, e, beta,
+                            pflag, mP);
   note_launch();
   return e0;
+}
+
+cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int ldg, float* Ag,
+                            int lda, float* d, float* e, float* beta, const int* pflag, int mP) {
+  return tridiag_cluster_t<float>(st, m, K, G, ldg, Ag, lda, d, e, beta, pflag, mP);
+}
+cudaError_t tridiag_cluster(cudaStream_t st, int m, int K, const double* G, int ldg, double* Ag,
+                            int lda, double* d, double* e, double* beta, const int* pflag, int mP) {
+  return tridiag_cluster_t<double>(st, m, K, G, ldg, Ag, lda, d, e, beta, pflag, mP);
 }
 
 // The same for every descriptor of a lockstep batch (m <= mmax <= 512 each): one launch of
