@@ -432,7 +432,24 @@ __device__ void lift_dropped(int m, int K, const double* __restrict__ G, int ldg
 
 // ---------------------------------------------------------------------------------------
 __device__ inline float sdiv(float a, float b) { return __fdividef(a, b); }
-__device__ inline double sdiv(double a, double b) { return a / b; }
+// 1 / b in FP64 from the hardware's reciprocal estimate (rcp.approx.ftz.f64) refined by two
+// steps of Newton's iteration for the reciprocal, r <- r + r (1 - b r), each of which about
+// doubles the correct bits: a few FP64 FMAs instead of an IEEE division, which matters at
+// GB300's FP64 rate.  Not correctly rounded (within a few ulps); b must be normal.
+__device__ __forceinline__ double rcp_newton(double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  r = fma(r, fma(-b, r, 1.0), r);
+  r = fma(r, fma(-b, r, 1.0), r);
+  return r;
+}
+
+// FP64 a / b as a * (1 / b) by rcp_newton where b is a normal number (a few ulps; inverse
+// iteration and Sturm counts need no correctly rounded quotient), else an IEEE division.
+__device__ inline double sdiv(double a, double b) {
+  const double ab = fabs(b);
+  return (ab >= 2.2250738585072014e-308 && ab <= 1e300) ? a * rcp_newton(b) : a / b;
+}
 
 template <typename T>
 __device__ int sturm_count(int m, const T* __restrict__ d, const T* __restrict__ e2, T x,
@@ -443,7 +460,9 @@ __device__ int sturm_count(int m, const T* __restrict__ d, const T* __restrict__
   if (q <= 0) ++c;
 #pragma unroll 4
   for (int i = 1; i < m; ++i) {
-    q = d[i] - x - sdiv(e2[i - 1], q);
+    // |q| > pivmin >= the smallest normal number: FP64 takes the Newton reciprocal unguarded
+    if constexpr (sizeof(T) == 8) q = d[i] - x - e2[i - 1] * rcp_newton(q);
+    else q = d[i] - x - sdiv(e2[i - 1], q);
     if (fabs(q) <= pivmin) q = -pivmin;
     if (q <= 0) ++c;
   }
@@ -1583,13 +1602,14 @@ __global__ void __launch_bounds__(NW * 32) k_rr_eig_reg_b(const RrDesc* __restri
 constexpr int EV_MMAX = 256;
 
 // Eigenvalue blockIdx.x of the tridiagonal T = (d, e) (m rows: m_full, less mP when *pflag is
-// 0) by 9-point multisection on Sturm counts with 8 lanes -- the arithmetic of rr_multisect --
-// after the Gershgorin bounds of rr_phase_eigvals, recomputed by every CTA.
+// 0) by 33-point multisection on Sturm counts with the 32 lanes of the CTA's warp (an FP64 warp
+// instruction costs the same with 8 lanes or 32), after the Gershgorin bounds of
+// rr_phase_eigvals, recomputed by every CTA.
 template <typename T>
 __global__ void __launch_bounds__(32)
     k_rr_eigvals_cta(int m_full, int K, int mP, const int* pflag, const T* __restrict__ d,
                      const T* __restrict__ e, T* __restrict__ lam, int* status) {
-  constexpr int LG = 8;
+  constexpr int LG = 32;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ T e2[EV_MMAX];
   const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
@@ -1617,13 +1637,13 @@ __global__ void __launch_bounds__(32)
   const T abstol = Lim<T>::eps() * tnorm;
   if (lane >= LG) return;
   const int sl = lane;
-  const unsigned gmask = (1u << LG) - 1u;
+  const unsigned gmask = 0xffffffffu;
   T a = glo, b = ghi;
   for (int it = 0; it < 64; ++it) {
     T tol = max((T)2 * Lim<T>::eps() * max(fabs(a), fabs(b)), abstol) + (T)4 * pivmin;
     if (b - a <= tol) break;
     T h = (b - a) / (T)(LG + 1);
-    int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
+    const int c = sturm_count(m, d, e2, a + h * (T)(sl + 1), pivmin);
     unsigned bal = __ballot_sync(gmask, c > j);
     int first = bal ? (__ffs(bal) - 1) : LG;
     T na = first == 0 ? a : a + h * (T)first;
@@ -1653,24 +1673,37 @@ __global__ void __launch_bounds__(32)
     const int i = lane + 32 * u;
     za[u] = i < m ? Z[(long long)i * K + j] : (T)0;
   }
-  for (int kr = m - 3; kr >= 0; --kr) {
-    const T bet = beta[kr];
-    if (bet == (T)0) continue;
-    const int k1 = kr + 1;
+  // reflector kr: v_i = 1 at i = kr + 1, the stored row beyond, 0 before; the next one is
+  // loaded while the current one's dot product reduces
+  auto load_v = [&](int kr, T (&cv)[NS]) {
     const T* vk = Ag + (long long)kr * lda;
-    T cv[NS];
-    T sa = 0;
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
       const int i = lane + 32 * u;
-      cv[u] = (i == k1) ? (T)1 : ((i > k1 && i < m) ? vk[i] : (T)0);
-      sa = fma(cv[u], za[u], sa);
+      cv[u] = (i == kr + 1) ? (T)1 : ((i > kr + 1 && i < m) ? vk[i] : (T)0);
     }
+  };
+  T cv[NS], nv[NS];
+  if (m >= 3) load_v(m - 3, cv);
+  for (int kr = m - 3; kr >= 0; --kr) {
+    const T bet = beta[kr];
+    if (kr > 0) load_v(kr - 1, nv);
+    if (bet == (T)0) {
+#pragma unroll
+      for (int u = 0; u < NS; ++u) cv[u] = nv[u];
+      continue;
+    }
+    T sa = 0;
+#pragma unroll
+    for (int u = 0; u < NS; ++u) sa = fma(cv[u], za[u], sa);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(FULL, sa, o);
     sa *= bet;
 #pragma unroll
-    for (int u = 0; u < NS; ++u) za[u] = fma(-sa, cv[u], za[u]);
+    for (int u = 0; u < NS; ++u) {
+      za[u] = fma(-sa, cv[u], za[u]);
+      cv[u] = nv[u];
+    }
   }
 #pragma unroll
   for (int u = 0; u < NS; ++u) {

@@ -47,7 +47,14 @@ __device__ __forceinline__ void st_remote(double* p, int t, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
 }
 __device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+// FP64: the reciprocal estimate refined by two Newton steps r <- r + r (1 - x r) (within a few
+// ulps; the correctly rounded __drcp_rn is a long instruction sequence at the FP64 rate)
+__device__ __forceinline__ double rcp_rn(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
 // Cluster-wide barrier; its release / acquire orders the distributed shared memory stores.
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" :::
@@ -80,6 +87,9 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
                                                   T* __restrict__ b_out, const int* pflag,
                                                   int mP) {
   constexpr int MMAX = TC_NH * RS;
+  constexpr bool kF64 = sizeof(T) == 8;
+  __shared__ T vsc[kF64 ? MMAX : 1];  // FP64: the scaled reflector v of the step
+  __shared__ T sh_bet, sh_iv0, sh_kc;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ T xs[MMAX];      // x of the current step (every row)
   __shared__ T pvec[MMAX];    // p of the current step (every row)
@@ -163,26 +173,47 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
       }
       cluster_sync();
       // (b)
-      T sg = (T)0;
+      T bet = (T)0, iv0 = (T)0;
+      auto scalars = [&]() {
+        T sg = (T)0;
 #pragma unroll
-      for (int j = 0; j < TC_NH / 32; ++j) sg += rs2all[lane + 32 * j];
+        for (int j = 0; j < TC_NH / 32; ++j) sg += rs2all[lane + 32 * j];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(FULL, sg, o);
-      const T x0 = xs[k1];
-      T bet = (T)0, iv0 = (T)0, ek = x0;
-      if (sg != (T)0) {
-        const T mu = sqrt(x0 * x0 + sg);
-        const T v0 = x0 + copysign(mu, x0);
-        iv0 = rcp_rn(v0);
-        bet = (T)2 * rcp_rn((T)1 + sg * iv0 * iv0);
-        ek = -copysign(mu, x0);
-      }
-      if (rank == 0 && tid == 0) {
-        e_out[k] = ek;
-        b_out[k] = bet;
+        for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(FULL, sg, o);
+        const T x0 = xs[k1];
+        T ek = x0;
+        if (sg != (T)0) {
+          const T mu = sqrt(x0 * x0 + sg);
+          const T v0 = x0 + copysign(mu, x0);
+          iv0 = rcp_rn(v0);
+          bet = (T)2 * rcp_rn((T)1 + sg * iv0 * iv0);
+          ek = -copysign(mu, x0);
+        }
+        if (rank == 0 && tid == 0) {
+          e_out[k] = ek;
+          b_out[k] = bet;
+        }
+      };
+      if constexpr (kF64) {
+        // FP64 runs at 2 FMA per clock per SM: warp 0 forms the reflector scalars and the
+        // scaled v once for the CTA instead of every thread doing so
+        if (warp == 0) {
+          scalars();
+          if (lane == 0) {
+            sh_bet = bet;
+            sh_iv0 = iv0;
+          }
+          for (int i = lane; i < MMAX; i += 32) vsc[i] = i == k1 ? (T)1 : xs[i] * iv0;
+        }
+        __syncthreads();
+        bet = sh_bet;
+        iv0 = sh_iv0;
+      } else {
+        scalars();
       }
       // v on the owned columns is re-read from xs where it is needed (registers hold A)
       auto vcol = [&](int c) {
+        if constexpr (kF64) return vsc[cl + 32 * c];
         const T v = xs[cl + 32 * c] * iv0;
         return (c <= q + 1 && cl + 32 * c == k1) ? (T)1 : v;
       };
@@ -190,7 +221,8 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
 #pragma unroll
       for (int r = 0; r < RS; ++r) {
         const int i = h + TC_NH * r;
-        vr[r] = i == k1 ? (T)1 : xs[i] * iv0;
+        if constexpr (kF64) vr[r] = vsc[i];
+        else vr[r] = i == k1 ? (T)1 : xs[i] * iv0;
       }
       // (c)
       T sacc[RS];
@@ -200,7 +232,8 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
       for (int c = q; c < CS; ++c) {
         const T vc = vcol(c);
 #pragma unroll
-        for (int r = r0; r < RS; ++r) sacc[r] = fma(A[r][c], vc, sacc[r]);
+        for (int r = r0; r < RS; ++r)
+          if (h + TC_NH * r < m) sacc[r] = fma(A[r][c], vc, sacc[r]);  // rows >= m stay zero
       }
       T pvp = (T)0;
 #pragma unroll
@@ -224,12 +257,25 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
       }
       cluster_sync();
       // (d)
-      T pv = (T)0;
+      auto pvsum = [&]() {
+        T pv = (T)0;
 #pragma unroll
-      for (int j = 0; j < TC_NH / 32; ++j) pv += rpvall[lane + 32 * j];
+        for (int j = 0; j < TC_NH / 32; ++j) pv += rpvall[lane + 32 * j];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(FULL, pv, o);
-      const T kc = bet * (T)0.5 * pv;
+        for (int o = 16; o > 0; o >>= 1) pv += __shfl_xor_sync(FULL, pv, o);
+        return bet * (T)0.5 * pv;
+      };
+      T kc;
+      if constexpr (kF64) {
+        if (warp == 0) {
+          const T t = pvsum();
+          if (lane == 0) sh_kc = t;
+        }
+        __syncthreads();
+        kc = sh_kc;
+      } else {
+        kc = pvsum();
+      }
       T wr[RS];
 #pragma unroll
       for (int r = r0; r < RS; ++r) wr[r] = fma(-kc, vr[r], pr[r]);
@@ -238,7 +284,8 @@ __device__ __forceinline__ void k_tridiag_cl_body(int m_full, int K, const doubl
         const T vc = vcol(c);
         const T wj = fma(-kc, vc, pvec[cl + 32 * c]);
 #pragma unroll
-        for (int r = r0; r < RS; ++r) A[r][c] = fma(-vr[r], wj, fma(-wr[r], vc, A[r][c]));
+        for (int r = r0; r < RS; ++r)
+          if (h + TC_NH * r < m) A[r][c] = fma(-vr[r], wj, fma(-wr[r], vc, A[r][c]));
       }
     }
   }
@@ -323,6 +370,9 @@ static cudaError_t tridiag_cluster_t(cudaStream_t st, int m, int K, const double
   if constexpr (f32)
     e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl<float, TC_RS, TC_CS>, m, K, G, ldg, Ag, lda, d, e,
                             beta, pflag, mP);
+  else if (m <= 160)  // FP64 pays for every column slot: the narrowest shape that holds m
+    e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl<double, 2, 5>, m, K, G, ldg, Ag, lda, d, e, beta,
+                            pflag, mP);
   else
     e0 = cudaLaunchKernelEx(&cfg, k_tridiag_cl<double, 2, 8>, m, K, G, ldg, Ag, lda, d, e, beta,
                             pflag, mP);
