@@ -61,19 +61,22 @@ def test_inject_rejects_bad_arguments(sc, ctx):
         assert e.value.code == sc.SC_EINVAL
 
 
+@pytest.mark.parametrize("K", [11, 24])
 @pytest.mark.parametrize("prec", [0, 2])
-def test_direction_block_breakdown_falls_back_like_the_oracle(sc, ctx, monkeypatch, prec):
+def test_direction_block_breakdown_falls_back_like_the_oracle(sc, ctx, monkeypatch, prec, K):
     """Pass 5 reports its direction block P as broken down: that pass's Rayleigh-Ritz step runs
     on [X R] (one fallback), the next P is R Y_R, and the iteration carries on.  The oracle with
-    the same breakdown planted (its Cholesky-QR of P raises at pass 5) gives the same result."""
+    the same breakdown planted (its Cholesky-QR of P raises at pass 5) gives the same result.
+    K = 24 (m = 72) takes the FP64 Rayleigh-Ritz spread over SMs, whose last kernel re-arms
+    the breakdown flag."""
     import oracle.spectral as OS
 
-    g = W.dcsbm(3000, 11, seed=5)
+    g = W.dcsbm(3000, K, seed=5)
     L = O.laplacian_csr(g.n, g.src, g.dst)
     G = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
-    X0 = W.start_block(2, g.n, 11)
+    X0 = W.start_block(2, g.n, K)
     sc.sc_debug_inject(ctx, sc.SC_INJECT_P_BREAKDOWN, 4)  # the 5th pass (0-based 4)
-    lam, resid, X, info = sc.sc_lobpcg(ctx, G, 11, iters=12, prec=prec, X0=X0)
+    lam, resid, X, info = sc.sc_lobpcg(ctx, G, K, iters=12, prec=prec, X0=X0)
     sc.sc_debug_inject(ctx, sc.SC_INJECT_NONE)
     assert info["fallbacks"] == 1 and info["iters_done"] == 12
     # the Cholesky-QR calls made by lobpcg itself: two for the start block, then one for P in
