@@ -302,9 +302,11 @@ __device__ int ldl_inv_reg(int n, float* M, int ldm, float* dd, float* buf, floa
         }
       }
       if (g == k1 % NHW) {
+        // row k + 1 = 16 q + kw + 1 lies in slot (16 q + kw + 1) / NHW: at most 16 / NHW slots
+        // past r0 = 16 q / NHW, so only those are tested
         const int rk = k1 / NHW;
 #pragma unroll
-        for (int r = r0; r < RS; ++r)
+        for (int r = r0; r < RS && r <= r0 + 16 / NHW; ++r)
           if (r == rk) {
 #pragma unroll
             for (int c = 0; c < CS; ++c)

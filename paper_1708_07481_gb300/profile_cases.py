@@ -1,6 +1,7 @@
 """Small, self-contained cases for kernel profiling (ncu -k / -c on one kernel).
 
     python -m paper_1708_07481_gb300.profile_cases rr    # 3 Rayleigh-Ritz solves, m = 132, K = 44
+    python -m paper_1708_07481_gb300.profile_cases rr64  # the same in FP64 (spread over SMs)
     python -m paper_1708_07481_gb300.profile_cases lob   # 3 LOBPCG passes, DC-SBM n = 50,000, K = 44
     python -m paper_1708_07481_gb300.profile_cases big   # 2 LOBPCG passes, DC-SBM n = 300,000, K = 160
     python -m paper_1708_07481_gb300.profile_cases kmeans  # k-means, 50,000 unit rows, d = k = 44
@@ -23,15 +24,16 @@ from . import workload as W
 def main(argv=None):
     mode = (argv or sys.argv[1:] or ["rr"])[0]
     ctx = sc.sc_ctx_create(0)
-    if mode == "rr":
+    if mode in ("rr", "rr64"):
         rng = np.random.default_rng(0)
         m, K = 132, 44
         ev = np.concatenate([np.sort(rng.uniform(0, 12, K)),
                              np.sort(rng.uniform(10, 200, m - K))])
         Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
         G = (Q * ev) @ Q.T
+        prec = sc.SC_PREC_FP32 if mode == "rr" else sc.SC_PREC_FP64
         for _ in range(3):
-            sc.sc_rr_solve(ctx, G, K, sc.SC_PREC_FP32)
+            sc.sc_rr_solve(ctx, G, K, prec)
     elif mode == "lob":
         g = W.dcsbm(50000, 44, seed=0)
         Gr = sc.sc_build_laplacian(ctx, g.n, g.src, g.dst)
@@ -52,7 +54,7 @@ def main(argv=None):
         for _ in range(2):
             sc.sc_kmeans(ctx, E, 44, iters=50, seed=5)
     else:
-        raise SystemExit(f"unknown case {mode!r}: rr, lob, big or kmeans")
+        raise SystemExit(f"unknown case {mode!r}: rr, rr64, lob, big or kmeans")
     print("ok", mode)
 
 
