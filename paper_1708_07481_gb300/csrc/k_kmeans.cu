@@ -78,36 +78,93 @@ __global__ void k_pp_first(int n, const double* u, int* seeds, int* chosen) {
   }
 }
 
+// Shared memory of the D2 update: the seed row in FP64 (cs, d) and FP32 (cs32), block-sum slots
+// (sh, 40), the rows' new FP64 distances (dv, PB) and the list of rows to compute (lst, PB + 1).
+struct PpSmem {
+  double *cs, *sh, *dv;
+  float* cs32;
+  int* lst;
+};
+__host__ __device__ inline size_t pp_smem_bytes(int d) {
+  return sizeof(double) * ((size_t)d + 40 + PB) + sizeof(float) * (size_t)((d + 1) & ~1) +
+         sizeof(int) * (PB + 1);
+}
+__device__ inline PpSmem pp_smem(void* raw, int d) {
+  PpSmem m;
+  m.cs = (double*)raw;
+  m.sh = m.cs + d;
+  m.dv = m.sh + 40;
+  m.cs32 = (float*)(m.dv + PB);
+  m.lst = (int*)(m.cs32 + ((d + 1) & ~1));
+  return m;
+}
+
 // Block b of the D2 update: D2_i <- min(D2_i, ||E_i - c||^2) for the PB rows of block b, c in
-// cs (FP64), and the block's sum into bsum[b].
+// cs (FP64), and the block's sum into bsum[b].  After the first round a row is screened first
+// with its FP32 distance s: with unit rounding u = 2^-24, the FP32 sum of d squared differences
+// is within a relative gamma = (d + 2) u of the exact one (all terms are nonnegative), so when
+// s (1 - 2 gamma) > D2_i the exact distance exceeds D2_i and the row keeps D2_i.  The other rows
+// get the FP64 distance, gathered into a list so that the FP64 warp instructions (GB300 runs an
+// FP64 warp instruction at 2 FMA per clock per SM, lanes masked off or not) run on full warps.
+// Every row ends with the value the plain FP64 update gives.
 __device__ __forceinline__ void pp_update_block(int b, int n, int d, const float* __restrict__ E,
-                                                long long lde, int t, const double* cs,
-                                                double* sh, double* D2, double* bsum) {
-  long long i = (long long)b * PB + threadIdx.x;
-  double v = 0.0;
+                                                long long lde, int t, const PpSmem& sm,
+                                                double* D2, double* bsum) {
+  const long long i = (long long)b * PB + threadIdx.x;
+  if (threadIdx.x == 0) sm.lst[PB] = 0;
+  __syncthreads();
+  double old = 0.0;
+  bool need = false;
   if (i < n) {
-    const float* e = E + i * lde;
+    if (t == 0) {
+      need = true;
+    } else {
+      old = D2[i];
+      const float* e = E + i * lde;
+      float sf = 0.f;
+      for (int c = 0; c < d; ++c) {
+        const float df = e[c] - sm.cs32[c];
+        sf = fmaf(df, df, sf);
+      }
+      const double gam = (double)(d + 2) * 0x1p-24;
+      need = !((double)sf * (1.0 - 2.0 * gam) > old);
+    }
+  }
+  if (need) sm.lst[atomicAdd(&sm.lst[PB], 1)] = threadIdx.x;
+  __syncthreads();
+  const int cnt = sm.lst[PB];
+  for (int q = threadIdx.x; q < cnt; q += PB) {
+    const int r = sm.lst[q];
+    const long long ii = (long long)b * PB + r;
+    const float* e = E + ii * lde;
     double acc = 0.0;
     for (int c = 0; c < d; ++c) {
-      double df = (double)e[c] - cs[c];
+      double df = (double)e[c] - sm.cs[c];
       acc = fma(df, df, acc);
     }
-    v = (t == 0) ? acc : fmin(D2[i], acc);
-    D2[i] = v;
+    const double nv = (t == 0) ? acc : fmin(D2[ii], acc);
+    D2[ii] = nv;
+    sm.dv[r] = nv;
   }
-  double bs = block_sum_d(v, sh);
+  __syncthreads();
+  const double v = i < n ? (need ? sm.dv[threadIdx.x] : old) : 0.0;
+  double bs = block_sum_d(v, sm.sh);
   if (threadIdx.x == 0) bsum[b] = bs;
 }
 
 __global__ void __launch_bounds__(PB)
     k_pp_update(int n, int d, const float* __restrict__ E, long long lde, const int* seeds, int t,
                 double* D2, double* bsum) {
-  extern __shared__ double cs[];  // d + 33
-  double* sh = cs + d;
+  extern __shared__ double pp_raw[];  // pp_smem_bytes(d)
+  const PpSmem sm = pp_smem(pp_raw, d);
   const int s = seeds[t];
-  for (int c = threadIdx.x; c < d; c += blockDim.x) cs[c] = (double)E[(long long)s * lde + c];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    const float x = E[(long long)s * lde + c];
+    sm.cs[c] = (double)x;
+    sm.cs32[c] = x;
+  }
   __syncthreads();
-  pp_update_block(blockIdx.x, n, d, E, lde, t, cs, sh, D2, bsum);
+  pp_update_block(blockIdx.x, n, d, E, lde, t, sm, D2, bsum);
 }
 
 // The pick of round t by one CTA of PB threads.  D2 and the block sums are read through L2
@@ -232,8 +289,8 @@ __device__ bool grid_barrier(unsigned* bar, int* flag) {
 __global__ void __launch_bounds__(PB)
     k_pp_all(int n, int d, int k, const float* __restrict__ E, long long lde, const double* u,
              int* seeds, int* chosen, double* D2, double* bsum, unsigned* bar, int* flag) {
-  extern __shared__ double cs[];  // d + 40
-  double* sh = cs + d;
+  extern __shared__ double pp_raw[];  // pp_smem_bytes(d)
+  const PpSmem sm = pp_smem(pp_raw, d);
   const int nb = (n + PB - 1) / PB;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     long long i = (long long)floor(u[0] * (double)n);
@@ -245,10 +302,14 @@ __global__ void __launch_bounds__(PB)
   if (!grid_barrier(bar, flag)) return;
   for (int t = 0; t + 1 < k; ++t) {
     const int sd = __ldcg(seeds + t);
-    for (int c = threadIdx.x; c < d; c += PB) cs[c] = (double)E[(long long)sd * lde + c];
+    for (int c = threadIdx.x; c < d; c += PB) {
+      const float x = E[(long long)sd * lde + c];
+      sm.cs[c] = (double)x;
+      sm.cs32[c] = x;
+    }
     __syncthreads();
     for (int b = blockIdx.x; b < nb; b += gridDim.x)
-      pp_update_block(b, n, d, E, lde, t, cs, sh, D2, bsum);
+      pp_update_block(b, n, d, E, lde, t, sm, D2, bsum);
     if (!grid_barrier(bar, flag)) return;
     if (blockIdx.x == 0) pp_pick_body(n, nb, D2, bsum, u, t + 1, seeds, chosen);
     if (!grid_barrier(bar, flag)) return;
@@ -539,7 +600,7 @@ cudaError_t kmeanspp(cudaStream_t st, Alloc& al, int n, int d, int k, const floa
   } else {
     cudaMemcpyAsync(u, u_host, sizeof(double) * k, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(chosen, 0, sizeof(int) * n, st);
-    size_t sm = sizeof(double) * (d + 40);
+    size_t sm = pp_smem_bytes(d);
     // one cooperative launch for every round when the device runs one (all CTAs resident)
     bool persistent = false;
     if (bar) {
