@@ -339,12 +339,16 @@ constexpr int ACH = 64;  // centroids per shared-memory chunk in the assignment
 
 // One row per thread; the row lives in registers (D >= d, D a multiple of 4), the centroids
 // stream through shared memory in chunks of ACH.
-template <int D>
+// SUM: the CTA also forms its rows' per-cluster FP64 column sums and counts (the partial of the
+// centroid update, one per CTA of 256 rows, rows in order) into part / pcnt, so that no separate
+// pass over E is needed; its shared memory then holds the rows (256 d floats), the sums (k d
+// doubles), the labels and the counts after the centroid chunks.
+template <int D, bool SUM>
 __global__ void __launch_bounds__(256)
     k_assign(int n, int d, int k, const float* __restrict__ E, long long lde,
              const float* __restrict__ C32, const float* __restrict__ cn,
              const double* __restrict__ C64, int* labels, int* changes, int first, double tie,
-             const int* ctl) {
+             const int* ctl, double* part = nullptr, int* pcnt = nullptr) {
   if (ctl[0]) return;  // converged in an earlier round (uniform: written by an earlier kernel)
   extern __shared__ float csm[];  // ACH * D
   __shared__ int nchg;
@@ -431,23 +435,53 @@ __global__ void __launch_bounds__(256)
     if (first || old != bj) atomicAdd(&nchg, 1);
     labels[i] = bj;
   }
+  if constexpr (SUM) {
+    float* rows = csm + (size_t)ACH * D;                      // 256 x d
+    double* acc = reinterpret_cast<double*>(rows + 256 * d);  // k x d
+    int* lab = reinterpret_cast<int*>(acc + (size_t)k * d);   // 256
+    int* cnt = lab + 256;                                     // k
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      if (q < d) rows[t * d + q] = ev[q];
+    lab[t] = i < n ? bj : -1;
+    for (int q = t; q < k * d; q += 256) acc[q] = 0.0;
+    for (int j = t; j < k; j += 256) cnt[j] = 0;
+    __syncthreads();
+    if (i < n) atomicAdd(&cnt[bj], 1);  // integer counts: any order gives the same total
+    if (t < d) {
+      for (int r = 0; r < 256; ++r) {
+        const int l = lab[r];
+        if (l >= 0) acc[(size_t)l * d + t] += (double)rows[r * d + t];
+      }
+    }
+    __syncthreads();
+    double* pb = part + (size_t)blockIdx.x * k * d;
+    for (int q = t; q < k * d; q += 256) pb[q] = acc[q];
+    for (int j = t; j < k; j += 256) pcnt[(size_t)blockIdx.x * k + j] = cnt[j];
+  }
   __syncthreads();
   if (threadIdx.x == 0 && nchg) atomicAdd(changes, nchg);
 }
 
 using AssignFn = void (*)(int, int, int, const float*, long long, const float*, const float*,
-                          const double*, int*, int*, int, double, const int*);
+                          const double*, int*, int*, int, double, const int*, double*, int*);
 
-inline AssignFn assign_for(int d, int* D) {
-  if (d <= 16) { *D = 16; return k_assign<16>; }
-  if (d <= 32) { *D = 32; return k_assign<32>; }
-  if (d <= 48) { *D = 48; return k_assign<48>; }
-  if (d <= 64) { *D = 64; return k_assign<64>; }
-  if (d <= 96) { *D = 96; return k_assign<96>; }
-  if (d <= 128) { *D = 128; return k_assign<128>; }
-  if (d <= 192) { *D = 192; return k_assign<192>; }
-  *D = 512;
-  return k_assign<512>;
+inline AssignFn assign_for(int d, int* D, bool sum) {
+#define SC_ASSIGN_PICK(DD)                                          \
+  {                                                                 \
+    *D = DD;                                                        \
+    return sum ? k_assign<DD, true> : k_assign<DD, false>;          \
+  }
+  if (d <= 16) SC_ASSIGN_PICK(16)
+  if (d <= 32) SC_ASSIGN_PICK(32)
+  if (d <= 48) SC_ASSIGN_PICK(48)
+  if (d <= 64) SC_ASSIGN_PICK(64)
+  if (d <= 96) SC_ASSIGN_PICK(96)
+  if (d <= 128) SC_ASSIGN_PICK(128)
+  if (d <= 192) SC_ASSIGN_PICK(192)
+  SC_ASSIGN_PICK(512)
+#undef SC_ASSIGN_PICK
 }
 
 // Per-CTA FP64 cluster sums over a contiguous row range.  Rows pass through shared memory in
@@ -664,8 +698,10 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
   long long rpc = (n + nct - 1) / nct;
   nct = (n + rpc - 1) / rpc;
   if (nct < 1) nct = 1;
-  double* part = al.get<double>((size_t)nct * k * d);
-  int* pcnt = al.get<int>((size_t)nct * k);
+  const long long nab = (n + 255) / 256;  // assignment CTAs: the partials when they are fused
+  const long long npart = std::max(nct, nab);
+  double* part = al.get<double>((size_t)npart * k * d);
+  int* pcnt = al.get<int>((size_t)npart * k);
   double* ipart = al.get<double>(152);
   int* tstat = al.get<int>(1);  // time-outs of the tensor-core assignment's bounded waits
   // The assignment runs on tensor cores (assign_tc) for large n k d, or when SC_TUNE_ASSIGN=1;
@@ -682,8 +718,19 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
     k_init_cent<<<k, 128, 0, st>>>(d, k, E, lde, seeds, C64, C32, cn);
     note_launch();
     int Dp = 0;
-    AssignFn afn = assign_for(d, &Dp);
+    AssignFn afn = assign_for(d, &Dp, false);
     size_t asm_bytes = sizeof(float) * (size_t)ACH * Dp;
+    // The CUDA-core assignment also forms the centroid update's partial sums when its rows,
+    // the k x d FP64 sums, the labels and the counts fit beside the centroid chunks
+    const size_t fused_bytes = asm_bytes + sizeof(float) * 256 * (size_t)d +
+                               sizeof(double) * (size_t)k * d + sizeof(int) * (256 + (size_t)k);
+    const bool fuse = fused_bytes <= 100 * 1024;
+    AssignFn afn_sum = assign_for(d, &Dp, true);
+    if (fuse) {
+      e = cudaFuncSetAttribute(afn_sum, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fused_bytes);
+      if (e != cudaSuccess) goto out;
+    }
     // opt in above 40 KB: the kernel's static shared memory comes on top of the dynamic part,
     // and the two together may not exceed the 48 KB default without the attribute
     if (asm_bytes > 40 * 1024) {
@@ -728,20 +775,27 @@ cudaError_t lloyd(cudaStream_t st, Alloc& al, int n, int d, int k, const float* 
           goto out;
         }
       }
+      const bool fused = !on_tc && fuse;
       if (!on_tc) {
         ProfScope ps(st, "kmeans_assign");
-        afn<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes + it,
-                                         it == 0, tie, ctl);
+        if (fused)
+          afn_sum<<<ab, 256, fused_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels,
+                                                changes + it, it == 0, tie, ctl, part, pcnt);
+        else
+          afn<<<ab, 256, asm_bytes, st>>>(n, d, k, E, lde, C32, cn, C64, labels, changes + it,
+                                           it == 0, tie, ctl, nullptr, nullptr);
         note_launch();
       }
       // a launch that did not start leaves the labels unwritten: stop here
       if ((e = cudaGetLastError()) != cudaSuccess) goto out;
-      k_cent_partial<<<(unsigned)nct, 64 * sub, psm, st>>>(n, d, k, E, lde, labels, rpc, part,
-                                                           pcnt, use_smem, sub, ctl, changes + it,
-                                                           it);
-      note_launch();
-      k_cent_reduce<<<k, 256, 0, st>>>(d, k, (int)nct, part, pcnt, C64, C32, cn, ctl,
-                                       changes + it, it);
+      if (!fused) {
+        k_cent_partial<<<(unsigned)nct, 64 * sub, psm, st>>>(n, d, k, E, lde, labels, rpc, part,
+                                                             pcnt, use_smem, sub, ctl,
+                                                             changes + it, it);
+        note_launch();
+      }
+      k_cent_reduce<<<k, 256, 0, st>>>(d, k, (int)(fused ? nab : nct), part, pcnt, C64, C32, cn,
+                                       ctl, changes + it, it);
       note_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) goto out;
       if ((it + 1) % 4 == 0 && it + 1 < iters) {
