@@ -290,6 +290,8 @@ struct RrDesc {
   int *status, *pflag, *nfallback;
   float* Ag;   // global-memory working set (rr_batch_scratch floats) or null
   float* tri;  // 3 m floats (d, e, beta of the cluster tridiagonalization) or null
+  float* lamx;  // K floats: the eigenvalues, when tri is set (found one CTA per eigenvalue)
+  int* mx;      // the solved size, when tri is set (for the column back-transformation)
 };
 struct SpmmDesc {
   long long row0;  // first row of this graph in the batch's concatenated row range
@@ -304,6 +306,7 @@ struct SpmmDesc {
 struct BatchGroup {
   int kind, first, count, param;
   size_t smem;
+  int aux;  // the group's largest K (Rayleigh-Ritz cluster group)
 };
 // Orders the descriptors by kernel shape and returns the groups; entries whose shape has no
 // batched form are left out of every group (their indices in *single) and run one by one.

@@ -1592,7 +1592,7 @@ __global__ void __launch_bounds__(NW * 32) k_rr_eig_reg_b(const RrDesc* __restri
                                        a.status, a.pflag, a.mP, a.nfallback, a.tri,
                                        a.tri ? a.tri + a.m : nullptr,
                                        a.tri ? a.tri + 2 * a.m : nullptr, a.tri ? a.m : 0,
-                                       nullptr, nullptr);
+                                       a.tri ? a.lamx : nullptr, a.tri ? a.mx : nullptr);
 }
 
 // ---- the FP64 Rayleigh-Ritz spread over SMs ---------------------------------------------
@@ -1601,21 +1601,21 @@ __global__ void __launch_bounds__(NW * 32) k_rr_eig_reg_b(const RrDesc* __restri
 // (k_tridiag_cl<double>), the eigenvalues here (one CTA per eigenvalue), the eigenvectors in
 // k_rr_eig_reg (one CTA: dependent LU chains), and the back-transformation in k_rr_back (one
 // CTA per column).
-constexpr int EV_MMAX = 256;
+constexpr int EV_MMAX = 512;
 
 // Eigenvalue blockIdx.x of the tridiagonal T = (d, e) (m rows: m_full, less mP when *pflag is
 // 0) by 33-point multisection on Sturm counts with the 32 lanes of the CTA's warp (an FP64 warp
 // instruction costs the same with 8 lanes or 32), after the Gershgorin bounds of
 // rr_phase_eigvals, recomputed by every CTA.
 template <typename T>
-__global__ void __launch_bounds__(32)
-    k_rr_eigvals_cta(int m_full, int K, int mP, const int* pflag, const T* __restrict__ d,
-                     const T* __restrict__ e, T* __restrict__ lam, int* status) {
+__device__ __forceinline__ void rr_eigval_one(int j, int m_full, int K, int mP, const int* pflag,
+                                              const T* __restrict__ d, const T* __restrict__ e,
+                                              T* __restrict__ lam, int* status) {
   constexpr int LG = 32;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ T e2[EV_MMAX];
   const int m = (pflag && *pflag == 0) ? m_full - mP : m_full;
-  const int lane = threadIdx.x, j = blockIdx.x;
+  const int lane = threadIdx.x;
   T lo = (T)3e38, hi = (T)-3e38, emax = 0;
   for (int i = lane; i < m; i += 32) {
     T r = fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : (T)0);
@@ -1657,17 +1657,30 @@ __global__ void __launch_bounds__(32)
   if (sl == 0) lam[j] = (T)0.5 * (a + b);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(32)
+    k_rr_eigvals_cta(int m_full, int K, int mP, const int* pflag, const T* __restrict__ d,
+                     const T* __restrict__ e, T* __restrict__ lam, int* status) {
+  rr_eigval_one<T>(blockIdx.x, m_full, K, mP, pflag, d, e, lam, status);
+}
+// Lockstep batch (FP32 cluster group): CTA (j, q) finds eigenvalue j of descriptor q.
+__global__ void __launch_bounds__(32) k_rr_eigvals_cta_b(const RrDesc* __restrict__ tab) {
+  const RrDesc a = tab[blockIdx.y];
+  if ((int)blockIdx.x >= a.K) return;  // uniform in the CTA
+  rr_eigval_one<float>(blockIdx.x, a.m, a.K, a.mP, a.pflag, a.tri, a.tri + a.m, a.lamx, a.status);
+}
+
 // Back-transformation Y = H_0 ... H_{m-3} Z of one column per CTA (one warp): the arithmetic
 // of k_rr_eig_reg's phase 4 for that column.  The reflectors are the rows of Ag (stride lda),
 // m the solved size k_rr_eig_reg left in *mext; CTA 0 then re-arms *pflag (nothing else reads
 // it before the next pass).
 template <typename T, int NS>
-__global__ void __launch_bounds__(32)
-    k_rr_back(int m_full, int K, const int* __restrict__ mext, const T* __restrict__ Ag, int lda,
-              const T* __restrict__ beta, const T* __restrict__ Z, T* __restrict__ Y, int* pflag,
-              int* nfallback) {
+__device__ __forceinline__ void rr_back_one(int j, int m_full, int K, const int* __restrict__ mext,
+                                            const T* __restrict__ Ag, int lda,
+                                            const T* __restrict__ beta, const T* __restrict__ Z,
+                                            T* __restrict__ Y, int* pflag, int* nfallback) {
   constexpr unsigned FULL = 0xffffffffu;
-  const int j = blockIdx.x, lane = threadIdx.x;
+  const int lane = threadIdx.x;
   const int m = *mext;
   T za[NS];
 #pragma unroll
@@ -1716,6 +1729,22 @@ __global__ void __launch_bounds__(32)
     if (*pflag == 0 && nfallback) *nfallback += 1;
     *pflag = 1;  // re-armed for the next pass
   }
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(32)
+    k_rr_back(int m_full, int K, const int* __restrict__ mext, const T* __restrict__ Ag, int lda,
+              const T* __restrict__ beta, const T* __restrict__ Z, T* __restrict__ Y, int* pflag,
+              int* nfallback) {
+  rr_back_one<T, NS>(blockIdx.x, m_full, K, mext, Ag, lda, beta, Z, Y, pflag, nfallback);
+}
+// Lockstep batch (FP32 cluster group): CTA (j, q) back-transforms column j of descriptor q.
+__global__ void __launch_bounds__(32) k_rr_back_b(const RrDesc* __restrict__ tab) {
+  const RrDesc a = tab[blockIdx.y];
+  if ((int)blockIdx.x >= a.K) return;  // uniform in the CTA
+  const float* Zg = a.Ag + (size_t)a.m * (a.m + 16);
+  rr_back_one<float, EV_MMAX / 32>(blockIdx.x, a.m, a.K, a.mx, a.Ag, a.m, a.tri + 2 * a.m, Zg,
+                                   a.Y, a.pflag, a.nfallback);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2249,10 +2278,12 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
   if constexpr (can_sm) {
     if (insm) kern = k_rr_eig_reg<T, NS, NW, true>;
   }
-  // FP64, 64 < m <= 256: the phases spread over SMs (tridiagonalization on a cluster, one CTA
-  // per eigenvalue, the eigenvectors here, one CTA per back-transformed column)
-  if constexpr (sizeof(T) == 8) {
-    if (!insm && m > 64 && m <= EV_MMAX) {
+  // FP64 (64 < m <= 256) and FP32 (160 < m <= 512): the phases spread over SMs
+  // (tridiagonalization on a cluster, one CTA per eigenvalue, the eigenvectors here, one CTA
+  // per back-transformed column)
+  {
+    constexpr bool f64 = sizeof(T) == 8;
+    if (!insm && (f64 ? (m > 64 && m <= 256) : (m > 160 && m <= EV_MMAX))) {
       T* tri = al.get<T>((size_t)3 * m + K);  // d, e, beta, eigenvalues
       int* mx = al.get<int>(1);
       cudaError_t e = (tri && mx) ? cudaSuccess : cudaErrorMemoryAllocation;
@@ -2268,8 +2299,8 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
         kern<<<1, NW * 32, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, d_status, pflag, mP,
                                      nfallback, tri, tri + m, tri + 2 * m, m, tri + 3 * m, mx);
         note_launch();
-        k_rr_back<T, EV_MMAX / 32><<<K, 32, 0, st>>>(m, K, mx, Ag, m, tri + 2 * m, Zg, Y, pflag,
-                                                     nfallback);
+        k_rr_back<T, (f64 ? 256 : EV_MMAX) / 32><<<K, 32, 0, st>>>(m, K, mx, Ag, m, tri + 2 * m,
+                                                                   Zg, Y, pflag, nfallback);
         note_launch();
         e = cudaGetLastError();
       }
@@ -2279,30 +2310,14 @@ cudaError_t rr_eig_reg(cudaStream_t st, Alloc& al, int m, int K, const double* G
       return e;
     }
   }
-  // FP32 with the matrix in global memory: the tridiagonalization runs on a cluster of CTAs
-  // holding the matrix in registers (k_tridiag_cl), the other phases here
-  T* tri = nullptr;
-  cudaError_t e = cudaSuccess;
-  if constexpr (sizeof(T) == 4) {
-    if (!insm && m > 160) {
-      tri = al.get<T>((size_t)3 * m);
-      if (!tri) e = cudaErrorMemoryAllocation;
-      if (e == cudaSuccess)
-        e = tridiag_cluster(st, m, K, G, ldg, (float*)Ag, m, (float*)tri, (float*)tri + m,
-                            (float*)tri + 2 * m, pflag, mP);
-    }
-  }
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess) {
     ProfScope ps(st, "rr_eig");
     kern<<<1, NW * 32, sm, st>>>(m, K, G, ldg, theta, Y, Ag, Zg, Ug, Gsg, d_status, pflag, mP,
-                                 nfallback, tri, tri ? tri + m : nullptr,
-                                 tri ? tri + 2 * m : nullptr, tri ? m : 0, nullptr, nullptr);
+                                 nfallback, nullptr, nullptr, nullptr, 0, nullptr, nullptr);
     note_launch();
     e = cudaGetLastError();
   }
-  al.put(tri);
   al.put(Ag);
   return e;
 }
@@ -2407,7 +2422,7 @@ void chol_batch_plan(std::vector<CholDesc>& d, std::vector<BatchGroup>& groups,
     const int k = kind(d[i]);
     int j = i, kamax = 0;
     while (j < (int)d.size() && kind(d[j]) == k) kamax = std::max(kamax, d[j++].ka);
-    BatchGroup gr{k, i, j - i, 0, 0};
+    BatchGroup gr{k, i, j - i, 0, 0, 0};
     if (k == 0) {
       gr.param = chol_rt_shape(kamax);
       for (int q = i; q < j; ++q) gr.smem = std::max(gr.smem, chol_rt_smem(d[q].ka, gr.param));
@@ -2477,7 +2492,7 @@ void rr_batch_plan(std::vector<RrDesc>& d, std::vector<BatchGroup>& groups,
     int mmax = 0;
     for (const RrDesc& a : in)
       if (rr_kind(a.m, a.K) == k) mmax = std::max(mmax, a.m);
-    BatchGroup gr{k, first, 0, 0, 0};
+    BatchGroup gr{k, first, 0, 0, 0, 0};
     if (k == 0) gr.param = rr_rt_rs(mmax);
     for (const RrDesc& a : in) {
       if (rr_kind(a.m, a.K) != k) continue;
@@ -2488,6 +2503,7 @@ void rr_batch_plan(std::vector<RrDesc>& d, std::vector<BatchGroup>& groups,
       else need = sizeof(float) * ((size_t)6 * a.m + 7 * (size_t)a.K + 3 * 16 + 8);
       if (k == 0 && need > 225 * 1024) continue;  // does not fit the group's register shape
       gr.smem = std::max(gr.smem, need);
+      gr.aux = std::max(gr.aux, a.K);
       d.push_back(a);
     }
     gr.count = (int)d.size() - first;
@@ -2516,6 +2532,10 @@ cudaError_t rr_batch_launch(cudaStream_t st, const RrDesc* dtab,
     if (g.kind == 3) {
       e = tridiag_cluster_batch(st, g.count, t, g.param);
       if (e != cudaSuccess) return e;
+      ProfScope ps(st, "rr_eig");
+      k_rr_eigvals_cta_b<<<dim3(g.aux, g.count), 32, 0, st>>>(t);
+      note_launch();
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     ProfScope ps(st, "rr_eig");
     if (g.kind == 0) {
@@ -2532,6 +2552,11 @@ cudaError_t rr_batch_launch(cudaStream_t st, const RrDesc* dtab,
       auto kern = k_rr_eig_reg_b<15, 16, false>;
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
       if (e == cudaSuccess) kern<<<g.count, 16 * 32, g.smem, st>>>(t);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      note_launch();
+      if (e == cudaSuccess) {
+        k_rr_back_b<<<dim3(g.aux, g.count), 32, 0, st>>>(t);
+      }
     }
     note_launch();
     if (e == cudaSuccess) e = cudaGetLastError();

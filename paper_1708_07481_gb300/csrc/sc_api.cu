@@ -1540,15 +1540,20 @@ struct Lockstep {
       cb.push_back(b);
       float* Ag = nullptr;
       float* tri = nullptr;
+      float* lamx = nullptr;
+      int* mx = nullptr;
       if (size_t f = rr_batch_scratch(m, K)) {
         Ag = q->template get<float>(f);
         if (!Ag) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: scratch");
       }
       if (rr_batch_cluster(m)) {
         tri = q->template get<float>((size_t)3 * m);
-        if (!tri) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: scratch");
+        lamx = q->template get<float>((size_t)K);
+        mx = q->template get<int>(1);
+        if (!tri || !lamx || !mx) return fail(c, SC_ENOMEM, "sc_lobpcg_batch: scratch");
       }
-      rd.push_back(RrDesc{m, K, m, K, q->G, q->theta, q->Y, q->dstatus, q->dP, q->dfb, Ag, tri});
+      rd.push_back(RrDesc{m, K, m, K, q->G, q->theta, q->Y, q->dstatus, q->dP, q->dfb, Ag, tri,
+                          lamx, mx});
       const int nv = (q->kp + K + 3) / 4;
       nvec_max = std::max(nvec_max, nv);
       // parity 0 = the pass starts with S at its setup buffer (Sa); the first pass has swapped
