@@ -39,6 +39,25 @@ constexpr int TT_AM_BYTES = TT_M * 12;                // assignment mode: the up
 constexpr int TT_SMEM_USE = TT_SMEM - 1024 - 256 - TT_AM_BYTES;  // stages (after alignment,
                                                                   // barriers, assignment part)
 
+#ifdef SC_TT_PHASES
+// Debug builds only: clock64() time of CTA thread 0 in each part of k_tall_tc's chunk loop,
+// summed over CTAs (0 chunk wait, 1 split, 2 MMA issue, 3 accumulator wait, 4 epilogue,
+// 5 whole loop, 6 CTAs, 7 chunks, 8 wait for the previous chunk's MMAs, 9 refill issue).
+__device__ long long g_tt_phase[10];
+#define TT_T(i)                        \
+  do {                                 \
+    if (tid == 0) {                    \
+      const long long t1_ = clock64(); \
+      tt_acc[i] += t1_ - tt_t0;        \
+      tt_t0 = t1_;                     \
+    }                                  \
+  } while (0)
+#else
+#define TT_T(i) \
+  do {          \
+  } while (0)
+#endif
+
 struct TcTall {
   int nseg;
   int nch[3];     // chunks of each A segment
@@ -133,6 +152,47 @@ __device__ __forceinline__ void tt_ld32(uint32_t tmem, int warp, int c0, uint32_
         "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Writes accumulator columns c0 .. c0 + 31 of one row (v = the 32 values of a tcgen05.ld):
+// out = beta Cin + acc, float4 stores where the output segment allows them.
+__device__ __forceinline__ void tt_store32(const TcTall& p, const uint32_t (&v)[32],
+                                           long long row, int c0) {
+  if (row >= p.n) return;
+#pragma unroll
+  for (int j4 = 0; j4 < 8; ++j4) {
+    const int col = c0 + 4 * j4;
+    if (col >= p.b) break;
+    const int s1 = col >= p.b0 ? 1 : 0;
+    const int cs = s1 ? col - p.b0 : col;
+    const int bs = s1 ? p.b - p.b0 : p.b0;
+    float r4[4] = {__uint_as_float(v[4 * j4]), __uint_as_float(v[4 * j4 + 1]),
+                   __uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3])};
+    if (p.vec[s1] && cs + 3 < bs) {
+      const float* cin = p.cin[s1];
+      if (cin) {
+        const float4 cv = *reinterpret_cast<const float4*>(cin + row * p.ldc[s1] + cs);
+        r4[0] = fmaf(p.beta, cv.x, r4[0]);
+        r4[1] = fmaf(p.beta, cv.y, r4[1]);
+        r4[2] = fmaf(p.beta, cv.z, r4[2]);
+        r4[3] = fmaf(p.beta, cv.w, r4[3]);
+      }
+      *reinterpret_cast<float4*>(p.out[s1] + row * p.ldo[s1] + cs) =
+          make_float4(r4[0], r4[1], r4[2], r4[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cj = col + j;
+        if (cj >= p.b) break;
+        const int t1 = cj >= p.b0 ? 1 : 0;
+        const int ct = t1 ? cj - p.b0 : cj;
+        const float* cn = p.cin[t1];
+        float x = r4[j];
+        if (cn) x = fmaf(p.beta, cn[row * p.ldc[t1] + ct], x);
+        p.out[t1][row * p.ldo[t1] + ct] = x;
+      }
+    }
+  }
 }
 
 // Assignment epilogue of a tile (every thread of the CTA calls it).  Thread (warp w, lane l)
@@ -304,27 +364,50 @@ __global__ void __launch_bounds__(TT_NTH, 1)
   // i % nchunks, stage i % nstg
   const int my_tiles = blockIdx.x < p.ntiles ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long total = (long long)my_tiles * p.nchunks;
-  auto issue = [&](long long i) {  // thread 0
-    const int s = (int)(i % nstg);
-    const int tile = blockIdx.x + (int)(i / p.nchunks) * gridDim.x;
-    const int ch = (int)(i % p.nchunks);
-    int q = 0, cc = ch;
+  // thread 0's next load (stage, chunk, tile), advanced without divisions
+  int is_s = 0, is_ch = 0, is_tile = blockIdx.x;
+  auto issue = [&]() {
+    int q = 0, cc = is_ch;
     while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
-    mbar_expect_tx(&full[s], TT_ATILE + 2 * wbytes);
-    tma_load_2d(a_big(s), maps[q], cc * TT_K, tile * TT_M, &full[s]);
-    bulk_load(w_big(s), p.wimg + (size_t)ch * 2 * wbytes, 2 * wbytes, &full[s]);
+    mbar_expect_tx(&full[is_s], TT_ATILE + 2 * wbytes);
+    tma_load_2d(a_big(is_s), maps[q], cc * TT_K, is_tile * TT_M, &full[is_s]);
+    bulk_load(w_big(is_s), p.wimg + (size_t)is_ch * 2 * wbytes, 2 * wbytes, &full[is_s]);
+    if (++is_s == nstg) is_s = 0;
+    if (++is_ch == p.nchunks) {
+      is_ch = 0;
+      is_tile += gridDim.x;
+    }
   };
-  long long issued = 0, mma_commits[TT_MAXSTG] = {0, 0, 0, 0}, acc_commits = 0;
+  long long issued = 0, acc_commits = 0;
+  // per stage: bit s of mpar = parity of the commits to mdone[s] so far, of many = any commit
+  uint32_t mpar = 0, many = 0;
   if (tid == 0)
-    for (; issued < total && issued < nstg; ++issued) issue(issued);
+    for (; issued < total && issued < nstg; ++issued) issue();
 
-  for (long long i = 0; i < total; ++i) {
-    const int s = (int)(i % nstg);
-    const int ch = (int)(i % p.nchunks);
-    const int tile = blockIdx.x + (int)(i / p.nchunks) * gridDim.x;
-    if (!mbar_wait(&full[s], (uint32_t)((i / nstg) & 1))) atomicExch(&abort_flag, 1);
+#ifdef SC_TT_PHASES
+  long long tt_acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long tt_t0 = clock64();
+  const long long tt_start = tt_t0;
+#endif
+  // chunk i: stage s = i % nstg (full-barrier parity fpar = (i / nstg) & 1), chunk ch of
+  // tile `tile`
+  int s = 0, ch = 0, tile = blockIdx.x;
+  uint32_t fpar = 0;
+  auto advance = [&]() {
+    if (++s == nstg) {
+      s = 0;
+      fpar ^= 1u;
+    }
+    if (++ch == p.nchunks) {
+      ch = 0;
+      tile += gridDim.x;
+    }
+  };
+  for (long long i = 0; i < total; ++i, advance()) {
+    if (!mbar_wait(&full[s], fpar)) atomicExch(&abort_flag, 1);
     __syncthreads();
     if (abort_flag) break;
+    TT_T(0);
     // split the staged FP32 A chunk in place: big over the FP32 values, small beside it
     {
       uint4* sbg = reinterpret_cast<uint4*>(a_big(s));
@@ -347,6 +430,7 @@ __global__ void __launch_bounds__(TT_NTH, 1)
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    TT_T(1);
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t ab = smem_u32(a_big(s)), as_ = smem_u32(a_sml(s));
@@ -360,21 +444,26 @@ __global__ void __launch_bounds__(TT_NTH, 1)
         mma_tf32(tmem, sw128_desc(ab + ko), sw128_desc(wb + ko), idesc, 1u);
       }
       mma_commit(&mdone[s]);
-      mma_commits[s] += 1;
+      mpar ^= 1u << s;
+      many |= 1u << s;
       if (ch == p.nchunks - 1) {
         mma_commit(accd);
         acc_commits += 1;
       }
+      TT_T(2);
       // refill the previous chunk's stage (its MMAs were issued one chunk ago): load
       // i + nstg - 1 goes where load i - 1 was
       if (i >= 1 && issued < total) {
-        const int sp = (int)((i - 1) % nstg);
-        if (!mbar_wait(&mdone[sp], (uint32_t)((mma_commits[sp] - 1) & 1))) {
+        const int sp = s == 0 ? nstg - 1 : s - 1;
+        const bool okw = mbar_wait(&mdone[sp], ((mpar >> sp) & 1u) ^ 1u);
+        TT_T(8);
+        if (!okw) {
           atomicExch(&abort_flag, 1);
         } else {
-          issue(issued);
+          issue();
           ++issued;
         }
+        TT_T(9);
       }
     }
     if (ch == p.nchunks - 1) {
@@ -385,6 +474,7 @@ __global__ void __launch_bounds__(TT_NTH, 1)
         if (tid == 0) atomicExch(&abort_flag, 1);
         break;
       }
+      TT_T(3);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long row = (long long)tile * TT_M + 32 * (warp & 3) + lane;
       if (p.amode) {
@@ -407,53 +497,28 @@ __global__ void __launch_bounds__(TT_NTH, 1)
               "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < p.n) {
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
-            const int col = c0 + 4 * j4;
-            if (col >= p.b) break;
-            const int s1 = col >= p.b0 ? 1 : 0;
-            const int cs = s1 ? col - p.b0 : col;
-            const int bs = s1 ? p.b - p.b0 : p.b0;
-            float r4[4] = {__uint_as_float(v[4 * j4]), __uint_as_float(v[4 * j4 + 1]),
-                           __uint_as_float(v[4 * j4 + 2]), __uint_as_float(v[4 * j4 + 3])};
-            if (p.vec[s1] && cs + 3 < bs) {
-              const float* cin = p.cin[s1];
-              if (cin) {
-                const float4 cv = *reinterpret_cast<const float4*>(cin + row * p.ldc[s1] + cs);
-                r4[0] = fmaf(p.beta, cv.x, r4[0]);
-                r4[1] = fmaf(p.beta, cv.y, r4[1]);
-                r4[2] = fmaf(p.beta, cv.z, r4[2]);
-                r4[3] = fmaf(p.beta, cv.w, r4[3]);
-              }
-              *reinterpret_cast<float4*>(p.out[s1] + row * p.ldo[s1] + cs) =
-                  make_float4(r4[0], r4[1], r4[2], r4[3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const int cj = col + j;
-                if (cj >= p.b) break;
-                const int t1 = cj >= p.b0 ? 1 : 0;
-                const int ct = t1 ? cj - p.b0 : cj;
-                const float* cn = p.cin[t1];
-                float x = r4[j];
-                if (cn) x = fmaf(p.beta, cn[row * p.ldc[t1] + ct], x);
-                p.out[t1][row * p.ldo[t1] + ct] = x;
-              }
-            }
-          }
-        }
+        tt_store32(p, v, row, c0);
       }
       // the accumulator is read: the next tile's first MMA may overwrite it
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
+      TT_T(4);
     }
   }
+#ifdef SC_TT_PHASES
+  if (tid == 0) {
+    tt_acc[5] = clock64() - tt_start;
+    for (int q = 0; q < 10; ++q)
+      if (q != 6 && q != 7) atomicAdd((unsigned long long*)&g_tt_phase[q], (unsigned long long)tt_acc[q]);
+    atomicAdd((unsigned long long*)&g_tt_phase[6], 1ull);
+    atomicAdd((unsigned long long*)&g_tt_phase[7], (unsigned long long)total);
+  }
+#endif
   // drain: wait (bounded) for this CTA's MMAs, and after a time-out for its copies in flight
   if (tid == 0) {
     bool ok = !abort_flag;
     for (int q = 0; q < nstg; ++q)
-      if (mma_commits[q] > 0) ok = mbar_wait(&mdone[q], (uint32_t)((mma_commits[q] - 1) & 1)) && ok;
+      if ((many >> q) & 1u) ok = mbar_wait(&mdone[q], ((mpar >> q) & 1u) ^ 1u) && ok;
     if (acc_commits > 0) ok = mbar_wait(accd, (uint32_t)((acc_commits - 1) & 1)) && ok;
     if (!ok) {
       // the latest load into each stage (a load into a stage is issued only after the one
@@ -469,6 +534,240 @@ __global__ void __launch_bounds__(TT_NTH, 1)
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(tcols)
+                 : "memory");
+  }
+}
+
+// The update (not the assignment mode) with the roles of a CTA on separate warps, so that the
+// copies, the TF32 split, the MMA issue and the epilogue of consecutive chunks and tiles
+// overlap instead of taking turns behind CTA-wide barriers:
+//   warp 0, lane 0: copies (A chunk + W^T chunk per stage; a stage is refilled once the MMAs
+//     that read it have completed, mbarrier `empty`);
+//   warps 2, 3, 8 .. 11: the in-place split of each landed A chunk (mbarrier `splitd`, one
+//     arrival per warp);
+//   warp 1, lane 0: the MMAs of each split chunk into one of two tensor-memory accumulators
+//     (alternating by tile), committing `empty` per chunk and `accf` per tile;
+//   warps 4 .. 7: the epilogue of each finished accumulator (lane quarter = warp % 4, every
+//     column), then `acce` frees it for the tile after next.
+// The arithmetic (products, their order, the accumulation) is that of k_tall_tc.  Every wait
+// is bounded; after a time-out the CTA records ST_TIMEOUT, waits (bounded) for its own copies
+// and MMAs in flight, frees its tensor memory and returns.
+constexpr int TW_NTH = 384;
+constexpr int TW_NSPLIT = 6;  // splitter warps
+
+__device__ __forceinline__ int tw_splitter(int warp) {
+  return warp >= 8 ? warp - 6 : ((warp == 2 || warp == 3) ? warp - 2 : -1);
+}
+
+__global__ void __launch_bounds__(TW_NTH, 1)
+    k_tall_ws(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+              const __grid_constant__ CUtensorMap map2, const __grid_constant__ TcTall p,
+              int* status) {
+  extern __shared__ __align__(1024) uint8_t tw_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)tw_raw + 1023) & ~(uintptr_t)1023);
+  const int nstg = p.nstg, sb = p.stage, wbytes = p.nn * 128;
+  uint64_t* bars = (uint64_t*)(base + (size_t)nstg * sb);
+  uint64_t* full = bars;                       // [nstg] A chunk and W^T chunk landed
+  uint64_t* splitd = bars + TT_MAXSTG;         // [nstg] A chunk split (one arrival per warp)
+  uint64_t* empty = bars + 2 * TT_MAXSTG;      // [nstg] MMAs reading the stage finished
+  uint64_t* accf = bars + 3 * TT_MAXSTG;       // [2] accumulator of a tile complete
+  uint64_t* acce = accf + 2;                   // [2] accumulator read by the epilogue
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const CUtensorMap* maps[3] = {&map0, &map1, &map2};
+  int tcols = 32;
+  while (tcols < p.nn) tcols <<= 1;
+  auto a_big = [&](int st) { return base + (size_t)st * sb; };
+  auto a_sml = [&](int st) { return base + (size_t)st * sb + TT_ATILE; };
+  auto w_big = [&](int st) { return base + (size_t)st * sb + 2 * TT_ATILE; };
+
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int q = 0; q < TT_MAXSTG; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&splitd[q], TW_NSPLIT);
+      mbar_init(&empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&accf[q], 1);
+      mbar_init(&acce[q], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int q = 0; q < p.nseg; ++q)
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)maps[q]) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(2 * tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.nn >> 3) << 17) |
+                         ((uint32_t)(TT_M >> 4) << 24);
+  const int my_tiles = blockIdx.x < p.ntiles ? (p.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long total = (long long)my_tiles * p.nchunks;
+  volatile int* vabort = &abort_flag;
+
+  // thread-local records for the drain after a time-out
+  long long issued = 0;           // copies issued (warp 0, lane 0)
+  uint32_t mpar = 0, many = 0;    // per stage: parity of the commits to empty[s], any commit
+  int acnt[2] = {0, 0};           // commits to accf[0 / 1]
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int st = 0, ch = 0, tile = blockIdx.x;
+      uint32_t rpar = 0;  // parity of the stage round (issue index / nstg)
+      for (long long i = 0; i < total; ++i) {
+        if (*vabort) break;
+        if (i >= nstg && !mbar_wait(&empty[st], rpar ^ 1u)) {  // the round before, consumed
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        int q = 0, cc = ch;
+        while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
+        mbar_expect_tx(&full[st], TT_ATILE + 2 * wbytes);
+        tma_load_2d(a_big(st), maps[q], cc * TT_K, tile * TT_M, &full[st]);
+        bulk_load(w_big(st), p.wimg + (size_t)ch * 2 * wbytes, 2 * wbytes, &full[st]);
+        ++issued;
+        if (++st == nstg) {
+          st = 0;
+          rpar ^= 1u;
+        }
+        if (++ch == p.nchunks) {
+          ch = 0;
+          tile += gridDim.x;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int st = 0, ch = 0, tl = 0;
+      uint32_t rpar = 0;
+      for (long long i = 0; i < total; ++i) {
+        if (*vabort) break;
+        if (!mbar_wait(&splitd[st], rpar)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        const int ab = tl & 1;
+        if (ch == 0 && tl >= 2 && !mbar_wait(&acce[ab], (uint32_t)(((tl >> 1) - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(ab * tcols);
+        const uint32_t abg = smem_u32(a_big(st)), asm_ = smem_u32(a_sml(st));
+        const uint32_t wb = smem_u32(w_big(st)), ws = wb + wbytes;
+#pragma unroll
+        for (int ks = 0; ks < TT_K / 8; ++ks) {
+          const uint32_t ko = ks * 32;
+          const uint32_t acc0 = (ch > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(acc, sw128_desc(asm_ + ko), sw128_desc(wb + ko), idesc, acc0);
+          mma_tf32(acc, sw128_desc(abg + ko), sw128_desc(ws + ko), idesc, 1u);
+          mma_tf32(acc, sw128_desc(abg + ko), sw128_desc(wb + ko), idesc, 1u);
+        }
+        mma_commit(&empty[st]);
+        mpar ^= 1u << st;
+        many |= 1u << st;
+        if (ch == p.nchunks - 1) {
+          mma_commit(&accf[ab]);
+          acnt[ab] += 1;
+        }
+        if (++st == nstg) {
+          st = 0;
+          rpar ^= 1u;
+        }
+        if (++ch == p.nchunks) {
+          ch = 0;
+          ++tl;
+        }
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // epilogue: lane quarter warp % 4 (rows 32 (warp % 4) + lane of the tile), every column
+    for (int tl = 0; tl < my_tiles; ++tl) {
+      if (*vabort) break;
+      const int ab = tl & 1;
+      if (!mbar_wait(&accf[ab], (uint32_t)((tl >> 1) & 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const long long row =
+          (long long)(blockIdx.x + tl * gridDim.x) * TT_M + 32 * (warp & 3) + lane;
+      for (int c0 = 0; c0 < p.b; c0 += 32) {  // uniform in the warp
+        uint32_t v[32];
+        tt_ld32(tmem + (uint32_t)(ab * tcols), warp, c0, v);
+        tt_store32(p, v, row, c0);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[ab]);
+    }
+  } else {
+    const int sw = tw_splitter(warp);  // 0 .. TW_NSPLIT - 1
+    int st = 0;
+    uint32_t rpar = 0;
+    for (long long i = 0; i < total; ++i) {
+      if (*vabort) break;
+      if (!mbar_wait(&full[st], rpar)) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      // big over the FP32 values, small beside them (the arithmetic of k_tall_tc's split)
+      uint4* sbg = reinterpret_cast<uint4*>(a_big(st));
+      uint4* ssm = reinterpret_cast<uint4*>(a_sml(st));
+      for (int v = sw * 32 + lane; v < TT_ATILE / 16; v += TW_NSPLIT * 32) {
+        const uint4 x = sbg[v];
+        uint4 bg, sm;
+        bg.x = to_tf32(__uint_as_float(x.x));
+        bg.y = to_tf32(__uint_as_float(x.y));
+        bg.z = to_tf32(__uint_as_float(x.z));
+        bg.w = to_tf32(__uint_as_float(x.w));
+        sm.x = to_tf32(__uint_as_float(x.x) - __uint_as_float(bg.x));
+        sm.y = to_tf32(__uint_as_float(x.y) - __uint_as_float(bg.y));
+        sm.z = to_tf32(__uint_as_float(x.z) - __uint_as_float(bg.z));
+        sm.w = to_tf32(__uint_as_float(x.w) - __uint_as_float(bg.w));
+        sbg[v] = bg;
+        ssm[v] = sm;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&splitd[st]);
+      if (++st == nstg) {
+        st = 0;
+        rpar ^= 1u;
+      }
+    }
+  }
+
+  __syncthreads();
+  if (*vabort) {
+    // drain: this CTA's MMAs, then its copies in flight (the latest load into each stage
+    // covers the ones before it)
+    if (warp == 1 && lane == 0) {
+      for (int q = 0; q < nstg; ++q)
+        if ((many >> q) & 1u) mbar_wait(&empty[q], ((mpar >> q) & 1u) ^ 1u);
+      for (int q = 0; q < 2; ++q)
+        if (acnt[q] > 0) mbar_wait(&accf[q], (uint32_t)((acnt[q] - 1) & 1));
+    }
+    if (warp == 0 && lane == 0)
+      for (long long j = issued > nstg ? issued - nstg : 0; j < issued; ++j)
+        mbar_wait(&full[j % nstg], (uint32_t)((j / nstg) & 1));
+    if (tid == 0) atomicOr(status, ST_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * tcols)
                  : "memory");
   }
 }
@@ -581,6 +880,7 @@ static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<flo
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_tall_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM);
+    cudaFuncSetAttribute(k_tall_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM);
   });
   {
     ProfScope ps(st, am ? "kmeans_assign" : "tall_gemm");
@@ -588,13 +888,29 @@ static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<flo
     k_tall_wsplit<<<(unsigned)std::min<long long>((tot + 255) / 256, 1024), 256, 0, st>>>(p, img);
     note_launch();
     const int grid = std::min(p.ntiles, 152);
-    k_tall_tc<<<grid, TT_NTH, TT_SMEM, st>>>(m[0], m[1], m[2], p, d_status);
+    if (am)
+      k_tall_tc<<<grid, TT_NTH, TT_SMEM, st>>>(m[0], m[1], m[2], p, d_status);
+    else
+      k_tall_ws<<<grid, TW_NTH, TT_SMEM, st>>>(m[0], m[1], m[2], p, d_status);
     note_launch();
   }
   e = cudaGetLastError();
   cudaFreeAsync(img, st);
   return e;
 }
+
+#ifdef SC_TT_PHASES
+}  // namespace sc
+// Debug builds only: the k_tall_tc phase sums (see g_tt_phase) since the previous call, which
+// clears them.
+extern "C" int sc_debug_tt_phases(long long* out) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return -6;
+  if (cudaMemcpyFromSymbol(out, sc::g_tt_phase, sizeof(long long) * 10) != cudaSuccess) return -6;
+  long long z[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  return cudaMemcpyToSymbol(sc::g_tt_phase, z, sizeof(z)) == cudaSuccess ? 0 : -6;
+}
+namespace sc {
+#endif
 
 // k-means assignment on tensor cores: the update kernel with A = E (n x d rows) and W = C^T (the
 // k x d FP32 centroids read transposed), its epilogue turning e_i . c_j into labels (k <= 256;

@@ -27,6 +27,11 @@ __device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+// One arrival (release semantics at CTA scope) on an mbarrier.
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Bounded wait for phase `parity` of an mbarrier: at most `limit` polls and at most
 // WAIT_CLOCKS SM clocks (about two seconds); returns false on timeout.  try_wait suspends the
 // thread in hardware between polls, so no software back-off is added (a sleep after each

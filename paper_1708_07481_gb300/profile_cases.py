@@ -5,6 +5,7 @@
     python -m paper_1708_07481_gb300.profile_cases lob   # 3 LOBPCG passes, DC-SBM n = 50,000, K = 44
     python -m paper_1708_07481_gb300.profile_cases big   # 2 LOBPCG passes, DC-SBM n = 300,000, K = 160
     python -m paper_1708_07481_gb300.profile_cases kmeans  # k-means, 50,000 unit rows, d = k = 44
+    python -m paper_1708_07481_gb300.profile_cases tall  # tall updates n = 50,000, 132 -> 44
 
 `rr` feeds the dense Rayleigh-Ritz solve a 132 x 132 FP64 Gram with K = 44 small and 88 large
 eigenvalues (the spectrum shape of the [X R P] projection at n = 50,000, K = 44).  `lob`
@@ -53,8 +54,17 @@ def main(argv=None):
         E = (E / np.linalg.norm(E, axis=1, keepdims=True)).astype(np.float32)
         for _ in range(2):
             sc.sc_kmeans(ctx, E, 44, iters=50, seed=5)
+    elif mode == "tall":
+        # the update [X R P] Y of the bench workload (n = 50,000, 3K = 132 -> K = 44): three on
+        # tensor cores, then three on CUDA cores
+        rng = np.random.default_rng(0)
+        A = rng.standard_normal((50000, 132), dtype=np.float32)
+        Wm = rng.standard_normal((132, 44), dtype=np.float32)
+        for prec in (sc.SC_PREC_MIXED, sc.SC_PREC_FP32):
+            for _ in range(3):
+                sc.sc_tall_update(ctx, A, Wm, prec=prec)
     else:
-        raise SystemExit(f"unknown case {mode!r}: rr, rr64, lob, big or kmeans")
+        raise SystemExit(f"unknown case {mode!r}: rr, rr64, lob, big, kmeans or tall")
     print("ok", mode)
 
 
