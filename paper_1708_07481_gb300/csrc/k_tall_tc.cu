@@ -15,7 +15,7 @@
 //   comes with the A chunk as one bulk copy completing on the same mbarrier.
 // Each A segment is cut into chunks of 32 columns (the last one zero-filled by the TMA past
 // the segment's width; the matching rows of W^T are zero).  A persistent CTA walks row tiles
-// of 128 with up to four staged chunks in flight (as many as fit beside each other); one thread
+// of 128 with up to six staged chunks in flight (as many as fit beside each other); one thread
 // issues the copies and the MMAs (4 K-steps x 3 products per chunk), commits per stage and per
 // tile, and refills the previous chunk's stage; eight warps read the accumulator with
 // tcgen05.ld (warp w: rows 32 (w % 4) .. +32, columns 32 (w / 4) + 64 j .. +32) and write
@@ -31,7 +31,7 @@ namespace {
 
 constexpr int TT_M = 128;     // rows per tile (MMA M)
 constexpr int TT_K = 32;      // columns per chunk (one 128-byte swizzle row of FP32)
-constexpr int TT_MAXSTG = 4;  // staged chunks in flight, at most
+constexpr int TT_MAXSTG = 6;  // staged chunks in flight, at most
 constexpr int TT_NTH = 256;   // eight warps: warps w, w + 4 share lane quarter w % 4
 constexpr int TT_ATILE = TT_M * TT_K * 4;             // 16 KB: one FP32 (then big) A chunk
 constexpr int TT_SMEM = 225 * 1024;                   // dynamic shared memory of a CTA
@@ -52,8 +52,24 @@ __device__ long long g_tt_phase[10];
       tt_t0 = t1_;                     \
     }                                  \
   } while (0)
+// The same for k_tall_ws, per role (the first thread of the role's first warp): 0 copies:
+// wait for a free stage, 1 copies: issue, 2 split: wait for a chunk, 3 split: work,
+// 4 MMA: wait for a split chunk, 5 MMA: wait for a free accumulator, 6 MMA: issue,
+// 7 epilogue: wait for an accumulator, 8 epilogue: work, 9 the CTA's loop, 10 CTAs, 11 chunks.
+__device__ long long g_tw_phase[12];
+#define TW_T(i)                        \
+  do {                                 \
+    if (tw_me) {                       \
+      const long long t1_ = clock64(); \
+      tw_acc[i] += t1_ - tw_t0;        \
+      tw_t0 = t1_;                     \
+    }                                  \
+  } while (0)
 #else
 #define TT_T(i) \
+  do {          \
+  } while (0)
+#define TW_T(i) \
   do {          \
   } while (0)
 #endif
@@ -615,6 +631,12 @@ __global__ void __launch_bounds__(TW_NTH, 1)
   const long long total = (long long)my_tiles * p.nchunks;
   volatile int* vabort = &abort_flag;
 
+#ifdef SC_TT_PHASES
+  long long tw_acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const bool tw_me = lane == 0 && (warp == 0 || warp == 1 || warp == 2 || warp == 4);
+  long long tw_t0 = clock64();
+  const long long tw_start = tw_t0;
+#endif
   // thread-local records for the drain after a time-out
   long long issued = 0;           // copies issued (warp 0, lane 0)
   uint32_t mpar = 0, many = 0;    // per stage: parity of the commits to empty[s], any commit
@@ -630,12 +652,14 @@ __global__ void __launch_bounds__(TW_NTH, 1)
           atomicExch(&abort_flag, 1);
           break;
         }
+        TW_T(0);
         int q = 0, cc = ch;
         while (q + 1 < p.nseg && cc >= p.nch[q]) cc -= p.nch[q++];
         mbar_expect_tx(&full[st], TT_ATILE + 2 * wbytes);
         tma_load_2d(a_big(st), maps[q], cc * TT_K, tile * TT_M, &full[st]);
         bulk_load(w_big(st), p.wimg + (size_t)ch * 2 * wbytes, 2 * wbytes, &full[st]);
         ++issued;
+        TW_T(1);
         if (++st == nstg) {
           st = 0;
           rpar ^= 1u;
@@ -656,11 +680,13 @@ __global__ void __launch_bounds__(TW_NTH, 1)
           atomicExch(&abort_flag, 1);
           break;
         }
+        TW_T(4);
         const int ab = tl & 1;
         if (ch == 0 && tl >= 2 && !mbar_wait(&acce[ab], (uint32_t)(((tl >> 1) - 1) & 1))) {
           atomicExch(&abort_flag, 1);
           break;
         }
+        TW_T(5);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + (uint32_t)(ab * tcols);
         const uint32_t abg = smem_u32(a_big(st)), asm_ = smem_u32(a_sml(st));
@@ -680,6 +706,7 @@ __global__ void __launch_bounds__(TW_NTH, 1)
           mma_commit(&accf[ab]);
           acnt[ab] += 1;
         }
+        TW_T(6);
         if (++st == nstg) {
           st = 0;
           rpar ^= 1u;
@@ -699,6 +726,7 @@ __global__ void __launch_bounds__(TW_NTH, 1)
         atomicExch(&abort_flag, 1);
         break;
       }
+      TW_T(7);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long row =
           (long long)(blockIdx.x + tl * gridDim.x) * TT_M + 32 * (warp & 3) + lane;
@@ -710,6 +738,7 @@ __global__ void __launch_bounds__(TW_NTH, 1)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[ab]);
+      TW_T(8);
     }
   } else {
     const int sw = tw_splitter(warp);  // 0 .. TW_NSPLIT - 1
@@ -721,6 +750,7 @@ __global__ void __launch_bounds__(TW_NTH, 1)
         atomicExch(&abort_flag, 1);
         break;
       }
+      TW_T(2);
       // big over the FP32 values, small beside them (the arithmetic of k_tall_tc's split)
       uint4* sbg = reinterpret_cast<uint4*>(a_big(st));
       uint4* ssm = reinterpret_cast<uint4*>(a_sml(st));
@@ -741,6 +771,7 @@ __global__ void __launch_bounds__(TW_NTH, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&splitd[st]);
+      TW_T(3);
       if (++st == nstg) {
         st = 0;
         rpar ^= 1u;
@@ -749,6 +780,17 @@ __global__ void __launch_bounds__(TW_NTH, 1)
   }
 
   __syncthreads();
+#ifdef SC_TT_PHASES
+  if (tw_me) {
+    tw_acc[9] = clock64() - tw_start;
+    for (int q = 0; q < 10; ++q)
+      if (tw_acc[q]) atomicAdd((unsigned long long*)&g_tw_phase[q], (unsigned long long)tw_acc[q]);
+  }
+  if (tid == 0) {
+    atomicAdd((unsigned long long*)&g_tw_phase[10], 1ull);
+    atomicAdd((unsigned long long*)&g_tw_phase[11], (unsigned long long)total);
+  }
+#endif
   if (*vabort) {
     // drain: this CTA's MMAs, then its copies in flight (the latest load into each stage
     // covers the ones before it)
@@ -901,13 +943,16 @@ static cudaError_t tall_gemm_tc_one(cudaStream_t st, long long n, const Cat3<flo
 
 #ifdef SC_TT_PHASES
 }  // namespace sc
-// Debug builds only: the k_tall_tc phase sums (see g_tt_phase) since the previous call, which
-// clears them.
+// Debug builds only: the k_tall_tc phase sums (out[0..9], see g_tt_phase) and the k_tall_ws
+// ones (out[10..21], see g_tw_phase) since the previous call, which clears them.
 extern "C" int sc_debug_tt_phases(long long* out) {
   if (cudaDeviceSynchronize() != cudaSuccess) return -6;
   if (cudaMemcpyFromSymbol(out, sc::g_tt_phase, sizeof(long long) * 10) != cudaSuccess) return -6;
-  long long z[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  return cudaMemcpyToSymbol(sc::g_tt_phase, z, sizeof(z)) == cudaSuccess ? 0 : -6;
+  if (cudaMemcpyFromSymbol(out + 10, sc::g_tw_phase, sizeof(long long) * 12) != cudaSuccess)
+    return -6;
+  long long z[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (cudaMemcpyToSymbol(sc::g_tw_phase, z, sizeof(z)) != cudaSuccess) return -6;
+  return cudaMemcpyToSymbol(sc::g_tt_phase, z, sizeof(long long) * 10) == cudaSuccess ? 0 : -6;
 }
 namespace sc {
 #endif
