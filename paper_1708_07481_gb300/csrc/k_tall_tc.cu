@@ -15,12 +15,17 @@
 //   comes with the A chunk as one bulk copy completing on the same mbarrier.
 // Each A segment is cut into chunks of 32 columns (the last one zero-filled by the TMA past
 // the segment's width; the matching rows of W^T are zero).  A persistent CTA walks row tiles
-// of 128 with up to six staged chunks in flight (as many as fit beside each other); one thread
-// issues the copies and the MMAs (4 K-steps x 3 products per chunk), commits per stage and per
-// tile, and refills the previous chunk's stage; eight warps read the accumulator with
-// tcgen05.ld (warp w: rows 32 (w % 4) .. +32, columns 32 (w / 4) + 64 j .. +32) and write
-// beta Cin + acc.  Every wait is bounded; on a time-out the CTA records ST_TIMEOUT, waits
-// (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
+// of 128 with up to six staged chunks in flight (as many as fit beside each other).  Two
+// kernels:
+//   k_tall_ws (the update): copies, the split, the MMA issue (4 K-steps x 3 products per
+//   chunk) and the epilogue run on separate warps, with two tensor-memory accumulators so
+//   that a tile's epilogue overlaps the next tile's MMAs;
+//   k_tall_tc (the k-means assignment mode): every thread splits each chunk, one thread issues
+//   the copies and the MMAs, commits per stage and per tile, and refills the previous chunk's
+//   stage; eight warps read the accumulator with tcgen05.ld (warp w: rows 32 (w % 4) .. +32,
+//   columns 32 (w / 4) + 64 j .. +32) for the assignment epilogue.
+// Every wait is bounded; on a time-out a CTA records ST_TIMEOUT, waits (bounded) for its
+// copies and MMAs in flight, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstring>
 
